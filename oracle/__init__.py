@@ -1,0 +1,14 @@
+"""CPU oracle for the dependence-analysis / actor-execution hot path.
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py``; never by the product package.
+"""
+from .oracle import (  # noqa: F401
+    analyze,
+    build,
+    csr_from_pairs,
+    mix32,
+    run_bodies,
+    spin,
+    topo_order,
+)
