@@ -1,0 +1,328 @@
+"""Benchmark: tasks/s and ns/task of implicit analysis + actor-style execution.
+
+Workload (one step): the three Task Bench graphs of width 1024 x 1000 steps
+(stencil radius 1, butterfly, random fan-in 5; seed 0), each encoded as region
+requirements on a 1024 x 1000 grid (a task writes its own cell and reads its
+predecessors' cells), EMPTY bodies. Per graph: ingest of the launches, GPU
+dependence analysis (binning, tile sweep, CSR) and one execution of the DAG.
+3,072,000 tasks per step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle on the same workload (host cores).
+With N > 1 (torchrun) every rank runs its own replica (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2508_16522_gb300 import tracegen as tg  # noqa: E402
+
+METRIC = "tasks/sec and ns/task overhead (analysis+execution) on 1 GB300, batched vs plain"
+UNIT = "tasks/s"
+WIDTH, STEPS = 1024, 1000
+TILE = (16, 16)
+WORKLOAD = "taskbench 1024x1000 (stencil, butterfly, random fan-in 5), region-encoded, EMPTY bodies"
+
+
+def load_traces():
+    return [tg.taskbench(WIDTH, STEPS, p, seed=0) for p in tg.PATTERNS]
+
+
+def config(tasks_per_step):
+    return {"workload": WORKLOAD, "patterns": list(tg.PATTERNS), "width": WIDTH, "steps_per_graph": STEPS,
+            "tasks_per_step": tasks_per_step, "tile": list(TILE),
+            "l2": "flushed between timed steps (512 MB write)", "inputs": "synthetic, seed 0"}
+
+
+# ---------------------------------------------------------------------------
+# the oracle, timed on host cores (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+def oracle_step(traces):
+    import oracle
+    t0 = time.perf_counter()
+    for tr in traces:
+        src, dst = oracle.analyze(tr)
+        rp, col = oracle.csr_from_pairs(tr.n, src, dst)
+        order = oracle.topo_order(tr.n, rp, col)
+        assert len(order) == tr.n
+    return time.perf_counter() - t0
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    traces = load_traces()
+    n_tasks = sum(t.n for t in traces)
+    for _ in range(args.warmup):
+        oracle_step(traces)
+    times = [oracle_step(traces) for _ in range(args.steps)]
+    total = sum(times)
+    value = n_tasks * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "ns_per_task": 1e9 / value, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32", "data": "synthetic", "config": config(n_tasks),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "each step = the full workload: per-cell oracle analysis + Kahn order"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].strip().lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# roofline bookkeeping
+# ---------------------------------------------------------------------------
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def kernel_source_sha(name):
+    src = {"exec": "exec.cu", "sweep": "sweep.cu"}[name]
+    return hashlib.sha256(open(os.path.join(ROOT, "paper_2508_16522_gb300", "csrc", src), "rb").read()).hexdigest()[:16]
+
+
+def committed_traffic(name):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current source of that kernel (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(p))[name]
+    except Exception:
+        return None
+    return d["bytes_per_launch"] if d.get("source_sha") == kernel_source_sha(name) else None
+
+
+def roofline(per_graph, peaks):
+    """per_graph: list of dicts (n, E, entries, pairs, ms_exec_kernel, ms_sweep_kernel) averaged
+    over the timed steps. Algorithmic bytes:
+      executor: 16 B per task (row_ptr pair, indeg read, counter re-arm) + 12 B per edge
+                (col read, counter read-modify-write)
+      sweep:    8 B per binned entry read + 8 B per candidate pair written."""
+    t_exec = sum(g["ms_exec_kernel"] for g in per_graph)
+    t_sweep = sum(g["ms_sweep_kernel"] for g in per_graph)
+    if t_exec >= t_sweep:
+        name, ms = "exec", t_exec
+        algo = sum(16 * g["n"] + 12 * g["E"] for g in per_graph)
+    else:
+        name, ms = "sweep", t_sweep
+        algo = sum(8 * g["entries"] + 8 * g["pairs"] for g in per_graph)
+    launches = len(per_graph)
+    achieved = (algo / launches) / (ms / launches * 1e-3) / 1e9
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    traffic = committed_traffic(name)
+    return {"kernel": {"exec": "k_exec (persistent executor)", "sweep": "k_sweep (tile interference sweep)"}[name],
+            "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "algorithmic_bytes_per_launch": algo / launches,
+            "avg_launch_ms": ms / launches, "peak_source": "measured" if peaks else "fallback",
+            "share_of_step": None}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2508_16522_gb300 import grt
+
+    traces = load_traces()
+    n_tasks = sum(t.n for t in traces)
+    stream = torch.cuda.Stream()
+    dev_inputs = [[torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (t.req_off, t.lo, t.hi, t.priv)]
+                  for t in traces]
+    host_inputs = [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (t.req_off, t.lo, t.hi, t.priv)]
+                   for t in traces]
+    graphs = [grt.Graph(2, t.dom_lo, t.dom_hi, tile=TILE, stream=stream, flags=grt.RT_GRAPH_PROFILE)
+              for t in traces]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    def step(inputs, defer=False):
+        for g, inp in zip(graphs, inputs):
+            g.clear()
+            g.launch(*inp, defer_check=defer)
+            g.analyze()
+            g.execute()
+            g.sync()
+
+    def stats():
+        out = []
+        for g in graphs:
+            s = g.stats()
+            out.append({"n": s["n_tasks"], "E": s["n_edges"], "entries": s["n_entries"], "pairs": s["n_pairs"],
+                        "ms_exec_kernel": s["ms_exec_kernel"], "ms_sweep_kernel": s["ms_sweep_kernel"],
+                        "ms_analyze": s["ms_analyze"], "ms_execute": s["ms_execute"]})
+        return out
+
+    def timed(inputs, k, defer=False):
+        ms, per = [], []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for i in range(k):
+            with torch.cuda.stream(stream):
+                flush.fill_(i & 255)
+            e0.record(stream)
+            step(inputs, defer)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            per.append(stats())
+        return ms, per
+
+    for _ in range(args.warmup):
+        step(dev_inputs)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = grt.rt_kernel_launches()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ms, per = timed(dev_inputs, args.steps)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    launches = grt.rt_kernel_launches() - l0
+    clk = clocks.stop()
+    total_ms = sum(ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+
+    # end to end through the host API: pinned host arrays, H2D inside the step
+    for _ in range(max(1, args.warmup // 2)):
+        step(host_inputs, defer=True)
+    e2e_ms, _ = timed(host_inputs, args.steps, defer=True)
+    h2d = sum(sum(int(a.numel() * a.element_size()) for a in inp) for inp in host_inputs)
+
+    value = world * n_tasks * args.steps / (total_ms * 1e-3)
+    e2e_value = n_tasks * args.steps / (sum(e2e_ms) * 1e-3)
+    avg = [{k: float(np.mean([p[i][k] for p in per])) for k in per[0][i]} for i in range(len(graphs))]
+    peaks = measured_peaks()
+    roof = roofline(avg, peaks)
+    roof["share_of_step"] = (roof["avg_launch_ms"] * len(graphs)) / (total_ms / args.steps) if world == 1 else None
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            secs = oracle_step(traces)
+            cpu = {"value": n_tasks / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": "one pass of the full workload (3 graphs, 3.07M tasks): per-cell oracle analysis "
+                             "+ Kahn order, single thread", "seconds": secs}
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "ns_per_task": 1e9 / value * world,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+                "data": "synthetic", "config": config(n_tasks), "form": "plain",
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": 8 * len(graphs), "ms_per_step": sum(e2e_ms) / args.steps,
+                        "validation": "on the device (RT_LAUNCH_DEFER_CHECK)"},
+                "roofline": roof, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches,
+                "wall_s_timed": wall,
+                "phases_ms_per_graph": [{k: round(v, 4) for k, v in a.items()} for a in avg]}
+        print(json.dumps(line), flush=True)
+    for g in graphs:
+        g.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

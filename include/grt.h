@@ -1,0 +1,249 @@
+/*
+ * grt.h -- C ABI of libgrt, a GPU-resident task-graph runtime for GB300.
+ *
+ * The library covers the data-parallel path behind per-task runtime overhead
+ * in "On the Duality of Task and Actor Programming Models" (arXiv 2508.16522):
+ *
+ *  - implicit dependence analysis: a program-ordered stream of task launches,
+ *    each with region requirements (inclusive int64 rectangles plus a read,
+ *    write or reduce-sum privilege), is turned into the task DAG on the GPU
+ *    (Section 2.2, implicitly-parallel task systems; Section 5);
+ *  - compiled-graph execution: the DAG runs actor-style, each task holding a
+ *    countdown of pending incoming edges and its out-edge (trigger) list, with
+ *    one atomic decrement per edge instead of events (Section 4.2,
+ *    Algorithm 1);
+ *  - trace replay: a captured DAG is re-executed without re-analysis
+ *    (Section 5, tracing);
+ *  - batched execution of many captured graphs in one persistent launch, and a
+ *    serving loop that admits graphs as they arrive (Section 4.1: a whole
+ *    graph is launched as a single operation).
+ *
+ * Edge rule (the paper does not define one; this is the library's reading):
+ *  (1) a task's rectangles on one cell combine into one privilege:
+ *      read+read = read, reduce+reduce = reduce, anything else = write;
+ *  (2) per cell, the accesses in program order form runs -- a write is a run
+ *      of its own, consecutive reads form one run, consecutive reduces form
+ *      one run -- and every member of a run gets an edge from every member of
+ *      the run before it;
+ *  (3) explicit predecessor lists (Fig. 3, launch(..., pre)) add their edges.
+ *  Edges are deduplicated; the DAG is stored as CSR by source with ascending
+ *  columns, which is the canonical form every result is compared in.
+ *
+ * Conventions
+ *  - Every call returns rt_status; nothing is thrown across the ABI. On an
+ *    error, rt_last_error() returns a thread-local message.
+ *  - Device work is ordered on the stream given at creation (a cudaStream_t
+ *    passed as void*); calls are asynchronous unless stated otherwise.
+ *  - The library owns everything it allocates (CSR, counters, ring, scratch);
+ *    the caller owns `state`/`out` buffers and every array it passes in.
+ *  - A task id is the position of its launch in the graph's program order
+ *    (0-based, across all rt_launch_batch calls).
+ *  - Every device wait is bounded: an executor that sees no progress for
+ *    timeout_ns gives up and reports RT_ERR_TIMEOUT; the context stays usable.
+ */
+#ifndef GRT_H
+#define GRT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rt_graph* rt_graph_t;
+typedef struct rt_batch* rt_batch_t;
+
+typedef enum {
+  RT_OK = 0,
+  RT_ERR_INVALID = 1, /* bad argument or launch data (nothing was appended) */
+  RT_ERR_OOM = 2,     /* device or host allocation failed, or a size limit was hit */
+  RT_ERR_CUDA = 3,    /* a CUDA call failed (e.g. no device) */
+  RT_ERR_TIMEOUT = 4, /* the executor made no progress for timeout_ns */
+  RT_ERR_STATE = 5,   /* call out of order (e.g. execute before analyze) */
+  RT_ERR_BUDGET = 6   /* serving: a request does not fit the memory budget */
+} rt_status;
+
+/* privileges of a region requirement */
+enum { RT_READ = 0, RT_WRITE = 1, RT_REDUCE_SUM = 2 };
+
+/* task bodies run in place by the executor (all integer, sums wrap mod 2^32)
+ *  EMPTY   nothing (pure runtime overhead)
+ *  SPIN    x = task id; spin_iters times x = x*1664525 + 1013904223; out[task] = x
+ *  COUNTER state[body_arg[task]] += 1 (plain, non-atomic read-modify-write)
+ *  CHECK   acc = mix32(task, sum of state over the task's read cells);
+ *          state[c] = mix32(acc, c) on its write cells;
+ *          state[c] += mix32(task, c) on its reduce cells (atomic);
+ *          out[task] = acc.  mix32(a, b) = fmix32(a ^ (b * 0x9E3779B1)),
+ *          fmix32 = murmur3's finaliser; c = row-major cell index.            */
+enum { RT_BODY_EMPTY = 0, RT_BODY_SPIN = 1, RT_BODY_COUNTER = 2, RT_BODY_CHECK = 3 };
+
+/* rt_launch_batch flags */
+enum {
+  RT_LAUNCH_HOST = 0,      /* arrays are host pointers, validated on the host */
+  RT_LAUNCH_DEVICE = 1,    /* arrays are device pointers, validated on the device
+                              (a bad batch is reported by rt_analyze) */
+  RT_LAUNCH_DEFER_CHECK = 2 /* with host pointers: validate on the device instead */
+};
+
+/* rt_graph_desc.flags */
+enum {
+  RT_GRAPH_TICKETS = 1, /* record per-task (start, finish) tickets of the last run */
+  RT_GRAPH_PROFILE = 2  /* time each analysis/execution kernel with CUDA events */
+};
+
+typedef struct {
+  int32_t ndim;                   /* 1 or 2 */
+  int64_t dom_lo[2], dom_hi[2];   /* inclusive domain bounds (index 1 unused for 1-D) */
+  int32_t body;                   /* RT_BODY_* */
+  int32_t spin_iters;             /* SPIN: iteration count (>= 0) */
+  void* state;                    /* int32 device buffer, caller-owned: one per cell
+                                     (CHECK, row-major) or per counter (COUNTER) */
+  int64_t state_elems;
+  void* out;                      /* int32 device buffer, one per task (SPIN, CHECK) */
+  int64_t out_elems;
+  void* stream;                   /* cudaStream_t; NULL = legacy default stream */
+  int32_t tile_w, tile_h;         /* analysis tile in cells; 0 = library default */
+  int64_t timeout_ns;             /* executor no-progress limit; 0 = 2 s */
+  int32_t flags;                  /* RT_GRAPH_* */
+} rt_graph_desc;
+
+/* Per-phase statistics of the last rt_analyze / execution (rt_graph_stats). */
+typedef struct {
+  int64_t n_tasks, n_rects, n_preds;
+  int64_t n_entries;      /* (rect, tile) pairs after binning */
+  int64_t n_pairs;        /* candidate (src, dst) pairs before deduplication */
+  int64_t n_edges;        /* distinct edges */
+  int64_t n_roots;
+  int32_t tile_w, tile_h;
+  float ms_analyze;       /* whole analysis, CUDA events (RT_GRAPH_PROFILE) */
+  float ms_bin, ms_sort_entries, ms_sweep, ms_sort_pairs, ms_csr;
+  float ms_execute;       /* last execution launch (seed + executor) */
+  float ms_exec_kernel;   /* the persistent executor kernel alone */
+  int32_t exec_blocks, exec_threads;
+  float ms_sweep_kernel;  /* the interference sweep kernel alone */
+} rt_graph_stats_t;
+
+/* Creates an empty graph. Makes no CUDA call (device buffers are allocated on
+ * first use), so argument errors are reported without a GPU.
+ * Errors: RT_ERR_INVALID (NULL args, ndim not 1/2, dom_lo > dom_hi, unknown
+ * body, tile larger than the supported maximum, negative sizes). */
+rt_status rt_graph_create(const rt_graph_desc* desc, rt_graph_t* out);
+
+/* Frees every library-owned buffer of the graph (waits for its stream). */
+rt_status rt_graph_destroy(rt_graph_t g);
+
+/* Drops all launches (keeps device buffers for reuse); the graph returns to
+ * the state right after rt_graph_create. */
+rt_status rt_graph_clear(rt_graph_t g);
+
+/* Appends n launches in program order (Fig. 3, launch(p, tid, args, pre);
+ * Section 2.2). Launch i of the batch gets task id (previous count + i).
+ *  req_off  int32[n+1], req_off[0] == 0, non-decreasing: launch i owns
+ *           rectangles [req_off[i], req_off[i+1]) of this batch
+ *  lo, hi   int64[R][ndim] inclusive bounds, R = req_off[n]; lo <= hi and
+ *           inside the domain
+ *  priv     uint8[R], RT_READ / RT_WRITE / RT_REDUCE_SUM
+ *  pred_off int32[n+1] and pred (optional, both NULL or both set): explicit
+ *           predecessor ids, each in [0, own id) -- backward edges only, so
+ *           the graph cannot have a cycle
+ *  body_arg int32[n] (optional; required for COUNTER): per-task body argument
+ *  flags    RT_LAUNCH_HOST / RT_LAUNCH_DEVICE / RT_LAUNCH_DEFER_CHECK
+ * The arrays are copied; the caller keeps ownership (pinned host arrays are
+ * copied asynchronously and must stay valid until rt_analyze returns). Errors: RT_ERR_INVALID
+ * (with host validation nothing is appended), RT_ERR_STATE (graph already
+ * analyzed: call rt_graph_clear first), RT_ERR_OOM, RT_ERR_CUDA. */
+rt_status rt_launch_batch(rt_graph_t g, int32_t n, const int32_t* req_off, const int64_t* lo,
+                          const int64_t* hi, const uint8_t* priv, const int32_t* pred_off,
+                          const int32_t* pred, const int32_t* body_arg, int32_t flags);
+
+/* Infers the DAG of all launches so far (tile binning, per-tile interference
+ * sweep, CSR construction) and prepares the countdown counters (Algorithm 1,
+ * Compile). Synchronises the stream a few times to size buffers. Errors:
+ * RT_ERR_INVALID (a device-validated batch was bad), RT_ERR_OOM, RT_ERR_CUDA. */
+rt_status rt_analyze(rt_graph_t g);
+
+/* Device pointers (library-owned, valid until the next analyze/clear/destroy)
+ * to the canonical CSR: row_ptr int32[n+1], col int32[E] (ascending within a
+ * row), indeg int32[n]. Synchronises the stream. RT_ERR_STATE before analyze. */
+rt_status rt_get_csr(rt_graph_t g, const int32_t** row_ptr, const int32_t** col,
+                     const int32_t** indeg, int64_t* n_tasks, int64_t* n_edges);
+
+/* Copies the canonical CSR into caller-owned buffers (host or device
+ * pointers, any of them may be NULL): row_ptr int32[n+1], col int32[E],
+ * indeg int32[n]. Synchronous. RT_ERR_STATE before analyze. */
+rt_status rt_copy_csr(rt_graph_t g, int32_t* row_ptr, int32_t* col, int32_t* indeg);
+
+/* Runs the DAG once (Algorithm 1: INIT seeds every task without incoming
+ * edges; each completion decrements its successors' counters and a counter
+ * reaching zero makes the task ready). Asynchronous: the status is reported by
+ * rt_sync. RT_ERR_STATE before rt_analyze. */
+rt_status rt_execute(rt_graph_t g);
+
+/* Replays the captured DAG `times` times without re-analysis (Section 5):
+ * counters are restored on the device and the runs happen back to back in one
+ * persistent launch (relaunched from a cached CUDA graph). Asynchronous. */
+rt_status rt_replay(rt_graph_t g, int32_t times);
+
+/* Launch shape of this graph's executor runs (0 = library default): number of
+ * persistent blocks, warps per block (1..8), how many published ring slots a
+ * warp claims at once (1..32) and how many newly ready successors a warp keeps
+ * for its own next batch instead of publishing them (0..64). These are the
+ * autotuner's knobs; results do not depend on them. */
+rt_status rt_graph_exec_config(rt_graph_t g, int32_t blocks, int32_t warps, int32_t claim, int32_t keep);
+
+/* Waits for the graph's stream; returns RT_OK, RT_ERR_TIMEOUT (the executor
+ * gave up; the next execution re-initialises the counters) or RT_ERR_CUDA. */
+rt_status rt_sync(rt_graph_t g);
+
+/* Statistics of the last analysis / execution (synchronises the stream). */
+rt_status rt_graph_stats(rt_graph_t g, rt_graph_stats_t* out);
+
+/* Device pointer to int32[2*n] (start, finish) tickets of the last run, drawn
+ * from one global counter (RT_GRAPH_TICKETS only; synchronises). */
+rt_status rt_get_tickets(rt_graph_t g, const int32_t** tickets);
+
+/* Copies the tickets of the last run into a caller buffer int32[2*n] (host or
+ * device). Synchronous. */
+rt_status rt_copy_tickets(rt_graph_t g, int32_t* out);
+
+/* Test hook for bounded waits: the next execution adds `extra` to the
+ * countdown of `task`, so that task never becomes ready and the executor must
+ * give up with RT_ERR_TIMEOUT after timeout_ns (no trap, no fault). */
+rt_status rt_debug_hold_task(rt_graph_t g, int32_t task, int32_t extra);
+
+/* ---- batched execution (Section 4.1: a registered graph runs as one op) --
+ * Builds one disjoint union of already-analyzed graphs: their CSRs, counters
+ * and roots are copied into batch-owned buffers (the captured traces), with
+ * task ids shifted so graph g's tasks follow graph g-1's. The batch still
+ * refers to each graph's body buffers (state/out) and launch data (CHECK
+ * body), so the graphs must outlive it. Errors: RT_ERR_STATE if a graph is not
+ * analyzed, RT_ERR_INVALID, RT_ERR_OOM, RT_ERR_CUDA. */
+rt_status rt_batch_create(const rt_graph_t* graphs, int32_t n_graphs, void* stream,
+                          rt_batch_t* out);
+
+/* One persistent launch in which every graph of the batch runs `replays` times;
+ * graph g's replay r+1 starts as soon as its replay r has finished,
+ * independently of the other graphs. exec_blocks/exec_warps/claim/keep (0 =
+ * default) are the launch shape of rt_graph_exec_config. Asynchronous. */
+rt_status rt_batch_execute(rt_batch_t b, int32_t replays, int32_t exec_blocks, int32_t exec_warps,
+                           int32_t claim, int32_t keep);
+
+rt_status rt_batch_sync(rt_batch_t b, float* ms_kernel);
+rt_status rt_batch_destroy(rt_batch_t b);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* rt_last_error(void);
+
+/* Number of persistent executor blocks per SM and the SM count of the current
+ * device (0 on failure); used by the autotuner. */
+rt_status rt_device_info(int32_t* num_sms, int32_t* exec_blocks_per_sm);
+
+/* Total number of kernels this library has launched in the process (for
+ * benchmarks that report how much GPU work a timed region issued). */
+rt_status rt_kernel_launches(int64_t* count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRT_H */

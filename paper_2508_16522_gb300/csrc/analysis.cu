@@ -1,0 +1,313 @@
+// analysis.cu -- implicit dependence analysis on the GPU.
+//
+// Pipeline (one graph, all launches so far):
+//  1. bin count:  each rectangle -> number of tiles it overlaps
+//  2. scan + expand: one (tile, packed entry) per overlap, written in
+//     rectangle order with coalesced int4 loads of the rectangle arrays
+//  3. stable radix sort by tile -> per tile, its candidates in program order
+//  4. sweep (sweep.cu): one warp per tile walks the candidates in program
+//     order, keeps per-cell run state in shared memory and emits (src, dst)
+//     pairs deduplicated per task within the tile
+//  5. radix sort of the 64-bit pair keys, unique, CSR by source: row counts
+//     and in-degrees by warp-aggregated atomics, row_ptr by a device scan
+//
+// The edge rule is the per-cell run reading of "infer the DAG from the data
+// usage of tasks" (Section 2.2, Section 5): a task's rectangles combine into
+// one privilege per cell, and each access gets edges from every member of the
+// run preceding its own run at that cell.
+#include "grt_internal.cuh"
+
+namespace grt {
+
+namespace {
+
+// error bits of the device-side validation
+constexpr uint32_t kErrReqOff = 1u, kErrRect = 2u, kErrPriv = 4u, kErrPred = 8u, kErrBodyArg = 16u;
+
+// Checks one appended batch whose offsets were already shifted to graph-wide
+// positions: req_off[0..n] must run from r_first to r_end without decreasing;
+// pred_off likewise from p_first to p_end, every pred in [0, own id).
+__global__ void k_validate_tasks(const int32_t* req_off, int32_t n, int64_t r_first, int64_t r_end,
+                                 const int32_t* pred_off, const int32_t* pred, int64_t p_first,
+                                 int64_t p_end, int32_t task_base, const int32_t* body_arg,
+                                 int64_t body_limit, uint32_t* err) {
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > n) return;
+  uint32_t e = 0;
+  if (i == 0 && (int64_t)req_off[0] != r_first) e |= kErrReqOff;
+  if (i == n && (int64_t)req_off[n] != r_end) e |= kErrReqOff;
+  if (pred_off && i == 0 && (int64_t)pred_off[0] != p_first) e |= kErrPred;
+  if (pred_off && i == n && (int64_t)pred_off[n] != p_end) e |= kErrPred;
+  if (i < n) {
+    if (req_off[i + 1] < req_off[i]) e |= kErrReqOff;
+    if (pred_off) {
+      int32_t a = pred_off[i], b = pred_off[i + 1];
+      if (b < a || (int64_t)a < p_first || (int64_t)b > p_end) {
+        e |= kErrPred;
+      } else {
+        for (int32_t k = a; k < b; ++k) {
+          int32_t p = pred[k];
+          if (p < 0 || p >= task_base + i) {
+            e |= kErrPred;
+            break;
+          }
+        }
+      }
+    }
+    if (body_arg && body_limit >= 0) {
+      int32_t v = body_arg[i];
+      if (v < 0 || (int64_t)v >= body_limit) e |= kErrBodyArg;
+    }
+  }
+  if (e) atomicOr(err, e);
+}
+
+__global__ void k_validate_rects(const int64_t* lo, const int64_t* hi, const uint8_t* priv, int64_t R,
+                                 AnalysisDims d, uint32_t* err) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  uint32_t e = 0;
+  for (int k = 0; k < d.ndim; ++k) {
+    int64_t a = lo[r * d.ndim + k], b = hi[r * d.ndim + k];
+    if (a > b || a < d.dom_lo[k] || b > d.dom_lo[k] + d.ext[k] - 1) e |= kErrRect;
+  }
+  if (priv[r] > 2) e |= kErrPriv;
+  if (e) atomicOr(err, e);
+}
+
+__global__ void k_add_offset(int32_t* a, int64_t n, int32_t add) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] += add;
+}
+
+// tile range of one rectangle (coordinates relative to the domain origin)
+struct TileRange {
+  int64_t lx, hx, ly, hy;  // relative inclusive bounds
+  int32_t tx0, ty0, ntx, nty;
+};
+
+__device__ __forceinline__ TileRange tile_range(const int64_t* lo, const int64_t* hi, int64_t r,
+                                                const AnalysisDims& d) {
+  TileRange t;
+  if (d.ndim == 2) {
+    // one 16-byte load per corner: the rectangle arrays are int64[R][2]
+    longlong2 a = *reinterpret_cast<const longlong2*>(lo + 2 * r);
+    longlong2 b = *reinterpret_cast<const longlong2*>(hi + 2 * r);
+    t.lx = a.x - d.dom_lo[0];
+    t.hx = b.x - d.dom_lo[0];
+    t.ly = a.y - d.dom_lo[1];
+    t.hy = b.y - d.dom_lo[1];
+  } else {
+    t.lx = lo[r] - d.dom_lo[0];
+    t.hx = hi[r] - d.dom_lo[0];
+    t.ly = 0;
+    t.hy = 0;
+  }
+  t.tx0 = (int32_t)(t.lx / d.tw);
+  t.ty0 = (int32_t)(t.ly / d.th);
+  t.ntx = (int32_t)(t.hx / d.tw) - t.tx0 + 1;
+  t.nty = (int32_t)(t.hy / d.th) - t.ty0 + 1;
+  return t;
+}
+
+__global__ void k_bin_count(const int32_t* req_off, int32_t n, const int64_t* lo, const int64_t* hi,
+                            AnalysisDims d, int32_t* rect_task, uint64_t* cnt) {
+  int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  for (int32_t r = req_off[t]; r < req_off[t + 1]; ++r) {
+    rect_task[r] = t;
+    TileRange tr = tile_range(lo, hi, r, d);
+    cnt[r] = (uint64_t)tr.ntx * (uint64_t)tr.nty;
+  }
+}
+
+// One warp per 32 rectangles; the warp writes each rectangle's entries
+// together (lane-strided) so that stores are coalesced and large rectangles
+// do not serialise on one lane.
+__global__ void k_bin_expand(const int32_t* rect_task, const int64_t* lo, const int64_t* hi,
+                             const uint8_t* priv, int64_t R, const uint64_t* off, AnalysisDims d,
+                             uint32_t* keys, uint64_t* payload) {
+  const int lane = threadIdx.x & 31;
+  int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+  bool valid = r < R;
+  TileRange tr{};
+  uint64_t base = 0, cnt = 0;
+  uint32_t task = 0, pv = 0;
+  if (valid) {
+    tr = tile_range(lo, hi, r, d);
+    base = off[r];
+    cnt = off[r + 1] - base;
+    task = (uint32_t)rect_task[r];
+    pv = priv[r];
+  }
+  for (int i = 0; i < 32; ++i) {
+    uint64_t c = __shfl_sync(0xffffffffu, cnt, i);
+    if (c == 0) continue;
+    uint64_t b = __shfl_sync(0xffffffffu, base, i);
+    int64_t lx = __shfl_sync(0xffffffffu, tr.lx, i), hx = __shfl_sync(0xffffffffu, tr.hx, i);
+    int64_t ly = __shfl_sync(0xffffffffu, tr.ly, i), hy = __shfl_sync(0xffffffffu, tr.hy, i);
+    int32_t tx0 = __shfl_sync(0xffffffffu, tr.tx0, i), ty0 = __shfl_sync(0xffffffffu, tr.ty0, i);
+    int32_t ntx = __shfl_sync(0xffffffffu, tr.ntx, i);
+    uint32_t tk = __shfl_sync(0xffffffffu, task, i), p = __shfl_sync(0xffffffffu, pv, i);
+    for (uint64_t k = lane; k < c; k += 32) {
+      int32_t tx = tx0 + (int32_t)(k % (uint64_t)ntx);
+      int32_t ty = ty0 + (int32_t)(k / (uint64_t)ntx);
+      int64_t ox = (int64_t)tx * d.tw, oy = (int64_t)ty * d.th;
+      int64_t x0 = (lx > ox ? lx : ox) - ox, x1 = (hx < ox + d.tw - 1 ? hx : ox + d.tw - 1) - ox;
+      int64_t y0 = (ly > oy ? ly : oy) - oy, y1 = (hy < oy + d.th - 1 ? hy : oy + d.th - 1) - oy;
+      keys[b + k] = (uint32_t)ty * (uint32_t)d.ntx + (uint32_t)tx;
+      payload[b + k] = pack_entry(tk, p, d.ndim, (uint32_t)x0, (uint32_t)x1, (uint32_t)y0, (uint32_t)y1);
+    }
+  }
+}
+
+__global__ void k_segments(const uint32_t* keys, int64_t M, uint32_t* seg_begin, uint32_t* seg_end) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= M) return;
+  uint32_t k = keys[e];
+  if (e == 0 || keys[e - 1] != k) seg_begin[k] = (uint32_t)e;
+  if (e == M - 1 || keys[e + 1] != k) seg_end[k] = (uint32_t)(e + 1);
+}
+
+__global__ void k_explicit_pairs(const int32_t* pred_off, const int32_t* pred, int32_t n, int key_bits,
+                                 uint64_t* pairs) {
+  int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  for (int32_t k = pred_off[t]; k < pred_off[t + 1]; ++k)
+    pairs[k] = ((uint64_t)(uint32_t)pred[k] << key_bits) | (uint32_t)t;
+}
+
+__global__ void k_unique_flags(const uint64_t* keys, int64_t P, uint32_t* flags) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P) return;
+  uint64_t k = keys[i];
+  flags[i] = (k != kEmpty64 && (i == 0 || keys[i - 1] != k)) ? 1u : 0u;
+}
+
+// warp-aggregated increment: lanes adding to the same counter elect one leader
+__device__ __forceinline__ void warp_agg_inc(int32_t* base, int32_t idx, bool active) {
+  int32_t key = active ? idx : -1;
+  unsigned peers = __match_any_sync(0xffffffffu, key);
+  if (active && (peers & lanemask_lt()) == 0) atomicAdd(base + idx, (int32_t)__popc(peers));
+}
+
+__global__ void k_emit_csr(const uint64_t* keys, const uint32_t* flags, const uint32_t* upos, int64_t P,
+                           int key_bits, int32_t* col, int32_t* rowcnt, int32_t* indeg) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool act = i < P && flags[i] != 0;
+  int32_t src = 0, dst = 0;
+  if (act) {
+    uint64_t k = keys[i];
+    src = (int32_t)(k >> key_bits);
+    dst = (int32_t)(k & ((1ull << key_bits) - 1ull));
+    col[upos[i]] = dst;
+  }
+  warp_agg_inc(rowcnt, src, act);
+  warp_agg_inc(indeg, dst, act);
+}
+
+__global__ void k_root_flags(const int32_t* indeg, int32_t n, uint32_t* flags) {
+  int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < n) flags[v] = indeg[v] == 0 ? 1u : 0u;
+}
+
+__global__ void k_roots_emit(const int32_t* indeg, const uint32_t* pos, int32_t n, int32_t task_base,
+                             int32_t graph, uint64_t* root_items, int32_t* count) {
+  int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  int32_t dg = indeg[v];
+  count[v] = dg;  // Algorithm 1: one pending-edge counter per node
+  if (dg == 0) root_items[pos[v]] = ((uint64_t)(uint32_t)graph << 32) | (uint32_t)(task_base + v);
+}
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+void launch_validate(const int32_t* req_off, int32_t n, int64_t r_first, const int64_t* lo,
+                     const int64_t* hi, const uint8_t* priv, int64_t R, const int32_t* pred_off,
+                     const int32_t* pred, int64_t p_first, int64_t p_end, int32_t task_base,
+                     const int32_t* body_arg, int64_t body_limit, AnalysisDims d, uint32_t* err,
+                     cudaStream_t s) {
+  count_launch();
+  k_validate_tasks<<<nblk((int64_t)n + 1, 256), 256, 0, s>>>(req_off, n, r_first, r_first + R, pred_off,
+                                                           pred, p_first, p_end, task_base, body_arg,
+                                                           body_limit, err);
+  if (R > 0) {
+    count_launch();
+    k_validate_rects<<<nblk(R, 256), 256, 0, s>>>(lo, hi, priv, R, d, err);
+  }
+}
+
+void launch_add_offset(int32_t* a, int64_t n, int32_t add, cudaStream_t s) {
+  if (n > 0 && add != 0) {
+    count_launch();
+    k_add_offset<<<nblk(n, 256), 256, 0, s>>>(a, n, add);
+  }
+}
+
+void launch_bin_count(const int32_t* req_off, int32_t n, const int64_t* lo, const int64_t* hi,
+                      int64_t R, AnalysisDims d, int32_t* rect_task, uint64_t* cnt, cudaStream_t s) {
+  (void)R;
+  if (n > 0) {
+    count_launch();
+    k_bin_count<<<nblk(n, 256), 256, 0, s>>>(req_off, n, lo, hi, d, rect_task, cnt);
+  }
+}
+
+void launch_bin_expand(const int32_t* rect_task, const int64_t* lo, const int64_t* hi,
+                       const uint8_t* priv, int64_t R, const uint64_t* off, AnalysisDims d,
+                       uint32_t* keys, uint64_t* payload, cudaStream_t s) {
+  if (R > 0) {
+    count_launch();
+    k_bin_expand<<<nblk(R, 256), 256, 0, s>>>(rect_task, lo, hi, priv, R, off, d, keys, payload);
+  }
+}
+
+void launch_segments(const uint32_t* keys, int64_t M, uint32_t* seg_begin, uint32_t* seg_end,
+                     cudaStream_t s) {
+  if (M > 0) {
+    count_launch();
+    k_segments<<<nblk(M, 256), 256, 0, s>>>(keys, M, seg_begin, seg_end);
+  }
+}
+
+void launch_explicit_pairs(const int32_t* pred_off, const int32_t* pred, int32_t n, int key_bits,
+                           uint64_t* pairs, cudaStream_t s) {
+  if (n > 0) {
+    count_launch();
+    k_explicit_pairs<<<nblk(n, 256), 256, 0, s>>>(pred_off, pred, n, key_bits, pairs);
+  }
+}
+
+void launch_unique_flags(const uint64_t* keys, int64_t P, uint32_t* flags, cudaStream_t s) {
+  if (P > 0) {
+    count_launch();
+    k_unique_flags<<<nblk(P, 256), 256, 0, s>>>(keys, P, flags);
+  }
+}
+
+void launch_emit_csr(const uint64_t* keys, const uint32_t* flags, const uint32_t* upos, int64_t P,
+                     int key_bits, int32_t* col, int32_t* rowcnt, int32_t* indeg, cudaStream_t s) {
+  if (P > 0) {
+    count_launch();
+    k_emit_csr<<<nblk(P, 256), 256, 0, s>>>(keys, flags, upos, P, key_bits, col, rowcnt, indeg);
+  }
+}
+
+void launch_roots(const int32_t* indeg, int32_t n, uint32_t* flags, cudaStream_t s) {
+  if (n > 0) {
+    count_launch();
+    k_root_flags<<<nblk(n, 256), 256, 0, s>>>(indeg, n, flags);
+  }
+}
+
+void launch_roots_emit(const int32_t* indeg, const uint32_t* pos, int32_t n, int32_t task_base,
+                       int32_t graph, uint64_t* root_items, int32_t* count, cudaStream_t s) {
+  if (n > 0) {
+    count_launch();
+    k_roots_emit<<<nblk(n, 256), 256, 0, s>>>(indeg, pos, n, task_base, graph, root_items, count);
+  }
+}
+
+}  // namespace grt

@@ -1,0 +1,1089 @@
+// api.cu -- host orchestration behind the C ABI of grt.h.
+//
+// Owns every library buffer, validates inputs, sequences the analysis and
+// execution kernels on the graph's stream, caches CUDA graphs for replays and
+// builds batches. Nothing here computes the method's results: all of that
+// runs in the kernels of analysis.cu, sweep.cu, primitives.cu and exec.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "grt_internal.cuh"
+
+using namespace grt;
+
+namespace {
+
+thread_local std::string g_err;
+
+rt_status fail(rt_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define CK(call)                                                                             \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess) return fail(RT_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+#define CKR(call)                           \
+  do {                                      \
+    rt_status r_ = (call);                  \
+    if (r_ != RT_OK) return r_;             \
+  } while (0)
+
+// grow-only device buffer
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  rt_status reserve(size_t bytes, cudaStream_t s, size_t keep = 0) {
+    if (bytes <= cap && p) return RT_OK;
+    size_t nc = std::max<size_t>(bytes, keep ? cap * 2 : bytes);
+    nc = std::max<size_t>(nc, 256);
+    void* np = nullptr;
+    cudaError_t e = cudaMalloc(&np, nc);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(RT_ERR_OOM, "cudaMalloc(%zu bytes): %s", nc, cudaGetErrorString(e));
+    }
+    if (keep && p) {
+      e = cudaMemcpyAsync(np, p, keep, cudaMemcpyDeviceToDevice, s);
+      if (e != cudaSuccess) return fail(RT_ERR_CUDA, "grow copy: %s", cudaGetErrorString(e));
+    }
+    if (p) cudaFree(p);  // synchronous: the copy above has finished
+    p = np;
+    cap = nc;
+    return RT_OK;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+  template <class T>
+  T* as() const {
+    return reinterpret_cast<T*>(p);
+  }
+};
+
+struct DeviceInfo {
+  bool init = false;
+  int device = -1, num_sms = 0, exec_bps = 0;
+};
+DeviceInfo g_dev;
+
+rt_status ensure_device() {
+  int dev = -1;
+  CK(cudaGetDevice(&dev));
+  if (g_dev.init && g_dev.device == dev) return RT_OK;
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, dev));
+  g_dev.device = dev;
+  g_dev.num_sms = prop.multiProcessorCount;
+  g_dev.exec_bps = exec_max_blocks_per_sm(8);
+  if (g_dev.exec_bps < 1) g_dev.exec_bps = 1;
+  g_dev.init = true;
+  return RT_OK;
+}
+
+int bits_for(uint64_t v) {  // smallest b with 2^b > v
+  int b = 0;
+  while (b < 63 && (1ull << b) <= v) ++b;
+  return b;
+}
+
+enum { EV_A0 = 0, EV_BIN, EV_SORTE, EV_SWEEP, EV_SORTP, EV_CSR, EV_X0, EV_XK0, EV_XK1, EV_SW0, EV_SW1, EV_COUNT };
+
+}  // namespace
+
+struct rt_graph {
+  rt_graph_desc desc{};
+  cudaStream_t s = nullptr;
+  AnalysisDims dims{};
+  int64_t ncells = 0;
+  int32_t n = 0;
+  int64_t R = 0, P = 0;
+  bool has_pred = false, has_body_arg = false;
+  DevBuf req_off, lo, hi, priv, pred_off, pred, body_arg;
+  DevBuf err;  // uint32 device-side validation bits
+  bool pending_validate = false;
+  // analysis
+  DevBuf rect_task, cnt, keys, keys_alt, pay, pay_alt, seg_b, seg_e, pairs, pairs_alt, flags, upos;
+  DevBuf col, row_ptr, indeg, count, rootpos, root_items, ws, misc;
+  // execution
+  DevBuf ring, ctrl, gtable, done_g, tickets;
+  uint32_t* hpin = nullptr;  // pinned readback area (64 words)
+  bool analyzed = false, dirty = false, status_pending = false;
+  int64_t n_edges = 0, n_roots = 0, n_entries = 0, n_pairs = 0;
+  int32_t hold_task = -1, hold_extra = 0;
+  cudaGraphExec_t replay_exec = nullptr;
+  int32_t replay_times = 0;
+  cudaStream_t cap_stream = nullptr;
+  cudaEvent_t ev[EV_COUNT] = {};
+  bool ev_ok = false, analyze_timed = false, exec_timed = false;
+  ExecGraph gt_host{};  // last table entry written to gtable
+  bool gt_valid = false;
+  int exec_blocks = 0, exec_warps = 8;
+  int cfg_blocks = 0, cfg_warps = 0, cfg_claim = 0, cfg_keep = 0;  // rt_graph_exec_config
+};
+
+struct rt_batch {
+  cudaStream_t s = nullptr;
+  int32_t G = 0, G_nonempty = 0;
+  int64_t T = 0, E = 0, Rtot = 0;
+  DevBuf row_ptr, col, indeg, count, root_items, gtable, done_g, ring, ctrl;
+  uint32_t* hpin = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  bool dirty = false;
+  int need_fence = 0;
+};
+
+namespace {
+
+rt_status graph_events(rt_graph* g) {
+  if (g->ev_ok) return RT_OK;
+  for (int i = 0; i < EV_COUNT; ++i) CK(cudaEventCreate(&g->ev[i]));
+  g->ev_ok = true;
+  return RT_OK;
+}
+
+void drop_replay_graph(rt_graph* g) {
+  if (g->replay_exec) cudaGraphExecDestroy(g->replay_exec);
+  g->replay_exec = nullptr;
+  g->replay_times = 0;
+}
+
+rt_status check_desc(const rt_graph_desc* d, AnalysisDims* out, int64_t* ncells) {
+  if (!d) return fail(RT_ERR_INVALID, "desc is NULL");
+  if (d->ndim != 1 && d->ndim != 2) return fail(RT_ERR_INVALID, "ndim must be 1 or 2 (got %d)", d->ndim);
+  AnalysisDims a{};
+  a.ndim = d->ndim;
+  for (int k = 0; k < 2; ++k) {
+    if (k < d->ndim) {
+      if (d->dom_lo[k] > d->dom_hi[k]) return fail(RT_ERR_INVALID, "dom_lo[%d] > dom_hi[%d]", k, k);
+      a.dom_lo[k] = d->dom_lo[k];
+      a.ext[k] = d->dom_hi[k] - d->dom_lo[k] + 1;
+      if (a.ext[k] <= 0 || a.ext[k] > (1ll << 40)) return fail(RT_ERR_INVALID, "domain extent out of range");
+    } else {
+      a.dom_lo[k] = 0;
+      a.ext[k] = 1;
+    }
+  }
+  if (d->body < RT_BODY_EMPTY || d->body > RT_BODY_CHECK) return fail(RT_ERR_INVALID, "unknown body %d", d->body);
+  if (d->spin_iters < 0) return fail(RT_ERR_INVALID, "spin_iters < 0");
+  if (d->state_elems < 0 || d->out_elems < 0 || d->timeout_ns < 0)
+    return fail(RT_ERR_INVALID, "negative size");
+  if (d->tile_w < 0 || d->tile_h < 0) return fail(RT_ERR_INVALID, "negative tile");
+  if (d->ndim == 2) {
+    a.tw = d->tile_w ? d->tile_w : 16;
+    a.th = d->tile_h ? d->tile_h : 16;
+    if (a.tw > kMaxTileSide2D || a.th > kMaxTileSide2D)
+      return fail(RT_ERR_INVALID, "2-D tile sides must be <= %d", kMaxTileSide2D);
+  } else {
+    a.tw = d->tile_w ? d->tile_w : 1024;
+    a.th = 1;
+    if (d->tile_h > 1) return fail(RT_ERR_INVALID, "1-D graphs have tile_h 1");
+    if (a.tw > kMaxTileSide1D) return fail(RT_ERR_INVALID, "1-D tile must be <= %d", kMaxTileSide1D);
+  }
+  if (a.tw * a.th > kMaxTileCells) return fail(RT_ERR_INVALID, "tile has more than %d cells", kMaxTileCells);
+  int64_t ntx = (a.ext[0] + a.tw - 1) / a.tw, nty = (a.ext[1] + a.th - 1) / a.th;
+  if (ntx * nty > (1ll << 26)) return fail(RT_ERR_INVALID, "domain has more than 2^26 tiles; use a larger tile");
+  a.ntx = (int)ntx;
+  a.nty = (int)nty;
+  int64_t cells = a.ext[0] * a.ext[1];
+  if (d->body == RT_BODY_CHECK) {
+    if (!d->state || d->state_elems < cells)
+      return fail(RT_ERR_INVALID, "CHECK body needs state with one int32 per cell (%lld)", (long long)cells);
+    if (cells > (1ll << 32)) return fail(RT_ERR_INVALID, "CHECK body needs at most 2^32 cells");
+  }
+  if (d->body == RT_BODY_COUNTER && (!d->state || d->state_elems <= 0))
+    return fail(RT_ERR_INVALID, "COUNTER body needs a state buffer");
+  *out = a;
+  *ncells = cells;
+  return RT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rt_last_error(void) { return g_err.c_str(); }
+
+rt_status rt_device_info(int32_t* num_sms, int32_t* exec_blocks_per_sm) {
+  CKR(ensure_device());
+  if (num_sms) *num_sms = g_dev.num_sms;
+  if (exec_blocks_per_sm) *exec_blocks_per_sm = g_dev.exec_bps;
+  return RT_OK;
+}
+
+rt_status rt_graph_create(const rt_graph_desc* desc, rt_graph_t* out) {
+  if (!out) return fail(RT_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  AnalysisDims a;
+  int64_t cells;
+  CKR(check_desc(desc, &a, &cells));
+  rt_graph* g = new (std::nothrow) rt_graph();
+  if (!g) return fail(RT_ERR_OOM, "host allocation failed");
+  g->desc = *desc;
+  if (g->desc.timeout_ns == 0) g->desc.timeout_ns = 2000000000ll;
+  g->s = (cudaStream_t)desc->stream;
+  g->dims = a;
+  g->ncells = cells;
+  *out = g;
+  return RT_OK;
+}
+
+rt_status rt_graph_clear(rt_graph_t g) {
+  if (!g) return fail(RT_ERR_INVALID, "graph is NULL");
+  g->n = 0;
+  g->R = 0;
+  g->P = 0;
+  g->has_pred = g->has_body_arg = false;
+  g->pending_validate = false;
+  g->analyzed = false;
+  g->dirty = false;
+  g->n_edges = g->n_roots = g->n_entries = g->n_pairs = 0;
+  g->hold_task = -1;
+  drop_replay_graph(g);
+  return RT_OK;
+}
+
+rt_status rt_graph_destroy(rt_graph_t g) {
+  if (!g) return RT_OK;
+  if (g->ev_ok || g->ring.p || g->req_off.p) cudaStreamSynchronize(g->s);
+  drop_replay_graph(g);
+  DevBuf* bufs[] = {&g->req_off, &g->lo, &g->hi, &g->priv, &g->pred_off, &g->pred, &g->body_arg,
+                    &g->err, &g->rect_task, &g->cnt, &g->keys, &g->keys_alt, &g->pay, &g->pay_alt,
+                    &g->seg_b, &g->seg_e, &g->pairs, &g->pairs_alt, &g->flags, &g->upos, &g->col,
+                    &g->row_ptr, &g->indeg, &g->count, &g->rootpos, &g->root_items, &g->ws, &g->misc,
+                    &g->ring, &g->ctrl, &g->gtable, &g->done_g, &g->tickets};
+  for (DevBuf* b : bufs) b->release();
+  if (g->hpin) cudaFreeHost(g->hpin);
+  if (g->ev_ok)
+    for (int i = 0; i < EV_COUNT; ++i) cudaEventDestroy(g->ev[i]);
+  if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+  delete g;
+  return RT_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// launch ingest
+// ---------------------------------------------------------------------------
+namespace {
+
+rt_status host_validate(const rt_graph* g, int32_t n, const int32_t* req_off, const int64_t* lo,
+                        const int64_t* hi, const uint8_t* priv, const int32_t* pred_off,
+                        const int32_t* pred, const int32_t* body_arg) {
+  const AnalysisDims& d = g->dims;
+  if (req_off[0] != 0) return fail(RT_ERR_INVALID, "req_off[0] must be 0 (got %d)", req_off[0]);
+  for (int32_t i = 0; i < n; ++i)
+    if (req_off[i + 1] < req_off[i]) return fail(RT_ERR_INVALID, "req_off decreases at launch %d", i);
+  const int64_t R = req_off[n];
+  for (int64_t r = 0; r < R; ++r) {
+    for (int k = 0; k < d.ndim; ++k) {
+      const int64_t a = lo[r * d.ndim + k], b = hi[r * d.ndim + k];
+      if (a > b) return fail(RT_ERR_INVALID, "rect %lld: lo > hi in dim %d", (long long)r, k);
+      if (a < d.dom_lo[k] || b > d.dom_lo[k] + d.ext[k] - 1)
+        return fail(RT_ERR_INVALID, "rect %lld outside the domain in dim %d", (long long)r, k);
+    }
+    if (priv[r] > 2) return fail(RT_ERR_INVALID, "rect %lld: privilege %d", (long long)r, (int)priv[r]);
+  }
+  if (pred_off) {
+    if (pred_off[0] != 0) return fail(RT_ERR_INVALID, "pred_off[0] must be 0");
+    for (int32_t i = 0; i < n; ++i) {
+      if (pred_off[i + 1] < pred_off[i]) return fail(RT_ERR_INVALID, "pred_off decreases at launch %d", i);
+      for (int32_t k = pred_off[i]; k < pred_off[i + 1]; ++k)
+        if (pred[k] < 0 || pred[k] >= g->n + i)
+          return fail(RT_ERR_INVALID, "launch %d: predecessor %d is not an earlier task", g->n + i, pred[k]);
+    }
+  }
+  if (body_arg && g->desc.body == RT_BODY_COUNTER)
+    for (int32_t i = 0; i < n; ++i)
+      if (body_arg[i] < 0 || (int64_t)body_arg[i] >= g->desc.state_elems)
+        return fail(RT_ERR_INVALID, "launch %d: body_arg %d outside the state buffer", g->n + i, body_arg[i]);
+  return RT_OK;
+}
+
+rt_status copy_in(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  if (!bytes) return RT_OK;
+  CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
+  return RT_OK;
+}
+
+rt_status ensure_pinned(rt_graph* g) {
+  if (g->hpin) return RT_OK;
+  CK(cudaMallocHost(&g->hpin, 64 * sizeof(uint32_t)));
+  return RT_OK;
+}
+
+}  // namespace
+
+extern "C" rt_status rt_launch_batch(rt_graph_t g, int32_t n, const int32_t* req_off, const int64_t* lo,
+                                     const int64_t* hi, const uint8_t* priv, const int32_t* pred_off,
+                                     const int32_t* pred, const int32_t* body_arg, int32_t flags) {
+  if (!g) return fail(RT_ERR_INVALID, "graph is NULL");
+  if (g->analyzed) return fail(RT_ERR_STATE, "graph already analyzed; call rt_graph_clear first");
+  if (n < 0) return fail(RT_ERR_INVALID, "n < 0");
+  if (n == 0) return RT_OK;
+  if (!req_off) return fail(RT_ERR_INVALID, "req_off is NULL");
+  if ((pred_off == nullptr) != (pred == nullptr))
+    return fail(RT_ERR_INVALID, "pred_off and pred must both be set or both be NULL");
+  if (g->desc.body == RT_BODY_COUNTER && !body_arg)
+    return fail(RT_ERR_INVALID, "COUNTER body needs body_arg");
+  if (flags & ~(RT_LAUNCH_DEVICE | RT_LAUNCH_DEFER_CHECK)) return fail(RT_ERR_INVALID, "unknown flags");
+  if ((int64_t)g->n + n >= (int64_t)INT32_MAX) return fail(RT_ERR_INVALID, "too many tasks");
+  const bool dev = (flags & RT_LAUNCH_DEVICE) != 0;
+  const bool on_device_check = dev || (flags & RT_LAUNCH_DEFER_CHECK);
+  const int D = g->dims.ndim;
+  int64_t R = 0, Pb = 0;
+  int32_t first[2] = {0, 0};
+  if (!dev) {
+    R = req_off[n];
+    Pb = pred_off ? pred_off[n] : 0;
+    first[0] = req_off[0];
+    first[1] = pred_off ? pred_off[0] : 0;
+    if (R < 0 || Pb < 0) return fail(RT_ERR_INVALID, "negative rect or pred count");
+    if (R > 0 && (!lo || !hi || !priv)) return fail(RT_ERR_INVALID, "rect arrays are NULL");
+    if (!on_device_check) CKR(host_validate(g, n, req_off, lo, hi, priv, pred_off, pred, body_arg));
+  }
+  CKR(ensure_device());
+  CKR(ensure_pinned(g));
+  cudaStream_t s = g->s;
+  if (dev) {
+    // the batch's sizes live on the device: read both ends of the offset arrays
+    CK(cudaMemcpyAsync(g->hpin + 0, req_off, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(g->hpin + 1, req_off + n, 4, cudaMemcpyDeviceToHost, s));
+    if (pred_off) {
+      CK(cudaMemcpyAsync(g->hpin + 2, pred_off, 4, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(g->hpin + 3, pred_off + n, 4, cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    first[0] = (int32_t)g->hpin[0];
+    R = (int32_t)g->hpin[1];
+    first[1] = pred_off ? (int32_t)g->hpin[2] : 0;
+    Pb = pred_off ? (int32_t)g->hpin[3] : 0;
+    if (R < 0 || Pb < 0) return fail(RT_ERR_INVALID, "negative rect or pred count");
+    if (R > 0 && (!lo || !hi || !priv)) return fail(RT_ERR_INVALID, "rect arrays are NULL");
+  }
+  if (first[0] != 0) return fail(RT_ERR_INVALID, "req_off[0] must be 0");
+  if (first[1] != 0) return fail(RT_ERR_INVALID, "pred_off[0] must be 0");
+  if (g->R + R >= (int64_t)INT32_MAX || g->P + Pb >= (int64_t)INT32_MAX)
+    return fail(RT_ERR_INVALID, "too many rects or preds");
+
+  const int32_t n0 = g->n;
+  const int64_t R0 = g->R, P0 = g->P;
+  // offsets: position 0 of the batch is the previous end, so copy [1..n]
+  CKR(g->req_off.reserve((size_t)(n0 + n + 1) * 4, s, (size_t)(n0 + 1) * 4));
+  if (n0 == 0) CK(cudaMemsetAsync(g->req_off.p, 0, 4, s));
+  CKR(copy_in(g->req_off.as<int32_t>() + n0 + 1, req_off + 1, (size_t)n * 4, s));
+  launch_add_offset(g->req_off.as<int32_t>() + n0 + 1, n, (int32_t)R0, s);
+  if (R > 0) {
+    CKR(g->lo.reserve((size_t)(R0 + R) * D * 8, s, (size_t)R0 * D * 8));
+    CKR(g->hi.reserve((size_t)(R0 + R) * D * 8, s, (size_t)R0 * D * 8));
+    CKR(g->priv.reserve((size_t)(R0 + R), s, (size_t)R0));
+    CKR(copy_in(g->lo.as<int64_t>() + R0 * D, lo, (size_t)R * D * 8, s));
+    CKR(copy_in(g->hi.as<int64_t>() + R0 * D, hi, (size_t)R * D * 8, s));
+    CKR(copy_in(g->priv.as<uint8_t>() + R0, priv, (size_t)R, s));
+  }
+  if (pred_off || g->has_pred) {
+    CKR(g->pred_off.reserve((size_t)(n0 + n + 1) * 4, s, g->has_pred ? (size_t)(n0 + 1) * 4 : 0));
+    if (!g->has_pred) CK(cudaMemsetAsync(g->pred_off.p, 0, (size_t)(n0 + 1) * 4, s));
+    int32_t* po = g->pred_off.as<int32_t>() + n0 + 1;
+    if (pred_off) {
+      CKR(copy_in(po, pred_off + 1, (size_t)n * 4, s));
+    } else {
+      CK(cudaMemsetAsync(po, 0, (size_t)n * 4, s));
+    }
+    launch_add_offset(po, n, (int32_t)P0, s);
+    if (Pb > 0) {
+      CKR(g->pred.reserve((size_t)(P0 + Pb) * 4, s, (size_t)P0 * 4));
+      CKR(copy_in(g->pred.as<int32_t>() + P0, pred, (size_t)Pb * 4, s));
+    }
+    g->has_pred = true;
+  }
+  if (body_arg || g->has_body_arg) {
+    CKR(g->body_arg.reserve((size_t)(n0 + n) * 4, s, g->has_body_arg ? (size_t)n0 * 4 : 0));
+    if (!g->has_body_arg && n0) CK(cudaMemsetAsync(g->body_arg.p, 0, (size_t)n0 * 4, s));
+    if (body_arg) {
+      CKR(copy_in(g->body_arg.as<int32_t>() + n0, body_arg, (size_t)n * 4, s));
+    } else {
+      CK(cudaMemsetAsync(g->body_arg.as<int32_t>() + n0, 0, (size_t)n * 4, s));
+    }
+    g->has_body_arg = true;
+  }
+  if (on_device_check) {
+    if (!g->err.p) {
+      CKR(g->err.reserve(256, s));
+      CK(cudaMemsetAsync(g->err.p, 0, 4, s));
+    }
+    const int64_t limit = g->desc.body == RT_BODY_COUNTER ? g->desc.state_elems : -1;
+    launch_validate(g->req_off.as<int32_t>() + n0, n, R0, g->lo.as<int64_t>() + R0 * D,
+                    g->hi.as<int64_t>() + R0 * D, g->priv.as<uint8_t>() + R0, R,
+                    g->has_pred ? g->pred_off.as<int32_t>() + n0 : nullptr, g->pred.as<int32_t>(), P0,
+                    P0 + Pb, n0, body_arg ? g->body_arg.as<int32_t>() + n0 : nullptr, limit, g->dims,
+                    g->err.as<uint32_t>(), s);
+    g->pending_validate = true;
+  }
+  CK(cudaGetLastError());
+  g->n += n;
+  g->R += R;
+  g->P += Pb;
+  return RT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// analysis
+// ---------------------------------------------------------------------------
+namespace {
+
+const char* err_bits_text(uint32_t e) {
+  if (e & 2u) return "a rectangle has lo > hi or lies outside the domain";
+  if (e & 4u) return "a privilege is not read/write/reduce";
+  if (e & 1u) return "req_off does not start at 0, decreases, or does not end at the rect count";
+  if (e & 8u) return "a predecessor is not an earlier task (or pred_off is malformed)";
+  if (e & 16u) return "a body_arg lies outside the state buffer";
+  return "invalid launch data";
+}
+
+rt_status reserve_ws(rt_graph* g, size_t bytes) { return g->ws.reserve(bytes + 1024, g->s); }
+
+rt_status run_analysis(rt_graph* g) {
+  cudaStream_t s = g->s;
+  const AnalysisDims& d = g->dims;
+  const int32_t n = g->n;
+  const int64_t R = g->R;
+  const bool prof = (g->desc.flags & RT_GRAPH_PROFILE) != 0;
+  if (prof) {
+    CKR(graph_events(g));
+    CK(cudaEventRecord(g->ev[EV_A0], s));
+  }
+  const int B = std::max(bits_for((uint64_t)n), 1);  // pair key = src << B | dst
+  if (2 * B > 62) return fail(RT_ERR_OOM, "too many tasks for 64-bit pair keys");
+  const int64_t ntiles = (int64_t)d.ntx * d.nty;
+  CKR(g->misc.reserve(256, s));
+  unsigned long long* cursor = reinterpret_cast<unsigned long long*>(g->misc.p);
+  uint32_t* tile_counter = reinterpret_cast<uint32_t*>(g->misc.as<char>() + 64);
+  volatile uint64_t* h64 = reinterpret_cast<volatile uint64_t*>(g->hpin);  // 32 x u64
+
+  // ---- 1-3: binning ------------------------------------------------------
+  int64_t M = 0;
+  const uint32_t* skeys = nullptr;
+  const uint64_t* spay = nullptr;
+  if (R > 0) {
+    CKR(g->rect_task.reserve((size_t)R * 4, s));
+    CKR(g->cnt.reserve((size_t)(R + 1) * 8, s));
+    CKR(reserve_ws(g, scan_ws_elems<uint64_t>(R) * 8));
+    launch_bin_count(g->req_off.as<int32_t>(), n, g->lo.as<int64_t>(), g->hi.as<int64_t>(), R, d,
+                     g->rect_task.as<int32_t>(), g->cnt.as<uint64_t>(), s);
+    scan_exclusive<uint64_t>(g->cnt.as<uint64_t>(), g->cnt.as<uint64_t>(), R, g->ws.as<uint64_t>(), s);
+    CK(cudaMemcpyAsync((void*)&h64[0], g->cnt.as<uint64_t>() + R, 8, cudaMemcpyDeviceToHost, s));
+  }
+  h64[1] = 0;
+  if (g->pending_validate) CK(cudaMemcpyAsync((void*)&h64[1], g->err.p, 4, cudaMemcpyDeviceToHost, s));
+  if (R > 0 || g->pending_validate) CK(cudaStreamSynchronize(s));
+  if (g->pending_validate && (uint32_t)h64[1] != 0u)
+    return fail(RT_ERR_INVALID, "device validation: %s", err_bits_text((uint32_t)h64[1]));
+  g->pending_validate = false;
+  if (R > 0) M = (int64_t)h64[0];
+  if (M >= (1ll << 30)) return fail(RT_ERR_OOM, "%lld tile entries (limit 2^30); use a larger tile", (long long)M);
+  g->n_entries = M;
+  if (M > 0) {
+    CKR(g->keys.reserve((size_t)M * 4, s));
+    CKR(g->keys_alt.reserve((size_t)M * 4, s));
+    CKR(g->pay.reserve((size_t)M * 8, s));
+    CKR(g->pay_alt.reserve((size_t)M * 8, s));
+    CKR(g->seg_b.reserve((size_t)ntiles * 4, s));
+    CKR(g->seg_e.reserve((size_t)ntiles * 4, s));
+    CKR(reserve_ws(g, radix_ws_bytes(M)));
+    launch_bin_expand(g->rect_task.as<int32_t>(), g->lo.as<int64_t>(), g->hi.as<int64_t>(),
+                      g->priv.as<uint8_t>(), R, g->cnt.as<uint64_t>(), d, g->keys.as<uint32_t>(),
+                      g->pay.as<uint64_t>(), s);
+    if (prof) CK(cudaEventRecord(g->ev[EV_BIN], s));
+    const int tbits = std::max(bits_for((uint64_t)(ntiles - 1)), 1);
+    const int flip = radix_sort<uint32_t>(g->keys.as<uint32_t>(), g->keys_alt.as<uint32_t>(),
+                                          g->pay.as<uint64_t>(), g->pay_alt.as<uint64_t>(), M, tbits,
+                                          g->ws.p, s);
+    skeys = flip ? g->keys_alt.as<uint32_t>() : g->keys.as<uint32_t>();
+    spay = flip ? g->pay_alt.as<uint64_t>() : g->pay.as<uint64_t>();
+    CK(cudaMemsetAsync(g->seg_b.p, 0, (size_t)ntiles * 4, s));
+    CK(cudaMemsetAsync(g->seg_e.p, 0, (size_t)ntiles * 4, s));
+    launch_segments(skeys, M, g->seg_b.as<uint32_t>(), g->seg_e.as<uint32_t>(), s);
+    if (prof) CK(cudaEventRecord(g->ev[EV_SORTE], s));
+  } else if (prof) {
+    CK(cudaEventRecord(g->ev[EV_BIN], s));
+    CK(cudaEventRecord(g->ev[EV_SORTE], s));
+  }
+
+  // ---- 4: sweep (+ explicit preds) ---------------------------------------
+  const int64_t Pe = g->has_pred ? g->P : 0;
+  unsigned long long cap = (unsigned long long)Pe + (M > 0 ? std::max<unsigned long long>(2ull * M, 1ull << 16) : 0ull);
+  int64_t Ptot = Pe;
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    CKR(g->pairs.reserve((size_t)std::max<unsigned long long>(cap, 1) * 8, s));
+    CKR(g->pairs_alt.reserve((size_t)std::max<unsigned long long>(cap, 1) * 8, s));
+    if (Pe > 0)
+      launch_explicit_pairs(g->pred_off.as<int32_t>(), g->pred.as<int32_t>(), n, B,
+                            g->pairs.as<uint64_t>(), s);
+    if (M == 0) break;
+    h64[2] = (uint64_t)Pe;
+    CK(cudaMemcpyAsync(cursor, (const void*)&h64[2], 8, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(tile_counter, 0, 4, s));
+    SweepOut o{g->pairs.as<uint64_t>(), cap, cursor, tile_counter, B};
+    const int warps = sweep_warps_per_block(d.tw * d.th);
+    const int64_t want = (ntiles + warps - 1) / warps;
+    const int blocks = (int)std::min<int64_t>(want, (int64_t)g_dev.num_sms * 8);
+    if (prof) CK(cudaEventRecord(g->ev[EV_SW0], s));
+    launch_sweep(spay, g->seg_b.as<uint32_t>(), g->seg_e.as<uint32_t>(), d, o, std::max(blocks, 1), s);
+    if (prof) CK(cudaEventRecord(g->ev[EV_SW1], s));
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync((void*)&h64[3], cursor, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    Ptot = (int64_t)h64[3];
+    if ((unsigned long long)Ptot <= cap) break;
+    cap = (unsigned long long)Ptot + (Ptot >> 3);  // the sweep counted what it needed: rerun once
+    if (attempt == 3) return fail(RT_ERR_OOM, "pair buffer kept overflowing");
+  }
+  if (Ptot >= (1ll << 31) - 1) return fail(RT_ERR_OOM, "%lld candidate pairs (limit 2^31)", (long long)Ptot);
+  if (prof) CK(cudaEventRecord(g->ev[EV_SWEEP], s));
+  g->n_pairs = Ptot;
+
+  // ---- 5: dedupe + CSR -----------------------------------------------------
+  CKR(g->flags.reserve((size_t)(Ptot + 1) * 4, s));
+  CKR(g->upos.reserve((size_t)(Ptot + 1) * 4, s));
+  CKR(g->col.reserve((size_t)std::max<int64_t>(Ptot, 1) * 4, s));
+  CKR(g->row_ptr.reserve((size_t)(n + 1) * 4, s));
+  CKR(g->indeg.reserve((size_t)n * 4, s));
+  CKR(g->count.reserve((size_t)n * 4, s));
+  CKR(g->rootpos.reserve((size_t)(n + 1) * 4, s));
+  CKR(g->root_items.reserve((size_t)n * 8, s));
+  CKR(reserve_ws(g, std::max(radix_ws_bytes(Ptot),
+                             scan_ws_elems<uint32_t>(std::max<int64_t>(Ptot, n) + 1) * 4)));
+  const int flip = radix_sort<uint64_t>(g->pairs.as<uint64_t>(), g->pairs_alt.as<uint64_t>(), nullptr,
+                                        nullptr, Ptot, 2 * B, g->ws.p, s);
+  const uint64_t* sp = flip ? g->pairs_alt.as<uint64_t>() : g->pairs.as<uint64_t>();
+  if (prof) CK(cudaEventRecord(g->ev[EV_SORTP], s));
+  launch_unique_flags(sp, Ptot, g->flags.as<uint32_t>(), s);
+  scan_exclusive<uint32_t>(g->flags.as<uint32_t>(), g->upos.as<uint32_t>(), Ptot, g->ws.as<uint32_t>(), s);
+  CK(cudaMemsetAsync(g->row_ptr.p, 0, (size_t)(n + 1) * 4, s));
+  CK(cudaMemsetAsync(g->indeg.p, 0, (size_t)n * 4, s));
+  launch_emit_csr(sp, g->flags.as<uint32_t>(), g->upos.as<uint32_t>(), Ptot, B, g->col.as<int32_t>(),
+                  g->row_ptr.as<int32_t>(), g->indeg.as<int32_t>(), s);
+  scan_exclusive<uint32_t>(g->row_ptr.as<uint32_t>(), g->row_ptr.as<uint32_t>(), n, g->ws.as<uint32_t>(), s);
+  launch_roots(g->indeg.as<int32_t>(), n, g->rootpos.as<uint32_t>(), s);
+  scan_exclusive<uint32_t>(g->rootpos.as<uint32_t>(), g->rootpos.as<uint32_t>(), n, g->ws.as<uint32_t>(), s);
+  launch_roots_emit(g->indeg.as<int32_t>(), g->rootpos.as<uint32_t>(), n, 0, 0, g->root_items.as<uint64_t>(),
+                    g->count.as<int32_t>(), s);
+  if (prof) CK(cudaEventRecord(g->ev[EV_CSR], s));
+  CK(cudaMemcpyAsync(g->hpin + 8, g->upos.as<uint32_t>() + Ptot, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(g->hpin + 9, g->rootpos.as<uint32_t>() + n, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  g->n_edges = g->hpin[8];
+  g->n_roots = g->hpin[9];
+  g->analyze_timed = prof;
+  return RT_OK;
+}
+
+}  // namespace
+
+extern "C" rt_status rt_analyze(rt_graph_t g) {
+  if (!g) return fail(RT_ERR_INVALID, "graph is NULL");
+  if (g->analyzed) return RT_OK;
+  const int body = g->desc.body;
+  if ((body == RT_BODY_SPIN || body == RT_BODY_CHECK) && (!g->desc.out || g->desc.out_elems < g->n))
+    return fail(RT_ERR_INVALID, "SPIN/CHECK bodies need `out` with one int32 per task (%d)", g->n);
+  if (g->n > 0 && body == RT_BODY_COUNTER && !g->has_body_arg) return fail(RT_ERR_INVALID, "COUNTER needs body_arg");
+  CKR(ensure_device());
+  CKR(ensure_pinned(g));
+  drop_replay_graph(g);
+  if (g->n > 0) CKR(run_analysis(g));
+  else g->n_edges = g->n_roots = g->n_entries = g->n_pairs = 0;
+  g->analyzed = true;
+  g->dirty = false;
+  return RT_OK;
+}
+
+extern "C" rt_status rt_get_csr(rt_graph_t g, const int32_t** row_ptr, const int32_t** col,
+                                const int32_t** indeg, int64_t* n_tasks, int64_t* n_edges) {
+  if (!g) return fail(RT_ERR_INVALID, "graph is NULL");
+  if (!g->analyzed) return fail(RT_ERR_STATE, "graph not analyzed");
+  if (g->n > 0) CK(cudaStreamSynchronize(g->s));
+  if (row_ptr) *row_ptr = g->row_ptr.as<int32_t>();
+  if (col) *col = g->col.as<int32_t>();
+  if (indeg) *indeg = g->indeg.as<int32_t>();
+  if (n_tasks) *n_tasks = g->n;
+  if (n_edges) *n_edges = g->n_edges;
+  return RT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// execution
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kStatusWord = 40;  // hpin word receiving the executor status
+
+rt_status prepare_run(rt_graph* g, int32_t replays, ExecParams* out, int64_t* ring_clear) {
+  cudaStream_t s = g->s;
+  const uint64_t cap = (uint64_t)g->n * (uint64_t)replays + 64;
+  if (cap >= 0xFFFFFFF0ull) return fail(RT_ERR_INVALID, "tasks x replays must stay below 2^32 per launch");
+  const bool grow = cap * 8 > g->ring.cap || !g->ring.p;
+  if (grow) {
+    drop_replay_graph(g);
+    CKR(g->ring.reserve((size_t)cap * 8, s));
+  }
+  *ring_clear = (grow || g->dirty) ? (int64_t)(g->ring.cap / 8) : 0;
+  CKR(g->ctrl.reserve(sizeof(ExecCtrl), s));
+  CKR(g->done_g.reserve(64, s));
+  if (!g->gtable.p) {
+    CKR(g->gtable.reserve(sizeof(ExecGraph), s));
+  }
+  ExecGraph G{};
+  G.task_base = 0;
+  G.n_tasks = g->n;
+  G.root_base = 0;
+  G.n_roots = (int32_t)g->n_roots;
+  G.body = g->desc.body;
+  G.spin_iters = g->desc.spin_iters;
+  G.ndim = g->dims.ndim;
+  G.state = (int32_t*)g->desc.state;
+  G.out = (int32_t*)g->desc.out;
+  G.body_arg = g->body_arg.as<int32_t>();
+  G.req_off = g->req_off.as<int32_t>();
+  G.lo = g->lo.as<int64_t>();
+  G.hi = g->hi.as<int64_t>();
+  G.priv = g->priv.as<uint8_t>();
+  G.dom_lo[0] = g->dims.dom_lo[0];
+  G.dom_lo[1] = g->dims.dom_lo[1];
+  G.ext[0] = g->dims.ext[0];
+  G.ext[1] = g->dims.ext[1];
+  // the table lives in device memory; rewritten (synchronously) only when it changes
+  if (!g->gt_valid || memcmp(&G, &g->gt_host, sizeof G) != 0) {
+    CK(cudaStreamSynchronize(s));
+    CK(cudaMemcpy(g->gtable.p, &G, sizeof G, cudaMemcpyHostToDevice));
+    g->gt_host = G;
+    g->gt_valid = true;
+  }
+  if (g->desc.flags & RT_GRAPH_TICKETS) CKR(g->tickets.reserve((size_t)g->n * 8, s));
+  ExecParams p{};
+  p.row_ptr = g->row_ptr.as<int32_t>();
+  p.col = g->col.as<int32_t>();
+  p.indeg = g->indeg.as<int32_t>();
+  p.count = g->count.as<int32_t>();
+  p.ring = g->ring.as<uint64_t>();
+  p.ring_cap = (uint32_t)std::min<uint64_t>(g->ring.cap / 8, 0xFFFFFFF0ull);
+  p.n_graphs = 1;
+  p.root_items = g->root_items.as<uint64_t>();
+  p.graphs = g->gtable.as<ExecGraph>();
+  p.done_g = g->done_g.as<uint32_t>();
+  p.ctrl = g->ctrl.as<ExecCtrl>();
+  p.replays = replays;
+  p.graphs_target = 1;
+  p.timeout_ns = g->desc.timeout_ns;
+  p.claim = g->cfg_claim > 0 ? g->cfg_claim : 32;
+  p.keep = g->cfg_keep > 0 ? g->cfg_keep : 32;
+  p.tickets = (g->desc.flags & RT_GRAPH_TICKETS) ? g->tickets.as<int32_t>() : nullptr;
+  p.total_roots = (int32_t)g->n_roots;
+  p.need_fence = g->desc.body == RT_BODY_COUNTER || g->desc.body == RT_BODY_CHECK;
+  *out = p;
+  return RT_OK;
+}
+
+rt_status enqueue_run(rt_graph* g, const ExecParams& p, int64_t ring_clear, cudaStream_t s, bool timed) {
+  if (g->dirty || g->hold_task >= 0)
+    launch_reset_counts(g->count.as<int32_t>(), g->indeg.as<int32_t>(), g->n, g->hold_task, g->hold_extra, s);
+  if (timed) CK(cudaEventRecord(g->ev[EV_X0], s));
+  launch_seed(p, ring_clear, s);
+  const int warps = g->cfg_warps > 0 ? g->cfg_warps : 8;
+  const int blocks = g->cfg_blocks > 0 ? g->cfg_blocks : g_dev.num_sms;
+  if (timed) CK(cudaEventRecord(g->ev[EV_XK0], s));
+  launch_exec(p, blocks, warps, s);
+  if (timed) CK(cudaEventRecord(g->ev[EV_XK1], s));
+  CK(cudaMemcpyAsync(g->hpin + kStatusWord, &p.ctrl->status, 4, cudaMemcpyDeviceToHost, s));
+  g->exec_blocks = blocks;
+  g->exec_warps = warps;
+  return RT_OK;
+}
+
+rt_status start_run(rt_graph* g, int32_t replays) {
+  if (!g) return fail(RT_ERR_INVALID, "graph is NULL");
+  if (!g->analyzed) return fail(RT_ERR_STATE, "execute before analyze");
+  if (replays <= 0) return fail(RT_ERR_INVALID, "replays must be positive");
+  if (g->n == 0) {
+    g->hpin[kStatusWord] = 0;
+    g->status_pending = false;
+    return RT_OK;
+  }
+  if (g->hold_task >= g->n) return fail(RT_ERR_INVALID, "held task out of range");
+  CKR(ensure_device());
+  const bool timed = (g->desc.flags & RT_GRAPH_PROFILE) != 0;
+  if (timed) CKR(graph_events(g));
+  ExecParams p;
+  int64_t ring_clear = 0;
+  CKR(prepare_run(g, replays, &p, &ring_clear));
+  cudaStream_t s = g->s;
+  const bool special = g->dirty || g->hold_task >= 0 || ring_clear > 0 || timed ||
+                       (g->desc.flags & RT_GRAPH_TICKETS);
+  if (special || replays == 1) {
+    CKR(enqueue_run(g, p, ring_clear, s, timed));
+  } else {
+    // replay: a cached CUDA graph of {seed, executor, status read-back}
+    if (!g->replay_exec || g->replay_times != replays) {
+      drop_replay_graph(g);
+      if (!g->cap_stream) CK(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+      CK(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
+      rt_status st = enqueue_run(g, p, 0, g->cap_stream, false);
+      cudaGraph_t graph = nullptr;
+      cudaError_t e = cudaStreamEndCapture(g->cap_stream, &graph);
+      if (st != RT_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+      }
+      if (e != cudaSuccess) return fail(RT_ERR_CUDA, "capture: %s", cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&g->replay_exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return fail(RT_ERR_CUDA, "instantiate: %s", cudaGetErrorString(e));
+      g->replay_times = replays;
+    }
+    CK(cudaGraphLaunch(g->replay_exec, s));
+  }
+  CK(cudaGetLastError());
+  g->exec_timed = timed;
+  g->status_pending = true;
+  if (g->hold_task >= 0) {
+    g->hold_task = -1;
+    g->dirty = true;  // the held run cannot finish: re-arm every counter next time
+  } else {
+    g->dirty = false;
+  }
+  return RT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rt_status rt_execute(rt_graph_t g) { return start_run(g, 1); }
+
+rt_status rt_replay(rt_graph_t g, int32_t times) { return start_run(g, times); }
+
+rt_status rt_sync(rt_graph_t g) {
+  if (!g) return fail(RT_ERR_INVALID, "graph is NULL");
+  if (!g->hpin && !g->status_pending) return RT_OK;
+  CK(cudaStreamSynchronize(g->s));
+  CK(cudaGetLastError());
+  if (g->status_pending) {
+    g->status_pending = false;
+    const uint32_t st = g->hpin[kStatusWord];
+    if (st == (uint32_t)RT_ERR_TIMEOUT) {
+      g->dirty = true;
+      return fail(RT_ERR_TIMEOUT, "executor made no progress for %lld ns", (long long)g->desc.timeout_ns);
+    }
+    if (st != 0u) {
+      g->dirty = true;
+      return fail(RT_ERR_OOM, "executor ring overflow (status %u)", st);
+    }
+  }
+  return RT_OK;
+}
+
+rt_status rt_graph_stats(rt_graph_t g, rt_graph_stats_t* out) {
+  if (!g || !out) return fail(RT_ERR_INVALID, "NULL argument");
+  memset(out, 0, sizeof *out);
+  if (g->ev_ok || g->hpin) CK(cudaStreamSynchronize(g->s));
+  out->n_tasks = g->n;
+  out->n_rects = g->R;
+  out->n_preds = g->P;
+  out->n_entries = g->n_entries;
+  out->n_pairs = g->n_pairs;
+  out->n_edges = g->n_edges;
+  out->n_roots = g->n_roots;
+  out->tile_w = g->dims.tw;
+  out->tile_h = g->dims.th;
+  out->exec_blocks = g->exec_blocks;
+  out->exec_threads = g->exec_warps * 32;
+  if (g->ev_ok && g->analyze_timed) {
+    cudaEventElapsedTime(&out->ms_analyze, g->ev[EV_A0], g->ev[EV_CSR]);
+    cudaEventElapsedTime(&out->ms_bin, g->ev[EV_A0], g->ev[EV_BIN]);
+    cudaEventElapsedTime(&out->ms_sort_entries, g->ev[EV_BIN], g->ev[EV_SORTE]);
+    cudaEventElapsedTime(&out->ms_sweep, g->ev[EV_SORTE], g->ev[EV_SWEEP]);
+    cudaEventElapsedTime(&out->ms_sort_pairs, g->ev[EV_SWEEP], g->ev[EV_SORTP]);
+    cudaEventElapsedTime(&out->ms_csr, g->ev[EV_SORTP], g->ev[EV_CSR]);
+    if (g->n_entries > 0) cudaEventElapsedTime(&out->ms_sweep_kernel, g->ev[EV_SW0], g->ev[EV_SW1]);
+  }
+  if (g->ev_ok && g->exec_timed) {
+    cudaEventElapsedTime(&out->ms_execute, g->ev[EV_X0], g->ev[EV_XK1]);
+    cudaEventElapsedTime(&out->ms_exec_kernel, g->ev[EV_XK0], g->ev[EV_XK1]);
+  }
+  cudaGetLastError();
+  return RT_OK;
+}
+
+rt_status rt_get_tickets(rt_graph_t g, const int32_t** tickets) {
+  if (!g || !tickets) return fail(RT_ERR_INVALID, "NULL argument");
+  if (!(g->desc.flags & RT_GRAPH_TICKETS) || !g->tickets.p) return fail(RT_ERR_STATE, "no tickets recorded");
+  CK(cudaStreamSynchronize(g->s));
+  *tickets = g->tickets.as<int32_t>();
+  return RT_OK;
+}
+
+rt_status rt_graph_exec_config(rt_graph_t g, int32_t blocks, int32_t warps, int32_t claim, int32_t keep) {
+  if (!g) return fail(RT_ERR_INVALID, "graph is NULL");
+  if (blocks < 0 || warps < 0 || warps > 8 || claim < 0 || claim > 32 || keep < 0 || keep > 64)
+    return fail(RT_ERR_INVALID, "exec config out of range (warps 0..8, claim 0..32, keep 0..64)");
+  if (blocks > 0) {
+    CKR(ensure_device());
+    const int w = warps > 0 ? warps : 8;
+    if (blocks > g_dev.num_sms * std::max(exec_max_blocks_per_sm(w), 1))
+      return fail(RT_ERR_INVALID, "more persistent blocks than can be resident");
+  }
+  g->cfg_blocks = blocks;
+  g->cfg_warps = warps;
+  g->cfg_claim = claim;
+  g->cfg_keep = keep;
+  drop_replay_graph(g);
+  return RT_OK;
+}
+
+rt_status rt_debug_hold_task(rt_graph_t g, int32_t task, int32_t extra) {
+  if (!g) return fail(RT_ERR_INVALID, "graph is NULL");
+  if (task < 0 || extra <= 0) return fail(RT_ERR_INVALID, "task must be >= 0 and extra > 0");
+  g->hold_task = task;
+  g->hold_extra = extra;
+  return RT_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// batches: many captured graphs, one persistent launch
+// ---------------------------------------------------------------------------
+namespace {
+int exec_bps_for(int warps) {
+  static int cache[9] = {0};
+  if (warps < 1 || warps > 8) return 1;
+  if (!cache[warps]) cache[warps] = std::max(exec_max_blocks_per_sm(warps), 1);
+  return cache[warps];
+}
+}  // namespace
+
+extern "C" {
+
+rt_status rt_batch_create(const rt_graph_t* graphs, int32_t n_graphs, void* stream, rt_batch_t* out) {
+  if (!out) return fail(RT_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!graphs || n_graphs <= 0) return fail(RT_ERR_INVALID, "no graphs");
+  int64_t T = 0, E = 0, Rt = 0;
+  int32_t nonempty = 0;
+  for (int32_t i = 0; i < n_graphs; ++i) {
+    if (!graphs[i]) return fail(RT_ERR_INVALID, "graph %d is NULL", i);
+    if (!graphs[i]->analyzed) return fail(RT_ERR_STATE, "graph %d is not analyzed", i);
+    T += graphs[i]->n;
+    E += graphs[i]->n_edges;
+    Rt += graphs[i]->n_roots;
+    nonempty += graphs[i]->n > 0;
+  }
+  if (T >= (1ll << 31) - 1 || E >= (1ll << 31) - 1) return fail(RT_ERR_INVALID, "batch exceeds 2^31 tasks or edges");
+  CKR(ensure_device());
+  rt_batch* b = new (std::nothrow) rt_batch();
+  if (!b) return fail(RT_ERR_OOM, "host allocation failed");
+  b->s = (cudaStream_t)stream;
+  b->G = n_graphs;
+  b->G_nonempty = nonempty;
+  b->T = T;
+  b->E = E;
+  b->Rtot = Rt;
+  cudaStream_t s = b->s;
+  auto bail = [&](rt_status st) {
+    rt_batch_destroy(b);
+    return st;
+  };
+  rt_status st;
+  if ((st = b->row_ptr.reserve((size_t)(T + 1) * 4, s)) || (st = b->col.reserve((size_t)std::max<int64_t>(E, 1) * 4, s)) ||
+      (st = b->indeg.reserve((size_t)std::max<int64_t>(T, 1) * 4, s)) ||
+      (st = b->count.reserve((size_t)std::max<int64_t>(T, 1) * 4, s)) ||
+      (st = b->root_items.reserve((size_t)std::max<int64_t>(Rt, 1) * 8, s)) ||
+      (st = b->gtable.reserve((size_t)n_graphs * sizeof(ExecGraph), s)) ||
+      (st = b->done_g.reserve((size_t)n_graphs * 4, s)) || (st = b->ctrl.reserve(sizeof(ExecCtrl), s)))
+    return bail(st);
+  if (cudaMallocHost(&b->hpin, 256) != cudaSuccess || cudaEventCreate(&b->e0) != cudaSuccess ||
+      cudaEventCreate(&b->e1) != cudaSuccess)
+    return bail(fail(RT_ERR_CUDA, "batch host/event allocation failed"));
+  std::vector<ExecGraph> table((size_t)n_graphs);
+  int64_t tb = 0, eb = 0, rb = 0;
+  cudaMemsetAsync(b->row_ptr.p, 0, 4, s);
+  for (int32_t i = 0; i < n_graphs; ++i) {
+    rt_graph* g = graphs[i];
+    cudaStreamSynchronize(g->s);  // its analysis is complete
+    ExecGraph& G = table[(size_t)i];
+    G.task_base = (int32_t)tb;
+    G.n_tasks = g->n;
+    G.root_base = (int32_t)rb;
+    G.n_roots = (int32_t)g->n_roots;
+    G.body = g->desc.body;
+    G.spin_iters = g->desc.spin_iters;
+    G.ndim = g->dims.ndim;
+    G.state = (int32_t*)g->desc.state;
+    G.out = (int32_t*)g->desc.out;
+    G.body_arg = g->body_arg.as<int32_t>();
+    G.req_off = g->req_off.as<int32_t>();
+    G.lo = g->lo.as<int64_t>();
+    G.hi = g->hi.as<int64_t>();
+    G.priv = g->priv.as<uint8_t>();
+    G.dom_lo[0] = g->dims.dom_lo[0];
+    G.dom_lo[1] = g->dims.dom_lo[1];
+    G.ext[0] = g->dims.ext[0];
+    G.ext[1] = g->dims.ext[1];
+    if (G.body == RT_BODY_COUNTER || G.body == RT_BODY_CHECK) b->need_fence = 1;
+    if (g->n > 0) {
+      int32_t* rp = b->row_ptr.as<int32_t>() + tb;
+      cudaMemcpyAsync(rp, g->row_ptr.p, (size_t)(g->n + 1) * 4, cudaMemcpyDeviceToDevice, s);
+      launch_add_offset(rp, g->n + 1, (int32_t)eb, s);
+      if (g->n_edges > 0) {
+        int32_t* cl = b->col.as<int32_t>() + eb;
+        cudaMemcpyAsync(cl, g->col.p, (size_t)g->n_edges * 4, cudaMemcpyDeviceToDevice, s);
+        launch_add_offset(cl, g->n_edges, (int32_t)tb, s);
+      }
+      cudaMemcpyAsync(b->indeg.as<int32_t>() + tb, g->indeg.p, (size_t)g->n * 4, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(b->count.as<int32_t>() + tb, g->indeg.p, (size_t)g->n * 4, cudaMemcpyDeviceToDevice, s);
+      launch_rebase_roots(g->root_items.as<uint64_t>(), b->root_items.as<uint64_t>() + rb, (int32_t)g->n_roots, i,
+                          (int32_t)tb, s);
+    }
+    tb += g->n;
+    eb += g->n_edges;
+    rb += g->n_roots;
+  }
+  if (cudaMemcpyAsync(b->gtable.p, table.data(), table.size() * sizeof(ExecGraph), cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+    return bail(fail(RT_ERR_CUDA, "batch assembly failed"));
+  b->dirty = true;  // ring not yet initialised
+  *out = b;
+  return RT_OK;
+}
+
+rt_status rt_batch_execute(rt_batch_t b, int32_t replays, int32_t exec_blocks, int32_t exec_warps, int32_t claim,
+                           int32_t keep) {
+  if (!b) return fail(RT_ERR_INVALID, "batch is NULL");
+  if (replays <= 0) return fail(RT_ERR_INVALID, "replays must be positive");
+  const int warps = exec_warps > 0 ? std::min(exec_warps, 8) : 8;
+  const uint64_t cap = (uint64_t)b->T * (uint64_t)replays + 64;
+  if (cap >= 0xFFFFFFF0ull) return fail(RT_ERR_INVALID, "tasks x replays must stay below 2^32 per launch");
+  cudaStream_t s = b->s;
+  bool clear = b->dirty;
+  if (cap * 8 > b->ring.cap) {
+    CKR(b->ring.reserve((size_t)cap * 8, s));
+    clear = true;
+  }
+  if (b->dirty) launch_reset_counts(b->count.as<int32_t>(), b->indeg.as<int32_t>(), b->T, -1, 0, s);
+  ExecParams p{};
+  p.row_ptr = b->row_ptr.as<int32_t>();
+  p.col = b->col.as<int32_t>();
+  p.indeg = b->indeg.as<int32_t>();
+  p.count = b->count.as<int32_t>();
+  p.ring = b->ring.as<uint64_t>();
+  p.ring_cap = (uint32_t)std::min<uint64_t>(b->ring.cap / 8, 0xFFFFFFF0ull);
+  p.n_graphs = b->G;
+  p.root_items = b->root_items.as<uint64_t>();
+  p.graphs = b->gtable.as<ExecGraph>();
+  p.done_g = b->done_g.as<uint32_t>();
+  p.ctrl = b->ctrl.as<ExecCtrl>();
+  p.replays = replays;
+  p.graphs_target = b->G_nonempty;
+  p.timeout_ns = 2000000000ll;
+  p.claim = claim > 0 ? claim : 32;
+  p.keep = keep > 0 ? keep : 32;
+  p.tickets = nullptr;
+  p.total_roots = (int32_t)b->Rtot;
+  p.need_fence = b->need_fence;
+  launch_seed(p, clear ? (int64_t)(b->ring.cap / 8) : 0, s);
+  const int max_blocks = g_dev.num_sms * exec_bps_for(warps);
+  if (exec_blocks > max_blocks) return fail(RT_ERR_INVALID, "more persistent blocks than can be resident");
+  const int blocks = exec_blocks > 0 ? exec_blocks : g_dev.num_sms * std::min(exec_bps_for(warps), 2);
+  CK(cudaEventRecord(b->e0, s));
+  launch_exec(p, blocks, warps, s);
+  CK(cudaEventRecord(b->e1, s));
+  CK(cudaMemcpyAsync(b->hpin, &p.ctrl->status, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaGetLastError());
+  b->dirty = false;
+  return RT_OK;
+}
+
+rt_status rt_batch_sync(rt_batch_t b, float* ms_kernel) {
+  if (!b) return fail(RT_ERR_INVALID, "batch is NULL");
+  CK(cudaStreamSynchronize(b->s));
+  CK(cudaGetLastError());
+  if (ms_kernel) {
+    *ms_kernel = 0.f;
+    cudaEventElapsedTime(ms_kernel, b->e0, b->e1);
+    cudaGetLastError();
+  }
+  const uint32_t st = b->hpin[0];
+  b->hpin[0] = 0;
+  if (st == (uint32_t)RT_ERR_TIMEOUT) {
+    b->dirty = true;
+    return fail(RT_ERR_TIMEOUT, "batch executor made no progress");
+  }
+  if (st != 0u) {
+    b->dirty = true;
+    return fail(RT_ERR_OOM, "batch executor ring overflow");
+  }
+  return RT_OK;
+}
+
+rt_status rt_batch_destroy(rt_batch_t b) {
+  if (!b) return RT_OK;
+  cudaStreamSynchronize(b->s);
+  DevBuf* bufs[] = {&b->row_ptr, &b->col, &b->indeg, &b->count, &b->root_items, &b->gtable, &b->done_g, &b->ring, &b->ctrl};
+  for (DevBuf* x : bufs) x->release();
+  if (b->hpin) cudaFreeHost(b->hpin);
+  if (b->e0) cudaEventDestroy(b->e0);
+  if (b->e1) cudaEventDestroy(b->e1);
+  delete b;
+  return RT_OK;
+}
+
+}  // extern "C"
+
+extern "C" rt_status rt_copy_csr(rt_graph_t g, int32_t* row_ptr, int32_t* col, int32_t* indeg) {
+  if (!g) return fail(RT_ERR_INVALID, "graph is NULL");
+  if (!g->analyzed) return fail(RT_ERR_STATE, "graph not analyzed");
+  if (g->n == 0) {
+    if (row_ptr) {
+      int32_t z = 0;
+      CK(cudaMemcpy(row_ptr, &z, 4, cudaMemcpyDefault));
+    }
+    return RT_OK;
+  }
+  CK(cudaStreamSynchronize(g->s));
+  if (row_ptr) CK(cudaMemcpy(row_ptr, g->row_ptr.p, (size_t)(g->n + 1) * 4, cudaMemcpyDefault));
+  if (col && g->n_edges) CK(cudaMemcpy(col, g->col.p, (size_t)g->n_edges * 4, cudaMemcpyDefault));
+  if (indeg) CK(cudaMemcpy(indeg, g->indeg.p, (size_t)g->n * 4, cudaMemcpyDefault));
+  return RT_OK;
+}
+
+extern "C" rt_status rt_copy_tickets(rt_graph_t g, int32_t* out) {
+  const int32_t* t = nullptr;
+  CKR(rt_get_tickets(g, &t));
+  if (out && g->n) CK(cudaMemcpy(out, t, (size_t)g->n * 8, cudaMemcpyDefault));
+  return RT_OK;
+}
+
+extern "C" rt_status rt_kernel_launches(int64_t* count) {
+  if (!count) return fail(RT_ERR_INVALID, "count is NULL");
+  *count = grt::g_kernel_launches.load();
+  return RT_OK;
+}

@@ -1,0 +1,431 @@
+// exec.cu -- persistent actor-style executor of compiled task graphs.
+//
+// Section 4.2 / Algorithm 1 on one GPU. Each task has a countdown of pending
+// incoming edges and its CSR row of out-edges (the trigger list). A persistent
+// grid of warps plays the workers:
+//  * INIT: every task without incoming edges is seeded into a global ready
+//    ring (k_seed);
+//  * EXECUTE_OP: a warp takes up to 32 ready tasks (its own kept successors
+//    first, else a claim of published ring slots), re-arms each task's own
+//    counter for the next run, runs the bodies in place, then walks the
+//    batch's out-edges warp-cooperatively;
+//  * COMPLETED_EDGE: one atomic decrement per edge; the decrement that finds
+//    1 makes the successor ready. The warp keeps up to `keep` of them for its
+//    next batch and publishes the rest to the ring (reserve by one atomic on
+//    the tail, publish by store-release per slot).
+// Replays: a per-graph completion counter; the warp whose increment completes
+// graph g's run r seeds g's roots again for run r+1 (graphs in a batch advance
+// independently), until `replays` runs are done.
+// Every wait is bounded: a warp that sees no progress of the global executed
+// counter for timeout_ns sets status TIMEOUT and returns.
+#include "grt_internal.cuh"
+
+namespace grt {
+
+namespace {
+constexpr int kKeepMax = 64;
+constexpr unsigned kFull = 0xffffffffu;
+
+__global__ void k_reset_counts(int32_t* count, const int32_t* indeg, int64_t n, int32_t hold_task,
+                               int32_t hold_extra) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) count[i] = indeg[i] + (i == hold_task ? hold_extra : 0);
+}
+
+__global__ void k_seed(ExecParams p, int64_t ring_clear) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = i; k < ring_clear; k += stride) p.ring[k] = kEmpty64;
+  for (int64_t k = i; k < p.total_roots; k += stride) p.ring[k] = p.root_items[k];
+  for (int64_t k = i; k < p.n_graphs; k += stride) p.done_g[k] = 0;
+  if (i == 0) {
+    ExecCtrl* c = p.ctrl;
+    c->head = 0;
+    c->tail = (uint32_t)p.total_roots;
+    c->graphs_done = 0;
+    c->status = 0;
+    c->executed = 0;
+    c->ticket = 0;
+    c->err_where = 0;
+    c->err_info = 0;
+  }
+}
+
+__device__ __forceinline__ uint32_t cell_index(const ExecGraph& G, int64_t x, int64_t y) {
+  return (uint32_t)((y - G.dom_lo[1]) * G.ext[0] + (x - G.dom_lo[0]));
+}
+
+// CHECK body (order-sensitive): see grt.h. Lane-serial; meant for test sizes.
+__device__ void check_body(const ExecGraph& G, int j) {
+  const int r0 = G.req_off[j], r1 = G.req_off[j + 1];
+  const int D = G.ndim;
+  uint32_t acc = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    uint32_t sum = 0;
+    for (int e = r0; e < r1; ++e) {
+      const int64_t x0 = G.lo[(int64_t)e * D], x1 = G.hi[(int64_t)e * D];
+      const int64_t y0 = D == 2 ? G.lo[(int64_t)e * 2 + 1] : G.dom_lo[1];
+      const int64_t y1 = D == 2 ? G.hi[(int64_t)e * 2 + 1] : G.dom_lo[1];
+      for (int64_t y = y0; y <= y1; ++y) {
+        for (int64_t x = x0; x <= x1; ++x) {
+          bool seen = false;
+          for (int f = r0; f < e && !seen; ++f) {
+            const int64_t fx0 = G.lo[(int64_t)f * D], fx1 = G.hi[(int64_t)f * D];
+            const int64_t fy0 = D == 2 ? G.lo[(int64_t)f * 2 + 1] : y, fy1 = D == 2 ? G.hi[(int64_t)f * 2 + 1] : y;
+            seen = fx0 <= x && x <= fx1 && fy0 <= y && y <= fy1;
+          }
+          if (seen) continue;  // the first rectangle covering the cell handles it
+          uint32_t comb = G.priv[e];
+          for (int f = e + 1; f < r1; ++f) {
+            const int64_t fx0 = G.lo[(int64_t)f * D], fx1 = G.hi[(int64_t)f * D];
+            const int64_t fy0 = D == 2 ? G.lo[(int64_t)f * 2 + 1] : y, fy1 = D == 2 ? G.hi[(int64_t)f * 2 + 1] : y;
+            if (fx0 <= x && x <= fx1 && fy0 <= y && y <= fy1) comb = combine_priv(comb, G.priv[f]);
+          }
+          const uint32_t c = cell_index(G, x, y);
+          if (pass == 0) {
+            if (comb == (uint32_t)kKindRead) sum += (uint32_t)__ldcg(G.state + c);
+          } else if (comb == (uint32_t)kKindWrite) {
+            __stcg(G.state + c, (int32_t)mix32(acc, c));
+          } else if (comb == (uint32_t)kKindReduce) {
+            atomicAdd(reinterpret_cast<unsigned*>(G.state) + c, mix32((uint32_t)j, c));
+          }
+        }
+      }
+    }
+    if (pass == 0) acc = mix32((uint32_t)j, sum);
+  }
+  G.out[j] = (int32_t)acc;
+}
+
+// FENCE = false: the launch only has bodies that read nothing written by
+// other tasks (EMPTY, SPIN), so the order-sensitive bodies are compiled out.
+template <bool FENCE>
+__device__ __forceinline__ void run_body(const ExecGraph& G, int j) {
+  if (!FENCE) {
+    if (G.body == RT_BODY_SPIN) {
+      uint32_t x = (uint32_t)j;
+      for (int k = 0; k < G.spin_iters; ++k) x = x * 1664525u + 1013904223u;
+      G.out[j] = (int32_t)x;
+    }
+    return;
+  }
+  switch (G.body) {
+    case RT_BODY_SPIN: {
+      uint32_t x = (uint32_t)j;
+      for (int k = 0; k < G.spin_iters; ++k) x = x * 1664525u + 1013904223u;
+      G.out[j] = (int32_t)x;
+      break;
+    }
+    case RT_BODY_COUNTER: {
+      const int k = G.body_arg[j];
+      const int32_t v = __ldcg(G.state + k);
+      __stcg(G.state + k, (int32_t)((uint32_t)v + 1u));
+      break;
+    }
+    case RT_BODY_CHECK:
+      check_body(G, j);
+      break;
+    default:
+      break;
+  }
+}
+
+// pushes graph g's roots into the ring for its next run (warp-cooperative)
+__device__ void push_roots(const ExecParams& p, int g, int lane) {
+  const ExecGraph& G = p.graphs[g];
+  uint32_t base = 0;
+  if (lane == 0) base = atomicAdd(&p.ctrl->tail, (uint32_t)G.n_roots);
+  base = __shfl_sync(kFull, base, 0);
+  if ((uint64_t)base + (uint64_t)G.n_roots > (uint64_t)p.ring_cap) {
+    if (lane == 0) atomicCAS(&p.ctrl->status, 0u, (uint32_t)RT_ERR_OOM);
+    return;
+  }
+  for (int k = lane; k < G.n_roots; k += 32) st_release_u64(p.ring + base + k, p.root_items[G.root_base + k]);
+}
+
+// the warp whose count completed a run of graph g: next run or graph finished
+__device__ void on_run_complete(const ExecParams& p, int g, uint32_t runs_done, int lane) {
+  fence_acq_rel_gpu();  // acquire every re-armed counter of the finished run
+  if ((int)runs_done < p.replays)
+    push_roots(p, g, lane);
+  else if (lane == 0)
+    atomicAdd(&p.ctrl->graphs_done, 1u);
+}
+
+template <bool TICKETS, bool FENCE, bool SINGLE>
+__global__ void __launch_bounds__(256) k_exec(ExecParams p) {
+  extern __shared__ uint64_t lq_all[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint64_t* lq = lq_all + (size_t)warp * kKeepMax;
+  ExecCtrl* ctrl = p.ctrl;
+  const unsigned lt = lanemask_lt();
+  const uint32_t n0 = SINGLE ? (uint32_t)p.graphs[0].n_tasks : 0u;
+  int nl = 0;                    // kept ready tasks (warp-uniform)
+  uint32_t pend = 0;             // executed but not yet counted (warp-uniform)
+  uint64_t idle_since = 0, last_check = 0;  // lane 0
+  unsigned long long seen = 0;
+  uint32_t backoff = 64;
+
+  // adds this warp's executed tasks to the shared counters (convergent)
+  auto flush = [&]() {
+    if (pend == 0) return;
+    fence_acq_rel_gpu();  // release: bodies and re-armed counters before the count
+    if (SINGLE) {
+      uint32_t now = 0;
+      if (lane == 0) now = atomicAdd(&p.done_g[0], pend) + pend;
+      now = __shfl_sync(kFull, now, 0);
+      if (now % n0 == 0u) on_run_complete(p, 0, now / n0, lane);
+    } else if (lane == 0) {
+      atomicAdd(&ctrl->executed, (unsigned long long)pend);
+    }
+    pend = 0;
+  };
+
+  for (;;) {
+    uint64_t item = kEmpty64;
+    if (nl > 0) {
+      const int nb = nl < 32 ? nl : 32;
+      if (lane < nb) item = lq[nl - nb + lane];
+      nl -= nb;
+      __syncwarp();
+    } else {
+      uint32_t h0 = 0, got = 0;
+      if (lane == 0) {
+        uint32_t h = ld_relaxed_u32(&ctrl->head), t = ld_relaxed_u32(&ctrl->tail);
+        if (t > p.ring_cap) t = p.ring_cap;
+        while (h < t) {
+          uint32_t want = t - h;
+          if (want > (uint32_t)p.claim) want = (uint32_t)p.claim;
+          const uint32_t old = atomicCAS(&ctrl->head, h, h + want);
+          if (old == h) {
+            h0 = h;
+            got = want;
+            break;
+          }
+          h = old;
+          t = ld_relaxed_u32(&ctrl->tail);
+          if (t > p.ring_cap) t = p.ring_cap;
+        }
+      }
+      got = __shfl_sync(kFull, got, 0);
+      h0 = __shfl_sync(kFull, h0, 0);
+      if (got == 0) {
+        if (pend) {
+          flush();  // may seed the next run: look for work again first
+          continue;
+        }
+        int stop = 0;
+        if (lane == 0) {
+          const uint32_t st = ld_relaxed_u32(&ctrl->status);
+          const uint32_t gd = ld_relaxed_u32(&ctrl->graphs_done);
+          if (st != 0u || (int)gd >= p.graphs_target) {
+            stop = 1;
+          } else {
+            const uint64_t now = globaltimer_ns();
+            if (idle_since == 0) {
+              idle_since = last_check = now;
+              seen = SINGLE ? ld_relaxed_u32(&p.done_g[0]) : ld_relaxed_u64(&ctrl->executed);
+            } else if (now - last_check > 20000u) {
+              last_check = now;
+              const unsigned long long pr = SINGLE ? ld_relaxed_u32(&p.done_g[0]) : ld_relaxed_u64(&ctrl->executed);
+              if (pr != seen) {
+                seen = pr;
+                idle_since = now;
+              } else if (now - idle_since > (uint64_t)p.timeout_ns) {
+                atomicCAS(&ctrl->status, 0u, (uint32_t)RT_ERR_TIMEOUT);
+                stop = 1;
+              }
+            }
+          }
+        }
+        if (__shfl_sync(kFull, stop, 0)) break;
+        __nanosleep(backoff);
+        if (backoff < 2048) backoff <<= 1;
+        continue;
+      }
+      backoff = 64;
+      idle_since = 0;
+      if ((uint32_t)lane < got) {
+        uint64_t* slot = p.ring + h0 + lane;
+        uint64_t v = ld_acquire_u64(slot);
+        if (v == kEmpty64) {
+          // reserved but not yet published: the producer is between its two stores
+          const uint64_t t0 = globaltimer_ns();
+          while ((v = ld_acquire_u64(slot)) == kEmpty64) {
+            if (globaltimer_ns() - t0 > (uint64_t)p.timeout_ns) {
+              atomicCAS(&ctrl->status, 0u, (uint32_t)RT_ERR_TIMEOUT);
+              ctrl->err_where = 1;
+              break;
+            }
+            __nanosleep(32);
+          }
+        }
+        item = v;
+        if (v != kEmpty64) st_relaxed_u64(slot, kEmpty64);  // leave the ring clean for the next launch
+      }
+    }
+
+    if (FENCE) fence_acq_rel_gpu();  // acquire: predecessors' effects visible to the bodies
+    const bool has = item != kEmpty64;
+    const int v = (int)(uint32_t)item;
+    const int g = SINGLE ? 0 : (has ? (int)(item >> 32) : -1);
+    int rbeg = 0, deg = 0;
+    if (has) {
+      rbeg = p.row_ptr[v];
+      deg = p.row_ptr[v + 1] - rbeg;
+      p.count[v] = p.indeg[v];  // INIT's reset, done by the task itself for the next run
+      const ExecGraph& G = p.graphs[g];
+      if (TICKETS) p.tickets[2 * (int64_t)v] = (int32_t)atomicAdd(&ctrl->ticket, 1u);
+      run_body<FENCE>(G, v - G.task_base);
+      if (TICKETS) p.tickets[2 * (int64_t)v + 1] = (int32_t)atomicAdd(&ctrl->ticket, 1u);
+    }
+    if (FENCE || TICKETS) fence_acq_rel_gpu();  // release: bodies before the decrements
+
+    // COMPLETED_EDGE for every out-edge of the batch, 32 edges per step
+    int incl = deg;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int excl = incl - deg;
+    const int D = __shfl_sync(kFull, incl, 31);
+    for (int e0 = 0; e0 < D; e0 += 32) {
+      const int e = e0 + lane;
+      int owner = 0;
+#pragma unroll
+      for (int step = 16; step >= 1; step >>= 1) {
+        const int cand = owner + step;
+        const int ex = __shfl_sync(kFull, excl, cand);
+        if (ex <= e) owner = cand;
+      }
+      const int orb = __shfl_sync(kFull, rbeg, owner);
+      const int oex = __shfl_sync(kFull, excl, owner);
+      const uint64_t oitem = __shfl_sync(kFull, item, owner);
+      bool ready = false;
+      uint64_t nit = 0;
+      if (e < D) {
+        const int s = p.col[orb + (e - oex)];
+        ready = atomicSub(&p.count[s], 1) == 1;
+        nit = (oitem & 0xffffffff00000000ull) | (uint32_t)s;
+      }
+      const unsigned rm = __ballot_sync(kFull, ready);
+      if (rm) {
+        const int r = __popc(rm);
+        const int rank = __popc(rm & lt);
+        int room = p.keep - nl;
+        if (room < 0) room = 0;
+        if (ready && rank < room) lq[nl + rank] = nit;
+        const int nover = r > room ? r - room : 0;
+        if (nover > 0) {
+          uint32_t base = 0;
+          if (lane == 0) base = atomicAdd(&ctrl->tail, (uint32_t)nover);
+          base = __shfl_sync(kFull, base, 0);
+          if ((uint64_t)base + (uint64_t)nover > (uint64_t)p.ring_cap) {
+            if (lane == 0) atomicCAS(&ctrl->status, 0u, (uint32_t)RT_ERR_OOM);
+          } else if (ready && rank >= room) {
+            st_release_u64(p.ring + base + (rank - room), nit);
+          }
+        }
+        nl += r < room ? r : room;
+        __syncwarp();
+      }
+    }
+
+    // completion accounting
+    const unsigned hm = __ballot_sync(kFull, has);
+    if (SINGLE) {
+      pend += (uint32_t)__popc(hm);
+      if (pend >= 4096u) flush();
+    } else {
+      // per graph, immediately: a finished run re-seeds that graph at once
+      const int gkey = has ? g : -1;
+      const unsigned peers = __match_any_sync(kFull, gkey);
+      bool cross = false;
+      uint32_t runs_done = 0;
+      if (hm) fence_acq_rel_gpu();  // release: re-armed counters before the count
+      if (has && (peers & lt) == 0) {
+        const uint32_t c = (uint32_t)__popc(peers);
+        const uint32_t ng = (uint32_t)p.graphs[g].n_tasks;
+        const uint32_t now = atomicAdd(&p.done_g[g], c) + c;
+        if (now % ng == 0u) {
+          cross = true;
+          runs_done = now / ng;
+        }
+      }
+      pend += (uint32_t)__popc(hm);
+      if (pend >= 256u && lane == 0) {
+        atomicAdd(&ctrl->executed, (unsigned long long)pend);
+      }
+      if (pend >= 256u) pend = 0;
+      unsigned cm = __ballot_sync(kFull, cross);
+      while (cm) {
+        const int L = __ffs((int)cm) - 1;
+        cm &= cm - 1;
+        on_run_complete(p, __shfl_sync(kFull, g, L), __shfl_sync(kFull, runs_done, L), lane);
+      }
+    }
+  }
+}
+
+__global__ void k_rebase_roots(const uint64_t* src, uint64_t* dst, int32_t n, int32_t graph,
+                               int32_t task_base) {
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = ((uint64_t)(uint32_t)graph << 32) | (uint32_t)(task_base + (int32_t)(uint32_t)src[i]);
+}
+}  // namespace
+
+void launch_rebase_roots(const uint64_t* src, uint64_t* dst, int32_t n, int32_t graph, int32_t task_base,
+                         cudaStream_t s) {
+  if (n > 0) {
+    count_launch();
+    k_rebase_roots<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, dst, n, graph, task_base);
+  }
+}
+
+void launch_reset_counts(int32_t* count, const int32_t* indeg, int64_t n, int32_t hold_task,
+                         int32_t hold_extra, cudaStream_t s) {
+  if (n > 0) {
+    count_launch();
+    k_reset_counts<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(count, indeg, n, hold_task, hold_extra);
+  }
+}
+
+void launch_seed(ExecParams p, int64_t ring_clear, cudaStream_t s) {
+  int64_t work = ring_clear > p.total_roots ? ring_clear : p.total_roots;
+  if (work < p.n_graphs) work = p.n_graphs;
+  unsigned blocks = (unsigned)((work + 255) / 256);
+  if (blocks < 1) blocks = 1;
+  if (blocks > 4096) blocks = 4096;
+  count_launch();
+  k_seed<<<blocks, 256, 0, s>>>(p, ring_clear);
+}
+
+int exec_max_blocks_per_sm(int warps) {
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_exec<false, false, true>, warps * 32,
+                                                (size_t)warps * kKeepMax * sizeof(uint64_t));
+  return nb;
+}
+
+void launch_exec(ExecParams p, int blocks, int warps, cudaStream_t s) {
+  const size_t smem = (size_t)warps * kKeepMax * sizeof(uint64_t);
+  if (p.keep > kKeepMax) p.keep = kKeepMax;
+  if (p.keep < 0) p.keep = 0;
+  if (p.claim > 32) p.claim = 32;
+  if (p.claim < 1) p.claim = 1;
+  const bool single = p.n_graphs == 1;
+  const bool fence = p.need_fence != 0;
+  count_launch();
+#define GRT_EXEC(T, F, S) k_exec<T, F, S><<<blocks, warps * 32, smem, s>>>(p)
+  if (p.tickets) {
+    if (single) { if (fence) GRT_EXEC(true, true, true); else GRT_EXEC(true, false, true); }
+    else { if (fence) GRT_EXEC(true, true, false); else GRT_EXEC(true, false, false); }
+  } else {
+    if (single) { if (fence) GRT_EXEC(false, true, true); else GRT_EXEC(false, false, true); }
+    else { if (fence) GRT_EXEC(false, true, false); else GRT_EXEC(false, false, false); }
+  }
+#undef GRT_EXEC
+}
+
+}  // namespace grt

@@ -1,0 +1,229 @@
+// grt_internal.cuh -- device helpers and host/device structures of libgrt.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "grt.h"
+
+namespace grt {
+
+// number of kernels this library has launched (reported by rt_kernel_launches)
+extern std::atomic<long long> g_kernel_launches;
+inline void count_launch(long long k = 1) { g_kernel_launches.fetch_add(k, std::memory_order_relaxed); }
+
+constexpr uint64_t kEmpty64 = ~0ull;   // empty ring slot / sentinel pair key
+constexpr uint32_t kPosMask = (1u << 30) - 1;
+constexpr int kKindRead = 0, kKindWrite = 1, kKindReduce = 2, kKindNone = 3;
+
+// ---------------------------------------------------------------------------
+// analysis tiling limits: a binned entry packs task id (32 bits), privilege
+// (2 bits) and the rectangle clipped to its tile in local coordinates
+// (4 x 7 bits in 2-D, 2 x 14 bits in 1-D) into one 64-bit word.
+// ---------------------------------------------------------------------------
+constexpr int kMaxTileSide2D = 128;
+constexpr int kMaxTileSide1D = 16384;
+constexpr int kMaxTileCells = 1024;  // per-warp cell state lives in shared memory
+
+__host__ __device__ inline uint64_t pack_entry(uint32_t task, uint32_t priv, int ndim, uint32_t x0,
+                                               uint32_t x1, uint32_t y0, uint32_t y1) {
+  uint64_t p = (uint64_t)task | ((uint64_t)(priv & 3u) << 32);
+  if (ndim == 2)
+    p |= ((uint64_t)x0 << 34) | ((uint64_t)x1 << 41) | ((uint64_t)y0 << 48) | ((uint64_t)y1 << 55);
+  else
+    p |= ((uint64_t)x0 << 34) | ((uint64_t)x1 << 48);
+  return p;
+}
+
+struct Box {
+  int task, priv, x0, x1, y0, y1;
+};
+
+__device__ __forceinline__ Box unpack_entry(uint64_t p, int ndim) {
+  Box b;
+  b.task = (int)(uint32_t)(p & 0xffffffffu);
+  b.priv = (int)((p >> 32) & 3u);
+  if (ndim == 2) {
+    b.x0 = (int)((p >> 34) & 127u);
+    b.x1 = (int)((p >> 41) & 127u);
+    b.y0 = (int)((p >> 48) & 127u);
+    b.y1 = (int)((p >> 55) & 127u);
+  } else {
+    b.x0 = (int)((p >> 34) & 0x3fffu);
+    b.x1 = (int)((p >> 48) & 0x3fffu);
+    b.y0 = 0;
+    b.y1 = 0;
+  }
+  return b;
+}
+
+// ---------------------------------------------------------------------------
+// PTX wrappers (memory model: acquire/release at GPU scope)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+__device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u64(uint64_t* p, uint64_t v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed_u64(uint64_t* p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// one privilege per task per cell: read+read = read, reduce+reduce = reduce,
+// every other mix = write (0xFF = not yet touched)
+__device__ __forceinline__ uint32_t combine_priv(uint32_t have, uint32_t add) {
+  if (have == 0xFFu) return add;
+  return (have == add && add != (uint32_t)kKindWrite) ? add : (uint32_t)kKindWrite;
+}
+
+// murmur3's 32-bit finaliser and the CHECK body's mixing function
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+__device__ __forceinline__ uint32_t mix32(uint32_t a, uint32_t b) { return fmix32(a ^ (b * 0x9E3779B1u)); }
+
+// ---------------------------------------------------------------------------
+// executor structures
+// ---------------------------------------------------------------------------
+struct ExecGraph {  // one per graph of a launch (1 for rt_execute)
+  int32_t task_base, n_tasks, root_base, n_roots;
+  int32_t body, spin_iters, ndim, pad0;
+  int32_t* state;
+  int32_t* out;
+  const int32_t* body_arg;
+  const int32_t* req_off;  // local rect offsets of the graph's tasks (CHECK body)
+  const int64_t* lo;
+  const int64_t* hi;
+  const uint8_t* priv;
+  int64_t dom_lo[2];
+  int64_t ext[2];
+};
+
+struct ExecCtrl {  // reset before every executor launch; hot words on separate 128-byte lines
+  uint32_t head, pad_h[31];        // ring tickets claimed
+  uint32_t tail, pad_t[31];        // ring tickets reserved
+  uint32_t graphs_done, status;    // status: 0 ok, RT_ERR_TIMEOUT, RT_ERR_OOM (ring)
+  uint32_t err_where, err_info, pad_s[28];
+  unsigned long long executed;     // progress counter (flushed in batches)
+  uint32_t pad_e[30];
+  uint32_t ticket, pad_k[31];
+};
+
+struct ExecParams {
+  const int32_t* row_ptr;
+  const int32_t* col;
+  const int32_t* indeg;
+  int32_t* count;
+  uint64_t* ring;
+  uint32_t ring_cap;
+  int32_t n_graphs;
+  const uint64_t* root_items;  // (graph << 32 | global task id), per-graph ranges
+  const ExecGraph* graphs;
+  uint32_t* done_g;
+  ExecCtrl* ctrl;
+  int32_t replays;
+  int32_t graphs_target;  // graphs with at least one task
+  int64_t timeout_ns;
+  int32_t claim;          // max ring items a warp claims at once (<= 32)
+  int32_t keep;           // ready successors a warp keeps for itself (<= 64)
+  int32_t* tickets;       // optional int32[2 * total tasks]
+  int32_t total_roots;
+  int32_t need_fence;     // some body reads data written by its predecessors
+};
+
+// ---------------------------------------------------------------------------
+// kernels and launchers (defined in scan.cu, radix.cu, analysis.cu, exec.cu)
+// ---------------------------------------------------------------------------
+template <typename T>
+size_t scan_ws_elems(int64_t n);
+template <typename T>
+void scan_exclusive(const T* in, T* out, int64_t n, T* ws, cudaStream_t s);
+
+size_t radix_ws_bytes(int64_t n);
+// sorts (keys, vals) by key bits [0, nbits); ping-pongs between the two
+// buffers; returns 1 if the result is in the *_alt buffers
+template <typename K>
+int radix_sort(K* keys, K* keys_alt, uint64_t* vals, uint64_t* vals_alt, int64_t n, int nbits,
+               void* ws, cudaStream_t s);
+
+struct AnalysisDims {
+  int ndim;
+  int64_t dom_lo[2];
+  int64_t ext[2];
+  int tw, th;
+  int ntx, nty;
+};
+
+void launch_validate(const int32_t* req_off, int32_t n, int64_t r_first, const int64_t* lo,
+                     const int64_t* hi, const uint8_t* priv, int64_t R, const int32_t* pred_off,
+                     const int32_t* pred, int64_t p_first, int64_t p_end, int32_t task_base,
+                     const int32_t* body_arg, int64_t body_limit, AnalysisDims d, uint32_t* err,
+                     cudaStream_t s);
+void launch_add_offset(int32_t* a, int64_t n, int32_t add, cudaStream_t s);
+void launch_bin_count(const int32_t* req_off, int32_t n, const int64_t* lo, const int64_t* hi,
+                      int64_t R, AnalysisDims d, int32_t* rect_task, uint64_t* cnt, cudaStream_t s);
+void launch_bin_expand(const int32_t* rect_task, const int64_t* lo, const int64_t* hi,
+                       const uint8_t* priv, int64_t R, const uint64_t* off, AnalysisDims d,
+                       uint32_t* keys, uint64_t* payload, cudaStream_t s);
+void launch_segments(const uint32_t* keys, int64_t M, uint32_t* seg_begin, uint32_t* seg_end,
+                     cudaStream_t s);
+struct SweepOut {
+  uint64_t* pairs;
+  unsigned long long cap;
+  unsigned long long* cursor;
+  uint32_t* tile_counter;
+  int key_bits;
+};
+int sweep_warps_per_block(int tile_cells);
+size_t sweep_smem_bytes(int tile_cells, int warps);
+void launch_sweep(const uint64_t* payload, const uint32_t* seg_begin, const uint32_t* seg_end,
+                  AnalysisDims d, SweepOut o, int blocks, cudaStream_t s);
+void launch_explicit_pairs(const int32_t* pred_off, const int32_t* pred, int32_t n, int key_bits,
+                           uint64_t* pairs, cudaStream_t s);
+void launch_unique_flags(const uint64_t* keys, int64_t P, uint32_t* flags, cudaStream_t s);
+void launch_emit_csr(const uint64_t* keys, const uint32_t* flags, const uint32_t* upos, int64_t P,
+                     int key_bits, int32_t* col, int32_t* rowcnt, int32_t* indeg, cudaStream_t s);
+void launch_roots(const int32_t* indeg, int32_t n, uint32_t* flags, cudaStream_t s);
+void launch_roots_emit(const int32_t* indeg, const uint32_t* pos, int32_t n, int32_t task_base,
+                       int32_t graph, uint64_t* root_items, int32_t* count, cudaStream_t s);
+
+void launch_reset_counts(int32_t* count, const int32_t* indeg, int64_t n, int32_t hold_task,
+                         int32_t hold_extra, cudaStream_t s);
+void launch_rebase_roots(const uint64_t* src, uint64_t* dst, int32_t n, int32_t graph, int32_t task_base,
+                         cudaStream_t s);
+void launch_seed(ExecParams p, int64_t ring_clear, cudaStream_t s);
+void launch_exec(ExecParams p, int blocks, int warps, cudaStream_t s);
+int exec_max_blocks_per_sm(int warps);
+
+}  // namespace grt

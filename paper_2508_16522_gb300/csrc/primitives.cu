@@ -1,0 +1,279 @@
+// primitives.cu -- device exclusive scan and stable LSD radix sort.
+//
+// Scan: reduce-then-scan over blocks of 2048 items (256 threads x 8), the
+// block totals scanned recursively. out[n] receives the total, so arrays are
+// sized n+1; in == out is allowed.
+//
+// Radix sort: 8-bit digits, least significant first. Per pass: a per-block
+// digit histogram, an exclusive scan of the digit-major histogram matrix, and
+// a scatter whose in-block ranks are computed warp by warp with match_any (so
+// the sort is stable: keys keep their input order within a digit).
+
+#include "grt_internal.cuh"
+
+namespace grt {
+
+std::atomic<long long> g_kernel_launches{0};
+
+namespace {
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+template <typename T>
+__device__ T block_exclusive_sum(T v, T* warp_tot, T* block_total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) warp_tot[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    T w = lane < (kScanThreads / 32) ? warp_tot[lane] : T(0);
+    T wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      T y = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += y;
+    }
+    if (lane < (kScanThreads / 32)) warp_tot[lane] = wi - w;
+    if (lane == (kScanThreads / 32) - 1) *block_total = wi;
+  }
+  __syncthreads();
+  return incl - v + warp_tot[warp];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const T* in, int64_t n, T* partial) {
+  __shared__ T warp_tot[32];
+  __shared__ T tot;
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  T s = 0;
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    int64_t k = base + j * kScanThreads + threadIdx.x;  // coalesced
+    if (k < n) s += in[k];
+  }
+  (void)block_exclusive_sum<T>(s, warp_tot, &tot);
+  if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(const T* in, T* out, int64_t n,
+                                                           const T* block_base) {
+  __shared__ T stage[kScanTile];
+  __shared__ T warp_tot[32];
+  __shared__ T tot;
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  // coalesced load into shared memory, then each thread owns 8 consecutive items
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    int64_t k = base + j * kScanThreads + threadIdx.x;
+    stage[j * kScanThreads + threadIdx.x] = k < n ? in[k] : T(0);
+  }
+  __syncthreads();
+  T v[kScanItems];
+  T s = 0;
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    v[j] = stage[threadIdx.x * kScanItems + j];
+    s += v[j];
+  }
+  T run = block_exclusive_sum<T>(s, warp_tot, &tot);
+  if (block_base) run += block_base[blockIdx.x];
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    stage[threadIdx.x * kScanItems + j] = run;
+    run += v[j];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    int64_t k = base + j * kScanThreads + threadIdx.x;
+    if (k < n) out[k] = stage[j * kScanThreads + threadIdx.x];
+  }
+  if (base + kScanTile >= n && threadIdx.x == 0) {
+    // the last block writes the grand total
+    T total = tot + (block_base ? block_base[blockIdx.x] : T(0));
+    out[n] = total;
+  }
+}
+}  // namespace
+
+template <typename T>
+size_t scan_ws_elems(int64_t n) {
+  size_t total = 0;
+  while (n > kScanTile) {
+    int64_t nb = (n + kScanTile - 1) / kScanTile;
+    total += 2 * nb + 1;
+    n = nb;
+  }
+  return total + 1;
+}
+
+template <typename T>
+void scan_exclusive(const T* in, T* out, int64_t n, T* ws, cudaStream_t s) {
+  if (n <= 0) {
+    cudaMemsetAsync(out, 0, sizeof(T), s);
+    return;
+  }
+  int64_t nb = (n + kScanTile - 1) / kScanTile;
+  if (nb == 1) {
+    count_launch();
+    k_scan_down<T><<<1, kScanThreads, 0, s>>>(in, out, n, nullptr);
+    return;
+  }
+  T* part = ws;
+  T* part_scan = ws + nb;
+  count_launch();
+  k_scan_reduce<T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, part);
+  scan_exclusive<T>(part, part_scan, nb, ws + 2 * nb + 1, s);
+  count_launch();
+  k_scan_down<T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, part_scan);
+}
+
+template size_t scan_ws_elems<uint32_t>(int64_t);
+template size_t scan_ws_elems<uint64_t>(int64_t);
+template void scan_exclusive<uint32_t>(const uint32_t*, uint32_t*, int64_t, uint32_t*, cudaStream_t);
+template void scan_exclusive<uint64_t>(const uint64_t*, uint64_t*, int64_t, uint64_t*, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// radix sort
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kRadixThreads = 256;
+constexpr int kRadixWarps = kRadixThreads / 32;
+constexpr int kRadixIpt = 16;                                 // keys per thread
+constexpr int kRadixTile = kRadixThreads * kRadixIpt;         // 4096 keys per block
+constexpr int kRadixWarpKeys = kRadixTile / kRadixWarps;      // 512 keys per warp
+
+template <typename K>
+__global__ void __launch_bounds__(kRadixThreads) k_radix_hist(const K* keys, int64_t n, int shift,
+                                                             uint32_t mask, uint32_t* hist,
+                                                             int64_t nblocks) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+#pragma unroll 4
+  for (int j = 0; j < kRadixIpt; ++j) {
+    int64_t k = base + j * kRadixThreads + threadIdx.x;
+    if (k < n) atomicAdd(&h[(uint32_t)(keys[k] >> shift) & mask], 1u);
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+template <typename K, bool HAS_V>
+__global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(
+    const K* __restrict__ keys, const uint64_t* __restrict__ vals, K* __restrict__ keys_out,
+    uint64_t* __restrict__ vals_out, int64_t n, int shift, uint32_t mask,
+    const uint32_t* __restrict__ offs, int64_t nblocks) {
+  __shared__ uint32_t wcnt[kRadixWarps][256];
+  __shared__ uint32_t boff[256];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int w = 0; w < kRadixWarps; ++w) wcnt[w][threadIdx.x] = 0;
+  boff[threadIdx.x] = offs[(int64_t)threadIdx.x * nblocks + blockIdx.x];
+  __syncthreads();
+  const int64_t wbase = (int64_t)blockIdx.x * kRadixTile + (int64_t)warp * kRadixWarpKeys;
+  K kv[kRadixIpt];
+  uint64_t vv[HAS_V ? kRadixIpt : 1];
+  uint32_t rk[kRadixIpt];
+  const unsigned lt = lanemask_lt();
+#pragma unroll
+  for (int r = 0; r < kRadixIpt; ++r) {
+    int64_t idx = wbase + r * 32 + lane;
+    bool valid = idx < n;
+    K k = valid ? keys[idx] : K(0);
+    kv[r] = k;
+    if (HAS_V) vv[HAS_V ? r : 0] = valid ? vals[idx] : 0ull;
+    uint32_t d = valid ? ((uint32_t)(k >> shift) & mask) : 256u;
+    unsigned peers = __match_any_sync(0xffffffffu, d);
+    uint32_t before = __popc(peers & lt);
+    uint32_t base = valid ? wcnt[warp][d] : 0u;
+    __syncwarp();
+    if (valid && before == 0) wcnt[warp][d] = base + __popc(peers);
+    __syncwarp();
+    rk[r] = base + before;
+  }
+  __syncthreads();
+  {
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < kRadixWarps; ++w) {
+      uint32_t t = wcnt[w][threadIdx.x];
+      wcnt[w][threadIdx.x] = run;
+      run += t;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kRadixIpt; ++r) {
+    int64_t idx = wbase + r * 32 + lane;
+    if (idx < n) {
+      uint32_t d = (uint32_t)(kv[r] >> shift) & mask;
+      uint32_t dst = boff[d] + wcnt[warp][d] + rk[r];
+      keys_out[dst] = kv[r];
+      if (HAS_V) vals_out[dst] = vv[HAS_V ? r : 0];
+    }
+  }
+}
+}  // namespace
+
+size_t radix_ws_bytes(int64_t n) {
+  int64_t nb = (n + kRadixTile - 1) / kRadixTile;
+  int64_t h = 256 * (nb > 0 ? nb : 1);
+  return (size_t)(2 * h + 1 + scan_ws_elems<uint32_t>(h)) * sizeof(uint32_t) + 256;
+}
+
+template <typename K>
+int radix_sort(K* keys, K* keys_alt, uint64_t* vals, uint64_t* vals_alt, int64_t n, int nbits,
+               void* ws, cudaStream_t s) {
+  if (n <= 1 || nbits <= 0) return 0;
+  int64_t nb = (n + kRadixTile - 1) / kRadixTile;
+  int64_t h = 256 * nb;
+  uint32_t* hist = (uint32_t*)ws;
+  uint32_t* offs = hist + h;
+  uint32_t* sws = offs + h + 1;
+  K* kin = keys;
+  K* kout = keys_alt;
+  uint64_t* vin = vals;
+  uint64_t* vout = vals_alt;
+  int flips = 0;
+  for (int shift = 0; shift < nbits; shift += 8) {
+    int bits = nbits - shift < 8 ? nbits - shift : 8;
+    uint32_t mask = (1u << bits) - 1u;
+    count_launch();
+    k_radix_hist<K><<<(unsigned)nb, kRadixThreads, 0, s>>>(kin, n, shift, mask, hist, nb);
+    scan_exclusive<uint32_t>(hist, offs, h, sws, s);
+    if (vals) {
+      count_launch();
+      k_radix_scatter<K, true><<<(unsigned)nb, kRadixThreads, 0, s>>>(kin, vin, kout, vout, n, shift,
+                                                                     mask, offs, nb);
+    }
+    else {
+      count_launch();
+      k_radix_scatter<K, false><<<(unsigned)nb, kRadixThreads, 0, s>>>(kin, nullptr, kout, nullptr, n,
+                                                                      shift, mask, offs, nb);
+    }
+    K* t = kin;
+    kin = kout;
+    kout = t;
+    uint64_t* tv = vin;
+    vin = vout;
+    vout = tv;
+    flips ^= 1;
+  }
+  return flips;
+}
+
+template int radix_sort<uint32_t>(uint32_t*, uint32_t*, uint64_t*, uint64_t*, int64_t, int, void*,
+                                  cudaStream_t);
+template int radix_sort<uint64_t>(uint64_t*, uint64_t*, uint64_t*, uint64_t*, int64_t, int, void*,
+                                  cudaStream_t);
+
+}  // namespace grt

@@ -1,0 +1,366 @@
+// sweep.cu -- per-tile interference sweep (the analysis hot loop).
+//
+// One warp owns one tile at a time (tiles handed out by an atomic counter).
+// The tile's candidates -- every (task, rectangle) overlapping it, in program
+// order, each packed as task | privilege | rectangle clipped to the tile --
+// are staged 32 at a time in shared memory with one coalesced 8-byte load per
+// lane. Each cell of the tile keeps its run state in shared memory (16 bytes):
+//
+//   x = start position of the current run | kind << 30
+//   y = position of its last member      | member count (1, 2, >=3) << 30
+//   z = start position of the previous run | its member count << 30
+//   w = position of the previous run's last member
+//
+// (positions index the tile's candidate list; a task's candidates are
+// consecutive there, and its first one stands for the task). A task touching a
+// cell either joins the current run (read after reads, reduce after reduces)
+// and takes edges from the previous run, or starts a new run and takes edges
+// from the current one. Runs of one or two members name them directly; longer
+// runs are enumerated by re-reading the candidates between their first and
+// last member (the ones covering the cell are exactly the members).
+//
+// Lanes split the cells of the task's rectangle; predecessors found by
+// several lanes are merged with match_any, and the survivors go through a
+// per-warp shared-memory hash set, so each (src, dst) pair leaves the tile once
+// per task. Pairs are appended to per-warp chunks of a global buffer (one
+// atomic per 512 pairs); unused chunk tails are filled with a sentinel key that
+// the later sort moves to the end.
+#include "grt_internal.cuh"
+
+namespace grt {
+
+namespace {
+constexpr int kHashSlots = 128;
+constexpr int kListCap = 64;
+constexpr uint32_t kChunk = 512;
+constexpr unsigned kFull = 0xffffffffu;
+
+__host__ __device__ inline size_t per_warp_bytes(int C) {
+  return (size_t)16 * C + (size_t)((C + 15) & ~15) + 32 * 8 + kHashSlots * 4 + kListCap * 8 + 16;
+}
+
+struct WarpSmem {
+  uint4* cell;
+  uint8_t* scr;
+  uint64_t* stage;
+  int* htab;
+  int* hlist;
+  int* hslot;
+  int* hcount;
+};
+
+struct Ctx {
+  const uint64_t* L;  // the tile's candidates
+  int n;              // number of candidates
+  int pos;            // position of the staged window
+  int cnt;            // entries in the window
+  int tw, ndim;
+  unsigned long long chunk_base;
+  uint32_t chunk_left;
+  int lane;
+};
+
+__device__ __forceinline__ void put_pair(const SweepOut& o, unsigned long long idx, uint64_t key) {
+  if (idx < o.cap) o.pairs[idx] = key;
+}
+
+__device__ __forceinline__ uint64_t pair_key(int src, int dst, int key_bits) {
+  return ((uint64_t)(uint32_t)src << key_bits) | (uint32_t)dst;
+}
+
+__device__ __forceinline__ uint64_t entry_at(const Ctx& x, const WarpSmem& w, int p) {
+  int q = p - x.pos;
+  return (q >= 0 && q < x.cnt) ? w.stage[q] : __ldg(x.L + p);
+}
+
+// lane-level insert (may run divergently)
+__device__ void hash_insert(const WarpSmem& w, const SweepOut& o, int src, int dst) {
+  if (*(volatile int*)w.hcount >= kListCap) {
+    put_pair(o, atomicAdd(o.cursor, 1ull), pair_key(src, dst, o.key_bits));
+    return;
+  }
+  uint32_t h = ((uint32_t)src * 2654435761u) >> 25;  // 7 bits -> 128 slots
+  for (;;) {
+    int old = atomicCAS(&w.htab[h], -1, src);
+    if (old == -1) {
+      int idx = atomicAdd(w.hcount, 1);
+      if (idx < kListCap) {
+        w.hlist[idx] = src;
+        w.hslot[idx] = (int)h;
+      } else {
+        put_pair(o, atomicAdd(o.cursor, 1ull), pair_key(src, dst, o.key_bits));
+      }
+      return;
+    }
+    if (old == src) return;
+    h = (h + 1) & (kHashSlots - 1);
+  }
+}
+
+// warp-convergent insert: lanes holding the same predecessor elect one
+__device__ __forceinline__ void warp_insert(const WarpSmem& w, const SweepOut& o, int src, int dst) {
+  unsigned peers = __match_any_sync(kFull, src);
+  if (src >= 0 && (peers & lanemask_lt()) == 0) hash_insert(w, o, src, dst);
+}
+
+// writes the task's distinct predecessors found in this tile (convergent)
+__device__ void flush(Ctx& x, const WarpSmem& w, const SweepOut& o, int dst) {
+  __syncwarp();
+  const int cnt = *(volatile int*)w.hcount;
+  const int m = cnt < kListCap ? cnt : kListCap;
+  if (m > 0) {
+    if (x.chunk_left < (uint32_t)m) {
+      for (uint32_t i = x.lane; i < x.chunk_left; i += 32) put_pair(o, x.chunk_base + i, kEmpty64);
+      unsigned long long nb = 0;
+      if (x.lane == 0) nb = atomicAdd(o.cursor, (unsigned long long)kChunk);
+      x.chunk_base = __shfl_sync(kFull, nb, 0);
+      x.chunk_left = kChunk;
+    }
+    for (int i = x.lane; i < m; i += 32) {
+      put_pair(o, x.chunk_base + i, pair_key(w.hlist[i], dst, o.key_bits));
+      if (cnt <= kListCap) w.htab[w.hslot[i]] = -1;
+    }
+    x.chunk_base += m;
+    x.chunk_left -= m;
+  }
+  if (cnt > kListCap)
+    for (int i = x.lane; i < kHashSlots; i += 32) w.htab[i] = -1;
+  __syncwarp();
+  if (x.lane == 0) *w.hcount = 0;
+  __syncwarp();
+}
+
+// Applies the access of the task whose first candidate sits at `gpos` to every
+// cell of box [x0,x1]x[y0,y1] with privilege `p` (use_scr: per-cell privilege
+// from the scratch bytes, consumed so a cell is applied once).
+__device__ void sweep_box(Ctx& x, const WarpSmem& w, const SweepOut& o, int x0, int x1, int y0,
+                          int y1, int gpos, int p, bool use_scr, int dst) {
+  const int bw = x1 - x0 + 1, bh = y1 - y0 + 1;
+  const int total = bw * bh;
+  int qx = x.lane % bw, qy = x.lane / bw;
+  const int dx = 32 % bw, dy = 32 / bw;
+  const int iters = (total + 31) >> 5;
+  for (int it = 0; it < iters; ++it) {
+    bool act = it * 32 + x.lane < total;
+    const int cx = x0 + qx, cy = y0 + qy;
+    int c = 0, pc = p;
+    if (act) {
+      c = cy * x.tw + cx;
+      if (use_scr) {
+        uint32_t sv = w.scr[c];
+        if (sv == 0xFFu) {
+          act = false;
+        } else {
+          pc = (int)sv;
+          w.scr[c] = 0xFFu;
+        }
+      }
+    }
+    int m1 = -1, m2 = -1;
+    uint32_t rs = 0, rl = 0, rc = 0;
+    if (act) {
+      uint4 s = w.cell[c];
+      const uint32_t ck = s.x >> 30;
+      if (ck == (uint32_t)pc && pc != kKindWrite) {
+        // join the current run: predecessors are the previous run
+        rs = s.z & kPosMask;
+        rl = s.w;
+        rc = s.z >> 30;
+        uint32_t cc = (s.y >> 30) + 1u;
+        if (cc > 3u) cc = 3u;
+        s.y = (uint32_t)gpos | (cc << 30);
+      } else {
+        // start a new run: predecessors are the current run
+        if (ck != (uint32_t)kKindNone) {
+          rs = s.x & kPosMask;
+          rl = s.y & kPosMask;
+          rc = s.y >> 30;
+        }
+        s.z = (s.x & kPosMask) | (rc << 30);
+        s.w = s.y & kPosMask;
+        s.x = (uint32_t)gpos | ((uint32_t)pc << 30);
+        s.y = (uint32_t)gpos | (1u << 30);
+      }
+      w.cell[c] = s;
+      if (rc >= 1u) m1 = (int)(uint32_t)entry_at(x, w, (int)rs);
+      if (rc >= 2u) m2 = (int)(uint32_t)entry_at(x, w, (int)rl);
+    }
+    warp_insert(w, o, m1, dst);
+    warp_insert(w, o, m2, dst);
+    if (act && rc == 3u) {
+      // three or more members: the candidates strictly between the first and
+      // the last member that cover this cell are the others
+      for (uint32_t q = rs + 1; q < rl; ++q) {
+        Box b = unpack_entry(entry_at(x, w, (int)q), x.ndim);
+        if (b.x0 <= cx && cx <= b.x1 && b.y0 <= cy && cy <= b.y1) hash_insert(w, o, b.task, dst);
+      }
+    }
+    qx += dx;
+    qy += dy;
+    if (qx >= bw) {
+      qx -= bw;
+      qy += 1;
+    }
+  }
+}
+
+// the cells of a box, lane-strided; marks the combined privilege in scratch
+__device__ void mark_box(const Ctx& x, const WarpSmem& w, const Box& b) {
+  const int bw = b.x1 - b.x0 + 1, total = bw * (b.y1 - b.y0 + 1);
+  for (int i = x.lane; i < total; i += 32) {
+    int c = (b.y0 + i / bw) * x.tw + b.x0 + i % bw;
+    w.scr[c] = (uint8_t)combine_priv(w.scr[c], (uint32_t)b.priv);
+  }
+}
+
+// one task's candidates at positions [a, b) of the tile list
+__device__ void process_group(Ctx& x, const WarpSmem& w, const SweepOut& o, int a, int b) {
+  const uint64_t first = entry_at(x, w, a);
+  const int dst = (int)(uint32_t)first;
+  const int g = b - a;
+  if (g == 1) {
+    Box bx = unpack_entry(first, x.ndim);
+    sweep_box(x, w, o, bx.x0, bx.x1, bx.y0, bx.y1, a, bx.priv, false, dst);
+  } else {
+    // disjoint rectangles need no privilege combination
+    bool overlap = g > 32;
+    if (!overlap) {
+      bool mine = false;
+      if (x.lane < g) {
+        Box bi = unpack_entry(entry_at(x, w, a + x.lane), x.ndim);
+        for (int j = x.lane + 1; j < g; ++j) {
+          Box bj = unpack_entry(entry_at(x, w, a + j), x.ndim);
+          if (bi.x0 <= bj.x1 && bj.x0 <= bi.x1 && bi.y0 <= bj.y1 && bj.y0 <= bi.y1) mine = true;
+        }
+      }
+      overlap = __any_sync(kFull, mine);
+    }
+    if (!overlap) {
+      for (int e = a; e < b; ++e) {
+        Box bx = unpack_entry(entry_at(x, w, e), x.ndim);
+        sweep_box(x, w, o, bx.x0, bx.x1, bx.y0, bx.y1, a, bx.priv, false, dst);
+      }
+    } else {
+      for (int e = a; e < b; ++e) {
+        mark_box(x, w, unpack_entry(entry_at(x, w, e), x.ndim));
+        __syncwarp();
+      }
+      for (int e = a; e < b; ++e) {
+        Box bx = unpack_entry(entry_at(x, w, e), x.ndim);
+        sweep_box(x, w, o, bx.x0, bx.x1, bx.y0, bx.y1, a, 0, true, dst);
+        __syncwarp();
+      }
+    }
+  }
+  flush(x, w, o, dst);
+}
+
+__global__ void __launch_bounds__(256) k_sweep(const uint64_t* __restrict__ payload,
+                                               const uint32_t* __restrict__ seg_begin,
+                                               const uint32_t* __restrict__ seg_end, AnalysisDims d,
+                                               SweepOut o) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int C = d.tw * d.th;
+  unsigned char* base = smem + (size_t)warp * per_warp_bytes(C);
+  WarpSmem w;
+  w.cell = reinterpret_cast<uint4*>(base);
+  w.scr = base + 16 * C;
+  w.stage = reinterpret_cast<uint64_t*>(base + 16 * C + ((C + 15) & ~15));
+  w.htab = reinterpret_cast<int*>(w.stage + 32);
+  w.hlist = w.htab + kHashSlots;
+  w.hslot = w.hlist + kListCap;
+  w.hcount = w.hslot + kListCap;
+  for (int i = lane; i < kHashSlots; i += 32) w.htab[i] = -1;
+  if (lane == 0) *w.hcount = 0;
+  __syncwarp();
+
+  Ctx x;
+  x.tw = d.tw;
+  x.ndim = d.ndim;
+  x.chunk_base = 0;
+  x.chunk_left = 0;
+  x.lane = lane;
+  const int ntiles = d.ntx * d.nty;
+  for (;;) {
+    int t = 0;
+    if (lane == 0) t = (int)atomicAdd(o.tile_counter, 1u);
+    t = __shfl_sync(kFull, t, 0);
+    if (t >= ntiles) break;
+    const uint32_t sb = seg_begin[t], se = seg_end[t];
+    if (sb >= se) continue;
+    for (int c = lane; c < C; c += 32) {
+      w.cell[c] = make_uint4((uint32_t)kKindNone << 30, 0u, 0u, 0u);
+      w.scr[c] = 0xFFu;
+    }
+    __syncwarp();
+    x.L = payload + sb;
+    x.n = (int)(se - sb);
+    int pos = 0;
+    while (pos < x.n) {
+      const int cnt = x.n - pos < 32 ? x.n - pos : 32;
+      const uint64_t my = lane < cnt ? x.L[pos + lane] : kEmpty64;
+      w.stage[lane] = my;
+      const uint64_t nxt = (pos + 32 < x.n) ? x.L[pos + 32] : kEmpty64;
+      x.pos = pos;
+      x.cnt = cnt;
+      __syncwarp();
+      const int mytask = (int)(uint32_t)my;
+      const int prevtask = __shfl_up_sync(kFull, mytask, 1);
+      const bool start = lane < cnt && (lane == 0 || mytask != prevtask);
+      const unsigned starts = __ballot_sync(kFull, start);
+      const int lasttask = __shfl_sync(kFull, mytask, cnt - 1);
+      const bool last_complete = (pos + cnt == x.n) || ((int)(uint32_t)nxt != lasttask);
+      const int last_start = 31 - __clz((int)starts);
+      const int end = last_complete ? cnt : last_start;
+      if (end == 0) {
+        // one task with more than 32 candidates in this tile: find its end
+        int gend = pos + 32;
+        for (;;) {
+          int idx = gend + lane;
+          int tk = idx < x.n ? (int)(uint32_t)x.L[idx] : -2;
+          unsigned diff = __ballot_sync(kFull, tk != lasttask);
+          if (diff) {
+            gend += __ffs((int)diff) - 1;
+            break;
+          }
+          gend += 32;
+        }
+        process_group(x, w, o, pos, gend);
+        pos = gend;
+        __syncwarp();
+        continue;
+      }
+      unsigned gs = starts & (end == 32 ? kFull : ((1u << end) - 1u));
+      while (gs) {
+        const int a = __ffs((int)gs) - 1;
+        gs &= gs - 1;
+        const int b = gs ? __ffs((int)gs) - 1 : end;
+        process_group(x, w, o, pos + a, pos + b);
+      }
+      pos += end;
+      __syncwarp();
+    }
+  }
+  for (uint32_t i = lane; i < x.chunk_left; i += 32) put_pair(o, x.chunk_base + i, kEmpty64);
+}
+}  // namespace
+
+int sweep_warps_per_block(int tile_cells) {
+  int w = (int)((96 * 1024) / per_warp_bytes(tile_cells));
+  return w < 1 ? 1 : (w > 8 ? 8 : w);
+}
+
+size_t sweep_smem_bytes(int tile_cells, int warps) { return per_warp_bytes(tile_cells) * warps; }
+
+void launch_sweep(const uint64_t* payload, const uint32_t* seg_begin, const uint32_t* seg_end,
+                  AnalysisDims d, SweepOut o, int blocks, cudaStream_t s) {
+  const int C = d.tw * d.th;
+  const int warps = sweep_warps_per_block(C);
+  const size_t bytes = sweep_smem_bytes(C, warps);
+  cudaFuncSetAttribute(k_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  count_launch();
+  k_sweep<<<blocks, warps * 32, bytes, s>>>(payload, seg_begin, seg_end, d, o);
+}
+
+}  // namespace grt

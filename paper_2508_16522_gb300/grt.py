@@ -1,0 +1,333 @@
+"""Thin ctypes binding of libgrt (include/grt.h).
+
+Argument marshalling only: every step of analysis and execution runs in the
+library's CUDA kernels. There is no fallback: if libgrt.so has not been built
+(``paper_2508_16522_gb300.build.build()``) every call raises.
+
+Functions keep the C names (rt_graph_create, rt_launch_batch, rt_analyze,
+rt_execute, rt_replay, rt_sync, ...) and raise GrtError on a non-OK status.
+``Graph`` and ``Batch`` are small conveniences that hold the handle and pass
+numpy arrays (host) or torch tensors (device, or pinned host) by pointer.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libgrt.so")
+
+RT_OK, RT_ERR_INVALID, RT_ERR_OOM, RT_ERR_CUDA, RT_ERR_TIMEOUT, RT_ERR_STATE, RT_ERR_BUDGET = range(7)
+STATUS_NAMES = ["RT_OK", "RT_ERR_INVALID", "RT_ERR_OOM", "RT_ERR_CUDA", "RT_ERR_TIMEOUT", "RT_ERR_STATE",
+                "RT_ERR_BUDGET"]
+RT_READ, RT_WRITE, RT_REDUCE_SUM = 0, 1, 2
+RT_BODY_EMPTY, RT_BODY_SPIN, RT_BODY_COUNTER, RT_BODY_CHECK = 0, 1, 2, 3
+RT_LAUNCH_HOST, RT_LAUNCH_DEVICE, RT_LAUNCH_DEFER_CHECK = 0, 1, 2
+RT_GRAPH_TICKETS, RT_GRAPH_PROFILE = 1, 2
+
+# every symbol include/grt.h declares (checked by the CPU tests)
+EXPORTS = ["rt_graph_create", "rt_graph_destroy", "rt_graph_clear", "rt_launch_batch", "rt_analyze",
+           "rt_get_csr", "rt_copy_csr", "rt_graph_exec_config", "rt_execute", "rt_replay", "rt_sync", "rt_graph_stats",
+           "rt_get_tickets", "rt_copy_tickets", "rt_debug_hold_task", "rt_batch_create",
+           "rt_batch_execute", "rt_batch_sync", "rt_batch_destroy", "rt_last_error", "rt_device_info",
+           "rt_kernel_launches"]
+
+
+class GrtError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        self.status = status
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 7 else status}: {msg}")
+
+
+class rt_graph_desc(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int32), ("dom_lo", ctypes.c_int64 * 2), ("dom_hi", ctypes.c_int64 * 2),
+                ("body", ctypes.c_int32), ("spin_iters", ctypes.c_int32), ("state", ctypes.c_void_p),
+                ("state_elems", ctypes.c_int64), ("out", ctypes.c_void_p), ("out_elems", ctypes.c_int64),
+                ("stream", ctypes.c_void_p), ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
+                ("timeout_ns", ctypes.c_int64), ("flags", ctypes.c_int32)]
+
+
+class rt_graph_stats_t(ctypes.Structure):
+    _fields_ = [("n_tasks", ctypes.c_int64), ("n_rects", ctypes.c_int64), ("n_preds", ctypes.c_int64),
+                ("n_entries", ctypes.c_int64), ("n_pairs", ctypes.c_int64), ("n_edges", ctypes.c_int64),
+                ("n_roots", ctypes.c_int64), ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
+                ("ms_analyze", ctypes.c_float), ("ms_bin", ctypes.c_float), ("ms_sort_entries", ctypes.c_float),
+                ("ms_sweep", ctypes.c_float), ("ms_sort_pairs", ctypes.c_float), ("ms_csr", ctypes.c_float),
+                ("ms_execute", ctypes.c_float), ("ms_exec_kernel", ctypes.c_float),
+                ("exec_blocks", ctypes.c_int32), ("exec_threads", ctypes.c_int32),
+                ("ms_sweep_kernel", ctypes.c_float)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads libgrt.so; raises if it has not been built (no fallback path)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libgrt.so not built at {path}: run paper_2508_16522_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    sig = {
+        "rt_graph_create": [ctypes.POINTER(rt_graph_desc), ctypes.POINTER(P)],
+        "rt_graph_destroy": [P],
+        "rt_graph_clear": [P],
+        "rt_launch_batch": [P, i32, P, P, P, P, P, P, P, i32],
+        "rt_analyze": [P],
+        "rt_get_csr": [P, P, P, P, P, P],
+        "rt_copy_csr": [P, P, P, P],
+        "rt_execute": [P],
+        "rt_replay": [P, i32],
+        "rt_sync": [P],
+        "rt_graph_stats": [P, ctypes.POINTER(rt_graph_stats_t)],
+        "rt_get_tickets": [P, P],
+        "rt_copy_tickets": [P, P],
+        "rt_debug_hold_task": [P, i32, i32],
+        "rt_batch_create": [P, i32, P, ctypes.POINTER(P)],
+        "rt_batch_execute": [P, i32, i32, i32, i32, i32],
+        "rt_graph_exec_config": [P, i32, i32, i32, i32],
+        "rt_batch_sync": [P, ctypes.POINTER(ctypes.c_float)],
+        "rt_batch_destroy": [P],
+        "rt_device_info": [ctypes.POINTER(i32), ctypes.POINTER(i32)],
+        "rt_kernel_launches": [ctypes.POINTER(i64)],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.rt_last_error.argtypes = []
+    lib.rt_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(st: int):
+    if st != RT_OK:
+        raise GrtError(st, load().rt_last_error().decode())
+
+
+# ---------------------------------------------------------------------------
+# C-named wrappers
+# ---------------------------------------------------------------------------
+def rt_graph_create(desc: rt_graph_desc) -> int:
+    h = ctypes.c_void_p()
+    _check(load().rt_graph_create(ctypes.byref(desc), ctypes.byref(h)))
+    return h.value
+
+
+def rt_graph_destroy(g):
+    _check(load().rt_graph_destroy(g))
+
+
+def rt_graph_clear(g):
+    _check(load().rt_graph_clear(g))
+
+
+def rt_launch_batch(g, n, req_off, lo, hi, priv, pred_off=None, pred=None, body_arg=None, flags=0):
+    _check(load().rt_launch_batch(g, n, req_off, lo, hi, priv, pred_off, pred, body_arg, flags))
+
+
+def rt_analyze(g):
+    _check(load().rt_analyze(g))
+
+
+def rt_execute(g):
+    _check(load().rt_execute(g))
+
+
+def rt_replay(g, times: int):
+    _check(load().rt_replay(g, times))
+
+
+def rt_sync(g):
+    _check(load().rt_sync(g))
+
+
+def rt_graph_stats(g) -> dict:
+    st = rt_graph_stats_t()
+    _check(load().rt_graph_stats(g, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def rt_debug_hold_task(g, task: int, extra: int = 1):
+    _check(load().rt_debug_hold_task(g, task, extra))
+
+
+def rt_device_info():
+    a, b = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().rt_device_info(ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def rt_kernel_launches() -> int:
+    c = ctypes.c_int64()
+    _check(load().rt_kernel_launches(ctypes.byref(c)))
+    return c.value
+
+
+def rt_last_error() -> str:
+    return load().rt_last_error().decode()
+
+
+# ---------------------------------------------------------------------------
+# conveniences
+# ---------------------------------------------------------------------------
+def _ptr(a):
+    """(pointer, is_device) of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None, False
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data, False
+    # torch tensor
+    assert a.is_contiguous()
+    return a.data_ptr(), bool(a.is_cuda)
+
+
+class Graph:
+    """Holds one rt_graph and the torch buffers its body writes."""
+
+    def __init__(self, ndim: int, dom_lo, dom_hi, body: int = RT_BODY_EMPTY, spin_iters: int = 256,
+                 state=None, out=None, stream=None, tile=(0, 0), timeout_ns: int = 0, flags: int = 0):
+        d = rt_graph_desc()
+        d.ndim = ndim
+        for k in range(ndim):
+            d.dom_lo[k] = int(dom_lo[k])
+            d.dom_hi[k] = int(dom_hi[k])
+        d.body = body
+        d.spin_iters = spin_iters
+        self.state, self.out = state, out
+        if state is not None:
+            d.state = state.data_ptr()
+            d.state_elems = state.numel()
+        if out is not None:
+            d.out = out.data_ptr()
+            d.out_elems = out.numel()
+        self.stream = stream
+        d.stream = None if stream is None else stream.cuda_stream
+        d.tile_w, d.tile_h = int(tile[0]), int(tile[1])
+        d.timeout_ns = timeout_ns
+        d.flags = flags
+        self.desc = d
+        self.h = rt_graph_create(d)
+        self._keep = []
+
+    def close(self):
+        if self.h:
+            rt_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def clear(self):
+        rt_graph_clear(self.h)
+
+    def launch(self, req_off, lo, hi, priv, pred_off=None, pred=None, body_arg=None, defer_check=False):
+        """Appends launches; numpy arrays are host pointers, CUDA tensors device pointers."""
+        n = int(len(req_off) - 1)
+        ptrs = [_ptr(a) for a in (req_off, lo, hi, priv, pred_off, pred, body_arg)]
+        dev = any(p[1] for p in ptrs)
+        if dev and not all(p[1] or p[0] is None for p in ptrs):
+            raise ValueError("mixing host and device arrays in one batch")
+        flags = RT_LAUNCH_DEVICE if dev else (RT_LAUNCH_DEFER_CHECK if defer_check else RT_LAUNCH_HOST)
+        self._keep = [req_off, lo, hi, priv, pred_off, pred, body_arg]  # alive until analyze
+        rt_launch_batch(self.h, n, *[p[0] for p in ptrs], flags)
+
+    def launch_trace(self, tr, device: bool = False, defer_check: bool = False):
+        arrs = [tr.req_off, tr.lo, tr.hi, tr.priv, tr.pred_off, tr.pred, tr.body_arg]
+        if device:
+            import torch
+            arrs = [None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrs]
+        self.launch(*arrs, defer_check=defer_check)
+
+    def analyze(self):
+        rt_analyze(self.h)
+        self._keep = []
+
+    def execute(self):
+        rt_execute(self.h)
+
+    def replay(self, times: int):
+        rt_replay(self.h, times)
+
+    def sync(self):
+        rt_sync(self.h)
+
+    def stats(self) -> dict:
+        return rt_graph_stats(self.h)
+
+    def exec_config(self, blocks: int = 0, warps: int = 0, claim: int = 0, keep: int = 0):
+        _check(load().rt_graph_exec_config(self.h, blocks, warps, claim, keep))
+
+    def hold_task(self, task: int, extra: int = 1):
+        rt_debug_hold_task(self.h, task, extra)
+
+    def csr(self):
+        """(row_ptr, col, indeg) copied to host numpy arrays."""
+        st = self.stats()
+        n, e = st["n_tasks"], st["n_edges"]
+        rp = np.empty(n + 1, np.int32)
+        col = np.empty(max(e, 1), np.int32)
+        ind = np.empty(max(n, 1), np.int32)
+        _check(load().rt_copy_csr(self.h, rp.ctypes.data, col.ctypes.data, ind.ctypes.data))
+        return rp, col[:e], ind[:n]
+
+    def tickets(self):
+        n = self.stats()["n_tasks"]
+        t = np.empty(2 * max(n, 1), np.int32)
+        _check(load().rt_copy_tickets(self.h, t.ctypes.data))
+        return t[:2 * n].reshape(n, 2)
+
+
+class Batch:
+    """A disjoint union of analyzed graphs run by one persistent launch."""
+
+    def __init__(self, graphs, stream=None):
+        self.graphs = list(graphs)  # the batch refers to their buffers
+        arr = (ctypes.c_void_p * len(self.graphs))(*[g.h for g in self.graphs])
+        h = ctypes.c_void_p()
+        s = None if stream is None else stream.cuda_stream
+        _check(load().rt_batch_create(arr, len(self.graphs), s, ctypes.byref(h)))
+        self.h = h.value
+
+    def execute(self, replays: int = 1, blocks: int = 0, warps: int = 0, claim: int = 0, keep: int = 0):
+        _check(load().rt_batch_execute(self.h, replays, blocks, warps, claim, keep))
+
+    def sync(self) -> float:
+        ms = ctypes.c_float()
+        _check(load().rt_batch_sync(self.h, ctypes.byref(ms)))
+        return ms.value
+
+    def close(self):
+        if self.h:
+            load().rt_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def body_name(b: int) -> str:
+    return ["EMPTY", "SPIN", "COUNTER", "CHECK"][b]
+
+
+def describe(st: dict) -> str:
+    return ", ".join(f"{k}={v:.3f}" if isinstance(v, float) else f"{k}={v}" for k, v in st.items())
+
+
+__all__ = [n for n in dir() if n.startswith("rt_") or n.startswith("RT_")] + [
+    "Graph", "Batch", "GrtError", "load", "EXPORTS"]
+

@@ -1,0 +1,241 @@
+"""GPU parity: libgrt (through the C ABI) against the CPU oracle.
+
+Edge sets are compared as canonical CSR arrays (bit-exact: all of this is
+integer work) and bodies by final state and per-task outputs, which must equal
+sequential program-order execution.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2508_16522_gb300 import grt
+from paper_2508_16522_gb300 import tracegen as tg
+
+from gpu_helpers import assert_csr_equal, gpu_graph, oracle_csr, random_traces_small
+
+pytestmark = pytest.mark.gpu
+
+
+def test_fig6c_fixture():
+    tr = tg.fig6_fixture()
+    g = gpu_graph(tr, tile=(1, 1))
+    g.analyze()
+    rp, col, ind = assert_csr_equal(g, tr)
+    assert ind.tolist() == [0, 1, 1, 2]
+    g.execute()
+    g.sync()
+    g.close()
+
+
+@pytest.mark.parametrize("tile", [(1024, 1), (256, 1), (100, 1), (17, 1)])
+def test_stencil_1d_counter(tile):
+    tr = tg.stencil_1d()
+    g = gpu_graph(tr, body=grt.RT_BODY_COUNTER, tile=tile, state_elems=16)
+    g.analyze()
+    assert_csr_equal(g, tr)
+    assert g.stats()["n_edges"] == 2985
+    g.execute()
+    g.sync()
+    assert g.state.cpu().tolist() == [100] * 16
+    g.replay(3)
+    g.sync()
+    assert g.state.cpu().tolist() == [400] * 16
+    g.close()
+
+
+@pytest.mark.parametrize("pattern", tg.PATTERNS)
+@pytest.mark.parametrize("encode", ["region", "explicit"])
+@pytest.mark.parametrize("tile", [(16, 16), (5, 7), (64, 4), (1, 1)])
+def test_taskbench_small(pattern, encode, tile):
+    tr = tg.taskbench(64, 40, pattern, seed=11, encode=encode)
+    g = gpu_graph(tr, tile=tile)
+    g.analyze()
+    assert_csr_equal(g, tr)
+    g.close()
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 4), (3, 5)])
+def test_random_traces_csr_and_check_body(tile):
+    for tr in random_traces_small(12):
+        t = tile if tr.ndim == 2 else (tile[0] * tile[1], 1)
+        g = gpu_graph(tr, body=grt.RT_BODY_CHECK, tile=t)
+        g.analyze()
+        assert_csr_equal(g, tr)
+        g.execute()
+        g.sync()
+        st, out = oracle.run_bodies(tr, oracle.oracle.BODY_CHECK)
+        assert np.array_equal(g.state.cpu().numpy(), st[:tr.n_cells]), tr.name
+        assert np.array_equal(g.out.cpu().numpy(), out[:tr.n]), tr.name
+        g.close()
+
+
+def test_tiny_exhaustive_privilege_mixes():
+    from test_oracle_pins import tiny_traces
+    for tr in tiny_traces():
+        for tile in ((1, 1), (4, 4)) if tr.ndim == 2 else ((1, 1), (5, 1)):
+            g = gpu_graph(tr, tile=tile)
+            g.analyze()
+            assert_csr_equal(g, tr)
+            g.close()
+
+
+def test_long_runs_and_many_predecessors():
+    """A cell read by 200 tasks then written (>= 3-member runs, >64 preds of one
+    task: hash-list overflow), and one task with 70 rectangles in one tile
+    (group longer than the 32-entry stage)."""
+    n_read = 200
+    lo = [[5, 5]] * n_read + [[0, 0]] + [[k % 8, k // 8] for k in range(70)] + [[5, 5]]
+    hi = [[5, 5]] * n_read + [[15, 15]] + [[k % 8, k // 8] for k in range(70)] + [[6, 6]]
+    priv = [0] * n_read + [1] + [k % 3 for k in range(70)] + [2]
+    counts = [1] * n_read + [1, 70, 1]
+    tr = tg._finish(2, [0, 0], [15, 15], counts, np.array(lo).reshape(-1), np.array(hi).reshape(-1),
+                    np.array(priv, np.uint8), name="longruns")
+    for tile in ((16, 16), (4, 4), (2, 3)):
+        g = gpu_graph(tr, body=grt.RT_BODY_CHECK, tile=tile)
+        g.analyze()
+        assert_csr_equal(g, tr)
+        g.execute()
+        g.sync()
+        st, out = oracle.run_bodies(tr, oracle.oracle.BODY_CHECK)
+        assert np.array_equal(g.state.cpu().numpy(), st) and np.array_equal(g.out.cpu().numpy(), out)
+        g.close()
+
+
+def test_edge_cases():
+    import torch
+    # empty graph
+    g = grt.Graph(2, [0, 0], [9, 9])
+    g.analyze()
+    g.execute()
+    g.sync()
+    rp, col, ind = g.csr()
+    assert rp.tolist() == [0] and len(col) == 0
+    g.close()
+    # tasks without rectangles (all roots), one rect covering the domain
+    tr = tg._finish(2, [-3, 7], [20, 40], [0, 0, 1, 0, 1],
+                    np.array([-3, 7, -3, 7]), np.array([20, 40, 0, 10]), np.array([1, 0], np.uint8))
+    for tile in ((16, 16), (128, 8)):
+        g = gpu_graph(tr, body=grt.RT_BODY_CHECK, tile=tile)
+        g.analyze()
+        assert_csr_equal(g, tr)
+        g.execute()
+        g.sync()
+        g.close()
+    # several appended batches, mixing explicit preds and regions, host and device
+    parts = [tg.taskbench(32, 6, "stencil", encode="region"), tg.taskbench(32, 6, "random", encode="explicit"),
+             tg.taskbench(32, 6, "butterfly", encode="region")]
+    whole = tg.concat(parts)
+    g = grt.Graph(2, whole.dom_lo, whole.dom_hi, tile=(8, 8))
+    base = 0
+    for k, p in enumerate(parts):
+        if p.pred is not None:
+            p = tg._finish(2, p.dom_lo, p.dom_hi, np.diff(p.req_off), p.lo.reshape(-1), p.hi.reshape(-1), p.priv,
+                           pred_counts=np.diff(p.pred_off), pred=p.pred + base)
+        g.launch_trace(p, device=(k == 1))
+        base += p.n
+    g.analyze()
+    assert_csr_equal(g, whole)
+    g.close()
+    del torch
+
+
+def test_device_validation_reports_invalid():
+    import torch
+    tr = tg.taskbench(16, 4, "stencil")
+    bad_hi = tr.hi.copy()
+    bad_hi[3, 0] = 99  # outside the 16-wide domain
+    g = grt.Graph(2, tr.dom_lo, tr.dom_hi)
+    g.launch(torch.from_numpy(tr.req_off).cuda(), torch.from_numpy(tr.lo).cuda(), torch.from_numpy(bad_hi).cuda(),
+             torch.from_numpy(tr.priv).cuda())
+    with pytest.raises(grt.GrtError) as e:
+        g.analyze()
+    assert e.value.status == grt.RT_ERR_INVALID and "outside" in str(e.value)
+    g.close()
+    # deferred host validation of a backward-pointing pred
+    g = grt.Graph(2, [0, 0], [1, 1])
+    g.launch(np.zeros(3, np.int32), np.zeros((0, 2), np.int64), np.zeros((0, 2), np.int64), np.zeros(0, np.uint8),
+             np.array([0, 0, 1], np.int32), np.array([1], np.int32), defer_check=True)
+    with pytest.raises(grt.GrtError) as e:
+        g.analyze()
+    assert "predecessor" in str(e.value)
+    g.close()
+
+
+def test_spin_and_empty_bodies():
+    tr = tg.taskbench(128, 30, "butterfly")
+    g = gpu_graph(tr, body=grt.RT_BODY_SPIN, spin_iters=256)
+    g.analyze()
+    g.execute()
+    g.sync()
+    want = np.array([oracle.spin(j, 256) for j in range(tr.n)], np.uint32).view(np.int32)
+    assert np.array_equal(g.out.cpu().numpy(), want)
+    g.close()
+
+
+def test_tickets_respect_every_edge():
+    for tr in [tg.taskbench(256, 60, "random"), tg.random_rects(grid=(64, 64), n=3000, side=(2, 24), seed=5)]:
+        g = gpu_graph(tr, flags=grt.RT_GRAPH_TICKETS)
+        g.analyze()
+        g.execute()
+        g.sync()
+        t = g.tickets()
+        rp, col, _ = g.csr()
+        src = np.repeat(np.arange(tr.n), np.diff(rp))
+        assert (t[:, 0] < t[:, 1]).all()
+        assert (t[src, 1] < t[col, 0]).all(), "a task started before one of its predecessors finished"
+        assert sorted(np.concatenate([t[:, 0], t[:, 1]]).tolist()) == list(range(2 * tr.n))
+        g.close()
+
+
+def test_replay_equals_sequential_repeats():
+    tr = tg.random_rects(grid=(40, 30), n=500, rects=(1, 3), side=(1, 12), seed=9)
+    g = gpu_graph(tr, body=grt.RT_BODY_CHECK, tile=(8, 8))
+    g.analyze()
+    g.replay(3)
+    g.sync()
+    st = None
+    for _ in range(3):
+        st, out = oracle.run_bodies(tr, oracle.oracle.BODY_CHECK, state=st)
+    assert np.array_equal(g.state.cpu().numpy(), st) and np.array_equal(g.out.cpu().numpy(), out)
+    # and again through the cached CUDA graph
+    g.replay(3)
+    g.sync()
+    for _ in range(3):
+        st, out = oracle.run_bodies(tr, oracle.oracle.BODY_CHECK, state=st)
+    assert np.array_equal(g.state.cpu().numpy(), st)
+    g.close()
+
+
+def test_bounded_wait_timeout_and_recovery():
+    tr = tg.taskbench(64, 20, "stencil")
+    g = gpu_graph(tr, body=grt.RT_BODY_SPIN, spin_iters=4, timeout_ns=300_000_000)
+    g.analyze()
+    g.hold_task(64 * 10 + 5)  # never becomes ready
+    g.execute()
+    with pytest.raises(grt.GrtError) as e:
+        g.sync()
+    assert e.value.status == grt.RT_ERR_TIMEOUT
+    # the context is still usable and the next run re-initialises the counters
+    g.execute()
+    g.sync()
+    want = np.array([oracle.spin(j, 4) for j in range(tr.n)], np.uint32).view(np.int32)
+    assert np.array_equal(g.out.cpu().numpy(), want)
+    g.close()
+
+
+@pytest.mark.parametrize("pattern", tg.PATTERNS)
+def test_taskbench_full_size(pattern):
+    """width 1024 x 1000 steps, region encoding, the benchmark's launch
+    configuration: CSR bit-exact against the oracle."""
+    tr = tg.taskbench(1024, 1000, pattern)
+    g = gpu_graph(tr, flags=grt.RT_GRAPH_TICKETS)
+    g.analyze()
+    rp, col, ind = assert_csr_equal(g, tr)
+    want = {"stencil": 3_066_930, "butterfly": 2_045_952, "random": 5_114_880}[pattern]
+    assert len(col) == want
+    g.execute()
+    g.sync()
+    t = g.tickets()
+    src = np.repeat(np.arange(tr.n), np.diff(rp))
+    assert (t[src, 1] < t[col, 0]).all()
+    g.close()
