@@ -1087,3 +1087,4 @@ extern "C" rt_status rt_kernel_launches(int64_t* count) {
   *count = grt::g_kernel_launches.load();
   return RT_OK;
 }
+

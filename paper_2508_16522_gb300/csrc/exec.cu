@@ -24,6 +24,7 @@ namespace grt {
 
 namespace {
 constexpr int kKeepMax = 64;
+constexpr int kEdgeRound = 8;  // 32-edge groups whose decrements are in flight together
 constexpr unsigned kFull = 0xffffffffu;
 
 __global__ void k_reset_counts(int32_t* count, const int32_t* indeg, int64_t n, int32_t hold_task,
@@ -281,7 +282,9 @@ __global__ void __launch_bounds__(256) k_exec(ExecParams p) {
     }
     if (FENCE || TICKETS) fence_acq_rel_gpu();  // release: bodies before the decrements
 
-    // COMPLETED_EDGE for every out-edge of the batch, 32 edges per step
+    // COMPLETED_EDGE for every out-edge of the batch. Up to 8 x 32 edges per
+    // round: all column loads, then all decrements, are issued before any
+    // result is used, so one round costs about one memory round trip.
     int incl = deg;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -290,27 +293,38 @@ __global__ void __launch_bounds__(256) k_exec(ExecParams p) {
     }
     const int excl = incl - deg;
     const int D = __shfl_sync(kFull, incl, 31);
-    for (int e0 = 0; e0 < D; e0 += 32) {
-      const int e = e0 + lane;
-      int owner = 0;
+    for (int e0 = 0; e0 < D; e0 += kEdgeRound * 32) {
+      int succ[kEdgeRound];
+      uint32_t gsel[kEdgeRound];
+      int old[kEdgeRound];
 #pragma unroll
-      for (int step = 16; step >= 1; step >>= 1) {
-        const int cand = owner + step;
-        const int ex = __shfl_sync(kFull, excl, cand);
-        if (ex <= e) owner = cand;
+      for (int k = 0; k < kEdgeRound; ++k) {
+        succ[k] = -1;
+        gsel[k] = 0;
+        if (e0 + k * 32 < D) {  // warp-uniform
+          const int e = e0 + k * 32 + lane;
+          int owner = 0;
+#pragma unroll
+          for (int step = 16; step >= 1; step >>= 1) {
+            const int cand = owner + step;
+            const int ex = __shfl_sync(kFull, excl, cand);
+            if (ex <= e) owner = cand;
+          }
+          const int orb = __shfl_sync(kFull, rbeg, owner);
+          const int oex = __shfl_sync(kFull, excl, owner);
+          gsel[k] = (uint32_t)(__shfl_sync(kFull, item, owner) >> 32);
+          if (e < D) succ[k] = p.col[orb + (e - oex)];
+        }
       }
-      const int orb = __shfl_sync(kFull, rbeg, owner);
-      const int oex = __shfl_sync(kFull, excl, owner);
-      const uint64_t oitem = __shfl_sync(kFull, item, owner);
-      bool ready = false;
-      uint64_t nit = 0;
-      if (e < D) {
-        const int s = p.col[orb + (e - oex)];
-        ready = atomicSub(&p.count[s], 1) == 1;
-        nit = (oitem & 0xffffffff00000000ull) | (uint32_t)s;
-      }
-      const unsigned rm = __ballot_sync(kFull, ready);
-      if (rm) {
+#pragma unroll
+      for (int k = 0; k < kEdgeRound; ++k) old[k] = succ[k] >= 0 ? atomicSub(&p.count[succ[k]], 1) : 0;
+#pragma unroll
+      for (int k = 0; k < kEdgeRound; ++k) {
+        if (e0 + k * 32 >= D) break;  // warp-uniform
+        const bool ready = succ[k] >= 0 && old[k] == 1;
+        const unsigned rm = __ballot_sync(kFull, ready);
+        if (!rm) continue;
+        const uint64_t nit = ((uint64_t)gsel[k] << 32) | (uint32_t)succ[k];
         const int r = __popc(rm);
         const int rank = __popc(rm & lt);
         int room = p.keep - nl;
