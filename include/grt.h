@@ -238,6 +238,33 @@ const char* rt_last_error(void);
  * device (0 on failure); used by the autotuner. */
 rt_status rt_device_info(int32_t* num_sms, int32_t* exec_blocks_per_sm);
 
+/* Runs a graph given as a caller-held CSR without allocating anything. The
+ * paper has no counterpart: this exists for callers that cannot allocate device
+ * memory when they run a graph -- code inside a memory-pool or arena manager
+ * that owns all device memory, or a latency-critical loop where cudaMalloc or
+ * cudaFree (which synchronises the device) is not allowed. The executor's
+ * scratch (countdown counters, ready ring, control words) lives in a fixed
+ * device array inside the library, about 3 MB, which every GPU that loads the
+ * library keeps until the process exits.
+ *  row_ptr int32[n_tasks+1], col int32[n_edges], indeg int32[n_tasks]: device
+ *          pointers, caller-owned, e.g. filled by rt_copy_csr; every column must
+ *          be a later task id (src < dst) and indeg must match the columns
+ *  out     int32[n_tasks] device buffer: the SPIN body's result per task
+ *          (x = task id; spin_iters times x = x*1664525 + 1013904223)
+ *  stream  cudaStream_t (NULL = legacy default stream)
+ * Synchronous: validates the CSR on the device (RT_ERR_INVALID if it is
+ * malformed), runs it once and returns the executor's status. n_tasks may be
+ * at most 262144 (2^18); larger graphs get RT_ERR_INVALID. No cudaMalloc,
+ * cudaFree or allocating library call is made. The first call on a device looks
+ * up the array's device address once; make that first call before capturing
+ * any stream. All calls share the one array and it keeps the previous call's
+ * contents (each call re-initialises what it needs), so calls whose GPU work
+ * overlaps -- from several streams or host threads -- race and corrupt each
+ * other: the caller must serialise them. */
+rt_status rt_execute_csr_static(const int32_t* row_ptr, const int32_t* col, const int32_t* indeg,
+                                int32_t n_tasks, int64_t n_edges, int32_t spin_iters, int32_t* out,
+                                void* stream);
+
 /* Total number of kernels this library has launched in the process (for
  * benchmarks that report how much GPU work a timed region issued). */
 rt_status rt_kernel_launches(int64_t* count);

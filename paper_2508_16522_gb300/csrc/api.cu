@@ -1088,3 +1088,19 @@ extern "C" rt_status rt_kernel_launches(int64_t* count) {
   return RT_OK;
 }
 
+extern "C" rt_status rt_execute_csr_static(const int32_t* row_ptr, const int32_t* col, const int32_t* indeg,
+                                           int32_t n_tasks, int64_t n_edges, int32_t spin_iters, int32_t* out,
+                                           void* stream) {
+  if (n_tasks < 0 || n_edges < 0 || spin_iters < 0) return fail(RT_ERR_INVALID, "negative size");
+  if (n_tasks > grt::static_max_tasks())
+    return fail(RT_ERR_INVALID, "rt_execute_csr_static handles at most %d tasks (got %d); use rt_execute",
+                grt::static_max_tasks(), n_tasks);
+  if (n_edges >= (1ll << 31)) return fail(RT_ERR_INVALID, "too many edges");
+  if (n_tasks == 0) return RT_OK;
+  if (!row_ptr || !indeg || !out || (n_edges > 0 && !col)) return fail(RT_ERR_INVALID, "NULL array");
+  const char* why = "";
+  rt_status st = grt::static_execute(row_ptr, col, indeg, n_tasks, n_edges, spin_iters, out,
+                                     (cudaStream_t)stream, 2000000000ll, &why);
+  if (st != RT_OK) return fail(st, "rt_execute_csr_static: %s", why);
+  return RT_OK;
+}

@@ -225,5 +225,9 @@ void launch_rebase_roots(const uint64_t* src, uint64_t* dst, int32_t n, int32_t 
 void launch_seed(ExecParams p, int64_t ring_clear, cudaStream_t s);
 void launch_exec(ExecParams p, int blocks, int warps, cudaStream_t s);
 int exec_max_blocks_per_sm(int warps);
+int32_t static_max_tasks();
+rt_status static_execute(const int32_t* row_ptr, const int32_t* col, const int32_t* indeg, int32_t n,
+                         int64_t n_edges, int32_t spin_iters, int32_t* out, cudaStream_t s,
+                         int64_t timeout_ns, const char** why);
 
 }  // namespace grt

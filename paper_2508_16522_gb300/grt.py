@@ -31,7 +31,7 @@ EXPORTS = ["rt_graph_create", "rt_graph_destroy", "rt_graph_clear", "rt_launch_b
            "rt_get_csr", "rt_copy_csr", "rt_graph_exec_config", "rt_execute", "rt_replay", "rt_sync", "rt_graph_stats",
            "rt_get_tickets", "rt_copy_tickets", "rt_debug_hold_task", "rt_batch_create",
            "rt_batch_execute", "rt_batch_sync", "rt_batch_destroy", "rt_last_error", "rt_device_info",
-           "rt_kernel_launches"]
+           "rt_kernel_launches", "rt_execute_csr_static"]
 
 
 class GrtError(RuntimeError):
@@ -96,6 +96,7 @@ def load(path: str = LIB_PATH):
         "rt_batch_destroy": [P],
         "rt_device_info": [ctypes.POINTER(i32), ctypes.POINTER(i32)],
         "rt_kernel_launches": [ctypes.POINTER(i64)],
+        "rt_execute_csr_static": [P, P, P, i32, i64, i32, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -169,6 +170,12 @@ def rt_kernel_launches() -> int:
     c = ctypes.c_int64()
     _check(load().rt_kernel_launches(ctypes.byref(c)))
     return c.value
+
+
+def rt_execute_csr_static(row_ptr, col, indeg, n_tasks: int, n_edges: int, spin_iters: int, out, stream=None):
+    """Executes a caller-held CSR (device pointers) with SPIN bodies, allocating
+    nothing; see include/grt.h for the limits and the sharing rule."""
+    _check(load().rt_execute_csr_static(row_ptr, col, indeg, n_tasks, n_edges, spin_iters, out, stream))
 
 
 def rt_last_error() -> str:
