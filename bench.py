@@ -38,14 +38,64 @@ TILE = (16, 16)
 WORKLOAD = "taskbench 1024x1000 (stencil, butterfly, random fan-in 5), region-encoded, EMPTY bodies"
 
 
-def load_traces():
-    return [tg.taskbench(WIDTH, STEPS, p, seed=0) for p in tg.PATTERNS]
+def load_traces(args=None):
+    steps = getattr(args, "graph_steps", STEPS)
+    pats = getattr(args, "patterns", ",".join(tg.PATTERNS)).split(",")
+    return [tg.taskbench(WIDTH, steps, p, seed=0) for p in pats]
 
 
-def config(tasks_per_step):
-    return {"workload": WORKLOAD, "patterns": list(tg.PATTERNS), "width": WIDTH, "steps_per_graph": STEPS,
+def config(tasks_per_step, args=None):
+    steps = getattr(args, "graph_steps", STEPS)
+    pats = getattr(args, "patterns", ",".join(tg.PATTERNS)).split(",")
+    wl = WORKLOAD if (steps == STEPS and len(pats) == 3) else f"REDUCED (profiling): taskbench {WIDTH}x{steps} {pats}"
+    return {"workload": wl, "patterns": pats, "width": WIDTH, "steps_per_graph": steps,
             "tasks_per_step": tasks_per_step, "tile": list(TILE),
             "l2": "flushed between timed steps (512 MB write)", "inputs": "synthetic, seed 0"}
+
+
+BATCH_GRAPHS, BATCH_REPLAYS = 4096, 20
+
+
+def run_batched(grt, torch, flush, steps):
+    """configs[3]: 4096 independent Task Bench graphs (sizes log-uniform
+    64..65536, patterns mixed), captured once (analysis), then 20 replays of
+    every graph in one persistent launch per step."""
+    t0 = time.perf_counter()
+    traces = tg.batch_graphs(BATCH_GRAPHS, seed=0)
+    gen_s = time.perf_counter() - t0
+    stream = torch.cuda.Stream()
+    graphs, ana_ms = [], 0.0
+    for tr in traces:
+        g = grt.Graph(2, tr.dom_lo, tr.dom_hi, tile=TILE, stream=stream, flags=grt.RT_GRAPH_PROFILE)
+        g.launch(*[torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (tr.req_off, tr.lo, tr.hi, tr.priv)])
+        g.analyze()
+        ana_ms += g.stats()["ms_analyze"]
+        graphs.append(g)
+    T = sum(t.n for t in traces)
+    E = sum(g.stats()["n_edges"] for g in graphs)
+    batch = grt.Batch(graphs, stream=stream)
+    batch.execute(replays=BATCH_REPLAYS)
+    batch.sync()
+    ms = []
+    for i in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(i & 255)
+        batch.execute(replays=BATCH_REPLAYS)
+        ms.append(batch.sync())
+    kern = float(np.mean(ms))
+    done = T * BATCH_REPLAYS
+    out = {"workload": f"{BATCH_GRAPHS} Task Bench graphs, sizes log-uniform 64..65536, stencil/butterfly/random "
+                       f"mixed, region-encoded, EMPTY bodies; {BATCH_REPLAYS} replays of every graph in one "
+                       "persistent launch", "graphs": BATCH_GRAPHS, "tasks": T, "edges": E,
+           "replays": BATCH_REPLAYS, "ms_per_launch": kern, "exec_tasks_per_s": done / (kern * 1e-3),
+           "exec_ns_per_task": kern * 1e6 / done, "analysis_ms_total": ana_ms,
+           "analysis_ns_per_task": ana_ms * 1e6 / T,
+           "tasks_per_s_incl_capture": done / ((kern + ana_ms) * 1e-3), "generate_s": gen_s,
+           "timed_launches": steps}
+    batch.close()
+    for g in graphs:
+        g.close()
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -66,7 +116,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    traces = load_traces()
+    traces = load_traces(args)
     n_tasks = sum(t.n for t in traces)
     for _ in range(args.warmup):
         oracle_step(traces)
@@ -76,7 +126,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "ns_per_task": 1e9 / value, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "int32", "data": "synthetic", "config": config(n_tasks),
+            "dtype": "int32", "data": "synthetic", "config": config(n_tasks, args),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "each step = the full workload: per-cell oracle analysis + Kahn order"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -205,7 +255,7 @@ def run_ours(args):
     __graft_entry__.build()
     from paper_2508_16522_gb300 import grt
 
-    traces = load_traces()
+    traces = load_traces(args)
     n_tasks = sum(t.n for t in traces)
     stream = torch.cuda.Stream()
     dev_inputs = [[torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (t.req_off, t.lo, t.hi, t.priv)]
@@ -230,7 +280,9 @@ def run_ours(args):
             s = g.stats()
             out.append({"n": s["n_tasks"], "E": s["n_edges"], "entries": s["n_entries"], "pairs": s["n_pairs"],
                         "ms_exec_kernel": s["ms_exec_kernel"], "ms_sweep_kernel": s["ms_sweep_kernel"],
-                        "ms_analyze": s["ms_analyze"], "ms_execute": s["ms_execute"]})
+                        "ms_analyze": s["ms_analyze"], "ms_bin": s["ms_bin"],
+                        "ms_sort_entries": s["ms_sort_entries"], "ms_sweep": s["ms_sweep"],
+                        "ms_sort_pairs": s["ms_sort_pairs"], "ms_csr": s["ms_csr"], "ms_execute": s["ms_execute"]})
         return out
 
     def timed(inputs, k, defer=False):
@@ -270,13 +322,18 @@ def run_ours(args):
         dist.barrier()
 
     # end to end through the host API: pinned host arrays, H2D inside the step
-    for _ in range(max(1, args.warmup // 2)):
-        step(host_inputs, defer=True)
-    e2e_ms, _ = timed(host_inputs, args.steps, defer=True)
+    e2e_ms = [float("nan")]
+    if not args.no_e2e:
+        for _ in range(max(1, args.warmup // 2)):
+            step(host_inputs, defer=True)
+        e2e_ms, _ = timed(host_inputs, args.steps, defer=True)
     h2d = sum(sum(int(a.numel() * a.element_size()) for a in inp) for inp in host_inputs)
+    batched = None
+    if world == 1 and not args.no_batched:
+        batched = run_batched(grt, torch, flush, max(1, min(args.steps, 3)))
 
     value = world * n_tasks * args.steps / (total_ms * 1e-3)
-    e2e_value = n_tasks * args.steps / (sum(e2e_ms) * 1e-3)
+    e2e_value = None if args.no_e2e else n_tasks * args.steps / (sum(e2e_ms) * 1e-3)
     avg = [{k: float(np.mean([p[i][k] for p in per])) for k in per[0][i]} for i in range(len(graphs))]
     peaks = measured_peaks()
     roof = roofline(avg, peaks)
@@ -293,11 +350,13 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "ns_per_task": 1e9 / value * world,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-                "data": "synthetic", "config": config(n_tasks), "form": "plain",
-                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                        "d2h_bytes_per_step": 8 * len(graphs), "ms_per_step": sum(e2e_ms) / args.steps,
-                        "validation": "on the device (RT_LAUNCH_DEFER_CHECK)"},
+                "data": "synthetic", "config": config(n_tasks, args), "form": "plain",
+                "e2e": None if args.no_e2e else {
+                    "value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": 8 * len(graphs), "ms_per_step": sum(e2e_ms) / args.steps,
+                    "validation": "on the device (RT_LAUNCH_DEFER_CHECK)"},
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches,
+                "batched": batched,
                 "wall_s_timed": wall,
                 "phases_ms_per_graph": [{k: round(v, 4) for k, v in a.items()} for a in avg]}
         print(json.dumps(line), flush=True)
@@ -316,6 +375,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--graph-steps", type=int, default=STEPS, help="profiling only: fewer steps per graph")
+    ap.add_argument("--patterns", default=",".join(tg.PATTERNS), help="profiling only: subset of patterns")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

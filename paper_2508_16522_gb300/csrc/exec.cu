@@ -157,7 +157,8 @@ template <bool TICKETS, bool FENCE, bool SINGLE>
 __global__ void __launch_bounds__(256) k_exec(ExecParams p) {
   extern __shared__ uint64_t lq_all[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint64_t* lq = lq_all + (size_t)warp * kKeepMax;
+  uint64_t* lq = lq_all + (size_t)warp * 2 * kKeepMax;  // kept items
+  uint64_t* lr = lq + kKeepMax;                          // their (row start, degree), prefetched
   ExecCtrl* ctrl = p.ctrl;
   const unsigned lt = lanemask_lt();
   const uint32_t n0 = SINGLE ? (uint32_t)p.graphs[0].n_tasks : 0u;
@@ -184,9 +185,13 @@ __global__ void __launch_bounds__(256) k_exec(ExecParams p) {
 
   for (;;) {
     uint64_t item = kEmpty64;
+    uint64_t rowinfo = kEmpty64;  // (row start | degree << 32) when already known
     if (nl > 0) {
       const int nb = nl < 32 ? nl : 32;
-      if (lane < nb) item = lq[nl - nb + lane];
+      if (lane < nb) {
+        item = lq[nl - nb + lane];
+        rowinfo = lr[nl - nb + lane];
+      }
       nl -= nb;
       __syncwarp();
     } else {
@@ -272,8 +277,13 @@ __global__ void __launch_bounds__(256) k_exec(ExecParams p) {
     const int g = SINGLE ? 0 : (has ? (int)(item >> 32) : -1);
     int rbeg = 0, deg = 0;
     if (has) {
-      rbeg = p.row_ptr[v];
-      deg = p.row_ptr[v + 1] - rbeg;
+      if (rowinfo != kEmpty64) {
+        rbeg = (int)(uint32_t)rowinfo;
+        deg = (int)(rowinfo >> 32);
+      } else {
+        rbeg = p.row_ptr[v];
+        deg = p.row_ptr[v + 1] - rbeg;
+      }
       p.count[v] = p.indeg[v];  // INIT's reset, done by the task itself for the next run
       const ExecGraph& G = p.graphs[g];
       if (TICKETS) p.tickets[2 * (int64_t)v] = (int32_t)atomicAdd(&ctrl->ticket, 1u);
@@ -297,6 +307,7 @@ __global__ void __launch_bounds__(256) k_exec(ExecParams p) {
       int succ[kEdgeRound];
       uint32_t gsel[kEdgeRound];
       int old[kEdgeRound];
+      int rs[kEdgeRound], re[kEdgeRound];
 #pragma unroll
       for (int k = 0; k < kEdgeRound; ++k) {
         succ[k] = -1;
@@ -316,8 +327,19 @@ __global__ void __launch_bounds__(256) k_exec(ExecParams p) {
           if (e < D) succ[k] = p.col[orb + (e - oex)];
         }
       }
+      // the successor's row bounds are read speculatively with its decrement
+      // (the CSR is immutable), so a successor kept by this warp starts
+      // without another dependent load
 #pragma unroll
-      for (int k = 0; k < kEdgeRound; ++k) old[k] = succ[k] >= 0 ? atomicSub(&p.count[succ[k]], 1) : 0;
+      for (int k = 0; k < kEdgeRound; ++k) {
+        old[k] = 0;
+        rs[k] = re[k] = 0;
+        if (succ[k] >= 0) {
+          old[k] = atomicSub(&p.count[succ[k]], 1);
+          rs[k] = __ldg(p.row_ptr + succ[k]);
+          re[k] = __ldg(p.row_ptr + succ[k] + 1);
+        }
+      }
 #pragma unroll
       for (int k = 0; k < kEdgeRound; ++k) {
         if (e0 + k * 32 >= D) break;  // warp-uniform
@@ -329,7 +351,10 @@ __global__ void __launch_bounds__(256) k_exec(ExecParams p) {
         const int rank = __popc(rm & lt);
         int room = p.keep - nl;
         if (room < 0) room = 0;
-        if (ready && rank < room) lq[nl + rank] = nit;
+        if (ready && rank < room) {
+          lq[nl + rank] = nit;
+          lr[nl + rank] = (uint32_t)rs[k] | ((uint64_t)(uint32_t)(re[k] - rs[k]) << 32);
+        }
         const int nover = r > room ? r - room : 0;
         if (nover > 0) {
           uint32_t base = 0;
@@ -418,12 +443,12 @@ void launch_seed(ExecParams p, int64_t ring_clear, cudaStream_t s) {
 int exec_max_blocks_per_sm(int warps) {
   int nb = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_exec<false, false, true>, warps * 32,
-                                                (size_t)warps * kKeepMax * sizeof(uint64_t));
+                                                (size_t)warps * 2 * kKeepMax * sizeof(uint64_t));
   return nb;
 }
 
 void launch_exec(ExecParams p, int blocks, int warps, cudaStream_t s) {
-  const size_t smem = (size_t)warps * kKeepMax * sizeof(uint64_t);
+  const size_t smem = (size_t)warps * 2 * kKeepMax * sizeof(uint64_t);
   if (p.keep > kKeepMax) p.keep = kKeepMax;
   if (p.keep < 0) p.keep = 0;
   if (p.claim > 32) p.claim = 32;

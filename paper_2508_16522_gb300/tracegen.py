@@ -129,43 +129,38 @@ def stencil_1d(pieces: int = 16, steps: int = 100, piece_elems: int = 1024) -> T
 # ---------------------------------------------------------------------------
 # Task Bench style grids
 # ---------------------------------------------------------------------------
-def taskbench_preds(width: int, steps: int, pattern: str, seed: int = 0) -> List[np.ndarray]:
-    """Predecessor *columns* (indices into step t-1) of every task of steps 1..,
-    as a [steps-1, width, k] array (k = 3 stencil with -1 padding, 2 butterfly,
-    5 random)."""
+def taskbench_preds(width: int, steps: int, pattern: str, seed: int = 0) -> np.ndarray:
+    """Predecessor *columns* (indices into step t-1) of every task of steps
+    1..steps-1, as an int64 [steps-1, width, k] array (k = 3 for the stencil,
+    with -1 where a neighbour falls off the edge; 2 butterfly; 5 random)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     cols = np.arange(width, dtype=np.int64)
-    out = []
+    T = max(steps - 1, 0)
     if pattern == "stencil":
         left = np.where(cols > 0, cols - 1, -1)
         right = np.where(cols < width - 1, cols + 1, -1)
         one = np.stack([left, cols, right], axis=1)
-        for _ in range(1, steps):
-            out.append(one)
-    elif pattern == "butterfly":
+        return np.broadcast_to(one, (T, width, 3)).copy()
+    if pattern == "butterfly":
         logw = max(int(round(math.log2(width))), 1)
         assert (1 << logw) == width, "butterfly needs a power-of-two width"
-        for t in range(1, steps):
-            partner = cols ^ (1 << (t % logw))
-            out.append(np.stack([cols, partner], axis=1))
-    elif pattern == "random":
+        t = np.arange(1, steps, dtype=np.int64)
+        partner = cols[None, :] ^ (np.int64(1) << (t % logw))[:, None]
+        return np.stack([np.broadcast_to(cols, (T, width)), partner], axis=2)
+    if pattern == "random":
         # k distinct columns of step t-1, uniform, per task (rejection: rows
         # with a repeated column are redrawn until all k are distinct)
         k = min(5, width)
-        picks = rng.integers(0, width, size=(max(steps - 1, 0), width, k))
+        picks = rng.integers(0, width, size=(T, width, k))
         while picks.size:
-            s = np.sort(picks, axis=2)
-            bad = (s[:, :, 1:] == s[:, :, :-1]).any(axis=2)
+            srt = np.sort(picks, axis=2)
+            bad = (srt[:, :, 1:] == srt[:, :, :-1]).any(axis=2)
             nb = int(bad.sum())
             if nb == 0:
-                picks = s
-                break
+                return srt
             picks[bad] = rng.integers(0, width, size=(nb, k))
-        for t in range(1, steps):
-            out.append(picks[t - 1])
-    else:
-        raise ValueError(pattern)
-    return out
+        return picks
+    raise ValueError(pattern)
 
 
 def taskbench(width: int = 1024, steps: int = 1000, pattern: str = "stencil", seed: int = 0,
@@ -174,64 +169,48 @@ def taskbench(width: int = 1024, steps: int = 1000, pattern: str = "stencil", se
 
     encode='region': domain is a width x steps grid, task (i, t) writes cell
     (i, t) and reads the cells of its preds (one 1x3 read rectangle for the
-    stencil, single-cell read rectangles otherwise).
+    stencil, single-cell read rectangles otherwise; reads first, then the write).
     encode='explicit': no rectangles, the preds are passed as explicit lists.
     """
     n = width * steps
-    pc = taskbench_preds(width, steps, pattern, seed)
+    pc = taskbench_preds(width, steps, pattern, seed)  # [T, w, k]
+    T = pc.shape[0]
+    ii = np.arange(width, dtype=np.int64)
+    tt = np.arange(1, steps, dtype=np.int64)
     if encode == "explicit":
-        counts = np.zeros(n, dtype=np.int64)
-        preds = []
+        base = ((tt - 1) * width)[:, None, None]
+        valid = pc >= 0
         pcount = np.zeros(n, dtype=np.int64)
-        for t, cols in enumerate(pc, start=1):
-            base = (t - 1) * width
-            if pattern == "stencil":
-                valid = cols >= 0
-                pcount[t * width:(t + 1) * width] = valid.sum(axis=1)
-                preds.append((cols + base)[valid])
-            else:
-                pcount[t * width:(t + 1) * width] = cols.shape[1]
-                preds.append((cols + base).reshape(-1))
-        pred = np.concatenate(preds) if preds else np.zeros(0, dtype=np.int64)
+        pcount[width:] = valid.sum(axis=2).reshape(-1)
+        pred = (pc + base)[valid]  # row-major: task order, then pred order
         empty = np.zeros((0,), dtype=np.int64)
-        return _finish(2, [0, 0], [width - 1, steps - 1], counts, empty, empty,
+        return _finish(2, [0, 0], [width - 1, steps - 1], np.zeros(n, np.int64), empty, empty,
                        np.zeros(0, dtype=np.uint8), pred_counts=pcount, pred=pred,
                        name=f"taskbench_{pattern}_{width}x{steps}_explicit")
-    # region encoding
-    ii = np.arange(width, dtype=np.int64)
-    lo_parts, hi_parts, pr_parts, cnt_parts = [], [], [], []
-    # step 0: only the write
-    w0lo = np.stack([ii, np.zeros(width, np.int64)], axis=1)
-    lo_parts.append(w0lo)
-    hi_parts.append(w0lo)
-    pr_parts.append(np.full(width, WRITE, np.uint8))
-    cnt_parts.append(np.ones(width, np.int64))
-    for t, cols in enumerate(pc, start=1):
-        tt = np.full(width, t, np.int64)
-        if pattern == "stencil":
-            rlo = np.stack([np.maximum(ii - 1, 0), tt - 1], axis=1)
-            rhi = np.stack([np.minimum(ii + 1, width - 1), tt - 1], axis=1)
-            wlo = np.stack([ii, tt], axis=1)
-            lo_t = np.stack([rlo, wlo], axis=1).reshape(-1, 2)
-            hi_t = np.stack([rhi, wlo], axis=1).reshape(-1, 2)
-            pr_t = np.tile(np.array([READ, WRITE], np.uint8), width)
-            cnt_parts.append(np.full(width, 2, np.int64))
-        else:
-            k = cols.shape[1]
-            rlo = np.stack([cols, np.broadcast_to(tt[:, None] - 1, cols.shape)], axis=2)  # [w,k,2]
-            wlo = np.stack([ii, tt], axis=1)[:, None, :]
-            allr = np.concatenate([rlo, wlo], axis=1).reshape(-1, 2)
-            lo_t = allr
-            hi_t = allr
-            pr_t = np.tile(np.array([READ] * k + [WRITE], np.uint8), width)
-            cnt_parts.append(np.full(width, k + 1, np.int64))
-        lo_parts.append(lo_t)
-        hi_parts.append(hi_t)
-        pr_parts.append(pr_t)
-    lo = np.concatenate(lo_parts)
-    hi = np.concatenate(hi_parts)
-    return _finish(2, [0, 0], [width - 1, steps - 1], np.concatenate(cnt_parts), lo.reshape(-1),
-                   hi.reshape(-1), np.concatenate(pr_parts),
+    # region encoding: step 0 writes only; later steps read then write
+    w0 = np.stack([ii, np.zeros(width, np.int64)], axis=1)
+    if pattern == "stencil":
+        rlo = np.stack([np.broadcast_to(np.maximum(ii - 1, 0), (T, width)),
+                        np.broadcast_to(tt[:, None] - 1, (T, width))], axis=2)
+        rhi = np.stack([np.broadcast_to(np.minimum(ii + 1, width - 1), (T, width)),
+                        np.broadcast_to(tt[:, None] - 1, (T, width))], axis=2)
+        wr = np.stack([np.broadcast_to(ii, (T, width)), np.broadcast_to(tt[:, None], (T, width))], axis=2)
+        lo_t = np.stack([rlo, wr], axis=2).reshape(-1, 2)
+        hi_t = np.stack([rhi, wr], axis=2).reshape(-1, 2)
+        pr_t = np.tile(np.array([READ, WRITE], np.uint8), T * width)
+        k = 1
+    else:
+        k = pc.shape[2]
+        rd = np.stack([pc, np.broadcast_to((tt - 1)[:, None, None], pc.shape)], axis=3)  # [T,w,k,2]
+        wr = np.stack([np.broadcast_to(ii, (T, width)), np.broadcast_to(tt[:, None], (T, width))], axis=2)
+        allr = np.concatenate([rd, wr[:, :, None, :]], axis=2).reshape(-1, 2)
+        lo_t = hi_t = allr
+        pr_t = np.tile(np.array([READ] * k + [WRITE], np.uint8), T * width)
+    lo = np.concatenate([w0, lo_t])
+    hi = np.concatenate([w0, hi_t])
+    counts = np.concatenate([np.ones(width, np.int64), np.full(T * width, k + 1, np.int64)])
+    return _finish(2, [0, 0], [width - 1, steps - 1], counts, lo.reshape(-1), hi.reshape(-1),
+                   np.concatenate([np.full(width, WRITE, np.uint8), pr_t]),
                    name=f"taskbench_{pattern}_{width}x{steps}_region")
 
 
