@@ -332,12 +332,26 @@ def run_ours(args):
     if world == 1 and not args.no_batched:
         batched = run_batched(grt, torch, flush, max(1, min(args.steps, 3)))
 
+    # the executor's own rooflines (dependent atomic latency, scattered atomics)
+    mb = grt.rt_microbench_atomics()
     value = world * n_tasks * args.steps / (total_ms * 1e-3)
     e2e_value = None if args.no_e2e else n_tasks * args.steps / (sum(e2e_ms) * 1e-3)
     avg = [{k: float(np.mean([p[i][k] for p in per])) for k in per[0][i]} for i in range(len(graphs))]
     peaks = measured_peaks()
     roof = roofline(avg, peaks)
     roof["share_of_step"] = (roof["avg_launch_ms"] * len(graphs)) / (total_ms / args.steps) if world == 1 else None
+    ex_ms = sum(a["ms_exec_kernel"] for a in avg)
+    edges = sum(a["E"] for a in avg)
+    depth = getattr(args, "graph_steps", STEPS)
+    step_ns = [1e6 * a["ms_exec_kernel"] / depth for a in avg]
+    atomic_roof = {
+        "measured": {k: round(v, 4) for k, v in mb.items()},
+        "exec_edge_decrements_gops": edges / (ex_ms * 1e-3) / 1e9,
+        "frac_of_scatter_atomic_throughput": edges / (ex_ms * 1e-3) / 1e9 / mb["scatter_atomic_gops"],
+        "ns_per_wavefront_step": [round(x, 1) for x in step_ns],
+        "dep_atomic_latencies_per_step": [round(x / mb["dep_atomic_ns"], 2) for x in step_ns],
+        "note": "each graph is 1000 dependent steps deep; a step cannot take less than one dependent atomic "
+                "round trip, so dep_atomic_latencies_per_step is the executor's distance from its latency floor"}
 
     line = None
     if rank == 0:
@@ -355,7 +369,8 @@ def run_ours(args):
                     "value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": 8 * len(graphs), "ms_per_step": sum(e2e_ms) / args.steps,
                     "validation": "on the device (RT_LAUNCH_DEFER_CHECK)"},
-                "roofline": roof, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches,
+                "roofline": roof, "atomic_roofline": atomic_roof, "cpu_baseline": cpu, "clocks": clk,
+                "gpu_launches": launches,
                 "batched": batched,
                 "wall_s_timed": wall,
                 "phases_ms_per_graph": [{k: round(v, 4) for k, v in a.items()} for a in avg]}

@@ -121,6 +121,11 @@ typedef struct {
   float ms_exec_kernel;   /* the persistent executor kernel alone */
   int32_t exec_blocks, exec_threads;
   float ms_sweep_kernel;  /* the interference sweep kernel alone */
+  int32_t pad0;
+  /* diagnostic counters of the last executor launch: batches, tasks, edges,
+   * ring claims, failed claim CASes, items published to the ring, idle polls,
+   * waits for a reserved slot, ready successors kept by their warp */
+  int64_t exec_counters[9];
 } rt_graph_stats_t;
 
 /* Creates an empty graph. Makes no CUDA call (device buffers are allocated on
@@ -229,6 +234,10 @@ rt_status rt_batch_execute(rt_batch_t b, int32_t replays, int32_t exec_blocks, i
                            int32_t claim, int32_t keep);
 
 rt_status rt_batch_sync(rt_batch_t b, float* ms_kernel);
+
+/* The first n (<= 9) diagnostic counters of the last batch launch, in the
+ * order of rt_graph_stats_t.exec_counters (synchronises). */
+rt_status rt_batch_counters(rt_batch_t b, int64_t* out, int32_t n);
 rt_status rt_batch_destroy(rt_batch_t b);
 
 /* Message of the last failed call on this thread ("" if none). */
@@ -243,9 +252,9 @@ rt_status rt_device_info(int32_t* num_sms, int32_t* exec_blocks_per_sm);
  * memory when they run a graph -- code inside a memory-pool or arena manager
  * that owns all device memory, or a latency-critical loop where cudaMalloc or
  * cudaFree (which synchronises the device) is not allowed. The executor's
- * scratch (countdown counters, ready ring, control words) lives in a fixed
- * device array inside the library, about 3 MB, which every GPU that loads the
- * library keeps until the process exits.
+ * scratch (countdown counters, ready ring, trigger records, control words)
+ * lives in a fixed device array inside the library, about 11 MB, which every
+ * GPU that loads the library keeps until the process exits.
  *  row_ptr int32[n_tasks+1], col int32[n_edges], indeg int32[n_tasks]: device
  *          pointers, caller-owned, e.g. filled by rt_copy_csr; every column must
  *          be a later task id (src < dst) and indeg must match the columns
@@ -264,6 +273,14 @@ rt_status rt_device_info(int32_t* num_sms, int32_t* exec_blocks_per_sm);
 rt_status rt_execute_csr_static(const int32_t* row_ptr, const int32_t* col, const int32_t* indeg,
                                 int32_t n_tasks, int64_t n_edges, int32_t spin_iters, int32_t* out,
                                 void* stream);
+
+/* The executor's rooflines, measured on the current device (synchronous,
+ * allocates a 64 MB scratch array): out[0] dependent atomic latency (ns),
+ * out[1] dependent L2 load latency (ns), out[2] scattered atomicSub throughput
+ * with the result used (G ops/s), out[3] the same without using the result,
+ * out[4] contended single-address atomicAdd (G ops/s), out[5] the same
+ * warp-aggregated (G thread-ops/s). n = how many of the six to return. */
+rt_status rt_microbench_atomics(double* out, int32_t n, void* stream);
 
 /* Total number of kernels this library has launched in the process (for
  * benchmarks that report how much GPU work a timed region issued). */

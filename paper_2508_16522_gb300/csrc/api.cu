@@ -120,7 +120,7 @@ struct rt_graph {
   bool pending_validate = false;
   // analysis
   DevBuf rect_task, cnt, keys, keys_alt, pay, pay_alt, seg_b, seg_e, pairs, pairs_alt, flags, upos;
-  DevBuf col, row_ptr, indeg, count, rootpos, root_items, ws, misc;
+  DevBuf col, row_ptr, indeg, count, rootpos, root_items, ws, misc, adj;
   // execution
   DevBuf ring, ctrl, gtable, done_g, tickets;
   uint32_t* hpin = nullptr;  // pinned readback area (64 words)
@@ -142,7 +142,7 @@ struct rt_batch {
   cudaStream_t s = nullptr;
   int32_t G = 0, G_nonempty = 0;
   int64_t T = 0, E = 0, Rtot = 0;
-  DevBuf row_ptr, col, indeg, count, root_items, gtable, done_g, ring, ctrl;
+  DevBuf row_ptr, col, indeg, count, root_items, gtable, done_g, ring, ctrl, adj;
   uint32_t* hpin = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   bool dirty = false;
@@ -266,7 +266,7 @@ rt_status rt_graph_destroy(rt_graph_t g) {
   DevBuf* bufs[] = {&g->req_off, &g->lo, &g->hi, &g->priv, &g->pred_off, &g->pred, &g->body_arg,
                     &g->err, &g->rect_task, &g->cnt, &g->keys, &g->keys_alt, &g->pay, &g->pay_alt,
                     &g->seg_b, &g->seg_e, &g->pairs, &g->pairs_alt, &g->flags, &g->upos, &g->col,
-                    &g->row_ptr, &g->indeg, &g->count, &g->rootpos, &g->root_items, &g->ws, &g->misc,
+                    &g->row_ptr, &g->indeg, &g->count, &g->rootpos, &g->root_items, &g->ws, &g->misc, &g->adj,
                     &g->ring, &g->ctrl, &g->gtable, &g->done_g, &g->tickets};
   for (DevBuf* b : bufs) b->release();
   if (g->hpin) cudaFreeHost(g->hpin);
@@ -325,7 +325,7 @@ rt_status copy_in(void* dst, const void* src, size_t bytes, cudaStream_t s) {
 
 rt_status ensure_pinned(rt_graph* g) {
   if (g->hpin) return RT_OK;
-  CK(cudaMallocHost(&g->hpin, 64 * sizeof(uint32_t)));
+  CK(cudaMallocHost(&g->hpin, 1024));
   return RT_OK;
 }
 
@@ -586,6 +586,8 @@ rt_status run_analysis(rt_graph* g) {
   scan_exclusive<uint32_t>(g->rootpos.as<uint32_t>(), g->rootpos.as<uint32_t>(), n, g->ws.as<uint32_t>(), s);
   launch_roots_emit(g->indeg.as<int32_t>(), g->rootpos.as<uint32_t>(), n, 0, 0, g->root_items.as<uint64_t>(),
                     g->count.as<int32_t>(), s);
+  CKR(g->adj.reserve((size_t)n * 32, s));
+  launch_pack_adj(g->row_ptr.as<int32_t>(), g->col.as<int32_t>(), g->indeg.as<int32_t>(), n, g->adj.as<int4>(), s);
   if (prof) CK(cudaEventRecord(g->ev[EV_CSR], s));
   CK(cudaMemcpyAsync(g->hpin + 8, g->upos.as<uint32_t>() + Ptot, 4, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(g->hpin + 9, g->rootpos.as<uint32_t>() + n, 4, cudaMemcpyDeviceToHost, s));
@@ -634,7 +636,8 @@ extern "C" rt_status rt_get_csr(rt_graph_t g, const int32_t** row_ptr, const int
 // ---------------------------------------------------------------------------
 namespace {
 
-constexpr int kStatusWord = 40;  // hpin word receiving the executor status
+constexpr int kStatusWord = 40;     // hpin word receiving the executor status
+constexpr int kCountersByte = 512;  // hpin byte offset of the executor's diagnostic counters
 
 rt_status prepare_run(rt_graph* g, int32_t replays, ExecParams* out, int64_t* ring_clear) {
   cudaStream_t s = g->s;
@@ -679,6 +682,7 @@ rt_status prepare_run(rt_graph* g, int32_t replays, ExecParams* out, int64_t* ri
   }
   if (g->desc.flags & RT_GRAPH_TICKETS) CKR(g->tickets.reserve((size_t)g->n * 8, s));
   ExecParams p{};
+  p.adj = g->adj.as<int4>();
   p.row_ptr = g->row_ptr.as<int32_t>();
   p.col = g->col.as<int32_t>();
   p.indeg = g->indeg.as<int32_t>();
@@ -693,8 +697,8 @@ rt_status prepare_run(rt_graph* g, int32_t replays, ExecParams* out, int64_t* ri
   p.replays = replays;
   p.graphs_target = 1;
   p.timeout_ns = g->desc.timeout_ns;
-  p.claim = g->cfg_claim > 0 ? g->cfg_claim : 32;
-  p.keep = g->cfg_keep > 0 ? g->cfg_keep : 32;
+  p.claim = g->cfg_claim > 0 ? g->cfg_claim : 8;
+  p.keep = g->cfg_keep > 0 ? g->cfg_keep : 16;
   p.tickets = (g->desc.flags & RT_GRAPH_TICKETS) ? g->tickets.as<int32_t>() : nullptr;
   p.total_roots = (int32_t)g->n_roots;
   p.need_fence = g->desc.body == RT_BODY_COUNTER || g->desc.body == RT_BODY_CHECK;
@@ -707,12 +711,14 @@ rt_status enqueue_run(rt_graph* g, const ExecParams& p, int64_t ring_clear, cuda
     launch_reset_counts(g->count.as<int32_t>(), g->indeg.as<int32_t>(), g->n, g->hold_task, g->hold_extra, s);
   if (timed) CK(cudaEventRecord(g->ev[EV_X0], s));
   launch_seed(p, ring_clear, s);
-  const int warps = g->cfg_warps > 0 ? g->cfg_warps : 8;
+  const int warps = g->cfg_warps > 0 ? g->cfg_warps : 2;
   const int blocks = g->cfg_blocks > 0 ? g->cfg_blocks : g_dev.num_sms;
   if (timed) CK(cudaEventRecord(g->ev[EV_XK0], s));
   launch_exec(p, blocks, warps, s);
   if (timed) CK(cudaEventRecord(g->ev[EV_XK1], s));
   CK(cudaMemcpyAsync(g->hpin + kStatusWord, &p.ctrl->status, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(reinterpret_cast<char*>(g->hpin) + kCountersByte, p.ctrl->counters,
+                     kCntCount * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
   g->exec_blocks = blocks;
   g->exec_warps = warps;
   return RT_OK;
@@ -824,6 +830,10 @@ rt_status rt_graph_stats(rt_graph_t g, rt_graph_stats_t* out) {
     cudaEventElapsedTime(&out->ms_csr, g->ev[EV_SORTP], g->ev[EV_CSR]);
     if (g->n_entries > 0) cudaEventElapsedTime(&out->ms_sweep_kernel, g->ev[EV_SW0], g->ev[EV_SW1]);
   }
+  if (g->hpin) {
+    const unsigned long long* c = reinterpret_cast<const unsigned long long*>(reinterpret_cast<char*>(g->hpin) + 512);
+    for (int k = 0; k < kCntCount && k < 9; ++k) out->exec_counters[k] = (int64_t)c[k];
+  }
   if (g->ev_ok && g->exec_timed) {
     cudaEventElapsedTime(&out->ms_execute, g->ev[EV_X0], g->ev[EV_XK1]);
     cudaEventElapsedTime(&out->ms_exec_kernel, g->ev[EV_XK0], g->ev[EV_XK1]);
@@ -919,7 +929,7 @@ rt_status rt_batch_create(const rt_graph_t* graphs, int32_t n_graphs, void* stre
       (st = b->gtable.reserve((size_t)n_graphs * sizeof(ExecGraph), s)) ||
       (st = b->done_g.reserve((size_t)n_graphs * 4, s)) || (st = b->ctrl.reserve(sizeof(ExecCtrl), s)))
     return bail(st);
-  if (cudaMallocHost(&b->hpin, 256) != cudaSuccess || cudaEventCreate(&b->e0) != cudaSuccess ||
+  if (cudaMallocHost(&b->hpin, 1024) != cudaSuccess || cudaEventCreate(&b->e0) != cudaSuccess ||
       cudaEventCreate(&b->e1) != cudaSuccess)
     return bail(fail(RT_ERR_CUDA, "batch host/event allocation failed"));
   std::vector<ExecGraph> table((size_t)n_graphs);
@@ -966,6 +976,8 @@ rt_status rt_batch_create(const rt_graph_t* graphs, int32_t n_graphs, void* stre
     eb += g->n_edges;
     rb += g->n_roots;
   }
+  if ((st = b->adj.reserve((size_t)std::max<int64_t>(T, 1) * 32, s))) return bail(st);
+  launch_pack_adj(b->row_ptr.as<int32_t>(), b->col.as<int32_t>(), b->indeg.as<int32_t>(), T, b->adj.as<int4>(), s);
   if (cudaMemcpyAsync(b->gtable.p, table.data(), table.size() * sizeof(ExecGraph), cudaMemcpyHostToDevice, s) !=
           cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess)
@@ -979,7 +991,7 @@ rt_status rt_batch_execute(rt_batch_t b, int32_t replays, int32_t exec_blocks, i
                            int32_t keep) {
   if (!b) return fail(RT_ERR_INVALID, "batch is NULL");
   if (replays <= 0) return fail(RT_ERR_INVALID, "replays must be positive");
-  const int warps = exec_warps > 0 ? std::min(exec_warps, 8) : 8;
+  const int warps = exec_warps > 0 ? std::min(exec_warps, 8) : 4;
   const uint64_t cap = (uint64_t)b->T * (uint64_t)replays + 64;
   if (cap >= 0xFFFFFFF0ull) return fail(RT_ERR_INVALID, "tasks x replays must stay below 2^32 per launch");
   cudaStream_t s = b->s;
@@ -990,6 +1002,7 @@ rt_status rt_batch_execute(rt_batch_t b, int32_t replays, int32_t exec_blocks, i
   }
   if (b->dirty) launch_reset_counts(b->count.as<int32_t>(), b->indeg.as<int32_t>(), b->T, -1, 0, s);
   ExecParams p{};
+  p.adj = b->adj.as<int4>();
   p.row_ptr = b->row_ptr.as<int32_t>();
   p.col = b->col.as<int32_t>();
   p.indeg = b->indeg.as<int32_t>();
@@ -1012,11 +1025,13 @@ rt_status rt_batch_execute(rt_batch_t b, int32_t replays, int32_t exec_blocks, i
   launch_seed(p, clear ? (int64_t)(b->ring.cap / 8) : 0, s);
   const int max_blocks = g_dev.num_sms * exec_bps_for(warps);
   if (exec_blocks > max_blocks) return fail(RT_ERR_INVALID, "more persistent blocks than can be resident");
-  const int blocks = exec_blocks > 0 ? exec_blocks : g_dev.num_sms * std::min(exec_bps_for(warps), 2);
+  const int blocks = exec_blocks > 0 ? exec_blocks : g_dev.num_sms * std::min(exec_bps_for(warps), 3);
   CK(cudaEventRecord(b->e0, s));
   launch_exec(p, blocks, warps, s);
   CK(cudaEventRecord(b->e1, s));
   CK(cudaMemcpyAsync(b->hpin, &p.ctrl->status, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(reinterpret_cast<char*>(b->hpin) + 512, p.ctrl->counters, kCntCount * sizeof(unsigned long long),
+                     cudaMemcpyDeviceToHost, s));
   CK(cudaGetLastError());
   b->dirty = false;
   return RT_OK;
@@ -1047,7 +1062,7 @@ rt_status rt_batch_sync(rt_batch_t b, float* ms_kernel) {
 rt_status rt_batch_destroy(rt_batch_t b) {
   if (!b) return RT_OK;
   cudaStreamSynchronize(b->s);
-  DevBuf* bufs[] = {&b->row_ptr, &b->col, &b->indeg, &b->count, &b->root_items, &b->gtable, &b->done_g, &b->ring, &b->ctrl};
+  DevBuf* bufs[] = {&b->row_ptr, &b->col, &b->indeg, &b->count, &b->root_items, &b->gtable, &b->done_g, &b->ring, &b->ctrl, &b->adj};
   for (DevBuf* x : bufs) x->release();
   if (b->hpin) cudaFreeHost(b->hpin);
   if (b->e0) cudaEventDestroy(b->e0);
@@ -1102,5 +1117,22 @@ extern "C" rt_status rt_execute_csr_static(const int32_t* row_ptr, const int32_t
   rt_status st = grt::static_execute(row_ptr, col, indeg, n_tasks, n_edges, spin_iters, out,
                                      (cudaStream_t)stream, 2000000000ll, &why);
   if (st != RT_OK) return fail(st, "rt_execute_csr_static: %s", why);
+  return RT_OK;
+}
+
+extern "C" rt_status rt_batch_counters(rt_batch_t b, int64_t* out, int32_t n) {
+  if (!b || !out || n < 0) return fail(RT_ERR_INVALID, "NULL argument");
+  CK(cudaStreamSynchronize(b->s));
+  const unsigned long long* c = reinterpret_cast<const unsigned long long*>(reinterpret_cast<char*>(b->hpin) + 512);
+  for (int k = 0; k < n; ++k) out[k] = k < kCntCount ? (int64_t)c[k] : 0;
+  return RT_OK;
+}
+
+extern "C" rt_status rt_microbench_atomics(double* out, int32_t n, void* stream) {
+  if (!out || n <= 0) return fail(RT_ERR_INVALID, "out is NULL");
+  CKR(ensure_device());
+  const char* why = "";
+  const rt_status st = grt::microbench(out, n, (cudaStream_t)stream, &why);
+  if (st != RT_OK) return fail(st, "microbenchmark: %s", why);
   return RT_OK;
 }

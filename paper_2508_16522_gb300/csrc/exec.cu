@@ -24,7 +24,8 @@ namespace grt {
 
 namespace {
 constexpr int kKeepMax = 64;
-constexpr int kEdgeRound = 8;  // 32-edge groups whose decrements are in flight together
+constexpr uint32_t kNoTicket = 0xFFFFFFFFu;
+constexpr int kEdgeRound = 4;  // 32-edge groups whose decrements are in flight together
 constexpr unsigned kFull = 0xffffffffu;
 
 __global__ void k_reset_counts(int32_t* count, const int32_t* indeg, int64_t n, int32_t hold_task,
@@ -49,6 +50,7 @@ __global__ void k_seed(ExecParams p, int64_t ring_clear) {
     c->ticket = 0;
     c->err_where = 0;
     c->err_info = 0;
+    for (int k = 0; k < kCntCount; ++k) c->counters[k] = 0;
   }
 }
 
@@ -153,20 +155,33 @@ __device__ void on_run_complete(const ExecParams& p, int g, uint32_t runs_done, 
     atomicAdd(&p.ctrl->graphs_done, 1u);
 }
 
+// per-warp shared memory of the executor
+struct WarpQ {
+  int4 adj[kKeepMax][2];  // trigger records of the kept ready tasks
+  int4 bat[32][2];        // trigger records of the current batch, one per lane
+  uint64_t item[kKeepMax];  // kept ready tasks (graph << 32 | task)
+};
+
 template <bool TICKETS, bool FENCE, bool SINGLE>
-__global__ void __launch_bounds__(256) k_exec(ExecParams p) {
-  extern __shared__ uint64_t lq_all[];
+__global__ void __launch_bounds__(256, 1) k_exec(ExecParams p) {
+  extern __shared__ int4 exec_smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint64_t* lq = lq_all + (size_t)warp * 2 * kKeepMax;  // kept items
-  uint64_t* lr = lq + kKeepMax;                          // their (row start, degree), prefetched
+  WarpQ& q = reinterpret_cast<WarpQ*>(exec_smem)[warp];
   ExecCtrl* ctrl = p.ctrl;
   const unsigned lt = lanemask_lt();
   const uint32_t n0 = SINGLE ? (uint32_t)p.graphs[0].n_tasks : 0u;
+  const int body0 = SINGLE ? p.graphs[0].body : 0;
+  const int spin0 = SINGLE ? p.graphs[0].spin_iters : 0;
+  int32_t* const out0 = SINGLE ? p.graphs[0].out : nullptr;  // task_base is 0 for a single graph
   int nl = 0;                    // kept ready tasks (warp-uniform)
   uint32_t pend = 0;             // executed but not yet counted (warp-uniform)
   uint64_t idle_since = 0, last_check = 0;  // lane 0
   unsigned long long seen = 0;
-  uint32_t backoff = 64;
+  uint32_t backoff = 32;
+  uint32_t my_t = kNoTicket;     // this lane's claimed ring ticket
+  unsigned long long cnt[kCntCount];  // diagnostics (lane 0's copy is flushed at exit)
+#pragma unroll
+  for (int k = 0; k < kCntCount; ++k) cnt[k] = 0;
 
   // adds this warp's executed tasks to the shared counters (convergent)
   auto flush = [&]() {
@@ -185,116 +200,123 @@ __global__ void __launch_bounds__(256) k_exec(ExecParams p) {
 
   for (;;) {
     uint64_t item = kEmpty64;
-    uint64_t rowinfo = kEmpty64;  // (row start | degree << 32) when already known
-    if (nl > 0) {
-      const int nb = nl < 32 ? nl : 32;
-      if (lane < nb) {
-        item = lq[nl - nb + lane];
-        rowinfo = lr[nl - nb + lane];
-      }
-      nl -= nb;
-      __syncwarp();
-    } else {
-      uint32_t h0 = 0, got = 0;
-      if (lane == 0) {
-        uint32_t h = ld_relaxed_u32(&ctrl->head), t = ld_relaxed_u32(&ctrl->tail);
-        if (t > p.ring_cap) t = p.ring_cap;
-        while (h < t) {
-          uint32_t want = t - h;
-          if (want > (uint32_t)p.claim) want = (uint32_t)p.claim;
-          const uint32_t old = atomicCAS(&ctrl->head, h, h + want);
-          if (old == h) {
-            h0 = h;
-            got = want;
-            break;
-          }
-          h = old;
-          t = ld_relaxed_u32(&ctrl->tail);
-          if (t > p.ring_cap) t = p.ring_cap;
+    int4 a0 = make_int4(0, 0, 0, -1), a1 = make_int4(-1, -1, -1, -1);  // trigger record
+    bool have_rec = false;
+    // 1. this lane's claimed ring ticket, if it has been published
+    bool waiting = my_t != kNoTicket;
+    if (waiting) {
+      if (my_t >= p.ring_cap) {
+        // past the ring: never filled; dropped when the run ends
+      } else {
+        const uint64_t vv = ld_acquire_u64(p.ring + my_t);
+        if (vv != kEmpty64) {
+          item = vv;
+          st_relaxed_u64(p.ring + my_t, kEmpty64);  // leave the ring clean for the next launch
+          my_t = kNoTicket;
+          waiting = false;
         }
-      }
-      got = __shfl_sync(kFull, got, 0);
-      h0 = __shfl_sync(kFull, h0, 0);
-      if (got == 0) {
-        if (pend) {
-          flush();  // may seed the next run: look for work again first
-          continue;
-        }
-        int stop = 0;
-        if (lane == 0) {
-          const uint32_t st = ld_relaxed_u32(&ctrl->status);
-          const uint32_t gd = ld_relaxed_u32(&ctrl->graphs_done);
-          if (st != 0u || (int)gd >= p.graphs_target) {
-            stop = 1;
-          } else {
-            const uint64_t now = globaltimer_ns();
-            if (idle_since == 0) {
-              idle_since = last_check = now;
-              seen = SINGLE ? ld_relaxed_u32(&p.done_g[0]) : ld_relaxed_u64(&ctrl->executed);
-            } else if (now - last_check > 20000u) {
-              last_check = now;
-              const unsigned long long pr = SINGLE ? ld_relaxed_u32(&p.done_g[0]) : ld_relaxed_u64(&ctrl->executed);
-              if (pr != seen) {
-                seen = pr;
-                idle_since = now;
-              } else if (now - idle_since > (uint64_t)p.timeout_ns) {
-                atomicCAS(&ctrl->status, 0u, (uint32_t)RT_ERR_TIMEOUT);
-                stop = 1;
-              }
-            }
-          }
-        }
-        if (__shfl_sync(kFull, stop, 0)) break;
-        __nanosleep(backoff);
-        if (backoff < 2048) backoff <<= 1;
-        continue;
-      }
-      backoff = 64;
-      idle_since = 0;
-      if ((uint32_t)lane < got) {
-        uint64_t* slot = p.ring + h0 + lane;
-        uint64_t v = ld_acquire_u64(slot);
-        if (v == kEmpty64) {
-          // reserved but not yet published: the producer is between its two stores
-          const uint64_t t0 = globaltimer_ns();
-          while ((v = ld_acquire_u64(slot)) == kEmpty64) {
-            if (globaltimer_ns() - t0 > (uint64_t)p.timeout_ns) {
-              atomicCAS(&ctrl->status, 0u, (uint32_t)RT_ERR_TIMEOUT);
-              ctrl->err_where = 1;
-              break;
-            }
-            __nanosleep(32);
-          }
-        }
-        item = v;
-        if (v != kEmpty64) st_relaxed_u64(slot, kEmpty64);  // leave the ring clean for the next launch
       }
     }
+    // 2. lanes without an item take this warp's kept ready tasks
+    if (nl > 0) {
+      const unsigned need = __ballot_sync(kFull, item == kEmpty64);
+      const int m = nl < __popc(need) ? nl : __popc(need);
+      const int r = __popc(need & lt);
+      if (item == kEmpty64 && r < m) {
+        item = q.item[nl - m + r];
+        a0 = q.adj[nl - m + r][0];
+        a1 = q.adj[nl - m + r][1];
+        have_rec = true;
+      }
+      nl -= m;
+      __syncwarp();
+    }
+    if (!__any_sync(kFull, item != kEmpty64)) {
+      if (!__any_sync(kFull, waiting)) {
+        // 3. claim the next `claim` tickets: one atomic, never fails; each
+        // lane then watches its own slot, so no shared word is polled
+        uint32_t h = 0;
+        if (lane == 0) {
+          h = atomicAdd(&ctrl->head, (uint32_t)p.claim);
+          ++cnt[kCntClaims];
+        }
+        h = __shfl_sync(kFull, h, 0);
+        if (lane < p.claim) my_t = h + (uint32_t)lane;
+        continue;
+      }
+      if (pend) {
+        flush();  // may seed the next run: look for work again first
+        continue;
+      }
+      ++cnt[kCntIdle];
+      int stop = 0;
+      if (lane == 0) {
+        const uint32_t st = ld_relaxed_u32(&ctrl->status);
+        const uint32_t gd = ld_relaxed_u32(&ctrl->graphs_done);
+        if (st != 0u || (int)gd >= p.graphs_target) {
+          stop = 1;
+        } else {
+          const uint64_t now = globaltimer_ns();
+          if (idle_since == 0) {
+            idle_since = last_check = now;
+            seen = SINGLE ? ld_relaxed_u32(&p.done_g[0]) : ld_relaxed_u64(&ctrl->executed);
+          } else if (now - last_check > 20000u) {
+            last_check = now;
+            const unsigned long long pr = SINGLE ? ld_relaxed_u32(&p.done_g[0]) : ld_relaxed_u64(&ctrl->executed);
+            if (pr != seen) {
+              seen = pr;
+              idle_since = now;
+            } else if (now - idle_since > (uint64_t)p.timeout_ns) {
+              atomicCAS(&ctrl->status, 0u, (uint32_t)RT_ERR_TIMEOUT);
+              stop = 1;
+            }
+          }
+        }
+      }
+      if (__shfl_sync(kFull, stop, 0)) break;
+      __nanosleep(backoff);
+      if (backoff < 512) backoff <<= 1;
+      continue;
+    }
+    backoff = 32;
+    idle_since = 0;
 
     if (FENCE) fence_acq_rel_gpu();  // acquire: predecessors' effects visible to the bodies
     const bool has = item != kEmpty64;
     const int v = (int)(uint32_t)item;
     const int g = SINGLE ? 0 : (has ? (int)(item >> 32) : -1);
-    int rbeg = 0, deg = 0;
+    if (has && !have_rec) {
+      a0 = __ldg(p.adj + 2 * (int64_t)v);
+      a1 = __ldg(p.adj + 2 * (int64_t)v + 1);
+    }
+    const int rbeg = has ? a0.x : 0;
+    const int deg = has ? a0.y : 0;
+    q.bat[lane][0] = a0;
+    q.bat[lane][1] = a1;
     if (has) {
-      if (rowinfo != kEmpty64) {
-        rbeg = (int)(uint32_t)rowinfo;
-        deg = (int)(rowinfo >> 32);
-      } else {
-        rbeg = p.row_ptr[v];
-        deg = p.row_ptr[v + 1] - rbeg;
-      }
-      p.count[v] = p.indeg[v];  // INIT's reset, done by the task itself for the next run
-      const ExecGraph& G = p.graphs[g];
+      p.count[v] = a0.z;  // INIT's reset, done by the task itself for the next run
       if (TICKETS) p.tickets[2 * (int64_t)v] = (int32_t)atomicAdd(&ctrl->ticket, 1u);
-      run_body<FENCE>(G, v - G.task_base);
+      if (SINGLE && !FENCE) {
+        if (body0 == RT_BODY_SPIN) {  // the one graph's fields live in registers
+          uint32_t x = (uint32_t)v;
+          for (int k = 0; k < spin0; ++k) x = x * 1664525u + 1013904223u;
+          out0[v] = (int32_t)x;
+        }
+      } else {
+        const ExecGraph& G = p.graphs[g];
+        run_body<FENCE>(G, v - G.task_base);
+      }
       if (TICKETS) p.tickets[2 * (int64_t)v + 1] = (int32_t)atomicAdd(&ctrl->ticket, 1u);
     }
     if (FENCE || TICKETS) fence_acq_rel_gpu();  // release: bodies before the decrements
+    __syncwarp();
 
-    // COMPLETED_EDGE for every out-edge of the batch. Up to 8 x 32 edges per
-    // round: all column loads, then all decrements, are issued before any
-    // result is used, so one round costs about one memory round trip.
+    // COMPLETED_EDGE for every out-edge of the batch, kEdgeRound x 32 edges per
+    // round. The first kAdjInline successors of a task come from its trigger
+    // record (no load); all decrements of a round are in flight together, and
+    // each successor's own record is read speculatively with its decrement, so
+    // a successor kept by this warp starts its next batch with no dependent
+    // load: about one memory round trip per wavefront step.
     int incl = deg;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -303,11 +325,12 @@ __global__ void __launch_bounds__(256) k_exec(ExecParams p) {
     }
     const int excl = incl - deg;
     const int D = __shfl_sync(kFull, incl, 31);
+    cnt[kCntEdges] += (unsigned)D;
     for (int e0 = 0; e0 < D; e0 += kEdgeRound * 32) {
       int succ[kEdgeRound];
       uint32_t gsel[kEdgeRound];
       int old[kEdgeRound];
-      int rs[kEdgeRound], re[kEdgeRound];
+      int4 r0[kEdgeRound], r1[kEdgeRound];
 #pragma unroll
       for (int k = 0; k < kEdgeRound; ++k) {
         succ[k] = -1;
@@ -324,20 +347,19 @@ __global__ void __launch_bounds__(256) k_exec(ExecParams p) {
           const int orb = __shfl_sync(kFull, rbeg, owner);
           const int oex = __shfl_sync(kFull, excl, owner);
           gsel[k] = (uint32_t)(__shfl_sync(kFull, item, owner) >> 32);
-          if (e < D) succ[k] = p.col[orb + (e - oex)];
+          if (e < D) {
+            const int j = e - oex;
+            succ[k] = j < kAdjInline ? reinterpret_cast<const int*>(&q.bat[owner][0])[3 + j] : p.col[orb + j];
+          }
         }
       }
-      // the successor's row bounds are read speculatively with its decrement
-      // (the CSR is immutable), so a successor kept by this warp starts
-      // without another dependent load
 #pragma unroll
       for (int k = 0; k < kEdgeRound; ++k) {
         old[k] = 0;
-        rs[k] = re[k] = 0;
         if (succ[k] >= 0) {
           old[k] = atomicSub(&p.count[succ[k]], 1);
-          rs[k] = __ldg(p.row_ptr + succ[k]);
-          re[k] = __ldg(p.row_ptr + succ[k] + 1);
+          r0[k] = __ldg(p.adj + 2 * (int64_t)succ[k]);
+          r1[k] = __ldg(p.adj + 2 * (int64_t)succ[k] + 1);
         }
       }
 #pragma unroll
@@ -352,8 +374,9 @@ __global__ void __launch_bounds__(256) k_exec(ExecParams p) {
         int room = p.keep - nl;
         if (room < 0) room = 0;
         if (ready && rank < room) {
-          lq[nl + rank] = nit;
-          lr[nl + rank] = (uint32_t)rs[k] | ((uint64_t)(uint32_t)(re[k] - rs[k]) << 32);
+          q.item[nl + rank] = nit;
+          q.adj[nl + rank][0] = r0[k];
+          q.adj[nl + rank][1] = r1[k];
         }
         const int nover = r > room ? r - room : 0;
         if (nover > 0) {
@@ -365,14 +388,19 @@ __global__ void __launch_bounds__(256) k_exec(ExecParams p) {
           } else if (ready && rank >= room) {
             st_release_u64(p.ring + base + (rank - room), nit);
           }
+          cnt[kCntPushed] += (unsigned)nover;
         }
-        nl += r < room ? r : room;
+        const int kept = r < room ? r : room;
+        cnt[kCntKept] += (unsigned)kept;
+        nl += kept;
         __syncwarp();
       }
     }
 
     // completion accounting
     const unsigned hm = __ballot_sync(kFull, has);
+    cnt[kCntBatches] += 1;
+    cnt[kCntTasks] += (unsigned)__popc(hm);
     if (SINGLE) {
       pend += (uint32_t)__popc(hm);
       if (pend >= 4096u) flush();
@@ -393,9 +421,7 @@ __global__ void __launch_bounds__(256) k_exec(ExecParams p) {
         }
       }
       pend += (uint32_t)__popc(hm);
-      if (pend >= 256u && lane == 0) {
-        atomicAdd(&ctrl->executed, (unsigned long long)pend);
-      }
+      if (pend >= 256u && lane == 0) atomicAdd(&ctrl->executed, (unsigned long long)pend);
       if (pend >= 256u) pend = 0;
       unsigned cm = __ballot_sync(kFull, cross);
       while (cm) {
@@ -405,6 +431,25 @@ __global__ void __launch_bounds__(256) k_exec(ExecParams p) {
       }
     }
   }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < kCntCount; ++k)
+      if (cnt[k]) atomicAdd(&ctrl->counters[k], cnt[k]);
+  }
+}
+
+// trigger record of each task: {row start, out-degree, in-degree, first
+// kAdjInline successors (-1 padded)}, two int4 per task
+__global__ void k_pack_adj(const int32_t* row_ptr, const int32_t* col, const int32_t* indeg, int64_t n,
+                           int4* adj) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  const int b = row_ptr[v], d = row_ptr[v + 1] - b;
+  int c[kAdjInline];
+#pragma unroll
+  for (int j = 0; j < kAdjInline; ++j) c[j] = j < d ? col[b + j] : -1;
+  adj[2 * v] = make_int4(b, d, indeg[v], c[0]);
+  adj[2 * v + 1] = make_int4(c[1], c[2], c[3], c[4]);
 }
 
 __global__ void k_rebase_roots(const uint64_t* src, uint64_t* dst, int32_t n, int32_t graph,
@@ -413,6 +458,14 @@ __global__ void k_rebase_roots(const uint64_t* src, uint64_t* dst, int32_t n, in
   if (i < n) dst[i] = ((uint64_t)(uint32_t)graph << 32) | (uint32_t)(task_base + (int32_t)(uint32_t)src[i]);
 }
 }  // namespace
+
+void launch_pack_adj(const int32_t* row_ptr, const int32_t* col, const int32_t* indeg, int64_t n, int4* adj,
+                     cudaStream_t s) {
+  if (n > 0) {
+    count_launch();
+    k_pack_adj<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(row_ptr, col, indeg, n, adj);
+  }
+}
 
 void launch_rebase_roots(const uint64_t* src, uint64_t* dst, int32_t n, int32_t graph, int32_t task_base,
                          cudaStream_t s) {
@@ -443,12 +496,12 @@ void launch_seed(ExecParams p, int64_t ring_clear, cudaStream_t s) {
 int exec_max_blocks_per_sm(int warps) {
   int nb = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_exec<false, false, true>, warps * 32,
-                                                (size_t)warps * 2 * kKeepMax * sizeof(uint64_t));
+                                                (size_t)warps * sizeof(WarpQ));
   return nb;
 }
 
 void launch_exec(ExecParams p, int blocks, int warps, cudaStream_t s) {
-  const size_t smem = (size_t)warps * 2 * kKeepMax * sizeof(uint64_t);
+  const size_t smem = (size_t)warps * sizeof(WarpQ);
   if (p.keep > kKeepMax) p.keep = kKeepMax;
   if (p.keep < 0) p.keep = 0;
   if (p.claim > 32) p.claim = 32;

@@ -138,9 +138,19 @@ struct ExecCtrl {  // reset before every executor launch; hot words on separate 
   unsigned long long executed;     // progress counter (flushed in batches)
   uint32_t pad_e[30];
   uint32_t ticket, pad_k[31];
+  unsigned long long counters[16];  // diagnostics, flushed once per warp at exit (see kCnt*)
 };
 
+// executor diagnostic counters (ExecCtrl::counters)
+enum { kCntBatches = 0, kCntTasks, kCntEdges, kCntClaims, kCntCasFail, kCntPushed, kCntIdle, kCntSlotWait,
+       kCntKept, kCntCount };
+
+// packed trigger record of one task (two int4): {row start, out-degree,
+// in-degree, first 5 successors (-1 padded)}
+constexpr int kAdjInline = 5;
+
 struct ExecParams {
+  const int4* adj;        // 2 x int4 per task: packed trigger records
   const int32_t* row_ptr;
   const int32_t* col;
   const int32_t* indeg;
@@ -218,6 +228,8 @@ void launch_roots(const int32_t* indeg, int32_t n, uint32_t* flags, cudaStream_t
 void launch_roots_emit(const int32_t* indeg, const uint32_t* pos, int32_t n, int32_t task_base,
                        int32_t graph, uint64_t* root_items, int32_t* count, cudaStream_t s);
 
+void launch_pack_adj(const int32_t* row_ptr, const int32_t* col, const int32_t* indeg, int64_t n, int4* adj,
+                     cudaStream_t s);
 void launch_reset_counts(int32_t* count, const int32_t* indeg, int64_t n, int32_t hold_task,
                          int32_t hold_extra, cudaStream_t s);
 void launch_rebase_roots(const uint64_t* src, uint64_t* dst, int32_t n, int32_t graph, int32_t task_base,
@@ -225,6 +237,7 @@ void launch_rebase_roots(const uint64_t* src, uint64_t* dst, int32_t n, int32_t 
 void launch_seed(ExecParams p, int64_t ring_clear, cudaStream_t s);
 void launch_exec(ExecParams p, int blocks, int warps, cudaStream_t s);
 int exec_max_blocks_per_sm(int warps);
+rt_status microbench(double* out, int n_out, cudaStream_t s, const char** why);
 int32_t static_max_tasks();
 rt_status static_execute(const int32_t* row_ptr, const int32_t* col, const int32_t* indeg, int32_t n,
                          int64_t n_edges, int32_t spin_iters, int32_t* out, cudaStream_t s,

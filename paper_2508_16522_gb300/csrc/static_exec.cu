@@ -7,11 +7,11 @@
 // embedded in a host process that owns all device memory. For them,
 // rt_execute_csr_static runs the persistent executor over a CSR the caller
 // already holds, with the executor's scratch (countdown counters, ready ring,
-// control block, graph table) in one file-scope device array instead of
-// library-allocated buffers.
+// trigger records, control block, graph table) in one file-scope device array
+// instead of library-allocated buffers.
 //
 // Limits and sharing: the array holds kStaticMaxTasks tasks worth of scratch
-// (about 3 MB) and stays resident on every device that loads the library until
+// (about 11 MB) and stays resident on every device that loads the library until
 // the process exits. All calls share it and it keeps the previous call's
 // contents, so each call first clears what must start from a known state;
 // calls whose GPU work overlaps (different streams, or host threads racing)
@@ -30,7 +30,8 @@ constexpr size_t kOffDone = 1024;                     // one uint32 per graph (1
 constexpr size_t kOffTable = 1280;                    // one ExecGraph
 constexpr size_t kOffCount = 2048;                    // int32 [kStaticMaxTasks]
 constexpr size_t kOffRing = kOffCount + (size_t)kStaticMaxTasks * 4;  // uint64 [max + 64]
-constexpr size_t kStaticBytes = kOffRing + ((size_t)kStaticMaxTasks + 64) * 8;
+constexpr size_t kOffAdj = kOffRing + ((size_t)kStaticMaxTasks + 64) * 8;  // int4 [2 * max]
+constexpr size_t kStaticBytes = kOffAdj + (size_t)kStaticMaxTasks * 32;
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
@@ -62,6 +63,7 @@ __global__ void k_static_reset(const int32_t* indeg, int32_t n, int32_t spin_ite
     c->ticket = 0;
     c->err_where = 0;
     c->err_info = 0;
+    for (int k = 0; k < kCntCount; ++k) c->counters[k] = 0;
     *reinterpret_cast<uint32_t*>(base + kOffDone) = 0u;
     ExecGraph G{};
     G.task_base = 0;
@@ -197,7 +199,9 @@ rt_status static_execute(const int32_t* row_ptr, const int32_t* col, const int32
   count_launch(2);
   k_static_reset<<<256, 256, 0, s>>>(indeg, n, spin_iters, out);
   k_static_seed<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(indeg, n);
+  launch_pack_adj(row_ptr, col, indeg, n, reinterpret_cast<int4*>(base + kOffAdj), s);
   ExecParams p{};
+  p.adj = reinterpret_cast<const int4*>(base + kOffAdj);
   p.row_ptr = row_ptr;
   p.col = col;
   p.indeg = indeg;

@@ -33,10 +33,14 @@ namespace {
 constexpr int kHashSlots = 128;
 constexpr int kListCap = 64;
 constexpr uint32_t kChunk = 512;
+constexpr int kLaneBuf = 16;     // predecessors one lane buffers in the lane-parallel path
+constexpr int kSmallCells = 16;  // largest box the lane-parallel path takes
+constexpr int kMaxRounds = 8;    // deeper conflict chains go to the warp-wide path
 constexpr unsigned kFull = 0xffffffffu;
 
 __host__ __device__ inline size_t per_warp_bytes(int C) {
-  return (size_t)16 * C + (size_t)((C + 15) & ~15) + 32 * 8 + kHashSlots * 4 + kListCap * 8 + 16;
+  return (size_t)16 * C + (size_t)((C + 15) & ~15) + 32 * 8 + kHashSlots * 4 + kListCap * 8 + 16 +
+         32 * kLaneBuf * 4;
 }
 
 struct WarpSmem {
@@ -47,6 +51,7 @@ struct WarpSmem {
   int* hlist;
   int* hslot;
   int* hcount;
+  int* lbuf;  // [32][kLaneBuf]
 };
 
 struct Ctx {
@@ -103,19 +108,25 @@ __device__ __forceinline__ void warp_insert(const WarpSmem& w, const SweepOut& o
   if (src >= 0 && (peers & lanemask_lt()) == 0) hash_insert(w, o, src, dst);
 }
 
+// Makes sure the warp's pair chunk has room for `need` (<= kChunk) pairs
+// (warp-convergent): pads the old chunk's tail with sentinels and takes a new
+// chunk with one atomic.
+__device__ void reserve_pairs(Ctx& x, const SweepOut& o, uint32_t need) {
+  if (x.chunk_left >= need) return;
+  for (uint32_t i = x.lane; i < x.chunk_left; i += 32) put_pair(o, x.chunk_base + i, kEmpty64);
+  unsigned long long nb = 0;
+  if (x.lane == 0) nb = atomicAdd(o.cursor, (unsigned long long)kChunk);
+  x.chunk_base = __shfl_sync(kFull, nb, 0);
+  x.chunk_left = kChunk;
+}
+
 // writes the task's distinct predecessors found in this tile (convergent)
 __device__ void flush(Ctx& x, const WarpSmem& w, const SweepOut& o, int dst) {
   __syncwarp();
   const int cnt = *(volatile int*)w.hcount;
   const int m = cnt < kListCap ? cnt : kListCap;
   if (m > 0) {
-    if (x.chunk_left < (uint32_t)m) {
-      for (uint32_t i = x.lane; i < x.chunk_left; i += 32) put_pair(o, x.chunk_base + i, kEmpty64);
-      unsigned long long nb = 0;
-      if (x.lane == 0) nb = atomicAdd(o.cursor, (unsigned long long)kChunk);
-      x.chunk_base = __shfl_sync(kFull, nb, 0);
-      x.chunk_left = kChunk;
-    }
+    reserve_pairs(x, o, (uint32_t)m);
     for (int i = x.lane; i < m; i += 32) {
       put_pair(o, x.chunk_base + i, pair_key(w.hlist[i], dst, o.key_bits));
       if (cnt <= kListCap) w.htab[w.hslot[i]] = -1;
@@ -128,6 +139,38 @@ __device__ void flush(Ctx& x, const WarpSmem& w, const SweepOut& o, int dst) {
   __syncwarp();
   if (x.lane == 0) *w.hcount = 0;
   __syncwarp();
+}
+
+// One access at cell c by the task whose first candidate sits at `gpos`, with
+// privilege pc: updates the cell's run state and returns the run whose members
+// precede the access (first position rs, last position rl, member count rc:
+// 0 none, 1, 2, 3 = three or more).
+__device__ __forceinline__ void apply_cell(const WarpSmem& w, int c, int gpos, int pc, uint32_t& rs, uint32_t& rl,
+                                           uint32_t& rc) {
+  uint4 s = w.cell[c];
+  const uint32_t ck = s.x >> 30;
+  rs = rl = rc = 0;
+  if (ck == (uint32_t)pc && pc != kKindWrite) {
+    // join the current run: predecessors are the previous run
+    rs = s.z & kPosMask;
+    rl = s.w;
+    rc = s.z >> 30;
+    uint32_t cc = (s.y >> 30) + 1u;
+    if (cc > 3u) cc = 3u;
+    s.y = (uint32_t)gpos | (cc << 30);
+  } else {
+    // start a new run: predecessors are the current run
+    if (ck != (uint32_t)kKindNone) {
+      rs = s.x & kPosMask;
+      rl = s.y & kPosMask;
+      rc = s.y >> 30;
+    }
+    s.z = (s.x & kPosMask) | (rc << 30);
+    s.w = s.y & kPosMask;
+    s.x = (uint32_t)gpos | ((uint32_t)pc << 30);
+    s.y = (uint32_t)gpos | (1u << 30);
+  }
+  w.cell[c] = s;
 }
 
 // Applies the access of the task whose first candidate sits at `gpos` to every
@@ -159,29 +202,7 @@ __device__ void sweep_box(Ctx& x, const WarpSmem& w, const SweepOut& o, int x0, 
     int m1 = -1, m2 = -1;
     uint32_t rs = 0, rl = 0, rc = 0;
     if (act) {
-      uint4 s = w.cell[c];
-      const uint32_t ck = s.x >> 30;
-      if (ck == (uint32_t)pc && pc != kKindWrite) {
-        // join the current run: predecessors are the previous run
-        rs = s.z & kPosMask;
-        rl = s.w;
-        rc = s.z >> 30;
-        uint32_t cc = (s.y >> 30) + 1u;
-        if (cc > 3u) cc = 3u;
-        s.y = (uint32_t)gpos | (cc << 30);
-      } else {
-        // start a new run: predecessors are the current run
-        if (ck != (uint32_t)kKindNone) {
-          rs = s.x & kPosMask;
-          rl = s.y & kPosMask;
-          rc = s.y >> 30;
-        }
-        s.z = (s.x & kPosMask) | (rc << 30);
-        s.w = s.y & kPosMask;
-        s.x = (uint32_t)gpos | ((uint32_t)pc << 30);
-        s.y = (uint32_t)gpos | (1u << 30);
-      }
-      w.cell[c] = s;
+      apply_cell(w, c, gpos, pc, rs, rl, rc);
       if (rc >= 1u) m1 = (int)(uint32_t)entry_at(x, w, (int)rs);
       if (rc >= 2u) m2 = (int)(uint32_t)entry_at(x, w, (int)rl);
     }
@@ -211,6 +232,89 @@ __device__ void mark_box(const Ctx& x, const WarpSmem& w, const Box& b) {
     int c = (b.y0 + i / bw) * x.tw + b.x0 + i % bw;
     w.scr[c] = (uint8_t)combine_priv(w.scr[c], (uint32_t)b.priv);
   }
+}
+
+// adds one predecessor to this lane's buffer (lane-parallel path)
+__device__ __forceinline__ void lane_add(const WarpSmem& w, const SweepOut& o, int lane, int& nb, int src,
+                                         int dst) {
+  for (int k = 0; k < nb; ++k)
+    if (w.lbuf[lane * kLaneBuf + k] == src) return;
+  if (nb < kLaneBuf) {
+    w.lbuf[lane * kLaneBuf + nb++] = src;
+  } else {
+    put_pair(o, atomicAdd(o.cursor, 1ull), pair_key(src, dst, o.key_bits));
+  }
+}
+
+// Lane-parallel processing of a staged window whose candidates [0, end) are all
+// small boxes: one candidate per lane. Candidates of different tasks whose
+// boxes overlap are ordered by levels (a candidate runs one round after every
+// earlier candidate it overlaps), so within a round lanes touch disjoint cells
+// and each cell still sees its accesses in program order. A task's several
+// candidates must be disjoint here (no privilege combination needed). Returns
+// false (nothing done) when the window does not qualify.
+__device__ bool stage_lanes(Ctx& x, const WarpSmem& w, const SweepOut& o, unsigned starts, int end) {
+  const int lane = x.lane;
+  const bool mine = lane < end;
+  Box b = unpack_entry(mine ? w.stage[lane] : 0ull, x.ndim);
+  const int cells = mine ? (b.x1 - b.x0 + 1) * (b.y1 - b.y0 + 1) : 0;
+  if (!__all_sync(kFull, cells <= kSmallCells)) return false;
+  // position of this candidate's task (its group's first candidate)
+  const unsigned upto = lane == 31 ? starts : (starts & ((2u << lane) - 1u));
+  const int gpos = x.pos + (upto ? 31 - __clz((int)upto) : 0);
+  int level = 0;
+  bool bad = false;
+  for (int j = 0; j < end; ++j) {
+    const int x0 = __shfl_sync(kFull, b.x0, j), x1 = __shfl_sync(kFull, b.x1, j);
+    const int y0 = __shfl_sync(kFull, b.y0, j), y1 = __shfl_sync(kFull, b.y1, j);
+    const int tj = __shfl_sync(kFull, b.task, j), lj = __shfl_sync(kFull, level, j);
+    if (mine && lane > j && b.x0 <= x1 && x0 <= b.x1 && b.y0 <= y1 && y0 <= b.y1) {
+      if (tj == b.task) bad = true;
+      else if (lj + 1 > level) level = lj + 1;
+    }
+  }
+  if (__any_sync(kFull, bad)) return false;
+  int maxl = level;
+#pragma unroll
+  for (int o2 = 16; o2 >= 1; o2 >>= 1) maxl = max(maxl, __shfl_xor_sync(kFull, maxl, o2));
+  if (maxl >= kMaxRounds) return false;  // nothing applied yet: the warp-wide path takes the window
+  for (int r = 0; r <= maxl; ++r) {
+    int nb = 0;
+    if (mine && level == r) {
+      const int bw = b.x1 - b.x0 + 1;
+      for (int i = 0; i < cells; ++i) {
+        const int cx = b.x0 + i % bw, cy = b.y0 + i / bw;
+        uint32_t rs, rl, rc;
+        apply_cell(w, cy * x.tw + cx, gpos, b.priv, rs, rl, rc);
+        if (rc >= 1u) lane_add(w, o, lane, nb, (int)(uint32_t)entry_at(x, w, (int)rs), b.task);
+        if (rc >= 2u) lane_add(w, o, lane, nb, (int)(uint32_t)entry_at(x, w, (int)rl), b.task);
+        if (rc == 3u) {
+          for (uint32_t q = rs + 1; q < rl; ++q) {
+            Box e = unpack_entry(entry_at(x, w, (int)q), x.ndim);
+            if (e.x0 <= cx && cx <= e.x1 && e.y0 <= cy && cy <= e.y1) lane_add(w, o, lane, nb, e.task, b.task);
+          }
+        }
+      }
+    }
+    // emit every lane's buffer into the warp's chunk
+    int incl = nb;
+#pragma unroll
+    for (int o2 = 1; o2 < 32; o2 <<= 1) {
+      const int y = __shfl_up_sync(kFull, incl, o2);
+      if (lane >= o2) incl += y;
+    }
+    const int total = __shfl_sync(kFull, incl, 31);
+    if (total > 0) {
+      reserve_pairs(x, o, (uint32_t)total);
+      const int base = incl - nb;
+      for (int k = 0; k < nb; ++k)
+        put_pair(o, x.chunk_base + base + k, pair_key(w.lbuf[lane * kLaneBuf + k], b.task, o.key_bits));
+      x.chunk_base += total;
+      x.chunk_left -= total;
+    }
+    __syncwarp();
+  }
+  return true;
 }
 
 // one task's candidates at positions [a, b) of the tile list
@@ -271,6 +375,7 @@ __global__ void __launch_bounds__(256) k_sweep(const uint64_t* __restrict__ payl
   w.hlist = w.htab + kHashSlots;
   w.hslot = w.hlist + kListCap;
   w.hcount = w.hslot + kListCap;
+  w.lbuf = w.hcount + 4;
   for (int i = lane; i < kHashSlots; i += 32) w.htab[i] = -1;
   if (lane == 0) *w.hcount = 0;
   __syncwarp();
@@ -332,6 +437,7 @@ __global__ void __launch_bounds__(256) k_sweep(const uint64_t* __restrict__ payl
         continue;
       }
       unsigned gs = starts & (end == 32 ? kFull : ((1u << end) - 1u));
+      if (stage_lanes(x, w, o, gs, end)) gs = 0;
       while (gs) {
         const int a = __ffs((int)gs) - 1;
         gs &= gs - 1;

@@ -30,8 +30,8 @@ RT_GRAPH_TICKETS, RT_GRAPH_PROFILE = 1, 2
 EXPORTS = ["rt_graph_create", "rt_graph_destroy", "rt_graph_clear", "rt_launch_batch", "rt_analyze",
            "rt_get_csr", "rt_copy_csr", "rt_graph_exec_config", "rt_execute", "rt_replay", "rt_sync", "rt_graph_stats",
            "rt_get_tickets", "rt_copy_tickets", "rt_debug_hold_task", "rt_batch_create",
-           "rt_batch_execute", "rt_batch_sync", "rt_batch_destroy", "rt_last_error", "rt_device_info",
-           "rt_kernel_launches", "rt_execute_csr_static"]
+           "rt_batch_execute", "rt_batch_sync", "rt_batch_counters", "rt_batch_destroy", "rt_last_error", "rt_device_info",
+           "rt_kernel_launches", "rt_execute_csr_static", "rt_microbench_atomics"]
 
 
 class GrtError(RuntimeError):
@@ -56,10 +56,15 @@ class rt_graph_stats_t(ctypes.Structure):
                 ("ms_sweep", ctypes.c_float), ("ms_sort_pairs", ctypes.c_float), ("ms_csr", ctypes.c_float),
                 ("ms_execute", ctypes.c_float), ("ms_exec_kernel", ctypes.c_float),
                 ("exec_blocks", ctypes.c_int32), ("exec_threads", ctypes.c_int32),
-                ("ms_sweep_kernel", ctypes.c_float)]
+                ("ms_sweep_kernel", ctypes.c_float), ("pad0", ctypes.c_int32),
+                ("exec_counters", ctypes.c_int64 * 9)]
+
+    COUNTER_NAMES = ("batches", "tasks", "edges", "claims", "cas_fail", "pushed", "idle", "slot_wait", "kept")
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("pad0", "exec_counters")}
+        d["exec_counters"] = dict(zip(self.COUNTER_NAMES, list(self.exec_counters)))
+        return d
 
 
 _lib = None
@@ -94,9 +99,11 @@ def load(path: str = LIB_PATH):
         "rt_graph_exec_config": [P, i32, i32, i32, i32],
         "rt_batch_sync": [P, ctypes.POINTER(ctypes.c_float)],
         "rt_batch_destroy": [P],
+        "rt_batch_counters": [P, ctypes.POINTER(i64), i32],
         "rt_device_info": [ctypes.POINTER(i32), ctypes.POINTER(i32)],
         "rt_kernel_launches": [ctypes.POINTER(i64)],
         "rt_execute_csr_static": [P, P, P, i32, i64, i32, P, P],
+        "rt_microbench_atomics": [ctypes.POINTER(ctypes.c_double), i32, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -176,6 +183,15 @@ def rt_execute_csr_static(row_ptr, col, indeg, n_tasks: int, n_edges: int, spin_
     """Executes a caller-held CSR (device pointers) with SPIN bodies, allocating
     nothing; see include/grt.h for the limits and the sharing rule."""
     _check(load().rt_execute_csr_static(row_ptr, col, indeg, n_tasks, n_edges, spin_iters, out, stream))
+
+
+def rt_microbench_atomics(stream=None) -> dict:
+    """The executor's measured rooflines (see include/grt.h)."""
+    out = (ctypes.c_double * 6)()
+    _check(load().rt_microbench_atomics(out, 6, stream))
+    names = ("dep_atomic_ns", "dep_l2_load_ns", "scatter_atomic_gops", "scatter_red_gops",
+             "contended_atomic_gops", "contended_warp_agg_gops")
+    return dict(zip(names, list(out)))
 
 
 def rt_last_error() -> str:
@@ -314,6 +330,11 @@ class Batch:
         ms = ctypes.c_float()
         _check(load().rt_batch_sync(self.h, ctypes.byref(ms)))
         return ms.value
+
+    def counters(self) -> dict:
+        arr = (ctypes.c_int64 * 9)()
+        _check(load().rt_batch_counters(self.h, arr, 9))
+        return dict(zip(rt_graph_stats_t.COUNTER_NAMES, list(arr)))
 
     def close(self):
         if self.h:

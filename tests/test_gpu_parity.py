@@ -239,3 +239,13 @@ def test_taskbench_full_size(pattern):
     src = np.repeat(np.arange(tr.n), np.diff(rp))
     assert (t[src, 1] < t[col, 0]).all()
     g.close()
+
+
+def test_microbench_reports_plausible_rooflines():
+    from gpu_helpers import ensure_built
+    ensure_built()
+    mb = grt.rt_microbench_atomics()
+    assert 50 < mb["dep_atomic_ns"] < 20000
+    assert 50 < mb["dep_l2_load_ns"] < 20000
+    for k in ("scatter_atomic_gops", "scatter_red_gops", "contended_atomic_gops", "contended_warp_agg_gops"):
+        assert 0.01 < mb[k] < 10000, (k, mb[k])
