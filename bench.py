@@ -98,6 +98,50 @@ def run_batched(grt, torch, flush, steps):
     return out
 
 
+SERVE_REQUESTS, SERVE_RATE = 2000, 50_000.0
+
+
+def run_served(grt, n_requests=SERVE_REQUESTS):
+    """configs[4]: Poisson arrivals (mean 50k graphs/s) of graphs with task
+    counts log-uniform 32..16384, 1-4 rects per launch on a 1024^2 grid (sides
+    log-uniform 4..256), admitted under an 8 GB device-memory budget. Requests
+    are submitted when due and stamped with their due time, so submission lag
+    counts as latency."""
+    t0 = time.perf_counter()
+    reqs = tg.served_stream(n_requests, rate_per_s=SERVE_RATE, seed=0)
+    gen_s = time.perf_counter() - t0
+    srv = grt.Server(2, [0, 0], [1023, 1023], body=grt.RT_BODY_EMPTY, budget_bytes=8 << 30, max_inflight=64,
+                     max_tasks=16384, workers=8, tile=TILE)
+    for r in reqs[:16]:  # warm-up: grow the pool's buffers
+        srv.submit(r.trace)
+    srv.drain()
+    base = grt.rt_now_ns() + 2_000_000
+    tickets = []
+    for r in reqs:
+        due = base + r.arrival_ns
+        while grt.rt_now_ns() < due:
+            pass
+        tickets.append(srv.submit(r.trace, arrival_ns=due))
+    srv.drain()
+    infos = [srv.poll(t) for t in tickets]
+    srv.close()
+    assert all(i["state"] == 3 for i in infos)
+    lat = np.array([i["done_ns"] - i["arrival_ns"] for i in infos]) / 1e6
+    svc = np.array([i["done_ns"] - i["admit_ns"] for i in infos]) / 1e6
+    ana = np.array([i["posted_ns"] - i["admit_ns"] for i in infos]) / 1e6
+    span = (max(i["done_ns"] for i in infos) - base) / 1e9
+    tasks = sum(i["n_tasks"] for i in infos)
+    return {"workload": f"{n_requests} requests, Poisson arrivals at {SERVE_RATE:.0f} graphs/s, task counts "
+                        "log-uniform 32..16384, 1-4 rects per launch on 1024^2 (sides log-uniform 4..256), "
+                        "EMPTY bodies, 8 GB budget, 64 slots, 8 analysis workers",
+            "requests": n_requests, "tasks": tasks, "offered_graphs_per_s": SERVE_RATE,
+            "achieved_graphs_per_s": n_requests / span, "tasks_per_s": tasks / span,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "service_ms": {"p50": float(np.percentile(svc, 50)), "p99": float(np.percentile(svc, 99))},
+            "analysis_ms": {"p50": float(np.percentile(ana, 50)), "p99": float(np.percentile(ana, 99))},
+            "generate_s": gen_s}
+
+
 # ---------------------------------------------------------------------------
 # the oracle, timed on host cores (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
@@ -331,6 +375,9 @@ def run_ours(args):
     batched = None
     if world == 1 and not args.no_batched:
         batched = run_batched(grt, torch, flush, max(1, min(args.steps, 3)))
+    served = None
+    if world == 1 and not args.no_served:
+        served = run_served(grt)
 
     # the executor's own rooflines (dependent atomic latency, scattered atomics)
     mb = grt.rt_microbench_atomics()
@@ -371,7 +418,7 @@ def run_ours(args):
                     "validation": "on the device (RT_LAUNCH_DEFER_CHECK)"},
                 "roofline": roof, "atomic_roofline": atomic_roof, "cpu_baseline": cpu, "clocks": clk,
                 "gpu_launches": launches,
-                "batched": batched,
+                "batched": batched, "served": served,
                 "wall_s_timed": wall,
                 "phases_ms_per_graph": [{k: round(v, 4) for k, v in a.items()} for a in avg]}
         print(json.dumps(line), flush=True)
@@ -392,6 +439,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--graph-steps", type=int, default=STEPS, help="profiling only: fewer steps per graph")
     ap.add_argument("--patterns", default=",".join(tg.PATTERNS), help="profiling only: subset of patterns")
     args = ap.parse_args()

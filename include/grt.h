@@ -240,6 +240,75 @@ rt_status rt_batch_sync(rt_batch_t b, float* ms_kernel);
 rt_status rt_batch_counters(rt_batch_t b, int64_t* out, int32_t n);
 rt_status rt_batch_destroy(rt_batch_t b);
 
+/* ---- serving (continuous batching) ---------------------------------------
+ * A server analyses requests (each a graph of launches with region
+ * requirements) as they arrive and executes them in one persistent kernel that
+ * admits new graphs while others are still running (Section 4.1: each graph
+ * runs as one operation; Section 2.2: dependences inferred from data usage).
+ * Requests are admitted in arrival order while a slot is free and the device
+ * memory they would hold fits the budget; analysis runs on `workers` host
+ * threads, each with its own stream, concurrently with the executing kernel. */
+typedef struct rt_server* rt_server_t;
+
+typedef struct {
+  int32_t ndim;                  /* every request shares this domain and tiling */
+  int64_t dom_lo[2], dom_hi[2];
+  int32_t tile_w, tile_h;        /* 0 = library default */
+  int32_t body;                  /* RT_BODY_EMPTY or RT_BODY_SPIN */
+  int32_t spin_iters;
+  int64_t budget_bytes;          /* device memory admitted requests may hold at once */
+  int32_t max_inflight;          /* graphs admitted at once, 1..1024 */
+  int32_t max_tasks;             /* tasks of the largest request accepted */
+  int32_t workers;               /* host threads analysing requests, 1..64 */
+  int32_t keep_results;          /* keep each request's CSR (and SPIN outputs) */
+  int32_t exec_blocks, exec_warps;  /* serving kernel shape, 0 = default */
+  int64_t timeout_ns;            /* stall limit of the serving kernel, 0 = 2 s */
+} rt_server_desc;
+
+typedef struct {
+  int32_t state;                 /* 0 queued, 1 analysing, 2 running, 3 done, 4 failed */
+  int32_t status;                /* rt_status of a failed request */
+  int64_t arrival_ns, admit_ns, posted_ns, done_ns;  /* rt_now_ns clock */
+  int64_t n_tasks, n_edges, footprint_bytes;
+} rt_request_info;
+
+/* CLOCK_MONOTONIC nanoseconds: the clock of arrival and completion stamps. */
+int64_t rt_now_ns(void);
+
+/* Starts a server: allocates its graph pool, ring and mapped mailbox, launches
+ * the serving kernel on its own stream and starts the worker threads. Errors:
+ * RT_ERR_INVALID, RT_ERR_OOM, RT_ERR_CUDA. */
+rt_status rt_server_create(const rt_server_desc* desc, rt_server_t* out);
+
+/* Queues one request: n launches as in rt_launch_batch (host arrays, copied
+ * before returning; no explicit preds). arrival_ns stamps its arrival (use
+ * rt_now_ns()). Errors: RT_ERR_INVALID (bad arrays, more than max_tasks),
+ * RT_ERR_BUDGET (it could never fit the budget), RT_ERR_STATE (stopping). */
+rt_status rt_server_submit(rt_server_t s, int32_t n, const int32_t* req_off, const int64_t* lo,
+                           const int64_t* hi, const uint8_t* priv, int64_t arrival_ns, int64_t* ticket);
+
+/* State and timings of one request (non-blocking). */
+rt_status rt_server_poll(rt_server_t s, int64_t ticket, rt_request_info* info);
+
+/* With keep_results: copies a finished request's canonical CSR (row_ptr
+ * int32[n+1], col int32[E]) and, for SPIN, its outputs (int32[n]) into host
+ * buffers (any may be NULL). RT_ERR_STATE if it is not done. */
+rt_status rt_server_result(rt_server_t s, int64_t ticket, int32_t* row_ptr, int32_t* col, int32_t* out);
+
+/* Waits until every submitted request is done or failed (or timeout_ns
+ * passes: RT_ERR_TIMEOUT), or the serving kernel reported a stall. */
+rt_status rt_server_drain(rt_server_t s, int64_t timeout_ns);
+
+/* Diagnostics: out[0] activations posted, [1] taken by the kernel, [2]
+ * finished, [3] kernel status, [4] tasks executed, [5] requests queued, [6]
+ * analysing, [7] running, [8] 1 while the serving kernel runs. */
+rt_status rt_server_stats(rt_server_t s, int64_t* out, int32_t n);
+
+/* Drains (30 s at most), asks the serving kernel to stop once idle (forcing it
+ * after 10 s), joins the threads and frees everything. If the kernel cannot be
+ * stopped its resources are left to the process exit: RT_ERR_TIMEOUT. */
+rt_status rt_server_destroy(rt_server_t s);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* rt_last_error(void);
 

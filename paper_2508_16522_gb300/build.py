@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(HERE, "_lib")
 SO = os.path.join(LIBDIR, "libgrt.so")
-SOURCES = ["primitives.cu", "analysis.cu", "sweep.cu", "exec.cu", "static_exec.cu", "microbench.cu", "api.cu"]
+SOURCES = ["primitives.cu", "analysis.cu", "sweep.cu", "exec.cu", "static_exec.cu", "microbench.cu", "serve.cu", "server.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -63,7 +63,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
                 raise RuntimeError("nvcc failed: " + " ".join(cmd))
     if force or jobs or not os.path.exists(SO):
         tmp = SO + f".tmp{os.getpid()}"
-        subprocess.check_call([cc, "-shared", "-o", tmp] + objs + ARCH + ["-lcudart"])
+        subprocess.check_call([cc, "-shared", "-o", tmp] + objs + ARCH + ["-lcudart", "-Xcompiler", "-pthread"])
         os.replace(tmp, SO)
     return SO
 

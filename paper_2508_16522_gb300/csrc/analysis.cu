@@ -310,4 +310,19 @@ void launch_roots_emit(const int32_t* indeg, const uint32_t* pos, int32_t n, int
   }
 }
 
+void preload_analysis() {
+  cudaFuncAttributes a;
+  cudaFuncGetAttributes(&a, k_validate_tasks);
+  cudaFuncGetAttributes(&a, k_validate_rects);
+  cudaFuncGetAttributes(&a, k_add_offset);
+  cudaFuncGetAttributes(&a, k_bin_count);
+  cudaFuncGetAttributes(&a, k_bin_expand);
+  cudaFuncGetAttributes(&a, k_segments);
+  cudaFuncGetAttributes(&a, k_explicit_pairs);
+  cudaFuncGetAttributes(&a, k_unique_flags);
+  cudaFuncGetAttributes(&a, k_emit_csr);
+  cudaFuncGetAttributes(&a, k_root_flags);
+  cudaFuncGetAttributes(&a, k_roots_emit);
+}
+
 }  // namespace grt

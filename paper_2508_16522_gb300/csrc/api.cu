@@ -8,7 +8,10 @@
 
 #include <algorithm>
 #include <cstdarg>
+#include <mutex>
 #include <cstdio>
+#include <cstdlib>
+#include <time.h>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -43,7 +46,10 @@ rt_status fail(rt_status s, const char* fmt, ...) {
     if (r_ != RT_OK) return r_;             \
   } while (0)
 
-// grow-only device buffer
+// grow-only device buffer, allocated stream-ordered on its owner's stream:
+// cudaMallocAsync / cudaFreeAsync never wait for work on other streams (a
+// plain cudaFree would wait for the whole device, including a serving kernel
+// that runs for the life of a server)
 struct DevBuf {
   void* p = nullptr;
   size_t cap = 0;
@@ -52,22 +58,22 @@ struct DevBuf {
     size_t nc = std::max<size_t>(bytes, keep ? cap * 2 : bytes);
     nc = std::max<size_t>(nc, 256);
     void* np = nullptr;
-    cudaError_t e = cudaMalloc(&np, nc);
+    cudaError_t e = cudaMallocAsync(&np, nc, s);
     if (e != cudaSuccess) {
       cudaGetLastError();
-      return fail(RT_ERR_OOM, "cudaMalloc(%zu bytes): %s", nc, cudaGetErrorString(e));
+      return fail(RT_ERR_OOM, "cudaMallocAsync(%zu bytes): %s", nc, cudaGetErrorString(e));
     }
     if (keep && p) {
       e = cudaMemcpyAsync(np, p, keep, cudaMemcpyDeviceToDevice, s);
       if (e != cudaSuccess) return fail(RT_ERR_CUDA, "grow copy: %s", cudaGetErrorString(e));
     }
-    if (p) cudaFree(p);  // synchronous: the copy above has finished
+    if (p) cudaFreeAsync(p, s);  // ordered after the copy on the same stream
     p = np;
     cap = nc;
     return RT_OK;
   }
-  void release() {
-    if (p) cudaFree(p);
+  void release(cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
     p = nullptr;
     cap = 0;
   }
@@ -82,10 +88,12 @@ struct DeviceInfo {
   int device = -1, num_sms = 0, exec_bps = 0;
 };
 DeviceInfo g_dev;
+std::mutex g_dev_mu;
 
 rt_status ensure_device() {
   int dev = -1;
   CK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_dev_mu);
   if (g_dev.init && g_dev.device == dev) return RT_OK;
   cudaDeviceProp prop;
   CK(cudaGetDeviceProperties(&prop, dev));
@@ -268,7 +276,8 @@ rt_status rt_graph_destroy(rt_graph_t g) {
                     &g->seg_b, &g->seg_e, &g->pairs, &g->pairs_alt, &g->flags, &g->upos, &g->col,
                     &g->row_ptr, &g->indeg, &g->count, &g->rootpos, &g->root_items, &g->ws, &g->misc, &g->adj,
                     &g->ring, &g->ctrl, &g->gtable, &g->done_g, &g->tickets};
-  for (DevBuf* b : bufs) b->release();
+  for (DevBuf* b : bufs) b->release(g->s);
+  cudaStreamSynchronize(g->s);
   if (g->hpin) cudaFreeHost(g->hpin);
   if (g->ev_ok)
     for (int i = 0; i < EV_COUNT; ++i) cudaEventDestroy(g->ev[i]);
@@ -382,6 +391,7 @@ extern "C" rt_status rt_launch_batch(rt_graph_t g, int32_t n, const int32_t* req
   if (first[1] != 0) return fail(RT_ERR_INVALID, "pred_off[0] must be 0");
   if (g->R + R >= (int64_t)INT32_MAX || g->P + Pb >= (int64_t)INT32_MAX)
     return fail(RT_ERR_INVALID, "too many rects or preds");
+  trace("launch_batch: validated");
 
   const int32_t n0 = g->n;
   const int64_t R0 = g->R, P0 = g->P;
@@ -438,6 +448,7 @@ extern "C" rt_status rt_launch_batch(rt_graph_t g, int32_t n, const int32_t* req
     g->pending_validate = true;
   }
   CK(cudaGetLastError());
+  trace("launch_batch: copies enqueued");
   g->n += n;
   g->R += R;
   g->P += Pb;
@@ -473,7 +484,9 @@ rt_status run_analysis(rt_graph* g) {
   const int B = std::max(bits_for((uint64_t)n), 1);  // pair key = src << B | dst
   if (2 * B > 62) return fail(RT_ERR_OOM, "too many tasks for 64-bit pair keys");
   const int64_t ntiles = (int64_t)d.ntx * d.nty;
+  trace("analyze: start");
   CKR(g->misc.reserve(256, s));
+  trace("analyze: misc reserved");
   unsigned long long* cursor = reinterpret_cast<unsigned long long*>(g->misc.p);
   uint32_t* tile_counter = reinterpret_cast<uint32_t*>(g->misc.as<char>() + 64);
   volatile uint64_t* h64 = reinterpret_cast<volatile uint64_t*>(g->hpin);  // 32 x u64
@@ -493,7 +506,9 @@ rt_status run_analysis(rt_graph* g) {
   }
   h64[1] = 0;
   if (g->pending_validate) CK(cudaMemcpyAsync((void*)&h64[1], g->err.p, 4, cudaMemcpyDeviceToHost, s));
+  trace("analyze: bin count enqueued");
   if (R > 0 || g->pending_validate) CK(cudaStreamSynchronize(s));
+  trace("analyze: bin count synced");
   if (g->pending_validate && (uint32_t)h64[1] != 0u)
     return fail(RT_ERR_INVALID, "device validation: %s", err_bits_text((uint32_t)h64[1]));
   g->pending_validate = false;
@@ -508,6 +523,7 @@ rt_status run_analysis(rt_graph* g) {
     CKR(g->seg_b.reserve((size_t)ntiles * 4, s));
     CKR(g->seg_e.reserve((size_t)ntiles * 4, s));
     CKR(reserve_ws(g, radix_ws_bytes(M)));
+    trace("analyze: entry buffers reserved");
     launch_bin_expand(g->rect_task.as<int32_t>(), g->lo.as<int64_t>(), g->hi.as<int64_t>(),
                       g->priv.as<uint8_t>(), R, g->cnt.as<uint64_t>(), d, g->keys.as<uint32_t>(),
                       g->pay.as<uint64_t>(), s);
@@ -549,8 +565,10 @@ rt_status run_analysis(rt_graph* g) {
     launch_sweep(spay, g->seg_b.as<uint32_t>(), g->seg_e.as<uint32_t>(), d, o, std::max(blocks, 1), s);
     if (prof) CK(cudaEventRecord(g->ev[EV_SW1], s));
     CK(cudaGetLastError());
+    trace("analyze: sweep enqueued");
     CK(cudaMemcpyAsync((void*)&h64[3], cursor, 8, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    trace("analyze: sweep synced");
     Ptot = (int64_t)h64[3];
     if ((unsigned long long)Ptot <= cap) break;
     cap = (unsigned long long)Ptot + (Ptot >> 3);  // the sweep counted what it needed: rerun once
@@ -591,7 +609,9 @@ rt_status run_analysis(rt_graph* g) {
   if (prof) CK(cudaEventRecord(g->ev[EV_CSR], s));
   CK(cudaMemcpyAsync(g->hpin + 8, g->upos.as<uint32_t>() + Ptot, 4, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(g->hpin + 9, g->rootpos.as<uint32_t>() + n, 4, cudaMemcpyDeviceToHost, s));
+  trace("analyze: csr enqueued");
   CK(cudaStreamSynchronize(s));
+  trace("analyze: csr synced");
   CK(cudaGetLastError());
   g->n_edges = g->hpin[8];
   g->n_roots = g->hpin[9];
@@ -1063,7 +1083,8 @@ rt_status rt_batch_destroy(rt_batch_t b) {
   if (!b) return RT_OK;
   cudaStreamSynchronize(b->s);
   DevBuf* bufs[] = {&b->row_ptr, &b->col, &b->indeg, &b->count, &b->root_items, &b->gtable, &b->done_g, &b->ring, &b->ctrl, &b->adj};
-  for (DevBuf* x : bufs) x->release();
+  for (DevBuf* x : bufs) x->release(b->s);
+  cudaStreamSynchronize(b->s);
   if (b->hpin) cudaFreeHost(b->hpin);
   if (b->e0) cudaEventDestroy(b->e0);
   if (b->e1) cudaEventDestroy(b->e1);
@@ -1136,3 +1157,40 @@ extern "C" rt_status rt_microbench_atomics(double* out, int32_t n, void* stream)
   if (st != RT_OK) return fail(st, "microbenchmark: %s", why);
   return RT_OK;
 }
+
+namespace grt {
+void set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+
+void trace(const char* what) {
+  static const bool on = [] {
+    const char* e = getenv("GRT_TRACE");
+    return e && e[0] == '1';
+  }();
+  if (!on) return;
+  timespec ts;
+  clock_gettime(CLOCK_MONOTONIC, &ts);
+  fprintf(stderr, "[grt %ld.%06ld] %s\n", (long)ts.tv_sec, ts.tv_nsec / 1000, what);
+  fflush(stderr);
+}
+
+rt_status graph_view(rt_graph_t g, GraphView* v) {
+  if (!g || !v) return fail(RT_ERR_INVALID, "NULL argument");
+  if (!g->analyzed) return fail(RT_ERR_STATE, "graph not analyzed");
+  v->adj = g->adj.as<int4>();
+  v->col = g->col.as<int32_t>();
+  v->count = g->count.as<int32_t>();
+  v->roots = g->root_items.as<uint64_t>();
+  v->n = g->n;
+  v->n_roots = (int32_t)g->n_roots;
+  v->n_edges = g->n_edges;
+  size_t f = 0;
+  const DevBuf* bufs[] = {&g->req_off, &g->lo, &g->hi, &g->priv, &g->pred_off, &g->pred, &g->body_arg, &g->err,
+                          &g->rect_task, &g->cnt, &g->keys, &g->keys_alt, &g->pay, &g->pay_alt, &g->seg_b,
+                          &g->seg_e, &g->pairs, &g->pairs_alt, &g->flags, &g->upos, &g->col, &g->row_ptr,
+                          &g->indeg, &g->count, &g->rootpos, &g->root_items, &g->ws, &g->misc, &g->adj,
+                          &g->ring, &g->ctrl, &g->gtable, &g->done_g, &g->tickets};
+  for (const DevBuf* b : bufs) f += b->cap;
+  v->footprint = f;
+  return RT_OK;
+}
+}  // namespace grt

@@ -520,4 +520,20 @@ void launch_exec(ExecParams p, int blocks, int warps, cudaStream_t s) {
 #undef GRT_EXEC
 }
 
+void preload_exec() {
+  cudaFuncAttributes a;
+  cudaFuncGetAttributes(&a, k_reset_counts);
+  cudaFuncGetAttributes(&a, k_seed);
+  cudaFuncGetAttributes(&a, k_pack_adj);
+  cudaFuncGetAttributes(&a, k_rebase_roots);
+  cudaFuncGetAttributes(&a, k_exec<false, false, true>);
+  cudaFuncGetAttributes(&a, k_exec<false, true, true>);
+  cudaFuncGetAttributes(&a, k_exec<true, false, true>);
+  cudaFuncGetAttributes(&a, k_exec<true, true, true>);
+  cudaFuncGetAttributes(&a, k_exec<false, false, false>);
+  cudaFuncGetAttributes(&a, k_exec<false, true, false>);
+  cudaFuncGetAttributes(&a, k_exec<true, false, false>);
+  cudaFuncGetAttributes(&a, k_exec<true, true, false>);
+}
+
 }  // namespace grt

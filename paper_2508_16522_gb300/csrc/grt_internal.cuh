@@ -10,6 +10,9 @@
 
 namespace grt {
 
+// opt-in host trace (environment GRT_TRACE=1): one timestamped line per step
+void trace(const char* what);
+
 // number of kernels this library has launched (reported by rt_kernel_launches)
 extern std::atomic<long long> g_kernel_launches;
 inline void count_launch(long long k = 1) { g_kernel_launches.fetch_add(k, std::memory_order_relaxed); }
@@ -173,6 +176,53 @@ struct ExecParams {
 };
 
 // ---------------------------------------------------------------------------
+// serving: one persistent executor admits analysed graphs while it runs
+// ---------------------------------------------------------------------------
+struct ServeSlot {         // device table entry of one admitted graph
+  const int4* adj;         // its trigger records
+  const int32_t* col;      // its CSR columns (successors past the inline ones)
+  int32_t* count;          // its countdown counters
+  const uint64_t* roots;   // its roots (low 32 bits: local task id)
+  int32_t* out;            // SPIN results, one per task (may be null for EMPTY)
+  int32_t n_tasks, n_roots, body, spin_iters;
+  uint32_t gen, pad[3];    // activation number, echoed at completion
+};
+
+struct ServeMailbox {      // host-mapped: written by the host, read by the kernel
+  volatile uint32_t posted;  // activations posted so far
+  volatile uint32_t stop;    // 1: leave once nothing is admitted or running
+  uint32_t pad[30];
+  volatile uint32_t queue[1024];  // slot of activation k at queue[k % 1024]
+};
+
+struct ServeDone {         // host-mapped: written by the kernel, read by the host
+  volatile uint32_t gen[1];  // per slot: gen of its last completed activation
+};
+
+struct ServeCtrl {         // device memory, hot words on separate lines
+  unsigned long long head, pad_h[15];  // ring tickets claimed
+  unsigned long long tail, pad_t[15];  // ring tickets reserved
+  uint32_t taken, pad_k[31];           // activations taken from the mailbox
+  uint32_t finished, status, pad_f[30];  // completed activations, error status
+  unsigned long long executed, pad_e[15];
+  unsigned long long counters[16];
+};
+
+struct ServeParams {
+  ServeSlot* slots;
+  uint32_t* done_s;        // per slot: tasks completed in its current activation
+  ServeCtrl* ctrl;
+  ServeMailbox* mail;      // device view of the mapped mailbox
+  uint32_t* done_gen;      // device view of the mapped completion words
+  uint64_t* items;         // circular ring, cap slots (power of two)
+  unsigned long long* seq; // per ring slot: sequence number
+  unsigned long long cap;
+  int32_t max_slots;
+  int32_t claim, keep;
+  int64_t timeout_ns;
+};
+
+// ---------------------------------------------------------------------------
 // kernels and launchers (defined in scan.cu, radix.cu, analysis.cu, exec.cu)
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -238,6 +288,26 @@ void launch_seed(ExecParams p, int64_t ring_clear, cudaStream_t s);
 void launch_exec(ExecParams p, int blocks, int warps, cudaStream_t s);
 int exec_max_blocks_per_sm(int warps);
 rt_status microbench(double* out, int n_out, cudaStream_t s, const char** why);
+void launch_serve_init(ServeParams p, cudaStream_t s);
+void preload_primitives();
+void preload_analysis();
+void preload_sweep();
+void preload_exec();
+void preload_serve();
+void set_last_error(const char* msg);
+void launch_serve(ServeParams p, int blocks, int warps, cudaStream_t s);
+
+// what the serving host code needs to know about an analysed graph
+struct GraphView {
+  const int4* adj;
+  const int32_t* col;
+  int32_t* count;
+  const uint64_t* roots;
+  int32_t n, n_roots;
+  int64_t n_edges;
+  size_t footprint;  // bytes of device memory the graph object holds
+};
+rt_status graph_view(rt_graph_t g, GraphView* v);
 int32_t static_max_tasks();
 rt_status static_execute(const int32_t* row_ptr, const int32_t* col, const int32_t* indeg, int32_t n,
                          int64_t n_edges, int32_t spin_iters, int32_t* out, cudaStream_t s,

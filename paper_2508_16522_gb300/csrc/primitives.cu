@@ -276,4 +276,21 @@ template int radix_sort<uint32_t>(uint32_t*, uint32_t*, uint64_t*, uint64_t*, in
 template int radix_sort<uint64_t>(uint64_t*, uint64_t*, uint64_t*, uint64_t*, int64_t, int, void*,
                                   cudaStream_t);
 
+// Loads every kernel of this file now (lazy module loading would otherwise
+// load a kernel at its first launch, which can wait on a running persistent
+// kernel, e.g. the serving kernel).
+void preload_primitives() {
+  cudaFuncAttributes a;
+  cudaFuncGetAttributes(&a, k_scan_reduce<uint32_t>);
+  cudaFuncGetAttributes(&a, k_scan_reduce<uint64_t>);
+  cudaFuncGetAttributes(&a, k_scan_down<uint32_t>);
+  cudaFuncGetAttributes(&a, k_scan_down<uint64_t>);
+  cudaFuncGetAttributes(&a, k_radix_hist<uint32_t>);
+  cudaFuncGetAttributes(&a, k_radix_hist<uint64_t>);
+  cudaFuncGetAttributes(&a, k_radix_scatter<uint32_t, true>);
+  cudaFuncGetAttributes(&a, k_radix_scatter<uint32_t, false>);
+  cudaFuncGetAttributes(&a, k_radix_scatter<uint64_t, true>);
+  cudaFuncGetAttributes(&a, k_radix_scatter<uint64_t, false>);
+}
+
 }  // namespace grt

@@ -469,4 +469,9 @@ void launch_sweep(const uint64_t* payload, const uint32_t* seg_begin, const uint
   k_sweep<<<blocks, warps * 32, bytes, s>>>(payload, seg_begin, seg_end, d, o);
 }
 
+void preload_sweep() {
+  cudaFuncAttributes a;
+  cudaFuncGetAttributes(&a, k_sweep);
+}
+
 }  // namespace grt

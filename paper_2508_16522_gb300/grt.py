@@ -31,7 +31,9 @@ EXPORTS = ["rt_graph_create", "rt_graph_destroy", "rt_graph_clear", "rt_launch_b
            "rt_get_csr", "rt_copy_csr", "rt_graph_exec_config", "rt_execute", "rt_replay", "rt_sync", "rt_graph_stats",
            "rt_get_tickets", "rt_copy_tickets", "rt_debug_hold_task", "rt_batch_create",
            "rt_batch_execute", "rt_batch_sync", "rt_batch_counters", "rt_batch_destroy", "rt_last_error", "rt_device_info",
-           "rt_kernel_launches", "rt_execute_csr_static", "rt_microbench_atomics"]
+           "rt_kernel_launches", "rt_execute_csr_static", "rt_microbench_atomics", "rt_now_ns",
+           "rt_server_create", "rt_server_submit", "rt_server_poll", "rt_server_result", "rt_server_drain",
+           "rt_server_stats", "rt_server_destroy"]
 
 
 class GrtError(RuntimeError):
@@ -46,6 +48,23 @@ class rt_graph_desc(ctypes.Structure):
                 ("state_elems", ctypes.c_int64), ("out", ctypes.c_void_p), ("out_elems", ctypes.c_int64),
                 ("stream", ctypes.c_void_p), ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
                 ("timeout_ns", ctypes.c_int64), ("flags", ctypes.c_int32)]
+
+
+class rt_server_desc(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int32), ("dom_lo", ctypes.c_int64 * 2), ("dom_hi", ctypes.c_int64 * 2),
+                ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("body", ctypes.c_int32),
+                ("spin_iters", ctypes.c_int32), ("budget_bytes", ctypes.c_int64), ("max_inflight", ctypes.c_int32),
+                ("max_tasks", ctypes.c_int32), ("workers", ctypes.c_int32), ("keep_results", ctypes.c_int32),
+                ("exec_blocks", ctypes.c_int32), ("exec_warps", ctypes.c_int32), ("timeout_ns", ctypes.c_int64)]
+
+
+class rt_request_info(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32), ("arrival_ns", ctypes.c_int64),
+                ("admit_ns", ctypes.c_int64), ("posted_ns", ctypes.c_int64), ("done_ns", ctypes.c_int64),
+                ("n_tasks", ctypes.c_int64), ("n_edges", ctypes.c_int64), ("footprint_bytes", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class rt_graph_stats_t(ctypes.Structure):
@@ -104,6 +123,13 @@ def load(path: str = LIB_PATH):
         "rt_kernel_launches": [ctypes.POINTER(i64)],
         "rt_execute_csr_static": [P, P, P, i32, i64, i32, P, P],
         "rt_microbench_atomics": [ctypes.POINTER(ctypes.c_double), i32, P],
+        "rt_server_create": [ctypes.POINTER(rt_server_desc), ctypes.POINTER(P)],
+        "rt_server_submit": [P, i32, P, P, P, P, i64, ctypes.POINTER(i64)],
+        "rt_server_poll": [P, i64, ctypes.POINTER(rt_request_info)],
+        "rt_server_result": [P, i64, P, P, P],
+        "rt_server_drain": [P, i64],
+        "rt_server_destroy": [P],
+        "rt_server_stats": [P, ctypes.POINTER(i64), i32],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -111,6 +137,8 @@ def load(path: str = LIB_PATH):
         f.restype = ctypes.c_int
     lib.rt_last_error.argtypes = []
     lib.rt_last_error.restype = ctypes.c_char_p
+    lib.rt_now_ns.argtypes = []
+    lib.rt_now_ns.restype = ctypes.c_int64
     _lib = lib
     return lib
 
@@ -359,3 +387,71 @@ def describe(st: dict) -> str:
 __all__ = [n for n in dir() if n.startswith("rt_") or n.startswith("RT_")] + [
     "Graph", "Batch", "GrtError", "load", "EXPORTS"]
 
+
+
+def rt_now_ns() -> int:
+    return int(load().rt_now_ns())
+
+
+class Server:
+    """Continuous-batching server: submit graphs (host arrays); each is
+    analysed by a worker thread and run by the persistent serving kernel."""
+
+    STATES = ("queued", "analysing", "running", "done", "failed")
+
+    def __init__(self, ndim, dom_lo, dom_hi, body=RT_BODY_EMPTY, spin_iters=256, budget_bytes=8 << 30,
+                 max_inflight=64, max_tasks=16384, workers=8, keep_results=False, tile=(0, 0),
+                 exec_blocks=0, exec_warps=0, timeout_ns=0):
+        d = rt_server_desc()
+        d.ndim = ndim
+        for k in range(ndim):
+            d.dom_lo[k] = int(dom_lo[k])
+            d.dom_hi[k] = int(dom_hi[k])
+        d.tile_w, d.tile_h = int(tile[0]), int(tile[1])
+        d.body, d.spin_iters = body, spin_iters
+        d.budget_bytes, d.max_inflight, d.max_tasks = budget_bytes, max_inflight, max_tasks
+        d.workers, d.keep_results = workers, int(bool(keep_results))
+        d.exec_blocks, d.exec_warps, d.timeout_ns = exec_blocks, exec_warps, timeout_ns
+        h = ctypes.c_void_p()
+        _check(load().rt_server_create(ctypes.byref(d), ctypes.byref(h)))
+        self.h = h.value
+
+    def submit(self, tr, arrival_ns=None) -> int:
+        t = ctypes.c_int64()
+        arrs = [np.ascontiguousarray(a) for a in (tr.req_off, tr.lo, tr.hi, tr.priv)]
+        _check(load().rt_server_submit(self.h, tr.n, *[a.ctypes.data for a in arrs],
+                                       rt_now_ns() if arrival_ns is None else int(arrival_ns), ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket) -> dict:
+        info = rt_request_info()
+        _check(load().rt_server_poll(self.h, ticket, ctypes.byref(info)))
+        return info.as_dict()
+
+    def result(self, ticket, n_tasks, n_edges, with_out=False):
+        rp = np.empty(n_tasks + 1, np.int32)
+        col = np.empty(max(n_edges, 1), np.int32)
+        out = np.empty(max(n_tasks, 1), np.int32) if with_out else None
+        _check(load().rt_server_result(self.h, ticket, rp.ctypes.data, col.ctypes.data,
+                                       None if out is None else out.ctypes.data))
+        return rp, col[:n_edges], (None if out is None else out[:n_tasks])
+
+    def stats(self) -> dict:
+        arr = (ctypes.c_int64 * 9)()
+        _check(load().rt_server_stats(self.h, arr, 9))
+        return dict(zip(("posted", "taken", "finished", "status", "executed", "queued", "analysing", "running",
+                         "kernel_running"), list(arr)))
+
+    def drain(self, timeout_ns=0):
+        _check(load().rt_server_drain(self.h, timeout_ns))
+
+    def close(self):
+        if self.h:
+            h, self.h = self.h, None
+            _check(load().rt_server_destroy(h))
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

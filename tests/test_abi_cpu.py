@@ -21,7 +21,7 @@ def lib():
 
 def declared_symbols():
     src = open(os.path.join(ROOT, "include", "grt.h")).read()
-    return sorted(set(re.findall(r"^(?:rt_status|const char\*)\s+(rt_\w+)\(", src, re.M)))
+    return sorted(set(re.findall(r"^(?:rt_status|const char\*|int64_t)\s+(rt_\w+)\(", src, re.M)))
 
 
 def test_exports_every_declared_symbol(lib):

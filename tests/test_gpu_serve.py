@@ -1,0 +1,104 @@
+"""Serving: requests analysed by worker threads and executed by one persistent
+kernel that admits new graphs while others run. Each request's result in the
+mix (canonical CSR and SPIN outputs) must equal its result alone."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2508_16522_gb300 import grt
+from paper_2508_16522_gb300 import tracegen as tg
+
+from gpu_helpers import ensure_built, oracle_csr
+
+pytestmark = pytest.mark.gpu
+
+GRID = (128, 128)
+
+
+def requests(k, seed, n_range=(32, 1500)):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(k):
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        out.append(tg.random_rects(grid=GRID, n=n, rects=(1, 4), side=(2, 32), seed=seed * 1000 + i))
+    return out
+
+
+def check_all(srv, tickets, traces, spin_iters):
+    for t, tr in zip(tickets, traces):
+        info = srv.poll(t)
+        assert info["state"] == 3, (tr.name, info)
+        assert info["arrival_ns"] <= info["admit_ns"] <= info["posted_ns"] <= info["done_ns"]
+        rp, col, out = srv.result(t, info["n_tasks"], info["n_edges"], with_out=True)
+        rp_o, col_o, _ = oracle_csr(tr)
+        assert np.array_equal(rp.astype(np.int64), rp_o) and np.array_equal(col, col_o), tr.name
+        want = np.array([oracle.spin(j, spin_iters) for j in range(tr.n)], np.uint32).view(np.int32)
+        assert np.array_equal(out, want), tr.name
+
+
+def test_burst_in_the_mix_equals_alone():
+    ensure_built()
+    traces = requests(60, seed=1)
+    srv = grt.Server(2, [0, 0], [GRID[0] - 1, GRID[1] - 1], body=grt.RT_BODY_SPIN, spin_iters=11,
+                     max_inflight=16, max_tasks=2048, workers=4, keep_results=True, budget_bytes=2 << 30)
+    tickets = [srv.submit(tr) for tr in traces]
+    srv.drain(60_000_000_000)
+    check_all(srv, tickets, traces, 11)
+    # the kernel keeps running: a second wave is admitted and executed too
+    more = requests(20, seed=2)
+    t2 = [srv.submit(tr) for tr in more]
+    srv.drain(60_000_000_000)
+    check_all(srv, t2, more, 11)
+    srv.close()
+
+
+def test_paced_arrivals_overlap_and_match():
+    ensure_built()
+    traces = requests(40, seed=3, n_range=(200, 2000))
+    srv = grt.Server(2, [0, 0], [GRID[0] - 1, GRID[1] - 1], body=grt.RT_BODY_SPIN, spin_iters=200,
+                     max_inflight=8, max_tasks=2048, workers=3, keep_results=True)
+    tickets = []
+    for tr in traces:
+        tickets.append(srv.submit(tr))
+        time.sleep(0.0005)
+    srv.drain(60_000_000_000)
+    check_all(srv, tickets, traces, 200)
+    infos = [srv.poll(t) for t in tickets]
+    # continuous batching: some request was admitted before an earlier one finished
+    overlap = any(infos[i + 1]["admit_ns"] < infos[i]["done_ns"] for i in range(len(infos) - 1))
+    assert overlap
+    srv.close()
+
+
+def test_small_budget_and_few_slots_serialise_but_stay_correct():
+    ensure_built()
+    traces = requests(12, seed=4, n_range=(100, 800))
+    # each request's estimate is ~8 MB + ...: a 40 MB budget admits at most a few
+    srv = grt.Server(2, [0, 0], [GRID[0] - 1, GRID[1] - 1], body=grt.RT_BODY_SPIN, spin_iters=5,
+                     max_inflight=2, max_tasks=1024, workers=2, keep_results=True, budget_bytes=40 << 20)
+    tickets = [srv.submit(tr) for tr in traces]
+    srv.drain(60_000_000_000)
+    check_all(srv, tickets, traces, 5)
+    # a request larger than max_tasks is refused outright
+    with pytest.raises(grt.GrtError) as e:
+        srv.submit(tg.random_rects(grid=GRID, n=1500, rects=(1, 1), side=(2, 3), seed=10))
+    assert e.value.status == grt.RT_ERR_INVALID
+    srv.close()
+
+
+def test_empty_request_and_budget_refusal():
+    ensure_built()
+    srv = grt.Server(2, [0, 0], [GRID[0] - 1, GRID[1] - 1], body=grt.RT_BODY_EMPTY, max_inflight=4,
+                     max_tasks=4096, workers=1, keep_results=True, budget_bytes=16 << 20)
+    empty = tg._finish(2, [0, 0], [GRID[0] - 1, GRID[1] - 1], np.zeros(0, np.int64), np.zeros(0, np.int64),
+                       np.zeros(0, np.int64), np.zeros(0, np.uint8))
+    t = srv.submit(empty)
+    srv.drain(10_000_000_000)
+    assert srv.poll(t)["state"] == 3
+    big = tg.random_rects(grid=GRID, n=4000, rects=(4, 4), side=(2, 4), seed=11)
+    with pytest.raises(grt.GrtError) as e:
+        srv.submit(big)  # estimate (> 16 MB) can never fit the budget
+    assert e.value.status == grt.RT_ERR_BUDGET
+    srv.close()
