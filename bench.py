@@ -124,8 +124,16 @@ def run_served(grt, n_requests=SERVE_REQUESTS):
         tickets.append(srv.submit(r.trace, arrival_ns=due))
     srv.drain()
     infos = [srv.poll(t) for t in tickets]
+    failed = []
+    for t, i in zip(tickets, infos):
+        if i["state"] != 3 and len(failed) < 3:
+            try:
+                srv.result(t, 0, 0)
+            except grt.GrtError as e:
+                failed.append(f"n={i['n_tasks']}: {e}")
     srv.close()
-    assert all(i["state"] == 3 for i in infos)
+    if failed:
+        raise RuntimeError("served requests failed: " + "; ".join(failed))
     lat = np.array([i["done_ns"] - i["arrival_ns"] for i in infos]) / 1e6
     svc = np.array([i["done_ns"] - i["admit_ns"] for i in infos]) / 1e6
     ana = np.array([i["posted_ns"] - i["admit_ns"] for i in infos]) / 1e6

@@ -292,7 +292,8 @@ rt_status rt_server_poll(rt_server_t s, int64_t ticket, rt_request_info* info);
 
 /* With keep_results: copies a finished request's canonical CSR (row_ptr
  * int32[n+1], col int32[E]) and, for SPIN, its outputs (int32[n]) into host
- * buffers (any may be NULL). RT_ERR_STATE if it is not done. */
+ * buffers (any may be NULL). RT_ERR_STATE if it is not done; a request that
+ * failed returns its own status, with the reason in rt_last_error(). */
 rt_status rt_server_result(rt_server_t s, int64_t ticket, int32_t* row_ptr, int32_t* col, int32_t* out);
 
 /* Waits until every submitted request is done or failed (or timeout_ns

@@ -545,9 +545,20 @@ rt_status run_analysis(rt_graph* g) {
 
   // ---- 4: sweep (+ explicit preds) ---------------------------------------
   const int64_t Pe = g->has_pred ? g->P : 0;
-  unsigned long long cap = (unsigned long long)Pe + (M > 0 ? std::max<unsigned long long>(2ull * M, 1ull << 16) : 0ull);
+  // Each sweep warp leaves holes in at most its last chunk, so the cursor ends
+  // below (pairs written) + (warps x chunk). The chunk is sized to keep that
+  // slack near half the first guess; an overflowed sweep has counted what it
+  // reserved, and a rerun with that much plus the slack always fits.
+  const int sweep_warps = sweep_warps_per_block(d.tw * d.th);
+  const int sweep_blocks =
+      (int)std::max<int64_t>(std::min<int64_t>((ntiles + sweep_warps - 1) / sweep_warps, (int64_t)g_dev.num_sms * 8), 1);
+  const unsigned long long W = (unsigned long long)sweep_blocks * (unsigned long long)sweep_warps;
+  const unsigned long long guess = M > 0 ? std::max<unsigned long long>(2ull * M, 1ull << 16) : 0ull;
+  uint32_t chunk = 32;
+  while (chunk < 512 && 2ull * chunk * W <= guess) chunk <<= 1;
+  unsigned long long cap = (unsigned long long)Pe + (M > 0 ? guess + W * chunk : 0ull);
   int64_t Ptot = Pe;
-  for (int attempt = 0; attempt < 4; ++attempt) {
+  for (int attempt = 0; attempt < 2; ++attempt) {
     CKR(g->pairs.reserve((size_t)std::max<unsigned long long>(cap, 1) * 8, s));
     CKR(g->pairs_alt.reserve((size_t)std::max<unsigned long long>(cap, 1) * 8, s));
     if (Pe > 0)
@@ -557,12 +568,9 @@ rt_status run_analysis(rt_graph* g) {
     h64[2] = (uint64_t)Pe;
     CK(cudaMemcpyAsync(cursor, (const void*)&h64[2], 8, cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(tile_counter, 0, 4, s));
-    SweepOut o{g->pairs.as<uint64_t>(), cap, cursor, tile_counter, B};
-    const int warps = sweep_warps_per_block(d.tw * d.th);
-    const int64_t want = (ntiles + warps - 1) / warps;
-    const int blocks = (int)std::min<int64_t>(want, (int64_t)g_dev.num_sms * 8);
+    SweepOut o{g->pairs.as<uint64_t>(), cap, cursor, tile_counter, B, chunk};
     if (prof) CK(cudaEventRecord(g->ev[EV_SW0], s));
-    launch_sweep(spay, g->seg_b.as<uint32_t>(), g->seg_e.as<uint32_t>(), d, o, std::max(blocks, 1), s);
+    launch_sweep(spay, g->seg_b.as<uint32_t>(), g->seg_e.as<uint32_t>(), d, o, sweep_blocks, s);
     if (prof) CK(cudaEventRecord(g->ev[EV_SW1], s));
     CK(cudaGetLastError());
     trace("analyze: sweep enqueued");
@@ -571,8 +579,8 @@ rt_status run_analysis(rt_graph* g) {
     trace("analyze: sweep synced");
     Ptot = (int64_t)h64[3];
     if ((unsigned long long)Ptot <= cap) break;
-    cap = (unsigned long long)Ptot + (Ptot >> 3);  // the sweep counted what it needed: rerun once
-    if (attempt == 3) return fail(RT_ERR_OOM, "pair buffer kept overflowing");
+    cap = (unsigned long long)Ptot + W * chunk;  // the sweep counted what it reserved: rerun once
+    if (attempt == 1) return fail(RT_ERR_OOM, "pair buffer overflowed twice");
   }
   if (Ptot >= (1ll << 31) - 1) return fail(RT_ERR_OOM, "%lld candidate pairs (limit 2^31)", (long long)Ptot);
   if (prof) CK(cudaEventRecord(g->ev[EV_SWEEP], s));

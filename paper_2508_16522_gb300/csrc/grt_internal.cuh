@@ -264,6 +264,7 @@ struct SweepOut {
   unsigned long long* cursor;
   uint32_t* tile_counter;
   int key_bits;
+  uint32_t chunk;  // pairs a warp reserves at a time (its last chunk may keep holes)
 };
 int sweep_warps_per_block(int tile_cells);
 size_t sweep_smem_bytes(int tile_cells, int warps);

@@ -47,6 +47,7 @@ struct Request {
   int64_t estimate = 0, footprint = 0, n_edges = 0;
   int state = 0, status = 0, slot = -1;
   std::vector<int32_t> row_ptr, col, out;  // results (keep_results)
+  std::string error;                       // why it failed (state 4)
 };
 
 struct Slot {
@@ -113,7 +114,8 @@ int64_t estimate_bytes(int32_t n, int64_t R) {
   return (8ll << 20) + (int64_t)n * 256 + R * 2048;
 }
 
-void fail_request(rt_server* s, Request* r, int status) {
+void fail_request(rt_server* s, Request* r, int status, std::string why) {
+  r->error = std::move(why);
   r->state = 4;
   r->status = status;
   r->done = now_ns();
@@ -175,7 +177,7 @@ void worker_main(rt_server* s) {
     }
     if (st != RT_OK) {
       std::lock_guard<std::mutex> lk(s->mu);
-      fail_request(s, r, st);
+      fail_request(s, r, st, last_err());
       s->budget_used -= r->estimate;
       s->free_slots.push_back(slot);
       --s->outstanding;
@@ -460,6 +462,7 @@ rt_status rt_server_result(rt_server_t s, int64_t ticket, int32_t* row_ptr, int3
   auto it = s->reqs.find(ticket);
   if (it == s->reqs.end()) return sfail(RT_ERR_INVALID, "unknown ticket");
   const Request* r = it->second.get();
+  if (r->state == 4) return sfail((rt_status)r->status, "request failed: " + r->error);
   if (r->state != 3) return sfail(RT_ERR_STATE, "request is not done");
   if (!s->desc.keep_results) return sfail(RT_ERR_STATE, "server does not keep results");
   if (row_ptr) memcpy(row_ptr, r->row_ptr.data(), r->row_ptr.size() * 4);

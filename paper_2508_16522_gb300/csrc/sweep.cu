@@ -32,7 +32,6 @@ namespace grt {
 namespace {
 constexpr int kHashSlots = 128;
 constexpr int kListCap = 64;
-constexpr uint32_t kChunk = 512;
 constexpr int kLaneBuf = 16;     // predecessors one lane buffers in the lane-parallel path
 constexpr int kSmallCells = 16;  // largest box the lane-parallel path takes
 constexpr int kMaxRounds = 8;    // deeper conflict chains go to the warp-wide path
@@ -108,16 +107,36 @@ __device__ __forceinline__ void warp_insert(const WarpSmem& w, const SweepOut& o
   if (src >= 0 && (peers & lanemask_lt()) == 0) hash_insert(w, o, src, dst);
 }
 
-// Makes sure the warp's pair chunk has room for `need` (<= kChunk) pairs
-// (warp-convergent): pads the old chunk's tail with sentinels and takes a new
-// chunk with one atomic.
-__device__ void reserve_pairs(Ctx& x, const SweepOut& o, uint32_t need) {
-  if (x.chunk_left >= need) return;
-  for (uint32_t i = x.lane; i < x.chunk_left; i += 32) put_pair(o, x.chunk_base + i, kEmpty64);
+// Where `need` pairs of one flush go: the first `split` fill the rest of the
+// warp's current chunk (from `a`), the others start a fresh contiguous run of
+// chunks (at `b`). Only a warp's last, partly used chunk is ever left with
+// holes, so the cursor exceeds the pairs written by less than one chunk per
+// warp (convergent).
+struct PairDst {
+  unsigned long long a, b;
+  uint32_t split;
+};
+
+__device__ PairDst reserve_pairs(Ctx& x, const SweepOut& o, uint32_t need) {
+  PairDst d{x.chunk_base, 0ull, need};
+  if (x.chunk_left >= need) {
+    x.chunk_base += need;
+    x.chunk_left -= need;
+    return d;
+  }
+  d.split = x.chunk_left;
+  const uint32_t rest = need - x.chunk_left;
+  const uint32_t k = (rest + o.chunk - 1) / o.chunk;
   unsigned long long nb = 0;
-  if (x.lane == 0) nb = atomicAdd(o.cursor, (unsigned long long)kChunk);
-  x.chunk_base = __shfl_sync(kFull, nb, 0);
-  x.chunk_left = kChunk;
+  if (x.lane == 0) nb = atomicAdd(o.cursor, (unsigned long long)k * o.chunk);
+  d.b = __shfl_sync(kFull, nb, 0);
+  x.chunk_base = d.b + rest;
+  x.chunk_left = k * o.chunk - rest;
+  return d;
+}
+
+__device__ __forceinline__ unsigned long long pair_pos(const PairDst& d, uint32_t i) {
+  return i < d.split ? d.a + i : d.b + (i - d.split);
 }
 
 // writes the task's distinct predecessors found in this tile (convergent)
@@ -126,13 +145,11 @@ __device__ void flush(Ctx& x, const WarpSmem& w, const SweepOut& o, int dst) {
   const int cnt = *(volatile int*)w.hcount;
   const int m = cnt < kListCap ? cnt : kListCap;
   if (m > 0) {
-    reserve_pairs(x, o, (uint32_t)m);
+    const PairDst pd = reserve_pairs(x, o, (uint32_t)m);
     for (int i = x.lane; i < m; i += 32) {
-      put_pair(o, x.chunk_base + i, pair_key(w.hlist[i], dst, o.key_bits));
+      put_pair(o, pair_pos(pd, (uint32_t)i), pair_key(w.hlist[i], dst, o.key_bits));
       if (cnt <= kListCap) w.htab[w.hslot[i]] = -1;
     }
-    x.chunk_base += m;
-    x.chunk_left -= m;
   }
   if (cnt > kListCap)
     for (int i = x.lane; i < kHashSlots; i += 32) w.htab[i] = -1;
@@ -305,12 +322,10 @@ __device__ bool stage_lanes(Ctx& x, const WarpSmem& w, const SweepOut& o, unsign
     }
     const int total = __shfl_sync(kFull, incl, 31);
     if (total > 0) {
-      reserve_pairs(x, o, (uint32_t)total);
+      const PairDst pd = reserve_pairs(x, o, (uint32_t)total);
       const int base = incl - nb;
       for (int k = 0; k < nb; ++k)
-        put_pair(o, x.chunk_base + base + k, pair_key(w.lbuf[lane * kLaneBuf + k], b.task, o.key_bits));
-      x.chunk_base += total;
-      x.chunk_left -= total;
+        put_pair(o, pair_pos(pd, (uint32_t)(base + k)), pair_key(w.lbuf[lane * kLaneBuf + k], b.task, o.key_bits));
     }
     __syncwarp();
   }

@@ -101,6 +101,35 @@ def test_long_runs_and_many_predecessors():
         g.close()
 
 
+def test_pair_buffer_overflow_reruns_once():
+    """A run of K readers then a run of K reducers over the same 4 tiles: every
+    reducer follows every reader, so each tile yields K^2 candidate pairs from
+    only 2K entries, far more than the first guess for the pair buffer. The
+    sweep overflows, reports what it reserved, and the rerun must fit and give
+    the oracle's CSR. Overlapping smaller boxes on top stress chunk splits."""
+    K = 256
+    rng = np.random.default_rng(7)
+    lo = [[0, 0]] * (2 * K)
+    hi = [[31, 31]] * (2 * K)
+    priv = [0] * K + [2] * K
+    for k in range(300):  # then many small overlapping boxes of mixed kinds
+        x, y = rng.integers(0, 30, 2)
+        lo.append([x, y])
+        hi.append([x + rng.integers(0, 3), y + rng.integers(0, 3)])
+        priv.append(int(rng.integers(0, 3)))
+    counts = [1] * len(priv)
+    tr = tg._finish(2, [0, 0], [31, 31], counts, np.array(lo).reshape(-1), np.array(hi).reshape(-1),
+                    np.array(priv, np.uint8), name="pair_overflow")
+    ref = oracle_csr(tr)
+    for tile in ((16, 16), (8, 8)):
+        g = gpu_graph(tr, tile=tile)
+        g.analyze()
+        assert_csr_equal(g, tr, ref)
+        st = g.stats()
+        assert st["n_pairs"] > 4 * st["n_entries"], st  # the first guess (2 x entries, >= 64K) was exceeded
+        g.close()
+
+
 def test_edge_cases():
     import torch
     # empty graph
