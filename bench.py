@@ -99,6 +99,7 @@ def run_batched(grt, torch, flush, steps):
 
 
 SERVE_REQUESTS, SERVE_RATE = 2000, 50_000.0
+SERVE_SLOTS, SERVE_WORKERS, SERVE_MAX_BATCH = 512, 4, 64
 
 
 def run_served(grt, n_requests=SERVE_REQUESTS):
@@ -110,20 +111,23 @@ def run_served(grt, n_requests=SERVE_REQUESTS):
     t0 = time.perf_counter()
     reqs = tg.served_stream(n_requests, rate_per_s=SERVE_RATE, seed=0)
     gen_s = time.perf_counter() - t0
-    srv = grt.Server(2, [0, 0], [1023, 1023], body=grt.RT_BODY_EMPTY, budget_bytes=8 << 30, max_inflight=64,
-                     max_tasks=16384, workers=8, tile=TILE)
+    srv = grt.Server(2, [0, 0], [1023, 1023], body=grt.RT_BODY_EMPTY, budget_bytes=8 << 30,
+                     max_inflight=SERVE_SLOTS, max_tasks=16384, workers=SERVE_WORKERS, tile=TILE,
+                     max_batch=SERVE_MAX_BATCH)
     for r in reqs[:16]:  # warm-up: grow the pool's buffers
         srv.submit(r.trace)
     srv.drain()
     base = grt.rt_now_ns() + 2_000_000
-    tickets = []
+    tickets, lag = [], []
     for r in reqs:
         due = base + r.arrival_ns
         while grt.rt_now_ns() < due:
             pass
         tickets.append(srv.submit(r.trace, arrival_ns=due))
+        lag.append(grt.rt_now_ns() - due)
     srv.drain()
     infos = [srv.poll(t) for t in tickets]
+    sst = srv.stats()
     failed = []
     for t, i in zip(tickets, infos):
         if i["state"] != 3 and len(failed) < 3:
@@ -141,12 +145,15 @@ def run_served(grt, n_requests=SERVE_REQUESTS):
     tasks = sum(i["n_tasks"] for i in infos)
     return {"workload": f"{n_requests} requests, Poisson arrivals at {SERVE_RATE:.0f} graphs/s, task counts "
                         "log-uniform 32..16384, 1-4 rects per launch on 1024^2 (sides log-uniform 4..256), "
-                        "EMPTY bodies, 8 GB budget, 64 slots, 8 analysis workers",
+                        f"EMPTY bodies, 8 GB budget, {SERVE_SLOTS} request slots, {SERVE_WORKERS} analysis "
+                        f"workers, up to {SERVE_MAX_BATCH} waiting requests analysed together",
             "requests": n_requests, "tasks": tasks, "offered_graphs_per_s": SERVE_RATE,
             "achieved_graphs_per_s": n_requests / span, "tasks_per_s": tasks / span,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "service_ms": {"p50": float(np.percentile(svc, 50)), "p99": float(np.percentile(svc, 99))},
             "analysis_ms": {"p50": float(np.percentile(ana, 50)), "p99": float(np.percentile(ana, 99))},
+            "mean_batch": sst["batched_requests"] / max(sst["batches"], 1),
+            "submit_lag_ms": {"p50": float(np.percentile(lag, 50)) / 1e6, "p99": float(np.percentile(lag, 99)) / 1e6},
             "generate_s": gen_s}
 
 

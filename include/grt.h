@@ -245,9 +245,13 @@ rt_status rt_batch_destroy(rt_batch_t b);
  * requirements) as they arrive and executes them in one persistent kernel that
  * admits new graphs while others are still running (Section 4.1: each graph
  * runs as one operation; Section 2.2: dependences inferred from data usage).
- * Requests are admitted in arrival order while a slot is free and the device
- * memory they would hold fits the budget; analysis runs on `workers` host
- * threads, each with its own stream, concurrently with the executing kernel. */
+ * Requests are admitted in arrival order while a request slot is free and the
+ * device memory they would hold fits the budget. A worker thread analyses
+ * every admitted request that is waiting (up to max_batch) as ONE graph, each
+ * request's rectangles shifted into a band of their own along the domain's
+ * last dimension, so the requests' DAGs stay disjoint; analysis runs on the
+ * workers' own streams, concurrently with the executing kernel, and each
+ * request completes on its own. */
 typedef struct rt_server* rt_server_t;
 
 typedef struct {
@@ -263,6 +267,9 @@ typedef struct {
   int32_t keep_results;          /* keep each request's CSR (and SPIN outputs) */
   int32_t exec_blocks, exec_warps;  /* serving kernel shape, 0 = default */
   int64_t timeout_ns;            /* stall limit of the serving kernel, 0 = 2 s */
+  int32_t max_batch;             /* requests analysed together, 1..1024, 0 = 64;
+                                    max_batch x max_tasks < 2^31 */
+  int32_t reserved0;             /* 0 */
 } rt_server_desc;
 
 typedef struct {
@@ -280,9 +287,10 @@ int64_t rt_now_ns(void);
  * RT_ERR_INVALID, RT_ERR_OOM, RT_ERR_CUDA. */
 rt_status rt_server_create(const rt_server_desc* desc, rt_server_t* out);
 
-/* Queues one request: n launches as in rt_launch_batch (host arrays, copied
- * before returning; no explicit preds). arrival_ns stamps its arrival (use
- * rt_now_ns()). Errors: RT_ERR_INVALID (bad arrays, more than max_tasks),
+/* Queues one request: n launches as in rt_launch_batch (host arrays, checked
+ * and copied before returning; no explicit preds). arrival_ns stamps its
+ * arrival (use rt_now_ns()). Errors: RT_ERR_INVALID (bad offsets, a rectangle
+ * empty or outside the domain, a bad privilege, more than max_tasks tasks),
  * RT_ERR_BUDGET (it could never fit the budget), RT_ERR_STATE (stopping). */
 rt_status rt_server_submit(rt_server_t s, int32_t n, const int32_t* req_off, const int64_t* lo,
                            const int64_t* hi, const uint8_t* priv, int64_t arrival_ns, int64_t* ticket);
@@ -302,7 +310,8 @@ rt_status rt_server_drain(rt_server_t s, int64_t timeout_ns);
 
 /* Diagnostics: out[0] activations posted, [1] taken by the kernel, [2]
  * finished, [3] kernel status, [4] tasks executed, [5] requests queued, [6]
- * analysing, [7] running, [8] 1 while the serving kernel runs. */
+ * analysing, [7] running, [8] 1 while the serving kernel runs, [9] batches
+ * analysed, [10] requests in them. */
 rt_status rt_server_stats(rt_server_t s, int64_t* out, int32_t n);
 
 /* Drains (30 s at most), asks the serving kernel to stop once idle (forcing it

@@ -1186,6 +1186,8 @@ rt_status graph_view(rt_graph_t g, GraphView* v) {
   if (!g->analyzed) return fail(RT_ERR_STATE, "graph not analyzed");
   v->adj = g->adj.as<int4>();
   v->col = g->col.as<int32_t>();
+  v->row_ptr = g->row_ptr.as<int32_t>();
+  v->rootpos = g->rootpos.as<uint32_t>();
   v->count = g->count.as<int32_t>();
   v->roots = g->root_items.as<uint64_t>();
   v->n = g->n;

@@ -178,14 +178,16 @@ struct ExecParams {
 // ---------------------------------------------------------------------------
 // serving: one persistent executor admits analysed graphs while it runs
 // ---------------------------------------------------------------------------
-struct ServeSlot {         // device table entry of one admitted graph
-  const int4* adj;         // its trigger records
-  const int32_t* col;      // its CSR columns (successors past the inline ones)
-  int32_t* count;          // its countdown counters
-  const uint64_t* roots;   // its roots (low 32 bits: local task id)
-  int32_t* out;            // SPIN results, one per task (may be null for EMPTY)
+struct ServeSlot {         // device table entry of one admitted request
+  const int4* adj;         // trigger records of the graph it was analysed in
+  const int32_t* col;      // that graph's CSR columns (successors past the inline ones)
+  int32_t* count;          // that graph's countdown counters
+  const uint64_t* roots;   // the request's roots (low 32 bits: task id in that graph)
+  int32_t* out;            // SPIN results, one per task of that graph (null for EMPTY)
   int32_t n_tasks, n_roots, body, spin_iters;
-  uint32_t gen, pad[3];    // activation number, echoed at completion
+  uint32_t gen;            // activation number, echoed at completion
+  int32_t base;            // the request's first task in that graph
+  uint32_t pad[2];
 };
 
 struct ServeMailbox {      // host-mapped: written by the host, read by the kernel
@@ -295,6 +297,9 @@ void preload_analysis();
 void preload_sweep();
 void preload_exec();
 void preload_serve();
+// out[2i] = rootpos[idx[i]], out[2i+1] = row_ptr[idx[i]] for i < k
+void launch_serve_gather(const uint32_t* rootpos, const int32_t* row_ptr, const int32_t* idx, int k, uint32_t* out,
+                         cudaStream_t s);
 void set_last_error(const char* msg);
 void launch_serve(ServeParams p, int blocks, int warps, cudaStream_t s);
 
@@ -302,6 +307,8 @@ void launch_serve(ServeParams p, int blocks, int warps, cudaStream_t s);
 struct GraphView {
   const int4* adj;
   const int32_t* col;
+  const int32_t* row_ptr;   // int32[n+1]
+  const uint32_t* rootpos;  // int32[n+1]: roots before each task (exclusive scan)
   int32_t* count;
   const uint64_t* roots;
   int32_t n, n_roots;

@@ -128,7 +128,7 @@ struct SlotView {
   const int32_t* col;
   int32_t* count;
   int32_t* out;
-  int32_t n_tasks, body, spin_iters;
+  int32_t n_tasks, body, spin_iters, base;
   uint32_t gen;
 };
 
@@ -144,6 +144,7 @@ __device__ __forceinline__ SlotView slot_view(const ServeParams& p, int slot) {
   v.body = __ldcg(&S->body);
   v.spin_iters = __ldcg(&S->spin_iters);
   v.gen = __ldcg(&S->gen);
+  v.base = __ldcg(&S->base);
   return v;
 }
 
@@ -270,7 +271,7 @@ __global__ void __launch_bounds__(256, 1) k_serve(ServeParams p) {
     if (has) {
       // (no counter re-arm: every served request is analysed afresh)
       if (S.body == RT_BODY_SPIN && S.out) {
-        uint32_t x = (uint32_t)v;
+        uint32_t x = (uint32_t)(v - S.base);  // the task's id within its request
         for (int k = 0; k < S.spin_iters; ++k) x = x * 1664525u + 1013904223u;
         S.out[v] = (int32_t)x;
         wrote = true;
@@ -377,7 +378,23 @@ __global__ void __launch_bounds__(256, 1) k_serve(ServeParams p) {
   }
 }
 
+__global__ void k_serve_gather(const uint32_t* rootpos, const int32_t* row_ptr, const int32_t* idx, int k,
+                               uint32_t* out) {
+  const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (i < k) {
+    const int t = idx[i];
+    out[2 * i] = rootpos[t];
+    out[2 * i + 1] = (uint32_t)row_ptr[t];
+  }
+}
+
 }  // namespace
+
+void launch_serve_gather(const uint32_t* rootpos, const int32_t* row_ptr, const int32_t* idx, int k, uint32_t* out,
+                         cudaStream_t s) {
+  count_launch();
+  k_serve_gather<<<(k + 127) / 128, 128, 0, s>>>(rootpos, row_ptr, idx, k, out);
+}
 
 void launch_serve_init(ServeParams p, cudaStream_t s) {
   unsigned long long work = p.cap > (unsigned long long)p.max_slots ? p.cap : (unsigned long long)p.max_slots;
@@ -405,6 +422,7 @@ void preload_serve() {
   cudaFuncAttributes a;
   cudaFuncGetAttributes(&a, k_serve_init);
   cudaFuncGetAttributes(&a, k_serve);
+  cudaFuncGetAttributes(&a, k_serve_gather);
 }
 
 }  // namespace grt

@@ -1,14 +1,23 @@
-// server.cu -- host side of serving: admission, analysis workers, completion.
+// server.cu -- host side of serving: admission, batched analysis, completion.
 //
-// Requests queue in arrival order. A worker thread admits the oldest request
-// when a slot of the graph pool is free and the device memory the request
-// would hold fits the budget, analyses it on the slot's own stream (the same
-// GPU analysis as rt_analyze), writes the slot's table entry and posts it
-// through the host-mapped mailbox to the serving kernel (serve.cu), which is
-// running all the time. A completion thread watches the host-mapped completion
-// words, stamps the finish time, copies results back if asked, and frees the
-// slot and its budget share. Several requests are analysed concurrently (one
-// per worker) while earlier ones execute: continuous batching.
+// Requests queue in arrival order. A worker thread takes every request that is
+// waiting (up to max_batch, while request slots are free and their estimated
+// device memory fits the budget) and analyses them TOGETHER as one graph: each
+// request's rectangles are shifted into a band of their own along the last
+// dimension of a stacked domain, so no rectangle of one request meets another's
+// and the batch's DAG is the disjoint union of the requests' DAGs (task v of
+// request j is task toff_j + v). One analysis, a few tens of kernel launches
+// and three host syncs, then serves the whole batch; the per-request costs
+// that remain are a table entry and a mailbox post.
+//
+// Every request keeps its own slot in the device table: the entry points into
+// the batch's CSR, countdown counters and trigger records, and at the
+// request's own roots. The serving kernel (serve.cu) carries the slot in every
+// ready item, so each request completes on its own, as soon as its last task
+// runs. A completion thread watches the host-mapped completion words, stamps
+// the finish time, copies results back if asked, frees the slot and, when the
+// batch's last request has finished, the batch graph and its budget share.
+// While one batch executes, workers analyse the next ones: continuous batching.
 #include <stdio.h>
 #include <time.h>
 
@@ -45,17 +54,37 @@ struct Request {
   std::vector<uint8_t> priv;
   int64_t arrival = 0, admit = 0, posted = 0, done = 0;
   int64_t estimate = 0, footprint = 0, n_edges = 0;
-  int state = 0, status = 0, slot = -1;
+  int state = 0, status = 0, slot = -1, batch = -1;
+  int32_t toff = 0;                        // first task in the batch graph
+  int64_t eoff = 0;                        // first edge in the batch graph's CSR
   std::vector<int32_t> row_ptr, col, out;  // results (keep_results)
   std::string error;                       // why it failed (state 4)
 };
 
-struct Slot {
-  rt_graph_t g = nullptr;
-  cudaStream_t stream = nullptr;
-  int32_t* out = nullptr;  // SPIN results, max_tasks int32 (device)
+struct Slot {      // one request's entry of the device table
   uint32_t gen = 0;
   Request* req = nullptr;
+};
+
+// pinned host memory that only grows; replaced buffers are freed with the
+// server (freeing pinned memory may synchronise the device, which the
+// resident serving kernel would turn into a wait for the server's end)
+struct HostBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+struct Batch {     // a pooled graph that analyses one batch of requests
+  rt_graph_t g = nullptr;
+  cudaStream_t stream = nullptr;
+  int32_t* out = nullptr;    // SPIN outputs of the whole batch (device)
+  int32_t* gidx = nullptr;   // task offsets of the batch's requests (device)
+  uint32_t* gout = nullptr;  // gathered root and edge offsets (device)
+  int32_t* hidx = nullptr;   // pinned mirrors of the two
+  uint32_t* hout = nullptr;
+  HostBuf req_off, lo, hi, priv;
+  int live = 0;              // requests of the batch not yet finished
+  int64_t footprint = 0;     // device bytes the batch graph holds
 };
 
 // error message of a failed library call, kept with the request
@@ -69,11 +98,16 @@ std::string last_err() {
 struct rt_server {
   rt_server_desc desc{};
   int device = 0;
+  int stack_dim = 0;               // requests are stacked along this dimension
+  int64_t band = 0;                // extent of one request's domain along it
   std::vector<Slot> slots;
   std::vector<int> free_slots;
+  std::vector<Batch> batches;
+  std::vector<int> free_batches;
+  std::vector<HostBuf> retired;    // outgrown pinned buffers
   // device
   ServeSlot* table = nullptr;
-  ServeSlot* table_h = nullptr;  // pinned staging: one entry per slot
+  ServeSlot* table_h = nullptr;    // pinned staging: one entry per slot
   uint32_t* done_s = nullptr;
   ServeCtrl* ctrl = nullptr;
   uint64_t* items = nullptr;
@@ -95,13 +129,14 @@ struct rt_server {
   int64_t next_ticket = 1;
   int64_t budget_used = 0;
   int64_t outstanding = 0;         // submitted, not yet done or failed
+  int64_t n_batches = 0, n_batched = 0;
   std::mutex post_mu;              // serialises mailbox posts
+  std::mutex pin_mu;               // guards `retired`
   bool stopping = false;
   std::atomic<bool> quit{false};
   std::vector<std::thread> workers;
   std::thread completer;
   std::vector<int> running;        // slots posted to the kernel (guarded by mu)
-  uint32_t kernel_status = 0;
   std::string fatal;
 };
 
@@ -114,113 +149,250 @@ int64_t estimate_bytes(int32_t n, int64_t R) {
   return (8ll << 20) + (int64_t)n * 256 + R * 2048;
 }
 
-void fail_request(rt_server* s, Request* r, int status, std::string why) {
+bool grow(rt_server* s, HostBuf& b, size_t bytes) {
+  if (b.cap >= bytes) return true;
+  size_t c = std::max<size_t>(bytes + bytes / 2, 1 << 16);
+  void* p = nullptr;
+  if (cudaHostAlloc(&p, c, cudaHostAllocDefault) != cudaSuccess) return false;
+  if (b.p) {
+    std::lock_guard<std::mutex> lk(s->pin_mu);
+    s->retired.push_back(b);
+  }
+  b.p = p;
+  b.cap = c;
+  return true;
+}
+
+void fail_request(Request* r, int status, std::string why) {
   r->error = std::move(why);
   r->state = 4;
   r->status = status;
   r->done = now_ns();
 }
 
+// Writes the batch's arrays in pinned memory: request j's launches follow
+// request j-1's, and its rectangles move j bands along the stacking dimension.
+rt_status build_union(rt_server* s, Batch& b, const std::vector<Request*>& rs, int32_t n_tot, int64_t R_tot) {
+  const int D = s->desc.ndim, sd = s->stack_dim;
+  if (R_tot > INT32_MAX) return RT_ERR_OOM;  // launch offsets are int32
+  if (!grow(s, b.req_off, (size_t)(n_tot + 1) * 4) || !grow(s, b.lo, (size_t)std::max<int64_t>(R_tot, 1) * D * 8) ||
+      !grow(s, b.hi, (size_t)std::max<int64_t>(R_tot, 1) * D * 8) ||
+      !grow(s, b.priv, (size_t)std::max<int64_t>(R_tot, 1)))
+    return RT_ERR_OOM;
+  int32_t* ro = static_cast<int32_t*>(b.req_off.p);
+  int64_t* lo = static_cast<int64_t*>(b.lo.p);
+  int64_t* hi = static_cast<int64_t*>(b.hi.p);
+  uint8_t* pv = static_cast<uint8_t*>(b.priv.p);
+  int64_t roff = 0;
+  for (size_t j = 0; j < rs.size(); ++j) {
+    Request* r = rs[j];
+    for (int32_t i = 0; i < r->n; ++i) ro[r->toff + i] = (int32_t)(roff + r->req_off[(size_t)i]);
+    const int64_t R = r->req_off[(size_t)r->n];
+    const int64_t shift = (int64_t)j * s->band;
+    int64_t* l = lo + roff * D;
+    int64_t* h = hi + roff * D;
+    std::memcpy(l, r->lo.data(), (size_t)R * D * 8);
+    std::memcpy(h, r->hi.data(), (size_t)R * D * 8);
+    if (shift)
+      for (int64_t k = 0; k < R; ++k) {
+        l[k * D + sd] += shift;
+        h[k * D + sd] += shift;
+      }
+    std::memcpy(pv + roff, r->priv.data(), (size_t)R);
+    roff += R;
+    // the request's own copy of its launches is no longer needed
+    std::vector<int32_t>().swap(r->req_off);
+    std::vector<int64_t>().swap(r->lo);
+    std::vector<int64_t>().swap(r->hi);
+    std::vector<uint8_t>().swap(r->priv);
+  }
+  ro[n_tot] = (int32_t)R_tot;
+  return RT_OK;
+}
+
 void worker_main(rt_server* s) {
   cudaSetDevice(s->device);
+  std::vector<Request*> rs;
   for (;;) {
-    Request* r = nullptr;
-    int slot = -1;
+    rs.clear();
+    int bi = -1;
+    int64_t est = 0;
     {
       std::unique_lock<std::mutex> lk(s->mu);
       s->cv.wait(lk, [&] {
         if (s->quit) return true;
-        if (s->pending.empty() || s->free_slots.empty()) return false;
+        if (s->pending.empty() || s->free_slots.empty() || s->free_batches.empty()) return false;
         return s->budget_used + s->pending.front()->estimate <= s->desc.budget_bytes;
       });
       if (s->quit) return;
-      r = s->pending.front();
-      s->pending.pop_front();
-      slot = s->free_slots.back();
-      s->free_slots.pop_back();
-      s->budget_used += r->estimate;
-      r->slot = slot;
-      r->state = 1;
-      r->admit = now_ns();
+      bi = s->free_batches.back();
+      s->free_batches.pop_back();
+      const int64_t t = now_ns();
+      // admit in arrival order: everything waiting that fits, up to max_batch
+      while (!s->pending.empty() && (int)rs.size() < s->desc.max_batch && !s->free_slots.empty() &&
+             s->budget_used + s->pending.front()->estimate <= s->desc.budget_bytes) {
+        Request* r = s->pending.front();
+        s->pending.pop_front();
+        r->slot = s->free_slots.back();
+        s->free_slots.pop_back();
+        s->budget_used += r->estimate;
+        est += r->estimate;
+        r->batch = bi;
+        r->state = 1;
+        r->admit = t;
+        rs.push_back(r);
+      }
     }
-    Slot& sl = s->slots[(size_t)slot];
-    trace("worker: admitted");
-    rt_status st = rt_graph_clear(sl.g);
-    if (st == RT_OK)
-      st = rt_launch_batch(sl.g, r->n, r->req_off.data(), r->lo.data(), r->hi.data(), r->priv.data(), nullptr,
-                           nullptr, nullptr, RT_LAUNCH_DEFER_CHECK);
-    if (st == RT_OK) st = rt_analyze(sl.g);
+    Batch& b = s->batches[(size_t)bi];
+    trace("worker: batch admitted");
+    int32_t n_tot = 0;
+    int64_t R_tot = 0;
+    for (Request* r : rs) {
+      r->toff = n_tot;
+      n_tot += r->n;
+      R_tot += r->req_off[(size_t)r->n];
+    }
+    const int B = (int)rs.size();
+    rt_status st = build_union(s, b, rs, n_tot, R_tot);
+    std::string why = st == RT_OK ? std::string() : std::string("pinned staging for the batch");
     GraphView v{};
-    if (st == RT_OK) st = graph_view(sl.g, &v);
-    if (st == RT_OK) {
-      ServeSlot e{};
-      e.adj = v.adj;
-      e.col = v.col;
-      e.count = v.count;
-      e.roots = v.roots;
-      e.out = sl.out;
-      e.n_tasks = v.n;
-      e.n_roots = v.n_roots;
-      e.body = s->desc.body;
-      e.spin_iters = s->desc.spin_iters;
-      e.gen = ++sl.gen;
-      // The entry must be in device memory before the kernel can see the
-      // post. A synchronous copy from pageable memory may return before its
-      // DMA has landed, so stage it in pinned memory and wait for the stream.
-      trace("worker: analysed, writing table");
-      s->table_h[slot] = e;
-      if (cudaMemcpyAsync(s->table + slot, s->table_h + slot, sizeof e, cudaMemcpyHostToDevice, sl.stream) !=
-              cudaSuccess ||
-          cudaStreamSynchronize(sl.stream) != cudaSuccess)
-        st = RT_ERR_CUDA;
-      trace("worker: table written");
+    if (st == RT_OK && n_tot > 0) {
+      st = rt_graph_clear(b.g);
+      if (st == RT_OK)
+        st = rt_launch_batch(b.g, n_tot, static_cast<int32_t*>(b.req_off.p), static_cast<int64_t*>(b.lo.p),
+                             static_cast<int64_t*>(b.hi.p), static_cast<uint8_t*>(b.priv.p), nullptr, nullptr,
+                             nullptr, RT_LAUNCH_DEFER_CHECK);
+      if (st == RT_OK) st = rt_analyze(b.g);
+      if (st == RT_OK) st = graph_view(b.g, &v);
+      if (st != RT_OK) why = last_err();
+      if (st == RT_OK) {
+        // each request's first root and first edge in the batch graph
+        for (int j = 0; j < B; ++j) b.hidx[j] = rs[(size_t)j]->toff;
+        b.hidx[B] = n_tot;
+        if (cudaMemcpyAsync(b.gidx, b.hidx, (size_t)(B + 1) * 4, cudaMemcpyHostToDevice, b.stream) != cudaSuccess)
+          st = RT_ERR_CUDA;
+        launch_serve_gather(v.rootpos, v.row_ptr, b.gidx, B + 1, b.gout, b.stream);
+        if (st == RT_OK &&
+            (cudaMemcpyAsync(b.hout, b.gout, (size_t)(B + 1) * 8, cudaMemcpyDeviceToHost, b.stream) != cudaSuccess ||
+             cudaStreamSynchronize(b.stream) != cudaSuccess))
+          st = RT_ERR_CUDA;
+        if (st != RT_OK) why = "root and edge offsets of the batch";
+      }
+      if (st == RT_OK) {
+        // The entries must be in device memory before the kernel can see the
+        // posts. A synchronous copy from pageable memory may return before its
+        // DMA has landed, so they are staged in pinned memory and the stream
+        // is waited for.
+        trace("worker: analysed, writing table");
+        for (int j = 0; j < B && st == RT_OK; ++j) {
+          Request* r = rs[(size_t)j];
+          if (r->n == 0) continue;
+          ServeSlot e{};
+          e.adj = v.adj;
+          e.col = v.col;
+          e.count = v.count;
+          e.roots = v.roots + b.hout[2 * j];
+          e.out = b.out;
+          e.n_tasks = r->n;
+          e.n_roots = (int32_t)(b.hout[2 * j + 2] - b.hout[2 * j]);
+          e.body = s->desc.body;
+          e.spin_iters = s->desc.spin_iters;
+          e.gen = ++s->slots[(size_t)r->slot].gen;
+          e.base = r->toff;
+          s->table_h[r->slot] = e;
+          if (cudaMemcpyAsync(s->table + r->slot, s->table_h + r->slot, sizeof e, cudaMemcpyHostToDevice,
+                              b.stream) != cudaSuccess)
+            st = RT_ERR_CUDA;
+        }
+        if (st == RT_OK && cudaStreamSynchronize(b.stream) != cudaSuccess) st = RT_ERR_CUDA;
+        if (st != RT_OK) why = "slot table write";
+        trace("worker: table written");
+      }
     }
-    if (st != RT_OK) {
+    std::vector<int> post;
+    {
       std::lock_guard<std::mutex> lk(s->mu);
-      fail_request(s, r, st, last_err());
-      s->budget_used -= r->estimate;
-      s->free_slots.push_back(slot);
-      --s->outstanding;
+      s->budget_used -= est;
+      if (st != RT_OK) {
+        for (Request* r : rs) {
+          fail_request(r, st, why);
+          s->free_slots.push_back(r->slot);
+          --s->outstanding;
+        }
+        s->free_batches.push_back(bi);
+      } else {
+        b.footprint = n_tot > 0 ? (int64_t)v.footprint : 0;
+        s->budget_used += b.footprint;
+        ++s->n_batches;
+        s->n_batched += B;
+        b.live = 0;
+        const int64_t t = now_ns();
+        for (int j = 0; j < B; ++j) {
+          Request* r = rs[(size_t)j];
+          r->posted = t;
+          r->footprint = n_tot > 0 ? b.footprint * r->n / n_tot : 0;
+          if (r->n == 0) {  // nothing to run: done at once
+            r->n_edges = 0;
+            r->state = 3;
+            r->done = t;
+            s->free_slots.push_back(r->slot);
+            --s->outstanding;
+            continue;
+          }
+          r->eoff = b.hout[2 * j + 1];
+          r->n_edges = (int64_t)b.hout[2 * j + 3] - (int64_t)b.hout[2 * j + 1];
+          r->state = 2;
+          s->slots[(size_t)r->slot].req = r;
+          s->running.push_back(r->slot);
+          post.push_back(r->slot);
+          ++b.live;
+        }
+        if (b.live == 0) {
+          s->budget_used -= b.footprint;
+          s->free_batches.push_back(bi);
+        }
+      }
       s->cv.notify_all();
       s->cv_done.notify_all();
-      continue;
     }
-    {
-      std::lock_guard<std::mutex> lk(s->mu);
-      s->budget_used += (int64_t)v.footprint - r->estimate;
-      r->footprint = (int64_t)v.footprint;
-      r->n_edges = v.n_edges;
-      r->posted = now_ns();
-      r->state = 2;
-      sl.req = r;
-      if (v.n == 0) {  // nothing to run: done at once
-        r->state = 3;
-        r->done = r->posted;
-        sl.req = nullptr;
-        s->budget_used -= r->footprint;
-        s->free_slots.push_back(slot);
-        --s->outstanding;
-        s->cv.notify_all();
-        s->cv_done.notify_all();
-        continue;
-      }
-      s->running.push_back(slot);
-    }
-    {
+    if (!post.empty()) {
       std::lock_guard<std::mutex> lk(s->post_mu);
       const uint32_t k = s->mail->posted;
-      s->mail->queue[k % 1024u] = (uint32_t)slot;
+      for (size_t i = 0; i < post.size(); ++i) s->mail->queue[(k + (uint32_t)i) % 1024u] = (uint32_t)post[i];
       std::atomic_thread_fence(std::memory_order_seq_cst);
-      s->mail->posted = k + 1;
+      s->mail->posted = k + (uint32_t)post.size();
       std::atomic_thread_fence(std::memory_order_seq_cst);
     }
   }
 }
 
+// Copies one finished request's part of its batch's CSR (and SPIN outputs)
+// back, renumbered from its own first task and edge.
+void copy_results(rt_server* s, Request* r) {
+  Batch& b = s->batches[(size_t)r->batch];
+  GraphView v{};
+  if (graph_view(b.g, &v) != RT_OK) return;
+  r->row_ptr.resize((size_t)r->n + 1);
+  r->col.resize((size_t)r->n_edges);
+  cudaMemcpyAsync(r->row_ptr.data(), v.row_ptr + r->toff, ((size_t)r->n + 1) * 4, cudaMemcpyDeviceToHost,
+                  s->copy_stream);
+  if (r->n_edges)
+    cudaMemcpyAsync(r->col.data(), v.col + r->eoff, (size_t)r->n_edges * 4, cudaMemcpyDeviceToHost, s->copy_stream);
+  if (s->desc.body == RT_BODY_SPIN) {
+    r->out.resize((size_t)r->n);
+    cudaMemcpyAsync(r->out.data(), b.out + r->toff, (size_t)r->n * 4, cudaMemcpyDeviceToHost, s->copy_stream);
+  }
+  cudaStreamSynchronize(s->copy_stream);
+  const int32_t e0 = r->row_ptr[0];
+  for (int32_t& x : r->row_ptr) x -= e0;
+  for (int32_t& x : r->col) x -= r->toff;
+}
+
 void completer_main(rt_server* s) {
   cudaSetDevice(s->device);
+  std::vector<int> done_slots;
   while (!s->quit) {
-    std::vector<int> done_slots;
+    done_slots.clear();
     {
       std::lock_guard<std::mutex> lk(s->mu);
       for (size_t i = 0; i < s->running.size();) {
@@ -236,25 +408,19 @@ void completer_main(rt_server* s) {
     }
     const int64_t t = now_ns();
     for (int slot : done_slots) {
-      Slot& sl = s->slots[(size_t)slot];
-      Request* r = sl.req;
+      Request* r = s->slots[(size_t)slot].req;
       r->done = t;
-      if (s->desc.keep_results) {
-        r->row_ptr.resize((size_t)r->n + 1);
-        r->col.resize((size_t)std::max<int64_t>(r->n_edges, 1));
-        rt_copy_csr(sl.g, r->row_ptr.data(), r->col.data(), nullptr);
-        r->col.resize((size_t)r->n_edges);
-        if (s->desc.body == RT_BODY_SPIN) {
-          r->out.resize((size_t)r->n);
-          cudaMemcpy(r->out.data(), sl.out, (size_t)r->n * 4, cudaMemcpyDeviceToHost);
-        }
-      }
+      if (s->desc.keep_results) copy_results(s, r);
       std::lock_guard<std::mutex> lk(s->mu);
       r->state = 3;
-      sl.req = nullptr;
-      s->budget_used -= r->footprint;
+      s->slots[(size_t)slot].req = nullptr;
       s->free_slots.push_back(slot);
       --s->outstanding;
+      Batch& b = s->batches[(size_t)r->batch];
+      if (--b.live == 0) {  // the batch's last request: its graph is free again
+        s->budget_used -= b.footprint;
+        s->free_batches.push_back(r->batch);
+      }
     }
     if (!done_slots.empty()) {
       std::lock_guard<std::mutex> lk(s->mu);
@@ -272,9 +438,6 @@ void completer_main(rt_server* s) {
   }
 }
 
-}  // namespace
-
-namespace {
 rt_status sfail(rt_status st, const std::string& m) {
   set_last_error(m.c_str());
   return st;
@@ -286,12 +449,27 @@ unsigned long long next_pow2(unsigned long long v) {
   return p;
 }
 
+void free_host(HostBuf& b) {
+  if (b.p) cudaFreeHost(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+}
+
 void free_server(rt_server* s) {
-  for (Slot& sl : s->slots) {
-    if (sl.g) rt_graph_destroy(sl.g);
-    if (sl.stream) cudaStreamDestroy(sl.stream);
-    if (sl.out) cudaFree(sl.out);
+  for (Batch& b : s->batches) {
+    if (b.g) rt_graph_destroy(b.g);
+    if (b.stream) cudaStreamDestroy(b.stream);
+    if (b.out) cudaFree(b.out);
+    if (b.gidx) cudaFree(b.gidx);
+    if (b.gout) cudaFree(b.gout);
+    if (b.hidx) cudaFreeHost(b.hidx);
+    if (b.hout) cudaFreeHost(b.hout);
+    free_host(b.req_off);
+    free_host(b.lo);
+    free_host(b.hi);
+    free_host(b.priv);
   }
+  for (HostBuf& h : s->retired) free_host(h);
   if (s->table) cudaFree(s->table);
   if (s->done_s) cudaFree(s->done_s);
   if (s->ctrl) cudaFree(s->ctrl);
@@ -304,6 +482,7 @@ void free_server(rt_server* s) {
   if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
   delete s;
 }
+
 }  // namespace
 
 extern "C" {
@@ -315,12 +494,24 @@ rt_status rt_server_create(const rt_server_desc* d, rt_server_t* out) {
   *out = nullptr;
   if (d->body != RT_BODY_EMPTY && d->body != RT_BODY_SPIN)
     return sfail(RT_ERR_INVALID, "serving supports EMPTY and SPIN bodies");
-  if (d->max_inflight < 1 || d->max_inflight > 1024 || d->workers < 1 || d->workers > 64 || d->max_tasks < 1 ||
-      d->budget_bytes <= 0 || d->spin_iters < 0 || d->exec_warps < 0 || d->exec_warps > 8 || d->exec_blocks < 0)
+  if (d->ndim < 1 || d->ndim > 2 || d->max_inflight < 1 || d->max_inflight > 1024 || d->workers < 1 ||
+      d->workers > 64 || d->max_tasks < 1 || d->budget_bytes <= 0 || d->spin_iters < 0 || d->exec_warps < 0 ||
+      d->exec_warps > 8 || d->exec_blocks < 0 || d->max_batch < 0 || d->max_batch > 1024)
     return sfail(RT_ERR_INVALID, "server descriptor out of range");
+  const int mb = d->max_batch > 0 ? d->max_batch : 64;
+  if ((int64_t)mb * d->max_tasks > (int64_t)INT32_MAX - 1)
+    return sfail(RT_ERR_INVALID, "max_batch x max_tasks must stay below 2^31");
+  for (int k = 0; k < d->ndim; ++k)
+    if (d->dom_hi[k] < d->dom_lo[k]) return sfail(RT_ERR_INVALID, "empty domain");
+  const int sd = d->ndim - 1;
+  const int64_t band = d->dom_hi[sd] - d->dom_lo[sd] + 1;
+  if (band <= 0 || band > ((int64_t)1 << 52) / mb) return sfail(RT_ERR_INVALID, "domain too long to stack");
   rt_server* s = new (std::nothrow) rt_server();
   if (!s) return sfail(RT_ERR_OOM, "host allocation failed");
   s->desc = *d;
+  s->desc.max_batch = mb;
+  s->stack_dim = sd;
+  s->band = band;
   if (s->desc.timeout_ns == 0) s->desc.timeout_ns = 2000000000ll;
   auto bail = [&](rt_status st, const std::string& m) {
     free_server(s);
@@ -329,25 +520,33 @@ rt_status rt_server_create(const rt_server_desc* d, rt_server_t* out) {
   if (cudaGetDevice(&s->device) != cudaSuccess) return bail(RT_ERR_CUDA, "no CUDA device");
   const int M = d->max_inflight;
   s->slots.resize((size_t)M);
-  for (int i = 0; i < M; ++i) {
-    Slot& sl = s->slots[(size_t)i];
-    if (d->body == RT_BODY_SPIN && cudaMalloc(&sl.out, (size_t)d->max_tasks * 4) != cudaSuccess)
-      return bail(RT_ERR_OOM, "slot output buffers");
-    if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess)
+  for (int i = 0; i < M; ++i) s->free_slots.push_back(M - 1 - i);
+  // enough batch graphs that workers analyse while earlier batches execute
+  const int P = std::max(1, std::min(M, 2 * d->workers + 2));
+  s->batches.resize((size_t)P);
+  for (int i = 0; i < P; ++i) {
+    Batch& b = s->batches[(size_t)i];
+    if (cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking) != cudaSuccess)
       return bail(RT_ERR_CUDA, "streams");
-    cudaStream_t st = sl.stream;
+    if ((d->body == RT_BODY_SPIN && cudaMalloc(&b.out, (size_t)mb * d->max_tasks * 4) != cudaSuccess) ||
+        cudaMalloc(&b.gidx, (size_t)(mb + 1) * 4) != cudaSuccess ||
+        cudaMalloc(&b.gout, (size_t)(mb + 1) * 8) != cudaSuccess ||
+        cudaHostAlloc(&b.hidx, (size_t)(mb + 1) * 4, cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc(&b.hout, (size_t)(mb + 1) * 8, cudaHostAllocDefault) != cudaSuccess)
+      return bail(RT_ERR_OOM, "batch buffers");
     rt_graph_desc gd{};
     gd.ndim = d->ndim;
     for (int k = 0; k < 2; ++k) {
       gd.dom_lo[k] = d->dom_lo[k];
       gd.dom_hi[k] = d->dom_hi[k];
     }
+    gd.dom_hi[sd] = d->dom_lo[sd] + band * mb - 1;  // max_batch bands
     gd.body = RT_BODY_EMPTY;  // the graph object only analyses; the serving kernel runs the bodies
-    gd.stream = st;
+    gd.stream = b.stream;
     gd.tile_w = d->tile_w;
     gd.tile_h = d->tile_h;
-    if (rt_graph_create(&gd, &sl.g) != RT_OK) return bail(RT_ERR_INVALID, last_err());
-    s->free_slots.push_back(M - 1 - i);
+    if (rt_graph_create(&gd, &b.g) != RT_OK) return bail(RT_ERR_INVALID, last_err());
+    s->free_batches.push_back(P - 1 - i);
   }
   s->cap = next_pow2((unsigned long long)M * (unsigned long long)d->max_tasks + 4096ull);
   if (cudaMalloc(&s->table, (size_t)M * sizeof(ServeSlot)) != cudaSuccess ||
@@ -388,15 +587,15 @@ rt_status rt_server_create(const rt_server_desc* d, rt_server_t* out) {
   preload_sweep();
   preload_exec();
   preload_serve();
-  // one tiny analysis per pool graph: first-use host allocations (pinned
+  // one tiny analysis per batch graph: first-use host allocations (pinned
   // staging words) happen now, not while the serving kernel runs
   {
     const int32_t ro[2] = {0, 1};
     const int64_t c[2] = {d->dom_lo[0], d->dom_lo[1]};
     const uint8_t pw = RT_WRITE;
-    for (Slot& sl : s->slots) {
-      if (rt_launch_batch(sl.g, 1, ro, c, c, &pw, nullptr, nullptr, nullptr, RT_LAUNCH_DEFER_CHECK) != RT_OK ||
-          rt_analyze(sl.g) != RT_OK || rt_graph_clear(sl.g) != RT_OK)
+    for (Batch& b : s->batches) {
+      if (rt_launch_batch(b.g, 1, ro, c, c, &pw, nullptr, nullptr, nullptr, RT_LAUNCH_DEFER_CHECK) != RT_OK ||
+          rt_analyze(b.g) != RT_OK || rt_graph_clear(b.g) != RT_OK)
         return bail(RT_ERR_CUDA, "pool warm-up: " + last_err());
     }
   }
@@ -417,23 +616,35 @@ rt_status rt_server_submit(rt_server_t s, int32_t n, const int32_t* req_off, con
   const int64_t R = req_off[n];
   if (req_off[0] != 0 || R < 0 || (R > 0 && (!lo || !hi || !priv)))
     return sfail(RT_ERR_INVALID, "req_off must start at 0 and rect arrays must be set");
+  // Checked here, on the host: a batch shares one domain, so a rectangle
+  // outside its request's domain would meet another request's rectangles.
   const int D = s->desc.ndim;
-  auto r = std::make_unique<Request>();
-  r->n = n;
-  r->req_off.assign(req_off, req_off + n + 1);
-  r->lo.assign(lo, lo + R * D);
-  r->hi.assign(hi, hi + R * D);
-  r->priv.assign(priv, priv + R);
-  r->arrival = arrival_ns;
-  r->estimate = estimate_bytes(n, R);
-  if (r->estimate > s->desc.budget_bytes) return sfail(RT_ERR_BUDGET, "request can never fit the memory budget");
+  for (int32_t i = 0; i < n; ++i)
+    if (req_off[i + 1] < req_off[i]) return sfail(RT_ERR_INVALID, "req_off decreases at launch " + std::to_string(i));
+  for (int64_t r = 0; r < R; ++r) {
+    for (int k = 0; k < D; ++k) {
+      const int64_t a = lo[r * D + k], b = hi[r * D + k];
+      if (a > b || a < s->desc.dom_lo[k] || b > s->desc.dom_hi[k])
+        return sfail(RT_ERR_INVALID, "rect " + std::to_string(r) + " empty or outside the domain");
+    }
+    if (priv[r] > RT_REDUCE_SUM) return sfail(RT_ERR_INVALID, "rect " + std::to_string(r) + ": bad privilege");
+  }
+  auto q = std::make_unique<Request>();
+  q->n = n;
+  q->req_off.assign(req_off, req_off + n + 1);
+  q->lo.assign(lo, lo + R * D);
+  q->hi.assign(hi, hi + R * D);
+  q->priv.assign(priv, priv + R);
+  q->arrival = arrival_ns;
+  q->estimate = estimate_bytes(n, R);
+  if (q->estimate > s->desc.budget_bytes) return sfail(RT_ERR_BUDGET, "request can never fit the memory budget");
   std::lock_guard<std::mutex> lk(s->mu);
   if (s->stopping) return sfail(RT_ERR_STATE, "server is stopping");
-  r->ticket = s->next_ticket++;
-  *ticket = r->ticket;
-  s->pending.push_back(r.get());
+  q->ticket = s->next_ticket++;
+  *ticket = q->ticket;
+  s->pending.push_back(q.get());
   ++s->outstanding;
-  s->reqs.emplace(r->ticket, std::move(r));
+  s->reqs.emplace(q->ticket, std::move(q));
   s->cv.notify_one();
   return RT_OK;
 }
@@ -465,8 +676,11 @@ rt_status rt_server_result(rt_server_t s, int64_t ticket, int32_t* row_ptr, int3
   if (r->state == 4) return sfail((rt_status)r->status, "request failed: " + r->error);
   if (r->state != 3) return sfail(RT_ERR_STATE, "request is not done");
   if (!s->desc.keep_results) return sfail(RT_ERR_STATE, "server does not keep results");
-  if (row_ptr) memcpy(row_ptr, r->row_ptr.data(), r->row_ptr.size() * 4);
-  if (col) memcpy(col, r->col.data(), r->col.size() * 4);
+  if (row_ptr) {
+    if (r->row_ptr.empty()) row_ptr[0] = 0;  // an empty request
+    else memcpy(row_ptr, r->row_ptr.data(), r->row_ptr.size() * 4);
+  }
+  if (col && !r->col.empty()) memcpy(col, r->col.data(), r->col.size() * 4);
   if (out && !r->out.empty()) memcpy(out, r->out.data(), r->out.size() * 4);
   return RT_OK;
 }
@@ -477,7 +691,7 @@ rt_status rt_server_drain(rt_server_t s, int64_t timeout_ns) {
   std::unique_lock<std::mutex> lk(s->mu);
   while (s->outstanding > 0) {
     if (!s->fatal.empty()) {
-      // describe what is still running: completed tasks vs the graph's size
+      // describe what is still running: completed tasks vs the request's size
       std::string m = "serving kernel stopped: " + s->fatal;
       uint32_t kst = 0;
       cudaMemcpyAsync(&kst, &s->ctrl->status, 4, cudaMemcpyDeviceToHost, s->copy_stream);
@@ -500,16 +714,15 @@ rt_status rt_server_drain(rt_server_t s, int64_t timeout_ns) {
     if (now_ns() > until) {
       int by_state[5] = {0, 0, 0, 0, 0};
       for (auto& kv : s->reqs) by_state[std::min(std::max(kv.second->state, 0), 4)]++;
-      unsigned long long info[2] = {0, 0};
-      cudaMemcpyAsync(info, &s->ctrl->taken, 4, cudaMemcpyDeviceToHost, s->copy_stream);
-      cudaMemcpyAsync(info + 1, &s->ctrl->finished, 4, cudaMemcpyDeviceToHost, s->copy_stream);
+      uint32_t w[2] = {0, 0};
+      cudaMemcpyAsync(&w[0], &s->ctrl->taken, 4, cudaMemcpyDeviceToHost, s->copy_stream);
+      cudaMemcpyAsync(&w[1], &s->ctrl->finished, 4, cudaMemcpyDeviceToHost, s->copy_stream);
       cudaStreamSynchronize(s->copy_stream);
       char buf[256];
       snprintf(buf, sizeof buf,
                "drain timed out: %d queued, %d analysing, %d running, %d done, %d failed; posted %u, "
                "taken %u, finished %u",
-               by_state[0], by_state[1], by_state[2], by_state[3], by_state[4], s->mail->posted,
-               (unsigned)info[0], (unsigned)info[1]);
+               by_state[0], by_state[1], by_state[2], by_state[3], by_state[4], s->mail->posted, w[0], w[1]);
       return sfail(RT_ERR_TIMEOUT, buf);
     }
     s->cv_done.wait_for(lk, std::chrono::milliseconds(5));
@@ -519,14 +732,14 @@ rt_status rt_server_drain(rt_server_t s, int64_t timeout_ns) {
 
 rt_status rt_server_stats(rt_server_t s, int64_t* out, int32_t n) {
   if (!s || !out || n < 0) return sfail(RT_ERR_INVALID, "NULL argument");
-  unsigned int w[4] = {0, 0, 0, 0};
+  uint32_t w[3] = {0, 0, 0};
   unsigned long long ex = 0;
   cudaMemcpyAsync(&w[0], &s->ctrl->taken, 4, cudaMemcpyDeviceToHost, s->copy_stream);
   cudaMemcpyAsync(&w[1], &s->ctrl->finished, 4, cudaMemcpyDeviceToHost, s->copy_stream);
   cudaMemcpyAsync(&w[2], &s->ctrl->status, 4, cudaMemcpyDeviceToHost, s->copy_stream);
   cudaMemcpyAsync(&ex, &s->ctrl->executed, 8, cudaMemcpyDeviceToHost, s->copy_stream);
   if (cudaStreamSynchronize(s->copy_stream) != cudaSuccess) return sfail(RT_ERR_CUDA, "stats copy");
-  int64_t v[9];
+  int64_t v[11];
   v[0] = s->mail->posted;
   v[1] = w[0];
   v[2] = w[1];
@@ -536,15 +749,16 @@ rt_status rt_server_stats(rt_server_t s, int64_t* out, int32_t n) {
   {
     std::lock_guard<std::mutex> lk(s->mu);
     for (auto& kv : s->reqs) by_state[std::min(std::max(kv.second->state, 0), 4)]++;
+    v[9] = s->n_batches;
+    v[10] = s->n_batched;
   }
   v[5] = by_state[0];
   v[6] = by_state[1];
   v[7] = by_state[2];
   v[8] = cudaStreamQuery(s->exec_stream) == cudaErrorNotReady ? 1 : 0;
-  for (int k = 0; k < n && k < 9; ++k) out[k] = v[k];
+  for (int k = 0; k < n && k < 11; ++k) out[k] = v[k];
   return RT_OK;
 }
-
 rt_status rt_server_destroy(rt_server_t s) {
   if (!s) return RT_OK;
   rt_status st = rt_server_drain(s, 30ll * 1000000000ll);

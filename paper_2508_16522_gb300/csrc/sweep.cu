@@ -19,6 +19,13 @@
 // runs are enumerated by re-reading the candidates between their first and
 // last member (the ones covering the cell are exactly the members).
 //
+// Before sweeping a tile, its columns and rows are split into classes at the
+// rectangle boundaries that fall inside it (a column class is a maximal run of
+// columns no candidate's edge separates). Every cell of a class is covered by
+// the same candidates, so the sweep runs on the class grid instead of the
+// cells: a rectangle covering the whole tile costs one class, not tw x th
+// cells, and the predecessor sets are the same.
+//
 // Lanes split the cells of the task's rectangle; predecessors found by
 // several lanes are merged with match_any, and the survivors go through a
 // per-warp shared-memory hash set, so each (src, dst) pair leaves the tile once
@@ -37,9 +44,12 @@ constexpr int kSmallCells = 16;  // largest box the lane-parallel path takes
 constexpr int kMaxRounds = 8;    // deeper conflict chains go to the warp-wide path
 constexpr unsigned kFull = 0xffffffffu;
 
+// class maps: tw + th <= C + 1 uint16 entries
+__host__ __device__ inline size_t class_map_bytes(int C) { return (size_t)((2 * (C + 1) + 15) & ~15); }
+
 __host__ __device__ inline size_t per_warp_bytes(int C) {
   return (size_t)16 * C + (size_t)((C + 15) & ~15) + 32 * 8 + kHashSlots * 4 + kListCap * 8 + 16 +
-         32 * kLaneBuf * 4;
+         32 * kLaneBuf * 4 + class_map_bytes(C);
 }
 
 struct WarpSmem {
@@ -51,7 +61,42 @@ struct WarpSmem {
   int* hslot;
   int* hcount;
   int* lbuf;  // [32][kLaneBuf]
+  uint16_t* cmx;  // column -> column class of the current tile
+  uint16_t* cmy;  // row -> row class
 };
+
+// A candidate's box in class coordinates. Within a tile, the columns (rows)
+// are split into classes at every rectangle boundary that falls inside it;
+// cells of one class are covered by exactly the same candidates, so their
+// run states evolve identically and one cell per class stands for all.
+__device__ __forceinline__ Box unpack_c(const WarpSmem& w, uint64_t p, int ndim) {
+  Box b = unpack_entry(p, ndim);
+  b.x0 = w.cmx[b.x0];
+  b.x1 = w.cmx[b.x1];
+  b.y0 = w.cmy[b.y0];
+  b.y1 = w.cmy[b.y1];
+  return b;
+}
+
+// in place: a[i] <- a[0] + ... + a[i] over a[0..L) (one warp, convergent)
+__device__ void scan_flags(uint16_t* a, int L, int lane) {
+  const int per = (L + 31) >> 5;
+  const int b0 = min(lane * per, L), b1 = min(b0 + per, L);
+  int sum = 0;
+  for (int i = b0; i < b1; ++i) sum += a[i];
+  int incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  int run = incl - sum;
+  for (int i = b0; i < b1; ++i) {
+    run += a[i];
+    a[i] = (uint16_t)run;
+  }
+  __syncwarp();
+}
 
 struct Ctx {
   const uint64_t* L;  // the tile's candidates
@@ -229,7 +274,7 @@ __device__ void sweep_box(Ctx& x, const WarpSmem& w, const SweepOut& o, int x0, 
       // three or more members: the candidates strictly between the first and
       // the last member that cover this cell are the others
       for (uint32_t q = rs + 1; q < rl; ++q) {
-        Box b = unpack_entry(entry_at(x, w, (int)q), x.ndim);
+        Box b = unpack_c(w, entry_at(x, w, (int)q), x.ndim);
         if (b.x0 <= cx && cx <= b.x1 && b.y0 <= cy && cy <= b.y1) hash_insert(w, o, b.task, dst);
       }
     }
@@ -273,7 +318,7 @@ __device__ __forceinline__ void lane_add(const WarpSmem& w, const SweepOut& o, i
 __device__ bool stage_lanes(Ctx& x, const WarpSmem& w, const SweepOut& o, unsigned starts, int end) {
   const int lane = x.lane;
   const bool mine = lane < end;
-  Box b = unpack_entry(mine ? w.stage[lane] : 0ull, x.ndim);
+  Box b = unpack_c(w, mine ? w.stage[lane] : 0ull, x.ndim);
   const int cells = mine ? (b.x1 - b.x0 + 1) * (b.y1 - b.y0 + 1) : 0;
   if (!__all_sync(kFull, cells <= kSmallCells)) return false;
   // position of this candidate's task (its group's first candidate)
@@ -307,7 +352,7 @@ __device__ bool stage_lanes(Ctx& x, const WarpSmem& w, const SweepOut& o, unsign
         if (rc >= 2u) lane_add(w, o, lane, nb, (int)(uint32_t)entry_at(x, w, (int)rl), b.task);
         if (rc == 3u) {
           for (uint32_t q = rs + 1; q < rl; ++q) {
-            Box e = unpack_entry(entry_at(x, w, (int)q), x.ndim);
+            Box e = unpack_c(w, entry_at(x, w, (int)q), x.ndim);
             if (e.x0 <= cx && cx <= e.x1 && e.y0 <= cy && cy <= e.y1) lane_add(w, o, lane, nb, e.task, b.task);
           }
         }
@@ -338,7 +383,7 @@ __device__ void process_group(Ctx& x, const WarpSmem& w, const SweepOut& o, int 
   const int dst = (int)(uint32_t)first;
   const int g = b - a;
   if (g == 1) {
-    Box bx = unpack_entry(first, x.ndim);
+    Box bx = unpack_c(w, first, x.ndim);
     sweep_box(x, w, o, bx.x0, bx.x1, bx.y0, bx.y1, a, bx.priv, false, dst);
   } else {
     // disjoint rectangles need no privilege combination
@@ -346,9 +391,9 @@ __device__ void process_group(Ctx& x, const WarpSmem& w, const SweepOut& o, int 
     if (!overlap) {
       bool mine = false;
       if (x.lane < g) {
-        Box bi = unpack_entry(entry_at(x, w, a + x.lane), x.ndim);
+        Box bi = unpack_c(w, entry_at(x, w, a + x.lane), x.ndim);
         for (int j = x.lane + 1; j < g; ++j) {
-          Box bj = unpack_entry(entry_at(x, w, a + j), x.ndim);
+          Box bj = unpack_c(w, entry_at(x, w, a + j), x.ndim);
           if (bi.x0 <= bj.x1 && bj.x0 <= bi.x1 && bi.y0 <= bj.y1 && bj.y0 <= bi.y1) mine = true;
         }
       }
@@ -356,16 +401,16 @@ __device__ void process_group(Ctx& x, const WarpSmem& w, const SweepOut& o, int 
     }
     if (!overlap) {
       for (int e = a; e < b; ++e) {
-        Box bx = unpack_entry(entry_at(x, w, e), x.ndim);
+        Box bx = unpack_c(w, entry_at(x, w, e), x.ndim);
         sweep_box(x, w, o, bx.x0, bx.x1, bx.y0, bx.y1, a, bx.priv, false, dst);
       }
     } else {
       for (int e = a; e < b; ++e) {
-        mark_box(x, w, unpack_entry(entry_at(x, w, e), x.ndim));
+        mark_box(x, w, unpack_c(w, entry_at(x, w, e), x.ndim));
         __syncwarp();
       }
       for (int e = a; e < b; ++e) {
-        Box bx = unpack_entry(entry_at(x, w, e), x.ndim);
+        Box bx = unpack_c(w, entry_at(x, w, e), x.ndim);
         sweep_box(x, w, o, bx.x0, bx.x1, bx.y0, bx.y1, a, 0, true, dst);
         __syncwarp();
       }
@@ -391,6 +436,8 @@ __global__ void __launch_bounds__(256) k_sweep(const uint64_t* __restrict__ payl
   w.hslot = w.hlist + kListCap;
   w.hcount = w.hslot + kListCap;
   w.lbuf = w.hcount + 4;
+  w.cmx = reinterpret_cast<uint16_t*>(w.lbuf + 32 * kLaneBuf);
+  w.cmy = w.cmx + d.tw;
   for (int i = lane; i < kHashSlots; i += 32) w.htab[i] = -1;
   if (lane == 0) *w.hcount = 0;
   __syncwarp();
@@ -409,13 +456,30 @@ __global__ void __launch_bounds__(256) k_sweep(const uint64_t* __restrict__ payl
     if (t >= ntiles) break;
     const uint32_t sb = seg_begin[t], se = seg_end[t];
     if (sb >= se) continue;
-    for (int c = lane; c < C; c += 32) {
+    x.L = payload + sb;
+    x.n = (int)(se - sb);
+    // class maps of this tile: mark every rectangle boundary inside it, then
+    // number the classes by a prefix sum
+    for (int i = lane; i < d.tw; i += 32) w.cmx[i] = 0;
+    for (int i = lane; i < d.th; i += 32) w.cmy[i] = 0;
+    __syncwarp();
+    for (int k = lane; k < x.n; k += 32) {
+      const Box b = unpack_entry(x.L[k], x.ndim);
+      if (b.x0 > 0) w.cmx[b.x0] = 1;
+      if (b.x1 + 1 < d.tw) w.cmx[b.x1 + 1] = 1;
+      if (b.y0 > 0) w.cmy[b.y0] = 1;
+      if (b.y1 + 1 < d.th) w.cmy[b.y1 + 1] = 1;
+    }
+    __syncwarp();
+    scan_flags(w.cmx, d.tw, lane);
+    scan_flags(w.cmy, d.th, lane);
+    const int cw = w.cmx[d.tw - 1] + 1, ch = w.cmy[d.th - 1] + 1;
+    x.tw = cw;  // row stride of the class grid
+    for (int c = lane; c < cw * ch; c += 32) {
       w.cell[c] = make_uint4((uint32_t)kKindNone << 30, 0u, 0u, 0u);
       w.scr[c] = 0xFFu;
     }
     __syncwarp();
-    x.L = payload + sb;
-    x.n = (int)(se - sb);
     int pos = 0;
     while (pos < x.n) {
       const int cnt = x.n - pos < 32 ? x.n - pos : 32;

@@ -55,7 +55,8 @@ class rt_server_desc(ctypes.Structure):
                 ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("body", ctypes.c_int32),
                 ("spin_iters", ctypes.c_int32), ("budget_bytes", ctypes.c_int64), ("max_inflight", ctypes.c_int32),
                 ("max_tasks", ctypes.c_int32), ("workers", ctypes.c_int32), ("keep_results", ctypes.c_int32),
-                ("exec_blocks", ctypes.c_int32), ("exec_warps", ctypes.c_int32), ("timeout_ns", ctypes.c_int64)]
+                ("exec_blocks", ctypes.c_int32), ("exec_warps", ctypes.c_int32), ("timeout_ns", ctypes.c_int64),
+                ("max_batch", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
 
 
 class rt_request_info(ctypes.Structure):
@@ -394,14 +395,15 @@ def rt_now_ns() -> int:
 
 
 class Server:
-    """Continuous-batching server: submit graphs (host arrays); each is
-    analysed by a worker thread and run by the persistent serving kernel."""
+    """Continuous-batching server: submit graphs (host arrays); worker threads
+    analyse the waiting ones together (up to max_batch per analysis) and the
+    persistent serving kernel runs them beside the graphs already running."""
 
     STATES = ("queued", "analysing", "running", "done", "failed")
 
     def __init__(self, ndim, dom_lo, dom_hi, body=RT_BODY_EMPTY, spin_iters=256, budget_bytes=8 << 30,
                  max_inflight=64, max_tasks=16384, workers=8, keep_results=False, tile=(0, 0),
-                 exec_blocks=0, exec_warps=0, timeout_ns=0):
+                 exec_blocks=0, exec_warps=0, timeout_ns=0, max_batch=0):
         d = rt_server_desc()
         d.ndim = ndim
         for k in range(ndim):
@@ -412,6 +414,7 @@ class Server:
         d.budget_bytes, d.max_inflight, d.max_tasks = budget_bytes, max_inflight, max_tasks
         d.workers, d.keep_results = workers, int(bool(keep_results))
         d.exec_blocks, d.exec_warps, d.timeout_ns = exec_blocks, exec_warps, timeout_ns
+        d.max_batch = max_batch
         h = ctypes.c_void_p()
         _check(load().rt_server_create(ctypes.byref(d), ctypes.byref(h)))
         self.h = h.value
@@ -437,10 +440,10 @@ class Server:
         return rp, col[:n_edges], (None if out is None else out[:n_tasks])
 
     def stats(self) -> dict:
-        arr = (ctypes.c_int64 * 9)()
-        _check(load().rt_server_stats(self.h, arr, 9))
+        arr = (ctypes.c_int64 * 11)()
+        _check(load().rt_server_stats(self.h, arr, 11))
         return dict(zip(("posted", "taken", "finished", "status", "executed", "queued", "analysing", "running",
-                         "kernel_running"), list(arr)))
+                         "kernel_running", "batches", "batched_requests"), list(arr)))
 
     def drain(self, timeout_ns=0):
         _check(load().rt_server_drain(self.h, timeout_ns))

@@ -46,6 +46,9 @@ def test_burst_in_the_mix_equals_alone():
     tickets = [srv.submit(tr) for tr in traces]
     srv.drain(60_000_000_000)
     check_all(srv, tickets, traces, 11)
+    st = srv.stats()
+    # requests that waited together were analysed together
+    assert st["batched_requests"] == 60 and st["batches"] < 60, st
     # the kernel keeps running: a second wave is admitted and executed too
     more = requests(20, seed=2)
     t2 = [srv.submit(tr) for tr in more]
@@ -101,4 +104,40 @@ def test_empty_request_and_budget_refusal():
     with pytest.raises(grt.GrtError) as e:
         srv.submit(big)  # estimate (> 16 MB) can never fit the budget
     assert e.value.status == grt.RT_ERR_BUDGET
+    srv.close()
+
+
+def test_one_request_per_batch_gives_the_same_results():
+    ensure_built()
+    traces = requests(16, seed=5, n_range=(50, 400))
+    srv = grt.Server(2, [0, 0], [GRID[0] - 1, GRID[1] - 1], body=grt.RT_BODY_SPIN, spin_iters=3,
+                     max_inflight=8, max_tasks=512, workers=2, keep_results=True, max_batch=1)
+    tickets = [srv.submit(tr) for tr in traces]
+    srv.drain(60_000_000_000)
+    check_all(srv, tickets, traces, 3)
+    st = srv.stats()
+    assert st["batches"] == 16 and st["batched_requests"] == 16, st
+    srv.close()
+
+
+def test_one_dimensional_requests_stack_along_x():
+    ensure_built()
+    traces = [tg.random_rects(grid=(997,), n=int(n), rects=(1, 4), side=(1, 90), seed=70 + i, ndim=1)
+              for i, n in enumerate((400, 37, 250, 1, 600, 128))]
+    srv = grt.Server(1, [0], [996], body=grt.RT_BODY_SPIN, spin_iters=7, max_inflight=6, max_tasks=600,
+                     workers=1, keep_results=True, max_batch=4)
+    tickets = [srv.submit(tr) for tr in traces]
+    srv.drain(60_000_000_000)
+    check_all(srv, tickets, traces, 7)
+    srv.close()
+
+
+def test_submit_rejects_rectangles_outside_the_domain():
+    ensure_built()
+    srv = grt.Server(2, [0, 0], [GRID[0] - 1, GRID[1] - 1], max_inflight=2, max_tasks=64, workers=1)
+    bad = tg._finish(2, [0, 0], [GRID[0] - 1, GRID[1] + 9], np.array([1]), np.array([0, GRID[1]]),
+                     np.array([3, GRID[1] + 2]), np.array([1], np.uint8))
+    with pytest.raises(grt.GrtError) as e:
+        srv.submit(bad)  # a rectangle past the domain would reach the next request's band
+    assert e.value.status == grt.RT_ERR_INVALID
     srv.close()
