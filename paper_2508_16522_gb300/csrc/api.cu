@@ -129,6 +129,7 @@ struct rt_graph {
   // analysis
   DevBuf rect_task, cnt, keys, keys_alt, pay, pay_alt, seg_b, seg_e, pairs, pairs_alt, flags, upos;
   DevBuf col, row_ptr, indeg, count, rootpos, root_items, ws, misc, adj;
+  DevBuf tflags;  // per tile: dropped a pair in the first sweep / in the rerun
   // execution
   DevBuf ring, ctrl, gtable, done_g, tickets;
   uint32_t* hpin = nullptr;  // pinned readback area (64 words)
@@ -204,7 +205,9 @@ rt_status check_desc(const rt_graph_desc* d, AnalysisDims* out, int64_t* ncells)
     if (d->tile_h > 1) return fail(RT_ERR_INVALID, "1-D graphs have tile_h 1");
     if (a.tw > kMaxTileSide1D) return fail(RT_ERR_INVALID, "1-D tile must be <= %d", kMaxTileSide1D);
   }
-  if (a.tw * a.th > kMaxTileCells) return fail(RT_ERR_INVALID, "tile has more than %d cells", kMaxTileCells);
+  // 2-D tiles larger than the per-warp cell state are swept in strips of
+  // column/row classes; a 1-D tile's classes must fit it at once
+  if (a.th == 1 && a.tw > kMaxClassCells) return fail(RT_ERR_INVALID, "1-D tile must be <= %d", kMaxClassCells);
   int64_t ntx = (a.ext[0] + a.tw - 1) / a.tw, nty = (a.ext[1] + a.th - 1) / a.th;
   if (ntx * nty > (1ll << 26)) return fail(RT_ERR_INVALID, "domain has more than 2^26 tiles; use a larger tile");
   a.ntx = (int)ntx;
@@ -275,7 +278,7 @@ rt_status rt_graph_destroy(rt_graph_t g) {
                     &g->err, &g->rect_task, &g->cnt, &g->keys, &g->keys_alt, &g->pay, &g->pay_alt,
                     &g->seg_b, &g->seg_e, &g->pairs, &g->pairs_alt, &g->flags, &g->upos, &g->col,
                     &g->row_ptr, &g->indeg, &g->count, &g->rootpos, &g->root_items, &g->ws, &g->misc, &g->adj,
-                    &g->ring, &g->ctrl, &g->gtable, &g->done_g, &g->tickets};
+                    &g->ring, &g->ctrl, &g->gtable, &g->done_g, &g->tickets, &g->tflags};
   for (DevBuf* b : bufs) b->release(g->s);
   cudaStreamSynchronize(g->s);
   if (g->hpin) cudaFreeHost(g->hpin);
@@ -547,9 +550,13 @@ rt_status run_analysis(rt_graph* g) {
   const int64_t Pe = g->has_pred ? g->P : 0;
   // Each sweep warp leaves holes in at most its last chunk, so the cursor ends
   // below (pairs written) + (warps x chunk). The chunk is sized to keep that
-  // slack near half the first guess; an overflowed sweep has counted what it
-  // reserved, and a rerun with that much plus the slack always fits.
-  const int sweep_warps = sweep_warps_per_block(d.tw * d.th);
+  // slack near half the first guess. If the buffer overflows, the sweep has
+  // flagged the tiles that dropped a pair and counted the pairs they emit;
+  // the buffer grows by that much plus the slack (the part already written is
+  // kept, the reserved tail past the old end becomes sentinels) and only the
+  // flagged tiles are swept again, appending. Their pairs written before the
+  // overflow are kept too: duplicates vanish in the dedupe.
+  const int sweep_warps = sweep_warps_per_block(d.tw, d.th);
   const int sweep_blocks =
       (int)std::max<int64_t>(std::min<int64_t>((ntiles + sweep_warps - 1) / sweep_warps, (int64_t)g_dev.num_sms * 8), 1);
   const unsigned long long W = (unsigned long long)sweep_blocks * (unsigned long long)sweep_warps;
@@ -557,31 +564,48 @@ rt_status run_analysis(rt_graph* g) {
   uint32_t chunk = 32;
   while (chunk < 512 && 2ull * chunk * W <= guess) chunk <<= 1;
   unsigned long long cap = (unsigned long long)Pe + (M > 0 ? guess + W * chunk : 0ull);
+  CKR(g->pairs.reserve((size_t)std::max<unsigned long long>(cap, 1) * 8, s));
+  if (Pe > 0)
+    launch_explicit_pairs(g->pred_off.as<int32_t>(), g->pred.as<int32_t>(), n, B, g->pairs.as<uint64_t>(), s);
   int64_t Ptot = Pe;
-  for (int attempt = 0; attempt < 2; ++attempt) {
-    CKR(g->pairs.reserve((size_t)std::max<unsigned long long>(cap, 1) * 8, s));
-    CKR(g->pairs_alt.reserve((size_t)std::max<unsigned long long>(cap, 1) * 8, s));
-    if (Pe > 0)
-      launch_explicit_pairs(g->pred_off.as<int32_t>(), g->pred.as<int32_t>(), n, B,
-                            g->pairs.as<uint64_t>(), s);
-    if (M == 0) break;
+  if (M > 0) {
+    unsigned long long* rerun = reinterpret_cast<unsigned long long*>(g->misc.as<char>() + 128);
+    CKR(g->tflags.reserve((size_t)ntiles * 2, s));
+    uint8_t* flags1 = g->tflags.as<uint8_t>();
+    uint8_t* flags2 = flags1 + ntiles;
+    CK(cudaMemsetAsync(flags1, 0, (size_t)ntiles * 2, s));
     h64[2] = (uint64_t)Pe;
     CK(cudaMemcpyAsync(cursor, (const void*)&h64[2], 8, cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(tile_counter, 0, 4, s));
-    SweepOut o{g->pairs.as<uint64_t>(), cap, cursor, tile_counter, B, chunk};
+    CK(cudaMemsetAsync(rerun, 0, 8, s));
+    SweepOut o{g->pairs.as<uint64_t>(), cap, cursor, tile_counter, B, chunk, nullptr, flags1, rerun};
     if (prof) CK(cudaEventRecord(g->ev[EV_SW0], s));
     launch_sweep(spay, g->seg_b.as<uint32_t>(), g->seg_e.as<uint32_t>(), d, o, sweep_blocks, s);
     if (prof) CK(cudaEventRecord(g->ev[EV_SW1], s));
     CK(cudaGetLastError());
     trace("analyze: sweep enqueued");
     CK(cudaMemcpyAsync((void*)&h64[3], cursor, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync((void*)&h64[5], rerun, 8, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     trace("analyze: sweep synced");
     Ptot = (int64_t)h64[3];
-    if ((unsigned long long)Ptot <= cap) break;
-    cap = (unsigned long long)Ptot + W * chunk;  // the sweep counted what it reserved: rerun once
-    if (attempt == 1) return fail(RT_ERR_OOM, "pair buffer overflowed twice");
+    if ((unsigned long long)Ptot > cap) {
+      const unsigned long long old_cap = cap;
+      cap = (unsigned long long)Ptot + (unsigned long long)h64[5] + W * chunk;
+      CKR(g->pairs.reserve((size_t)cap * 8, s, (size_t)old_cap * 8));
+      CK(cudaMemsetAsync(g->pairs.as<uint64_t>() + old_cap, 0xFF, (size_t)(Ptot - old_cap) * 8, s));
+      CK(cudaMemsetAsync(tile_counter, 0, 4, s));
+      SweepOut o2{g->pairs.as<uint64_t>(), cap, cursor, tile_counter, B, chunk, flags1, flags2, rerun};
+      launch_sweep(spay, g->seg_b.as<uint32_t>(), g->seg_e.as<uint32_t>(), d, o2, sweep_blocks, s);
+      if (prof) CK(cudaEventRecord(g->ev[EV_SW1], s));
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync((void*)&h64[3], cursor, 8, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      Ptot = (int64_t)h64[3];
+      if ((unsigned long long)Ptot > cap) return fail(RT_ERR_OOM, "pair buffer overflowed in the rerun");
+    }
   }
+  CKR(g->pairs_alt.reserve((size_t)std::max<int64_t>(Ptot, 1) * 8, s));
   if (Ptot >= (1ll << 31) - 1) return fail(RT_ERR_OOM, "%lld candidate pairs (limit 2^31)", (long long)Ptot);
   if (prof) CK(cudaEventRecord(g->ev[EV_SWEEP], s));
   g->n_pairs = Ptot;
@@ -1198,7 +1222,7 @@ rt_status graph_view(rt_graph_t g, GraphView* v) {
                           &g->rect_task, &g->cnt, &g->keys, &g->keys_alt, &g->pay, &g->pay_alt, &g->seg_b,
                           &g->seg_e, &g->pairs, &g->pairs_alt, &g->flags, &g->upos, &g->col, &g->row_ptr,
                           &g->indeg, &g->count, &g->rootpos, &g->root_items, &g->ws, &g->misc, &g->adj,
-                          &g->ring, &g->ctrl, &g->gtable, &g->done_g, &g->tickets};
+                          &g->ring, &g->ctrl, &g->gtable, &g->done_g, &g->tickets, &g->tflags};
   for (const DevBuf* b : bufs) f += b->cap;
   v->footprint = f;
   return RT_OK;

@@ -28,7 +28,7 @@ constexpr int kKindRead = 0, kKindWrite = 1, kKindReduce = 2, kKindNone = 3;
 // ---------------------------------------------------------------------------
 constexpr int kMaxTileSide2D = 128;
 constexpr int kMaxTileSide1D = 16384;
-constexpr int kMaxTileCells = 1024;  // per-warp cell state lives in shared memory
+constexpr int kMaxClassCells = 1024;  // per-warp cell state (shared memory): class cells swept at once
 
 __host__ __device__ inline uint64_t pack_entry(uint32_t task, uint32_t priv, int ndim, uint32_t x0,
                                                uint32_t x1, uint32_t y0, uint32_t y1) {
@@ -267,9 +267,12 @@ struct SweepOut {
   uint32_t* tile_counter;
   int key_bits;
   uint32_t chunk;  // pairs a warp reserves at a time (its last chunk may keep holes)
+  const uint8_t* only;       // non-null: sweep only the tiles flagged here
+  uint8_t* flag_out;         // non-null: flag the tiles that dropped a pair
+  unsigned long long* rerun; // pairs emitted by the tiles that dropped one
 };
-int sweep_warps_per_block(int tile_cells);
-size_t sweep_smem_bytes(int tile_cells, int warps);
+int sweep_warps_per_block(int tw, int th);
+size_t sweep_smem_bytes(int tw, int th, int warps);
 void launch_sweep(const uint64_t* payload, const uint32_t* seg_begin, const uint32_t* seg_end,
                   AnalysisDims d, SweepOut o, int blocks, cudaStream_t s);
 void launch_explicit_pairs(const int32_t* pred_off, const int32_t* pred, int32_t n, int key_bits,

@@ -42,14 +42,19 @@ constexpr int kListCap = 64;
 constexpr int kLaneBuf = 16;     // predecessors one lane buffers in the lane-parallel path
 constexpr int kSmallCells = 16;  // largest box the lane-parallel path takes
 constexpr int kMaxRounds = 8;    // deeper conflict chains go to the warp-wide path
+constexpr int kLongSpan = 64;    // run spans the whole warp scans together
 constexpr unsigned kFull = 0xffffffffu;
 
-// class maps: tw + th <= C + 1 uint16 entries
-__host__ __device__ inline size_t class_map_bytes(int C) { return (size_t)((2 * (C + 1) + 15) & ~15); }
+// cells of the class grid one warp sweeps at once (taller grids go in strips)
+__host__ __device__ inline int class_cap(int tw, int th) { return tw * th < kMaxClassCells ? tw * th : kMaxClassCells; }
 
-__host__ __device__ inline size_t per_warp_bytes(int C) {
+// class maps: tw + th uint16 entries
+__host__ __device__ inline size_t class_map_bytes(int tw, int th) { return (size_t)((2 * (tw + th) + 15) & ~15); }
+
+__host__ __device__ inline size_t per_warp_bytes(int tw, int th) {
+  const int C = class_cap(tw, th);
   return (size_t)16 * C + (size_t)((C + 15) & ~15) + 32 * 8 + kHashSlots * 4 + kListCap * 8 + 16 +
-         32 * kLaneBuf * 4 + class_map_bytes(C);
+         32 * kLaneBuf * 4 + class_map_bytes(tw, th);
 }
 
 struct WarpSmem {
@@ -63,20 +68,9 @@ struct WarpSmem {
   int* lbuf;  // [32][kLaneBuf]
   uint16_t* cmx;  // column -> column class of the current tile
   uint16_t* cmy;  // row -> row class
+  int* dropped;   // a pair of the current tile fell past the buffer's end
+  int* npairs;    // pairs the current tile emitted
 };
-
-// A candidate's box in class coordinates. Within a tile, the columns (rows)
-// are split into classes at every rectangle boundary that falls inside it;
-// cells of one class are covered by exactly the same candidates, so their
-// run states evolve identically and one cell per class stands for all.
-__device__ __forceinline__ Box unpack_c(const WarpSmem& w, uint64_t p, int ndim) {
-  Box b = unpack_entry(p, ndim);
-  b.x0 = w.cmx[b.x0];
-  b.x1 = w.cmx[b.x1];
-  b.y0 = w.cmy[b.y0];
-  b.y1 = w.cmy[b.y1];
-  return b;
-}
 
 // in place: a[i] <- a[0] + ... + a[i] over a[0..L) (one warp, convergent)
 __device__ void scan_flags(uint16_t* a, int L, int lane) {
@@ -104,13 +98,45 @@ struct Ctx {
   int pos;            // position of the staged window
   int cnt;            // entries in the window
   int tw, ndim;
+  int ylo, yhi;       // the strip of class rows being swept
   unsigned long long chunk_base;
   uint32_t chunk_left;
   int lane;
 };
 
-__device__ __forceinline__ void put_pair(const SweepOut& o, unsigned long long idx, uint64_t key) {
-  if (idx < o.cap) o.pairs[idx] = key;
+// A candidate's box in class coordinates. Within a tile, the columns (rows)
+// are split into classes at every rectangle boundary that falls inside it;
+// cells of one class are covered by exactly the same candidates, so their
+// run states evolve identically and one cell per class stands for all.
+// Rows are further clipped to the strip of class rows being swept, and
+// renumbered from its first; a candidate outside the strip gets an empty box
+// (x0 > x1, y0 > y1) that covers no cell. The overlap tests that order
+// candidates may still pair an empty box with another; that only orders it
+// more than needed.
+__device__ __forceinline__ Box unpack_c(const Ctx& x, const WarpSmem& w, uint64_t p) {
+  Box b = unpack_entry(p, x.ndim);
+  b.x0 = w.cmx[b.x0];
+  b.x1 = w.cmx[b.x1];
+  int y0 = w.cmy[b.y0], y1 = w.cmy[b.y1];
+  y0 = y0 > x.ylo ? y0 : x.ylo;
+  y1 = y1 < x.yhi ? y1 : x.yhi;
+  if (y0 > y1) {
+    b.x0 = b.y0 = 1;
+    b.x1 = b.y1 = 0;
+  } else {
+    b.y0 = y0 - x.ylo;
+    b.y1 = y1 - x.ylo;
+  }
+  return b;
+}
+
+__device__ __forceinline__ void put_pair(const WarpSmem& w, const SweepOut& o, unsigned long long idx,
+                                         uint64_t key) {
+  if (idx < o.cap) {
+    o.pairs[idx] = key;
+  } else if (key != kEmpty64) {
+    *w.dropped = 1;
+  }
 }
 
 __device__ __forceinline__ uint64_t pair_key(int src, int dst, int key_bits) {
@@ -125,7 +151,8 @@ __device__ __forceinline__ uint64_t entry_at(const Ctx& x, const WarpSmem& w, in
 // lane-level insert (may run divergently)
 __device__ void hash_insert(const WarpSmem& w, const SweepOut& o, int src, int dst) {
   if (*(volatile int*)w.hcount >= kListCap) {
-    put_pair(o, atomicAdd(o.cursor, 1ull), pair_key(src, dst, o.key_bits));
+    put_pair(w, o, atomicAdd(o.cursor, 1ull), pair_key(src, dst, o.key_bits));
+    atomicAdd(w.npairs, 1);
     return;
   }
   uint32_t h = ((uint32_t)src * 2654435761u) >> 25;  // 7 bits -> 128 slots
@@ -137,7 +164,8 @@ __device__ void hash_insert(const WarpSmem& w, const SweepOut& o, int src, int d
         w.hlist[idx] = src;
         w.hslot[idx] = (int)h;
       } else {
-        put_pair(o, atomicAdd(o.cursor, 1ull), pair_key(src, dst, o.key_bits));
+        put_pair(w, o, atomicAdd(o.cursor, 1ull), pair_key(src, dst, o.key_bits));
+        atomicAdd(w.npairs, 1);
       }
       return;
     }
@@ -191,8 +219,9 @@ __device__ void flush(Ctx& x, const WarpSmem& w, const SweepOut& o, int dst) {
   const int m = cnt < kListCap ? cnt : kListCap;
   if (m > 0) {
     const PairDst pd = reserve_pairs(x, o, (uint32_t)m);
+    if (x.lane == 0) atomicAdd(w.npairs, m);
     for (int i = x.lane; i < m; i += 32) {
-      put_pair(o, pair_pos(pd, (uint32_t)i), pair_key(w.hlist[i], dst, o.key_bits));
+      put_pair(w, o, pair_pos(pd, (uint32_t)i), pair_key(w.hlist[i], dst, o.key_bits));
       if (cnt <= kListCap) w.htab[w.hslot[i]] = -1;
     }
   }
@@ -240,6 +269,7 @@ __device__ __forceinline__ void apply_cell(const WarpSmem& w, int c, int gpos, i
 // from the scratch bytes, consumed so a cell is applied once).
 __device__ void sweep_box(Ctx& x, const WarpSmem& w, const SweepOut& o, int x0, int x1, int y0,
                           int y1, int gpos, int p, bool use_scr, int dst) {
+  if (x1 < x0 || y1 < y0) return;  // a candidate outside the strip (warp-uniform)
   const int bw = x1 - x0 + 1, bh = y1 - y0 + 1;
   const int total = bw * bh;
   int qx = x.lane % bw, qy = x.lane / bw;
@@ -270,12 +300,29 @@ __device__ void sweep_box(Ctx& x, const WarpSmem& w, const SweepOut& o, int x0, 
     }
     warp_insert(w, o, m1, dst);
     warp_insert(w, o, m2, dst);
-    if (act && rc == 3u) {
-      // three or more members: the candidates strictly between the first and
-      // the last member that cover this cell are the others
+    // three or more members: the candidates strictly between the first and
+    // the last member that cover the cell are the others. Short spans are
+    // scanned by their own lane, all lanes at once; each long span is scanned
+    // by the whole warp, 32 consecutive candidates per step.
+    const bool longspan = act && rc == 3u && rl - rs > (uint32_t)kLongSpan;
+    if (act && rc == 3u && !longspan) {
       for (uint32_t q = rs + 1; q < rl; ++q) {
-        Box b = unpack_c(w, entry_at(x, w, (int)q), x.ndim);
+        const Box b = unpack_c(x, w, entry_at(x, w, (int)q));
         if (b.x0 <= cx && cx <= b.x1 && b.y0 <= cy && cy <= b.y1) hash_insert(w, o, b.task, dst);
+      }
+    }
+    unsigned need = __ballot_sync(kFull, longspan);
+    while (need) {
+      const int l = __ffs((int)need) - 1;
+      need &= need - 1;
+      const int qs = __shfl_sync(kFull, (int)rs, l) + 1, qe = __shfl_sync(kFull, (int)rl, l);
+      const int lx = __shfl_sync(kFull, cx, l), ly = __shfl_sync(kFull, cy, l);
+      for (int q0 = qs; q0 < qe; q0 += 32) {
+        const int q = q0 + x.lane;
+        if (q < qe) {
+          const Box b = unpack_c(x, w, entry_at(x, w, q));
+          if (b.x0 <= lx && lx <= b.x1 && b.y0 <= ly && ly <= b.y1) hash_insert(w, o, b.task, dst);
+        }
       }
     }
     qx += dx;
@@ -304,7 +351,8 @@ __device__ __forceinline__ void lane_add(const WarpSmem& w, const SweepOut& o, i
   if (nb < kLaneBuf) {
     w.lbuf[lane * kLaneBuf + nb++] = src;
   } else {
-    put_pair(o, atomicAdd(o.cursor, 1ull), pair_key(src, dst, o.key_bits));
+    put_pair(w, o, atomicAdd(o.cursor, 1ull), pair_key(src, dst, o.key_bits));
+    atomicAdd(w.npairs, 1);
   }
 }
 
@@ -318,7 +366,7 @@ __device__ __forceinline__ void lane_add(const WarpSmem& w, const SweepOut& o, i
 __device__ bool stage_lanes(Ctx& x, const WarpSmem& w, const SweepOut& o, unsigned starts, int end) {
   const int lane = x.lane;
   const bool mine = lane < end;
-  Box b = unpack_c(w, mine ? w.stage[lane] : 0ull, x.ndim);
+  Box b = unpack_c(x, w, mine ? w.stage[lane] : 0ull);
   const int cells = mine ? (b.x1 - b.x0 + 1) * (b.y1 - b.y0 + 1) : 0;
   if (!__all_sync(kFull, cells <= kSmallCells)) return false;
   // position of this candidate's task (its group's first candidate)
@@ -352,7 +400,7 @@ __device__ bool stage_lanes(Ctx& x, const WarpSmem& w, const SweepOut& o, unsign
         if (rc >= 2u) lane_add(w, o, lane, nb, (int)(uint32_t)entry_at(x, w, (int)rl), b.task);
         if (rc == 3u) {
           for (uint32_t q = rs + 1; q < rl; ++q) {
-            Box e = unpack_c(w, entry_at(x, w, (int)q), x.ndim);
+            Box e = unpack_c(x, w, entry_at(x, w, (int)q));
             if (e.x0 <= cx && cx <= e.x1 && e.y0 <= cy && cy <= e.y1) lane_add(w, o, lane, nb, e.task, b.task);
           }
         }
@@ -368,9 +416,10 @@ __device__ bool stage_lanes(Ctx& x, const WarpSmem& w, const SweepOut& o, unsign
     const int total = __shfl_sync(kFull, incl, 31);
     if (total > 0) {
       const PairDst pd = reserve_pairs(x, o, (uint32_t)total);
+      if (lane == 0) atomicAdd(w.npairs, total);
       const int base = incl - nb;
       for (int k = 0; k < nb; ++k)
-        put_pair(o, pair_pos(pd, (uint32_t)(base + k)), pair_key(w.lbuf[lane * kLaneBuf + k], b.task, o.key_bits));
+        put_pair(w, o, pair_pos(pd, (uint32_t)(base + k)), pair_key(w.lbuf[lane * kLaneBuf + k], b.task, o.key_bits));
     }
     __syncwarp();
   }
@@ -383,7 +432,7 @@ __device__ void process_group(Ctx& x, const WarpSmem& w, const SweepOut& o, int 
   const int dst = (int)(uint32_t)first;
   const int g = b - a;
   if (g == 1) {
-    Box bx = unpack_c(w, first, x.ndim);
+    Box bx = unpack_c(x, w, first);
     sweep_box(x, w, o, bx.x0, bx.x1, bx.y0, bx.y1, a, bx.priv, false, dst);
   } else {
     // disjoint rectangles need no privilege combination
@@ -391,9 +440,9 @@ __device__ void process_group(Ctx& x, const WarpSmem& w, const SweepOut& o, int 
     if (!overlap) {
       bool mine = false;
       if (x.lane < g) {
-        Box bi = unpack_c(w, entry_at(x, w, a + x.lane), x.ndim);
+        Box bi = unpack_c(x, w, entry_at(x, w, a + x.lane));
         for (int j = x.lane + 1; j < g; ++j) {
-          Box bj = unpack_c(w, entry_at(x, w, a + j), x.ndim);
+          Box bj = unpack_c(x, w, entry_at(x, w, a + j));
           if (bi.x0 <= bj.x1 && bj.x0 <= bi.x1 && bi.y0 <= bj.y1 && bj.y0 <= bi.y1) mine = true;
         }
       }
@@ -401,16 +450,16 @@ __device__ void process_group(Ctx& x, const WarpSmem& w, const SweepOut& o, int 
     }
     if (!overlap) {
       for (int e = a; e < b; ++e) {
-        Box bx = unpack_c(w, entry_at(x, w, e), x.ndim);
+        Box bx = unpack_c(x, w, entry_at(x, w, e));
         sweep_box(x, w, o, bx.x0, bx.x1, bx.y0, bx.y1, a, bx.priv, false, dst);
       }
     } else {
       for (int e = a; e < b; ++e) {
-        mark_box(x, w, unpack_c(w, entry_at(x, w, e), x.ndim));
+        mark_box(x, w, unpack_c(x, w, entry_at(x, w, e)));
         __syncwarp();
       }
       for (int e = a; e < b; ++e) {
-        Box bx = unpack_c(w, entry_at(x, w, e), x.ndim);
+        Box bx = unpack_c(x, w, entry_at(x, w, e));
         sweep_box(x, w, o, bx.x0, bx.x1, bx.y0, bx.y1, a, 0, true, dst);
         __syncwarp();
       }
@@ -419,14 +468,14 @@ __device__ void process_group(Ctx& x, const WarpSmem& w, const SweepOut& o, int 
   flush(x, w, o, dst);
 }
 
-__global__ void __launch_bounds__(256) k_sweep(const uint64_t* __restrict__ payload,
+__global__ void __launch_bounds__(256, 3) k_sweep(const uint64_t* __restrict__ payload,
                                                const uint32_t* __restrict__ seg_begin,
                                                const uint32_t* __restrict__ seg_end, AnalysisDims d,
                                                SweepOut o) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int C = d.tw * d.th;
-  unsigned char* base = smem + (size_t)warp * per_warp_bytes(C);
+  const int C = class_cap(d.tw, d.th);
+  unsigned char* base = smem + (size_t)warp * per_warp_bytes(d.tw, d.th);
   WarpSmem w;
   w.cell = reinterpret_cast<uint4*>(base);
   w.scr = base + 16 * C;
@@ -438,8 +487,14 @@ __global__ void __launch_bounds__(256) k_sweep(const uint64_t* __restrict__ payl
   w.lbuf = w.hcount + 4;
   w.cmx = reinterpret_cast<uint16_t*>(w.lbuf + 32 * kLaneBuf);
   w.cmy = w.cmx + d.tw;
+  w.dropped = w.hcount + 1;
+  w.npairs = w.hcount + 2;
   for (int i = lane; i < kHashSlots; i += 32) w.htab[i] = -1;
-  if (lane == 0) *w.hcount = 0;
+  if (lane == 0) {
+    *w.hcount = 0;
+    *w.dropped = 0;
+    *w.npairs = 0;
+  }
   __syncwarp();
 
   Ctx x;
@@ -456,6 +511,7 @@ __global__ void __launch_bounds__(256) k_sweep(const uint64_t* __restrict__ payl
     if (t >= ntiles) break;
     const uint32_t sb = seg_begin[t], se = seg_end[t];
     if (sb >= se) continue;
+    if (o.only && !o.only[t]) continue;  // a rerun sweeps the tiles that dropped pairs
     x.L = payload + sb;
     x.n = (int)(se - sb);
     // class maps of this tile: mark every rectangle boundary inside it, then
@@ -475,74 +531,91 @@ __global__ void __launch_bounds__(256) k_sweep(const uint64_t* __restrict__ payl
     scan_flags(w.cmy, d.th, lane);
     const int cw = w.cmx[d.tw - 1] + 1, ch = w.cmy[d.th - 1] + 1;
     x.tw = cw;  // row stride of the class grid
-    for (int c = lane; c < cw * ch; c += 32) {
-      w.cell[c] = make_uint4((uint32_t)kKindNone << 30, 0u, 0u, 0u);
-      w.scr[c] = 0xFFu;
+    // a class grid larger than the cell state is swept in strips of class
+    // rows, each pass over every candidate (those outside see empty boxes)
+    const int cap = class_cap(d.tw, d.th);
+    const int strip = cw * ch <= cap ? ch : cap / cw;
+    for (x.ylo = 0; x.ylo < ch; x.ylo += strip) {
+      x.yhi = min(x.ylo + strip, ch) - 1;
+      for (int c = lane; c < cw * (x.yhi - x.ylo + 1); c += 32) {
+        w.cell[c] = make_uint4((uint32_t)kKindNone << 30, 0u, 0u, 0u);
+        w.scr[c] = 0xFFu;
+      }
+      __syncwarp();
+      int pos = 0;
+      while (pos < x.n) {
+        const int cnt = x.n - pos < 32 ? x.n - pos : 32;
+        const uint64_t my = lane < cnt ? x.L[pos + lane] : kEmpty64;
+        w.stage[lane] = my;
+        const uint64_t nxt = (pos + 32 < x.n) ? x.L[pos + 32] : kEmpty64;
+        x.pos = pos;
+        x.cnt = cnt;
+        __syncwarp();
+        const int mytask = (int)(uint32_t)my;
+        const int prevtask = __shfl_up_sync(kFull, mytask, 1);
+        const bool start = lane < cnt && (lane == 0 || mytask != prevtask);
+        const unsigned starts = __ballot_sync(kFull, start);
+        const int lasttask = __shfl_sync(kFull, mytask, cnt - 1);
+        const bool last_complete = (pos + cnt == x.n) || ((int)(uint32_t)nxt != lasttask);
+        const int last_start = 31 - __clz((int)starts);
+        const int end = last_complete ? cnt : last_start;
+        if (end == 0) {
+          // one task with more than 32 candidates in this tile: find its end
+          int gend = pos + 32;
+          for (;;) {
+            int idx = gend + lane;
+            int tk = idx < x.n ? (int)(uint32_t)x.L[idx] : -2;
+            unsigned diff = __ballot_sync(kFull, tk != lasttask);
+            if (diff) {
+              gend += __ffs((int)diff) - 1;
+              break;
+            }
+            gend += 32;
+          }
+          process_group(x, w, o, pos, gend);
+          pos = gend;
+          __syncwarp();
+          continue;
+        }
+        unsigned gs = starts & (end == 32 ? kFull : ((1u << end) - 1u));
+        if (stage_lanes(x, w, o, gs, end)) gs = 0;
+        while (gs) {
+          const int a = __ffs((int)gs) - 1;
+          gs &= gs - 1;
+          const int b = gs ? __ffs((int)gs) - 1 : end;
+          process_group(x, w, o, pos + a, pos + b);
+        }
+        pos += end;
+        __syncwarp();
+      }
+    }
+    // a tile that dropped a pair is marked for the rerun, with its pair count
+    __syncwarp();
+    if (lane == 0) {
+      if (*(volatile int*)w.dropped) {
+        if (o.flag_out) o.flag_out[t] = 1;
+        atomicAdd(o.rerun, (unsigned long long)*(volatile int*)w.npairs);
+      }
+      *w.dropped = 0;
+      *w.npairs = 0;
     }
     __syncwarp();
-    int pos = 0;
-    while (pos < x.n) {
-      const int cnt = x.n - pos < 32 ? x.n - pos : 32;
-      const uint64_t my = lane < cnt ? x.L[pos + lane] : kEmpty64;
-      w.stage[lane] = my;
-      const uint64_t nxt = (pos + 32 < x.n) ? x.L[pos + 32] : kEmpty64;
-      x.pos = pos;
-      x.cnt = cnt;
-      __syncwarp();
-      const int mytask = (int)(uint32_t)my;
-      const int prevtask = __shfl_up_sync(kFull, mytask, 1);
-      const bool start = lane < cnt && (lane == 0 || mytask != prevtask);
-      const unsigned starts = __ballot_sync(kFull, start);
-      const int lasttask = __shfl_sync(kFull, mytask, cnt - 1);
-      const bool last_complete = (pos + cnt == x.n) || ((int)(uint32_t)nxt != lasttask);
-      const int last_start = 31 - __clz((int)starts);
-      const int end = last_complete ? cnt : last_start;
-      if (end == 0) {
-        // one task with more than 32 candidates in this tile: find its end
-        int gend = pos + 32;
-        for (;;) {
-          int idx = gend + lane;
-          int tk = idx < x.n ? (int)(uint32_t)x.L[idx] : -2;
-          unsigned diff = __ballot_sync(kFull, tk != lasttask);
-          if (diff) {
-            gend += __ffs((int)diff) - 1;
-            break;
-          }
-          gend += 32;
-        }
-        process_group(x, w, o, pos, gend);
-        pos = gend;
-        __syncwarp();
-        continue;
-      }
-      unsigned gs = starts & (end == 32 ? kFull : ((1u << end) - 1u));
-      if (stage_lanes(x, w, o, gs, end)) gs = 0;
-      while (gs) {
-        const int a = __ffs((int)gs) - 1;
-        gs &= gs - 1;
-        const int b = gs ? __ffs((int)gs) - 1 : end;
-        process_group(x, w, o, pos + a, pos + b);
-      }
-      pos += end;
-      __syncwarp();
-    }
   }
-  for (uint32_t i = lane; i < x.chunk_left; i += 32) put_pair(o, x.chunk_base + i, kEmpty64);
+  for (uint32_t i = lane; i < x.chunk_left; i += 32) put_pair(w, o, x.chunk_base + i, kEmpty64);
 }
 }  // namespace
 
-int sweep_warps_per_block(int tile_cells) {
-  int w = (int)((96 * 1024) / per_warp_bytes(tile_cells));
+int sweep_warps_per_block(int tw, int th) {
+  int w = (int)((96 * 1024) / per_warp_bytes(tw, th));
   return w < 1 ? 1 : (w > 8 ? 8 : w);
 }
 
-size_t sweep_smem_bytes(int tile_cells, int warps) { return per_warp_bytes(tile_cells) * warps; }
+size_t sweep_smem_bytes(int tw, int th, int warps) { return per_warp_bytes(tw, th) * warps; }
 
 void launch_sweep(const uint64_t* payload, const uint32_t* seg_begin, const uint32_t* seg_end,
                   AnalysisDims d, SweepOut o, int blocks, cudaStream_t s) {
-  const int C = d.tw * d.th;
-  const int warps = sweep_warps_per_block(C);
-  const size_t bytes = sweep_smem_bytes(C, warps);
+  const int warps = sweep_warps_per_block(d.tw, d.th);
+  const size_t bytes = sweep_smem_bytes(d.tw, d.th, warps);
   cudaFuncSetAttribute(k_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   count_launch();
   k_sweep<<<blocks, warps * 32, bytes, s>>>(payload, seg_begin, seg_end, d, o);

@@ -130,6 +130,52 @@ def test_pair_buffer_overflow_reruns_once():
         g.close()
 
 
+def _max_classes(tr, tile):
+    """Largest class grid (column classes x row classes) of any tile: the
+    boundaries of the rectangles falling inside each tile, counted on the host."""
+    tw, th = tile
+    cuts = {}
+    for (x0, y0), (x1, y1) in zip(tr.lo, tr.hi):
+        for ty in range(y0 // th, y1 // th + 1):
+            for tx in range(x0 // tw, x1 // tw + 1):
+                cx, cy = cuts.setdefault((tx, ty), (set(), set()))
+                for v, base, side, st in ((x0, tx * tw, tw, cx), (x1 + 1, tx * tw, tw, cx),
+                                          (y0, ty * th, th, cy), (y1 + 1, ty * th, th, cy)):
+                    if base < v < base + side:
+                        st.add(v)
+    return max((len(a) + 1) * (len(b) + 1) for a, b in cuts.values())
+
+
+def test_large_tiles_sweep_class_grids_in_strips():
+    """Tiles up to 128x128: small rectangles make class grids larger than the
+    1024 cells a warp keeps, so those tiles are swept in strips of class rows."""
+    tr = tg.random_rects(grid=(200, 150), n=1500, rects=(1, 3), side=(1, 6), seed=21)
+    ref = oracle_csr(tr)
+    for tile in ((64, 64), (128, 32), (128, 128), (32, 128)):
+        assert _max_classes(tr, tile) > 1024, tile
+        g = gpu_graph(tr, body=grt.RT_BODY_CHECK, tile=tile)
+        g.analyze()
+        assert_csr_equal(g, tr, ref)
+        g.execute()
+        g.sync()
+        st, out = oracle.run_bodies(tr, oracle.oracle.BODY_CHECK)
+        assert np.array_equal(g.state.cpu().numpy(), st) and np.array_equal(g.out.cpu().numpy(), out)
+        g.close()
+
+
+def test_big_rectangles_on_large_tiles():
+    """Rectangles with sides log-uniform 16..512 on a 512^2 grid (the shape of
+    the 1M-launch 4096^2 workload, scaled down): most tiles have few classes,
+    so whole-tile rectangles cost one class each."""
+    tr = tg.random_rects(grid=(512, 512), n=500, rects=(1, 4), side=(16, 512), seed=22)
+    ref = oracle_csr(tr)
+    for tile in ((16, 16), (64, 64), (128, 128)):
+        g = gpu_graph(tr, tile=tile)
+        g.analyze()
+        assert_csr_equal(g, tr, ref)
+        g.close()
+
+
 def test_edge_cases():
     import torch
     # empty graph
