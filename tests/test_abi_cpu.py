@@ -52,7 +52,8 @@ def desc(**kw):
     (dict(body=7), "body"),
     (dict(spin=-1), "spin_iters"),
     (dict(tile=(256, 16)), "tile"),
-    (dict(tile=(64, 64)), "cells"),
+    (dict(tile=(16, 129)), "tile"),
+    (dict(ndim=1, lo=(0, 0), hi=(99999, 0), tile=(2048, 1)), "1-D tile"),
     (dict(body=grt.RT_BODY_CHECK), "CHECK"),
     (dict(body=grt.RT_BODY_CHECK, state=0x1000, state_elems=10), "CHECK"),
     (dict(body=grt.RT_BODY_COUNTER), "COUNTER"),
