@@ -34,7 +34,10 @@ from paper_2508_16522_gb300 import tracegen as tg  # noqa: E402
 METRIC = "tasks/sec and ns/task overhead (analysis+execution) on 1 GB300, batched vs plain"
 UNIT = "tasks/s"
 WIDTH, STEPS = 1024, 1000
-TILE = (16, 16)
+# The autotuner picks each workload's tile and launch shapes; this file holds
+# the shapes measured on this GPU model (one line per workload key), and a
+# workload missing from it is tuned on the spot (a few seconds) and appended.
+TUNE_CACHE = os.path.join(ROOT, "paper_2508_16522_gb300", "tune_cache.txt")
 WORKLOAD = "taskbench 1024x1000 (stencil, butterfly, random fan-in 5), region-encoded, EMPTY bodies"
 
 
@@ -44,12 +47,12 @@ def load_traces(args=None):
     return [tg.taskbench(WIDTH, steps, p, seed=0) for p in pats]
 
 
-def config(tasks_per_step, args=None):
+def config(tasks_per_step, args=None, tiles=None):
     steps = getattr(args, "graph_steps", STEPS)
     pats = getattr(args, "patterns", ",".join(tg.PATTERNS)).split(",")
     wl = WORKLOAD if (steps == STEPS and len(pats) == 3) else f"REDUCED (profiling): taskbench {WIDTH}x{steps} {pats}"
     return {"workload": wl, "patterns": pats, "width": WIDTH, "steps_per_graph": steps,
-            "tasks_per_step": tasks_per_step, "tile": list(TILE),
+            "tasks_per_step": tasks_per_step, "tiles": tiles,
             "l2": "flushed between timed steps (512 MB write)", "inputs": "synthetic, seed 0"}
 
 
@@ -65,8 +68,10 @@ def run_batched(grt, torch, flush, steps):
     gen_s = time.perf_counter() - t0
     stream = torch.cuda.Stream()
     graphs, ana_ms = [], 0.0
+    big = max(traces, key=lambda t: t.n)
+    tile = list(grt.rt_tune_tile(big, TUNE_CACHE)[:2])  # tuned on the largest graph
     for tr in traces:
-        g = grt.Graph(2, tr.dom_lo, tr.dom_hi, tile=TILE, stream=stream, flags=grt.RT_GRAPH_PROFILE)
+        g = grt.Graph(2, tr.dom_lo, tr.dom_hi, tile=tile, stream=stream, flags=grt.RT_GRAPH_PROFILE)
         g.launch(*[torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (tr.req_off, tr.lo, tr.hi, tr.priv)])
         g.analyze()
         ana_ms += g.stats()["ms_analyze"]
@@ -74,13 +79,15 @@ def run_batched(grt, torch, flush, steps):
     T = sum(t.n for t in traces)
     E = sum(g.stats()["n_edges"] for g in graphs)
     batch = grt.Batch(graphs, stream=stream)
-    batch.execute(replays=BATCH_REPLAYS)
+    shape = batch.tune(replays=BATCH_REPLAYS, cache_path=TUNE_CACHE)
+    launch = {k: shape[k] for k in ("blocks", "warps", "claim", "keep")}
+    batch.execute(replays=BATCH_REPLAYS, **launch)
     batch.sync()
     ms = []
     for i in range(steps):
         with torch.cuda.stream(stream):
             flush.fill_(i & 255)
-        batch.execute(replays=BATCH_REPLAYS)
+        batch.execute(replays=BATCH_REPLAYS, **launch)
         ms.append(batch.sync())
     kern = float(np.mean(ms))
     done = T * BATCH_REPLAYS
@@ -91,7 +98,7 @@ def run_batched(grt, torch, flush, steps):
            "exec_ns_per_task": kern * 1e6 / done, "analysis_ms_total": ana_ms,
            "analysis_ns_per_task": ana_ms * 1e6 / T,
            "tasks_per_s_incl_capture": done / ((kern + ana_ms) * 1e-3), "generate_s": gen_s,
-           "timed_launches": steps}
+           "timed_launches": steps, "autotune": {"tile": tile, "exec": shape}}
     batch.close()
     for g in graphs:
         g.close()
@@ -100,6 +107,22 @@ def run_batched(grt, torch, flush, steps):
 
 SERVE_REQUESTS, SERVE_RATE = 2000, 50_000.0
 SERVE_SLOTS, SERVE_WORKERS, SERVE_MAX_BATCH = 512, 4, 64
+
+
+def stacked_batch(traces, max_batch, band=1024):
+    """Requests as the server analyses a batch of them: request j's rectangles
+    move j bands along the last dimension of a domain max_batch bands long."""
+    counts, los, his = [], [], []
+    for j, tr in enumerate(traces):
+        lo, hi = tr.lo.copy(), tr.hi.copy()
+        lo[:, 1] += j * band
+        hi[:, 1] += j * band
+        counts.append(np.diff(tr.req_off))
+        los.append(lo)
+        his.append(hi)
+    return tg._finish(2, [0, 0], [band - 1, max_batch * band - 1], np.concatenate(counts),
+                      np.concatenate(los).reshape(-1), np.concatenate(his).reshape(-1),
+                      np.concatenate([t.priv for t in traces]), name="served_batch")
 
 
 def run_served(grt, n_requests=SERVE_REQUESTS):
@@ -111,8 +134,10 @@ def run_served(grt, n_requests=SERVE_REQUESTS):
     t0 = time.perf_counter()
     reqs = tg.served_stream(n_requests, rate_per_s=SERVE_RATE, seed=0)
     gen_s = time.perf_counter() - t0
+    # the tile is tuned on a batch of the size the stream produces (about 43)
+    tile = list(grt.rt_tune_tile(stacked_batch([r.trace for r in reqs[:43]], SERVE_MAX_BATCH), TUNE_CACHE)[:2])
     srv = grt.Server(2, [0, 0], [1023, 1023], body=grt.RT_BODY_EMPTY, budget_bytes=8 << 30,
-                     max_inflight=SERVE_SLOTS, max_tasks=16384, workers=SERVE_WORKERS, tile=TILE,
+                     max_inflight=SERVE_SLOTS, max_tasks=16384, workers=SERVE_WORKERS, tile=tile,
                      max_batch=SERVE_MAX_BATCH)
     for r in reqs[:16]:  # warm-up: grow the pool's buffers
         srv.submit(r.trace)
@@ -152,7 +177,7 @@ def run_served(grt, n_requests=SERVE_REQUESTS):
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "service_ms": {"p50": float(np.percentile(svc, 50)), "p99": float(np.percentile(svc, 99))},
             "analysis_ms": {"p50": float(np.percentile(ana, 50)), "p99": float(np.percentile(ana, 99))},
-            "mean_batch": sst["batched_requests"] / max(sst["batches"], 1),
+            "mean_batch": sst["batched_requests"] / max(sst["batches"], 1), "autotune": {"tile": tile},
             "submit_lag_ms": {"p50": float(np.percentile(lag, 50)) / 1e6, "p99": float(np.percentile(lag, 99)) / 1e6},
             "generate_s": gen_s}
 
@@ -321,8 +346,9 @@ def run_ours(args):
                   for t in traces]
     host_inputs = [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (t.req_off, t.lo, t.hi, t.priv)]
                    for t in traces]
-    graphs = [grt.Graph(2, t.dom_lo, t.dom_hi, tile=TILE, stream=stream, flags=grt.RT_GRAPH_PROFILE)
-              for t in traces]
+    tiles = [list(grt.rt_tune_tile(t, TUNE_CACHE)[:2]) for t in traces]
+    graphs = [grt.Graph(2, t.dom_lo, t.dom_hi, tile=tl, stream=stream, flags=grt.RT_GRAPH_PROFILE)
+              for t, tl in zip(traces, tiles)]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
 
     def step(inputs, defer=False):
@@ -360,6 +386,8 @@ def run_ours(args):
 
     for _ in range(args.warmup):
         step(dev_inputs)
+    exec_shapes = [g.tune(TUNE_CACHE) for g in graphs]  # outside the timed region
+    step(dev_inputs)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -426,7 +454,8 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "ns_per_task": 1e9 / value * world,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-                "data": "synthetic", "config": config(n_tasks, args), "form": "plain",
+                "data": "synthetic", "config": config(n_tasks, args, tiles), "form": "plain",
+                "autotune": {"tiles": tiles, "exec": exec_shapes, "cache": os.path.relpath(TUNE_CACHE, ROOT)},
                 "e2e": None if args.no_e2e else {
                     "value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": 8 * len(graphs), "ms_per_step": sum(e2e_ms) / args.steps,

@@ -240,6 +240,39 @@ rt_status rt_batch_sync(rt_batch_t b, float* ms_kernel);
 rt_status rt_batch_counters(rt_batch_t b, int64_t* out, int32_t n);
 rt_status rt_batch_destroy(rt_batch_t b);
 
+/* ---- autotuning -----------------------------------------------------------
+ * Results never depend on the analysis tile or the executor's launch shape;
+ * speed does, and the best values depend on the workload and the device. The
+ * tuners measure candidates on the caller's own workload and keep the fastest.
+ * cache_path (may be NULL) names a plain-text cache, one line per workload key
+ * (device name and SM count, kind, sizes, an input hash): a key found there is
+ * answered without running anything; a new result is appended. The paper
+ * fixes no such knobs (its runtime compiles one worker per processor). */
+typedef struct {
+  int32_t blocks, warps, claim, keep;  /* launch shape (rt_graph_exec_config) */
+  float ms;                            /* time of one run with it */
+  int32_t trials;                      /* shapes measured (0: from the cache) */
+} rt_exec_config;
+
+/* Analyses the launches (host arrays, as rt_launch_batch) once per candidate
+ * tile -- 8, 16, 32, 64 square in 2-D; 128..1024 in 1-D -- in a temporary
+ * graph built from desc (body, state, out and flags ignored), and returns the
+ * tile whose analysis was fastest (its ms in *ms, may be NULL). Errors:
+ * RT_ERR_INVALID (bad arguments, or no candidate could analyse the trace). */
+rt_status rt_tune_tile(const rt_graph_desc* desc, int32_t n, const int32_t* req_off, const int64_t* lo,
+                       const int64_t* hi, const uint8_t* priv, const char* cache_path, int32_t* tile_w,
+                       int32_t* tile_h, float* ms);
+
+/* Runs an analysed graph under candidate launch shapes (coordinate descent:
+ * warps x blocks per SM, then claim, then keep; best of two runs each) and
+ * configures it with the fastest (rt_graph_exec_config). The graph's bodies run
+ * once per trial: a state-changing body sees those runs. Synchronous. */
+rt_status rt_tune_exec(rt_graph_t g, const char* cache_path, rt_exec_config* best);
+
+/* The same for a batch launch of `replays` replays; returns the shape for
+ * rt_batch_execute (the batch keeps no configuration). Synchronous. */
+rt_status rt_tune_batch(rt_batch_t b, int32_t replays, const char* cache_path, rt_exec_config* best);
+
 /* ---- serving (continuous batching) ---------------------------------------
  * A server analyses requests (each a graph of launches with region
  * requirements) as they arrive and executes them in one persistent kernel that

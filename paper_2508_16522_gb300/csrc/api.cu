@@ -1205,6 +1205,14 @@ void trace(const char* what) {
   fflush(stderr);
 }
 
+rt_status batch_shape(rt_batch_t b, int64_t* graphs, int64_t* tasks, int64_t* edges) {
+  if (!b) return fail(RT_ERR_INVALID, "batch is NULL");
+  *graphs = b->G;
+  *tasks = b->T;
+  *edges = b->E;
+  return RT_OK;
+}
+
 rt_status graph_view(rt_graph_t g, GraphView* v) {
   if (!g || !v) return fail(RT_ERR_INVALID, "NULL argument");
   if (!g->analyzed) return fail(RT_ERR_STATE, "graph not analyzed");

@@ -319,6 +319,7 @@ struct GraphView {
   size_t footprint;  // bytes of device memory the graph object holds
 };
 rt_status graph_view(rt_graph_t g, GraphView* v);
+rt_status batch_shape(rt_batch_t b, int64_t* graphs, int64_t* tasks, int64_t* edges);
 int32_t static_max_tasks();
 rt_status static_execute(const int32_t* row_ptr, const int32_t* col, const int32_t* indeg, int32_t n,
                          int64_t n_edges, int32_t spin_iters, int32_t* out, cudaStream_t s,

@@ -33,7 +33,7 @@ EXPORTS = ["rt_graph_create", "rt_graph_destroy", "rt_graph_clear", "rt_launch_b
            "rt_batch_execute", "rt_batch_sync", "rt_batch_counters", "rt_batch_destroy", "rt_last_error", "rt_device_info",
            "rt_kernel_launches", "rt_execute_csr_static", "rt_microbench_atomics", "rt_now_ns",
            "rt_server_create", "rt_server_submit", "rt_server_poll", "rt_server_result", "rt_server_drain",
-           "rt_server_stats", "rt_server_destroy"]
+           "rt_server_stats", "rt_server_destroy", "rt_tune_tile", "rt_tune_exec", "rt_tune_batch"]
 
 
 class GrtError(RuntimeError):
@@ -57,6 +57,14 @@ class rt_server_desc(ctypes.Structure):
                 ("max_tasks", ctypes.c_int32), ("workers", ctypes.c_int32), ("keep_results", ctypes.c_int32),
                 ("exec_blocks", ctypes.c_int32), ("exec_warps", ctypes.c_int32), ("timeout_ns", ctypes.c_int64),
                 ("max_batch", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
+
+
+class rt_exec_config(ctypes.Structure):
+    _fields_ = [("blocks", ctypes.c_int32), ("warps", ctypes.c_int32), ("claim", ctypes.c_int32),
+                ("keep", ctypes.c_int32), ("ms", ctypes.c_float), ("trials", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class rt_request_info(ctypes.Structure):
@@ -131,6 +139,10 @@ def load(path: str = LIB_PATH):
         "rt_server_drain": [P, i64],
         "rt_server_destroy": [P],
         "rt_server_stats": [P, ctypes.POINTER(i64), i32],
+        "rt_tune_tile": [ctypes.POINTER(rt_graph_desc), i32, P, P, P, P, ctypes.c_char_p, ctypes.POINTER(i32),
+                         ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)],
+        "rt_tune_exec": [P, ctypes.c_char_p, ctypes.POINTER(rt_exec_config)],
+        "rt_tune_batch": [P, i32, ctypes.c_char_p, ctypes.POINTER(rt_exec_config)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -223,6 +235,25 @@ def rt_microbench_atomics(stream=None) -> dict:
     return dict(zip(names, list(out)))
 
 
+def _cache_arg(cache_path):
+    return None if cache_path is None else str(cache_path).encode()
+
+
+def rt_tune_tile(tr, cache_path=None, stream=None):
+    """Fastest analysis tile for this trace: (tile_w, tile_h, ms)."""
+    d = rt_graph_desc()
+    d.ndim = tr.ndim
+    for k in range(tr.ndim):
+        d.dom_lo[k] = int(tr.dom_lo[k])
+        d.dom_hi[k] = int(tr.dom_hi[k])
+    d.stream = None if stream is None else stream.cuda_stream
+    arrs = [np.ascontiguousarray(a) for a in (tr.req_off, tr.lo, tr.hi, tr.priv)]
+    tw, th, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+    _check(load().rt_tune_tile(ctypes.byref(d), tr.n, *[a.ctypes.data for a in arrs], _cache_arg(cache_path),
+                               ctypes.byref(tw), ctypes.byref(th), ctypes.byref(ms)))
+    return tw.value, th.value, ms.value
+
+
 def rt_last_error() -> str:
     return load().rt_last_error().decode()
 
@@ -283,6 +314,12 @@ class Graph:
 
     def clear(self):
         rt_graph_clear(self.h)
+
+    def tune(self, cache_path=None) -> dict:
+        """Measures launch shapes on this analysed graph and keeps the fastest."""
+        c = rt_exec_config()
+        _check(load().rt_tune_exec(self.h, _cache_arg(cache_path), ctypes.byref(c)))
+        return c.as_dict()
 
     def launch(self, req_off, lo, hi, priv, pred_off=None, pred=None, body_arg=None, defer_check=False):
         """Appends launches; numpy arrays are host pointers, CUDA tensors device pointers."""
@@ -359,6 +396,13 @@ class Batch:
         ms = ctypes.c_float()
         _check(load().rt_batch_sync(self.h, ctypes.byref(ms)))
         return ms.value
+
+    def tune(self, replays: int = 1, cache_path=None) -> dict:
+        """The fastest launch shape for this batch at `replays` replays; pass
+        blocks/warps/claim/keep of the result to execute()."""
+        c = rt_exec_config()
+        _check(load().rt_tune_batch(self.h, replays, _cache_arg(cache_path), ctypes.byref(c)))
+        return c.as_dict()
 
     def counters(self) -> dict:
         arr = (ctypes.c_int64 * 9)()
