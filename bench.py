@@ -196,6 +196,37 @@ def oracle_step(traces):
     return time.perf_counter() - t0
 
 
+def run_case_served_batch(args):
+    """Profiling case: the analysis of one batch of served requests (the first
+    43, stacked as the server analyses them) through a plain graph, with no
+    serving kernel resident, so that ncu can capture it. Not a bench line."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2508_16522_gb300 import grt
+    reqs = tg.served_stream(SERVE_REQUESTS, rate_per_s=SERVE_RATE, seed=0)[:43]
+    tr = stacked_batch([r.trace for r in reqs], SERVE_MAX_BATCH)
+    tile = list(grt.rt_tune_tile(tr, TUNE_CACHE)[:2])
+    stream = torch.cuda.Stream()
+    g = grt.Graph(2, tr.dom_lo, tr.dom_hi, tile=tile, stream=stream, flags=grt.RT_GRAPH_PROFILE)
+    inp = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (tr.req_off, tr.lo, tr.hi, tr.priv)]
+    runs = []
+    for k in range(args.warmup + args.steps):
+        g.clear()
+        g.launch(*inp)
+        g.analyze()
+        if k >= args.warmup:
+            runs.append(g.stats())
+    med = lambda key: float(np.median([r[key] for r in runs]))
+    print(json.dumps({"case": "served-batch", "requests": len(reqs), "tasks": tr.n, "rects": tr.n_rects,
+                      "tile": tile, "entries": runs[-1]["n_entries"], "pairs": runs[-1]["n_pairs"],
+                      "edges": runs[-1]["n_edges"], "ms_analyze": med("ms_analyze"),
+                      "ms_sweep_kernel": med("ms_sweep_kernel"), "ms_bin": med("ms_bin"),
+                      "ms_sort_pairs": med("ms_sort_pairs"), "runs": len(runs)}), flush=True)
+    g.close()
+    return 0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -486,11 +517,15 @@ def main():
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--graph-steps", type=int, default=STEPS, help="profiling only: fewer steps per graph")
     ap.add_argument("--patterns", default=",".join(tg.PATTERNS), help="profiling only: subset of patterns")
+    ap.add_argument("--case", default=None, choices=["served-batch"],
+                    help="profiling only: run one named analysis case instead of the bench")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.case == "served-batch":
+        return run_case_served_batch(args)
     return run_ours(args)
 
 

@@ -43,6 +43,7 @@ constexpr int kLaneBuf = 16;     // predecessors one lane buffers in the lane-pa
 constexpr int kSmallCells = 16;  // largest box the lane-parallel path takes
 constexpr int kMaxRounds = 8;    // deeper conflict chains go to the warp-wide path
 constexpr int kLongSpan = 64;    // run spans the whole warp scans together
+constexpr int kSegMinArea = 8;   // mean class cells per candidate from which rows go segmented
 constexpr unsigned kFull = 0xffffffffu;
 
 // cells of the class grid one warp sweeps at once (taller grids go in strips)
@@ -54,7 +55,8 @@ __host__ __device__ inline size_t class_map_bytes(int tw, int th) { return (size
 __host__ __device__ inline size_t per_warp_bytes(int tw, int th) {
   const int C = class_cap(tw, th);
   return (size_t)16 * C + (size_t)((C + 15) & ~15) + 32 * 8 + kHashSlots * 4 + kListCap * 8 + 16 +
-         32 * kLaneBuf * 4 + class_map_bytes(tw, th);
+         32 * kLaneBuf * 4 + class_map_bytes(tw, th) + (size_t)((4 * C + 15) & ~15);  // 16-byte multiple:
+                                                                                      // warps' uint4 cells stay aligned
 }
 
 struct WarpSmem {
@@ -70,6 +72,7 @@ struct WarpSmem {
   uint16_t* cmy;  // row -> row class
   int* dropped;   // a pair of the current tile fell past the buffer's end
   int* npairs;    // pairs the current tile emitted
+  uint32_t* seg;  // segment mode: per class row, bit x set where a segment starts
 };
 
 // in place: a[i] <- a[0] + ... + a[i] over a[0..L) (one warp, convergent)
@@ -99,6 +102,7 @@ struct Ctx {
   int cnt;            // entries in the window
   int tw, ndim;
   int ylo, yhi;       // the strip of class rows being swept
+  bool segmode;       // rows kept as segments of equal state (large boxes)
   unsigned long long chunk_base;
   uint32_t chunk_left;
   int lane;
@@ -426,6 +430,187 @@ __device__ bool stage_lanes(Ctx& x, const WarpSmem& w, const SweepOut& o, unsign
   return true;
 }
 
+// ---- segment mode ---------------------------------------------------------
+// Tiles whose candidates cover many classes keep each class row as segments of
+// equal run state: bit x of the row's mask is set where a segment starts, and
+// only a segment's first cell holds the state (and the privilege mark). A
+// candidate splits the segments at its box's edges, updates each covered
+// segment once, and merges neighbours left equal. The previous-run fields of a
+// state whose current run is a write are never read (nothing joins a write),
+// so they are zeroed, which lets the segments a write covers merge. One lane
+// owns one row of the box; predecessors of a segment are those of any of its
+// cells (they share the state), and the members of a run of three or more are
+// the candidates between its first and last member whose box meets the segment.
+
+__device__ __forceinline__ int seg_start_le(const uint32_t* row, int X) {  // bit 0 is always set
+  int k = X >> 5;
+  uint32_t m = row[k] & (0xffffffffu >> (31 - (X & 31)));
+  while (!m) m = row[--k];
+  return (k << 5) + 31 - __clz((int)m);
+}
+
+__device__ __forceinline__ int seg_next(const uint32_t* row, int X, int cw) {  // first start > X, or cw
+  if (X + 1 >= cw) return cw;
+  int k = (X + 1) >> 5;
+  const int W = (cw + 31) >> 5;
+  uint32_t m = row[k] & (0xffffffffu << ((X + 1) & 31));
+  while (!m) {
+    if (++k >= W) return cw;
+    m = row[k];
+  }
+  const int b = (k << 5) + __ffs((int)m) - 1;
+  return b < cw ? b : cw;
+}
+
+__device__ __forceinline__ void seg_split(const Ctx& x, const WarpSmem& w, uint32_t* row, int y, int X) {
+  if (X <= 0 || X >= x.tw) return;
+  if (row[X >> 5] & (1u << (X & 31))) return;
+  const int s0 = seg_start_le(row, X);
+  w.cell[y * x.tw + X] = w.cell[y * x.tw + s0];
+  w.scr[y * x.tw + X] = w.scr[y * x.tw + s0];
+  row[X >> 5] |= 1u << (X & 31);
+}
+
+// merges the segments starting in [x0, x1 + 1] into their left neighbour when
+// their state and mark equal it
+__device__ void seg_merge(const Ctx& x, const WarpSmem& w, uint32_t* row, int y, int x0, int x1) {
+  const int end = x1 + 1 < x.tw ? x1 + 1 : x.tw - 1;
+  int prev = x0 > 0 ? seg_start_le(row, x0 - 1) : -1;
+  for (int t = x0; t <= end; t = seg_next(row, t, x.tw)) {
+    if (!(row[t >> 5] & (1u << (t & 31)))) continue;  // only when t == x0 is not a start (x0 == 0 case)
+    if (prev >= 0) {
+      const uint4 a = w.cell[y * x.tw + prev], b = w.cell[y * x.tw + t];
+      if (a.x == b.x && a.y == b.y && a.z == b.z && a.w == b.w && w.scr[y * x.tw + prev] == w.scr[y * x.tw + t]) {
+        row[t >> 5] &= ~(1u << (t & 31));
+        continue;
+      }
+    }
+    prev = t;
+  }
+}
+
+// the access of the task whose first candidate is at `gpos` to the box's
+// segments (use_scr: privileges from the marks, each segment applied once;
+// the caller has split the rows already)
+__device__ void seg_box(Ctx& x, const WarpSmem& w, const SweepOut& o, const Box& b, int gpos, int p, bool use_scr,
+                        int dst) {
+  if (b.x1 < b.x0 || b.y1 < b.y0) return;  // a candidate outside the strip (warp-uniform)
+  const int W = (x.tw + 31) >> 5;
+  for (int r0 = b.y0; r0 <= b.y1; r0 += 32) {
+    const int y = r0 + x.lane;
+    const bool rowact = y <= b.y1;
+    uint32_t* row = w.seg + (rowact ? y : 0) * W;
+    if (rowact && !use_scr) {
+      seg_split(x, w, row, y, b.x0);
+      seg_split(x, w, row, y, b.x1 + 1);
+    }
+    int sx = b.x0;
+    bool more = rowact;
+    while (__any_sync(kFull, more)) {
+      int m1 = -1, m2 = -1, ex = 0;
+      uint32_t rs = 0, rl = 0, rc = 0;
+      bool act = false;
+      if (more) {
+        ex = seg_next(row, sx, x.tw) - 1;
+        const int c = y * x.tw + sx;
+        int pc = p;
+        act = true;
+        if (use_scr) {
+          const uint32_t sv = w.scr[c];
+          if (sv == 0xFFu) {
+            act = false;
+          } else {
+            pc = (int)sv;
+            w.scr[c] = 0xFFu;
+          }
+        }
+        if (act) {
+          apply_cell(w, c, gpos, pc, rs, rl, rc);
+          if (pc == kKindWrite) {
+            w.cell[c].z = 0u;
+            w.cell[c].w = 0u;
+          }
+          if (rc >= 1u) m1 = (int)(uint32_t)entry_at(x, w, (int)rs);
+          if (rc >= 2u) m2 = (int)(uint32_t)entry_at(x, w, (int)rl);
+        }
+      }
+      warp_insert(w, o, m1, dst);
+      warp_insert(w, o, m2, dst);
+      const bool longspan = act && rc == 3u && rl - rs > (uint32_t)kLongSpan;
+      if (act && rc == 3u && !longspan) {
+        for (uint32_t q = rs + 1; q < rl; ++q) {
+          const Box e = unpack_c(x, w, entry_at(x, w, (int)q));
+          if (e.y0 <= y && y <= e.y1 && e.x0 <= ex && sx <= e.x1) hash_insert(w, o, e.task, dst);
+        }
+      }
+      unsigned need = __ballot_sync(kFull, longspan);
+      while (need) {
+        const int l = __ffs((int)need) - 1;
+        need &= need - 1;
+        const int qs = __shfl_sync(kFull, (int)rs, l) + 1, qe = __shfl_sync(kFull, (int)rl, l);
+        const int ly = __shfl_sync(kFull, y, l), lx0 = __shfl_sync(kFull, sx, l), lx1 = __shfl_sync(kFull, ex, l);
+        for (int q0 = qs; q0 < qe; q0 += 32) {
+          const int q = q0 + x.lane;
+          if (q < qe) {
+            const Box e = unpack_c(x, w, entry_at(x, w, q));
+            if (e.y0 <= ly && ly <= e.y1 && e.x0 <= lx1 && lx0 <= e.x1) hash_insert(w, o, e.task, dst);
+          }
+        }
+      }
+      if (more) {
+        sx = ex + 1;
+        if (sx > b.x1) more = false;
+      }
+    }
+    // a group's boxes merge only after all of them ran (their edges must stay)
+    if (rowact && !use_scr) seg_merge(x, w, row, y, b.x0, b.x1);
+    __syncwarp();
+  }
+}
+
+// over the rows of box b: split at its edges (op 0), combine p into the marks
+// of the segments it covers (op 1), or merge equal neighbours (op 2)
+__device__ void seg_prepare(const Ctx& x, const WarpSmem& w, const Box& b, int p, int op) {
+  if (b.x1 < b.x0 || b.y1 < b.y0) return;
+  const int W = (x.tw + 31) >> 5;
+  for (int y = b.y0 + x.lane; y <= b.y1; y += 32) {
+    uint32_t* row = w.seg + y * W;
+    if (op == 0) {
+      seg_split(x, w, row, y, b.x0);
+      seg_split(x, w, row, y, b.x1 + 1);
+    } else if (op == 2) {
+      seg_merge(x, w, row, y, b.x0, b.x1);
+    } else {
+      for (int t = b.x0; t <= b.x1; t = seg_next(row, t, x.tw)) {
+        const int c = y * x.tw + t;
+        w.scr[c] = (uint8_t)combine_priv(w.scr[c], (uint32_t)p);
+      }
+    }
+  }
+  __syncwarp();
+}
+
+// one task's candidates at positions [a, b), segment mode
+__device__ void process_group_seg(Ctx& x, const WarpSmem& w, const SweepOut& o, int a, int b) {
+  const uint64_t first = entry_at(x, w, a);
+  const int dst = (int)(uint32_t)first;
+  if (b - a == 1) {
+    const Box bx = unpack_c(x, w, first);
+    seg_box(x, w, o, bx, a, bx.priv, false, dst);
+  } else {
+    // all edges first, so every segment is wholly inside or outside each box;
+    // then one combined privilege per segment, applied once
+    for (int e = a; e < b; ++e) seg_prepare(x, w, unpack_c(x, w, entry_at(x, w, e)), 0, 0);
+    for (int e = a; e < b; ++e) {
+      const Box bx = unpack_c(x, w, entry_at(x, w, e));
+      seg_prepare(x, w, bx, bx.priv, 1);
+    }
+    for (int e = a; e < b; ++e) seg_box(x, w, o, unpack_c(x, w, entry_at(x, w, e)), a, 0, true, dst);
+    for (int e = a; e < b; ++e) seg_prepare(x, w, unpack_c(x, w, entry_at(x, w, e)), 0, 2);
+  }
+  flush(x, w, o, dst);
+}
+
 // one task's candidates at positions [a, b) of the tile list
 __device__ void process_group(Ctx& x, const WarpSmem& w, const SweepOut& o, int a, int b) {
   const uint64_t first = entry_at(x, w, a);
@@ -487,6 +672,7 @@ __global__ void __launch_bounds__(256, 3) k_sweep(const uint64_t* __restrict__ p
   w.lbuf = w.hcount + 4;
   w.cmx = reinterpret_cast<uint16_t*>(w.lbuf + 32 * kLaneBuf);
   w.cmy = w.cmx + d.tw;
+  w.seg = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(w.cmx) + class_map_bytes(d.tw, d.th));
   w.dropped = w.hcount + 1;
   w.npairs = w.hcount + 2;
   for (int i = lane; i < kHashSlots; i += 32) w.htab[i] = -1;
@@ -531,15 +717,34 @@ __global__ void __launch_bounds__(256, 3) k_sweep(const uint64_t* __restrict__ p
     scan_flags(w.cmy, d.th, lane);
     const int cw = w.cmx[d.tw - 1] + 1, ch = w.cmy[d.th - 1] + 1;
     x.tw = cw;  // row stride of the class grid
+    // segment mode when the candidates cover many classes each
+    unsigned long long area = 0;
+    for (int k = lane; k < x.n; k += 32) {
+      const Box b = unpack_entry(x.L[k], x.ndim);
+      area += (unsigned long long)(w.cmx[b.x1] - w.cmx[b.x0] + 1) * (unsigned long long)(w.cmy[b.y1] - w.cmy[b.y0] + 1);
+    }
+#pragma unroll
+    for (int o2 = 16; o2 >= 1; o2 >>= 1) area += __shfl_xor_sync(kFull, area, o2);
+    x.segmode = area >= (unsigned long long)kSegMinArea * (unsigned long long)x.n;
     // a class grid larger than the cell state is swept in strips of class
     // rows, each pass over every candidate (those outside see empty boxes)
     const int cap = class_cap(d.tw, d.th);
     const int strip = cw * ch <= cap ? ch : cap / cw;
     for (x.ylo = 0; x.ylo < ch; x.ylo += strip) {
       x.yhi = min(x.ylo + strip, ch) - 1;
-      for (int c = lane; c < cw * (x.yhi - x.ylo + 1); c += 32) {
-        w.cell[c] = make_uint4((uint32_t)kKindNone << 30, 0u, 0u, 0u);
-        w.scr[c] = 0xFFu;
+      const int rows = x.yhi - x.ylo + 1;
+      if (x.segmode) {
+        const int W = (cw + 31) >> 5;
+        for (int i = lane; i < rows * W; i += 32) w.seg[i] = (i % W == 0) ? 1u : 0u;
+        for (int y = lane; y < rows; y += 32) {
+          w.cell[y * cw] = make_uint4((uint32_t)kKindNone << 30, 0u, 0u, 0u);
+          w.scr[y * cw] = 0xFFu;
+        }
+      } else {
+        for (int c = lane; c < cw * rows; c += 32) {
+          w.cell[c] = make_uint4((uint32_t)kKindNone << 30, 0u, 0u, 0u);
+          w.scr[c] = 0xFFu;
+        }
       }
       __syncwarp();
       int pos = 0;
@@ -572,18 +777,26 @@ __global__ void __launch_bounds__(256, 3) k_sweep(const uint64_t* __restrict__ p
             }
             gend += 32;
           }
-          process_group(x, w, o, pos, gend);
+          if (x.segmode) {
+            process_group_seg(x, w, o, pos, gend);
+          } else {
+            process_group(x, w, o, pos, gend);
+          }
           pos = gend;
           __syncwarp();
           continue;
         }
         unsigned gs = starts & (end == 32 ? kFull : ((1u << end) - 1u));
-        if (stage_lanes(x, w, o, gs, end)) gs = 0;
+        if (!x.segmode && stage_lanes(x, w, o, gs, end)) gs = 0;
         while (gs) {
           const int a = __ffs((int)gs) - 1;
           gs &= gs - 1;
           const int b = gs ? __ffs((int)gs) - 1 : end;
-          process_group(x, w, o, pos + a, pos + b);
+          if (x.segmode) {
+            process_group_seg(x, w, o, pos + a, pos + b);
+          } else {
+            process_group(x, w, o, pos + a, pos + b);
+          }
         }
         pos += end;
         __syncwarp();
