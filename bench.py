@@ -301,6 +301,15 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(value, device):
+    """The largest of every rank's value (the job's time is its slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ---------------------------------------------------------------------------
 # roofline bookkeeping
 # ---------------------------------------------------------------------------
@@ -434,9 +443,7 @@ def run_ours(args):
     clk = clocks.stop()
     total_ms = sum(ms)
     if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, "cuda")
         dist.barrier()
 
     # end to end through the host API: pinned host arrays, H2D inside the step
