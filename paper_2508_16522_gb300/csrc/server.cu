@@ -601,7 +601,10 @@ rt_status rt_server_create(const rt_server_desc* d, rt_server_t* out) {
   }
   if (cudaDeviceSynchronize() != cudaSuccess) return bail(RT_ERR_CUDA, "kernel preload");
   launch_serve_init(p, s->exec_stream);
-  launch_serve(p, d->exec_blocks > 0 ? d->exec_blocks : sms, d->exec_warps > 0 ? d->exec_warps : 4, s->exec_stream);
+  // Two warps per SM by default: the kernel stays resident beside the workers'
+  // analysis, and with more warps its registers would leave room for only two
+  // of the sweep's three blocks per SM.
+  launch_serve(p, d->exec_blocks > 0 ? d->exec_blocks : sms, d->exec_warps > 0 ? d->exec_warps : 2, s->exec_stream);
   if (cudaGetLastError() != cudaSuccess) return bail(RT_ERR_CUDA, "serving kernel launch");
   for (int i = 0; i < d->workers; ++i) s->workers.emplace_back(worker_main, s);
   s->completer = std::thread(completer_main, s);
