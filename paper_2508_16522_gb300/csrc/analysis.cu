@@ -121,9 +121,11 @@ __global__ void k_bin_count(const int32_t* req_off, int32_t n, const int64_t* lo
   }
 }
 
-// One warp per 32 rectangles; the warp writes each rectangle's entries
-// together (lane-strided) so that stores are coalesced and large rectangles
-// do not serialise on one lane.
+// One thread per rectangle: a rectangle over a few tiles writes its own
+// entries; the entries of a larger one are written by its whole warp
+// (lane-strided), so that large rectangles do not serialise on one lane.
+constexpr uint64_t kOwnTiles = 4;
+
 __global__ void k_bin_expand(const int32_t* rect_task, const int64_t* lo, const int64_t* hi,
                              const uint8_t* priv, int64_t R, const uint64_t* off, AnalysisDims d,
                              uint32_t* keys, uint64_t* payload) {
@@ -140,9 +142,26 @@ __global__ void k_bin_expand(const int32_t* rect_task, const int64_t* lo, const 
     task = (uint32_t)rect_task[r];
     pv = priv[r];
   }
-  for (int i = 0; i < 32; ++i) {
+  // A rectangle over at most kOwnTiles tiles (the usual case: one) is written
+  // by its own lane; consecutive rectangles then write consecutive entries, so
+  // the stores coalesce. Larger ones are written by the whole warp below.
+  const bool own = valid && cnt <= (uint64_t)kOwnTiles;
+  if (own) {
+    for (uint64_t k = 0; k < cnt; ++k) {
+      const int32_t tx = tr.tx0 + (int32_t)(k % (uint64_t)tr.ntx);
+      const int32_t ty = tr.ty0 + (int32_t)(k / (uint64_t)tr.ntx);
+      const int64_t ox = (int64_t)tx * d.tw, oy = (int64_t)ty * d.th;
+      const int64_t x0 = (tr.lx > ox ? tr.lx : ox) - ox, x1 = (tr.hx < ox + d.tw - 1 ? tr.hx : ox + d.tw - 1) - ox;
+      const int64_t y0 = (tr.ly > oy ? tr.ly : oy) - oy, y1 = (tr.hy < oy + d.th - 1 ? tr.hy : oy + d.th - 1) - oy;
+      keys[base + k] = (uint32_t)ty * (uint32_t)d.ntx + (uint32_t)tx;
+      payload[base + k] = pack_entry(task, pv, d.ndim, (uint32_t)x0, (uint32_t)x1, (uint32_t)y0, (uint32_t)y1);
+    }
+  }
+  unsigned shared = __ballot_sync(0xffffffffu, valid && !own && cnt > 0);
+  while (shared) {
+    const int i = __ffs((int)shared) - 1;
+    shared &= shared - 1;
     uint64_t c = __shfl_sync(0xffffffffu, cnt, i);
-    if (c == 0) continue;
     uint64_t b = __shfl_sync(0xffffffffu, base, i);
     int64_t lx = __shfl_sync(0xffffffffu, tr.lx, i), hx = __shfl_sync(0xffffffffu, tr.hx, i);
     int64_t ly = __shfl_sync(0xffffffffu, tr.ly, i), hy = __shfl_sync(0xffffffffu, tr.hy, i);
