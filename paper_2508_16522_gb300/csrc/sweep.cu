@@ -41,7 +41,7 @@ constexpr int kHashSlots = 128;
 constexpr int kListCap = 64;
 constexpr int kLaneBuf = 16;     // predecessors one lane buffers in the lane-parallel path
 constexpr int kSmallCells = 16;  // largest box the lane-parallel path takes
-constexpr int kMaxRounds = 8;    // deeper conflict chains go to the warp-wide path
+constexpr int kMaxRounds = 16;   // deeper conflict chains go to the warp-wide path
 constexpr int kLongSpan = 64;    // run spans the whole warp scans together
 constexpr int kSegMinArea = 8;   // mean class cells per candidate from which rows go segmented
 constexpr unsigned kFull = 0xffffffffu;
