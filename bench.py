@@ -53,6 +53,8 @@ def config(tasks_per_step, args=None, tiles=None):
     wl = WORKLOAD if (steps == STEPS and len(pats) == 3) else f"REDUCED (profiling): taskbench {WIDTH}x{steps} {pats}"
     return {"workload": wl, "patterns": pats, "width": WIDTH, "steps_per_graph": steps,
             "tasks_per_step": tasks_per_step, "tiles": tiles,
+            "streams": "one per graph; each graph goes through the single-graph API (launch, analyze, "
+                       "execute); a graph's analysis overlaps the previous graphs' execution",
             "l2": "flushed between timed steps (512 MB write)", "inputs": "synthetic, seed 0"}
 
 
@@ -382,22 +384,35 @@ def run_ours(args):
 
     traces = load_traces(args)
     n_tasks = sum(t.n for t in traces)
-    stream = torch.cuda.Stream()
+    # one stream per graph: the graphs of a step are independent, so one
+    # graph's analysis runs while another's persistent executor does
+    streams = [torch.cuda.Stream() for _ in traces]
+    stream = streams[0]
     dev_inputs = [[torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (t.req_off, t.lo, t.hi, t.priv)]
                   for t in traces]
     host_inputs = [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (t.req_off, t.lo, t.hi, t.priv)]
                    for t in traces]
     tiles = [list(grt.rt_tune_tile(t, TUNE_CACHE)[:2]) for t in traces]
-    graphs = [grt.Graph(2, t.dom_lo, t.dom_hi, tile=tl, stream=stream, flags=grt.RT_GRAPH_PROFILE)
-              for t, tl in zip(traces, tiles)]
+    graphs = [grt.Graph(2, t.dom_lo, t.dom_hi, tile=tl, stream=st, flags=grt.RT_GRAPH_PROFILE)
+              for t, tl, st in zip(traces, tiles, streams)]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
 
-    def step(inputs, defer=False):
+    def step(inputs, defer=False, overlap=True):
+        if not overlap:  # one graph after another
+            for g, inp in zip(graphs, inputs):
+                g.clear()
+                g.launch(*inp, defer_check=defer)
+                g.analyze()
+                g.execute()
+                g.sync()
+            return
         for g, inp in zip(graphs, inputs):
             g.clear()
-            g.launch(*inp, defer_check=defer)
-            g.analyze()
-            g.execute()
+            g.launch(*inp, defer_check=defer)  # copies in, asynchronous
+        for g in graphs:
+            g.analyze()  # waits for this graph's analysis only
+            g.execute()  # asynchronous: the next graph's analysis overlaps it
+        for g in graphs:
             g.sync()
 
     def stats():
@@ -411,14 +426,22 @@ def run_ours(args):
                         "ms_sort_pairs": s["ms_sort_pairs"], "ms_csr": s["ms_csr"], "ms_execute": s["ms_execute"]})
         return out
 
-    def timed(inputs, k, defer=False):
+    def timed(inputs, k, defer=False, overlap=True):
+        """CUDA events on the first graph's stream; the other streams start
+        after its start event and it waits for theirs before its end event."""
         ms, per = [], []
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        done = [torch.cuda.Event() for _ in streams]
         for i in range(k):
             with torch.cuda.stream(stream):
                 flush.fill_(i & 255)
             e0.record(stream)
-            step(inputs, defer)
+            for st in streams[1:]:
+                st.wait_event(e0)
+            step(inputs, defer, overlap)
+            for st, ev in zip(streams[1:], done[1:]):
+                ev.record(st)
+                stream.wait_event(ev)
             e1.record(stream)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
@@ -447,6 +470,9 @@ def run_ours(args):
         total_ms = max_over_ranks(total_ms, "cuda")
         dist.barrier()
 
+    # the same graphs one after another on their streams (no overlap), for reference
+    seq_ms, _ = timed(dev_inputs, args.steps, overlap=False)
+
     # end to end through the host API: pinned host arrays, H2D inside the step
     e2e_ms = [float("nan")]
     if not args.no_e2e:
@@ -474,6 +500,7 @@ def run_ours(args):
     avg = [{k: float(np.mean([p[i][k] for p in per])) for k in per[0][i]} for i in range(len(graphs))]
     peaks = measured_peaks()
     roof = roofline(avg, peaks)
+    # executor kernel time over step time; above 1 when the graphs' executions overlap
     roof["share_of_step"] = (roof["avg_launch_ms"] * len(graphs)) / (total_ms / args.steps) if world == 1 else None
     ex_ms = sum(a["ms_exec_kernel"] for a in avg)
     edges = sum(a["E"] for a in avg)
@@ -505,6 +532,9 @@ def run_ours(args):
                     "value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": 8 * len(graphs), "ms_per_step": sum(e2e_ms) / args.steps,
                     "validation": "on the device (RT_LAUNCH_DEFER_CHECK)"},
+                "sequential": {"ms_per_step": sum(seq_ms) / args.steps,
+                               "value": n_tasks * args.steps / (sum(seq_ms) * 1e-3),
+                               "note": "the three graphs one after another, no overlap between them"},
                 "roofline": roof, "atomic_roofline": atomic_roof, "cpu_baseline": cpu, "clocks": clk,
                 "gpu_launches": launches,
                 "batched": batched, "served": served,

@@ -18,6 +18,8 @@
 // independently), until `replays` runs are done.
 // Every wait is bounded: a warp that sees no progress of the global executed
 // counter for timeout_ns sets status TIMEOUT and returns.
+#include <mutex>
+
 #include "grt_internal.cuh"
 
 namespace grt {
@@ -500,7 +502,28 @@ int exec_max_blocks_per_sm(int warps) {
   return nb;
 }
 
+template <bool T, bool F, bool S>
+void prefer_shared() {
+  cudaFuncSetAttribute(k_exec<T, F, S>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       cudaSharedmemCarveoutMaxShared);
+}
+
 void launch_exec(ExecParams p, int blocks, int warps, cudaStream_t s) {
+  // An SM's shared-memory/L1 split is fixed while a block is resident. The
+  // executor is persistent and uses little shared memory; it asks for the
+  // largest carveout so that analysis kernels of other graphs (a sweep block
+  // takes tens of KB) can run beside it on other streams.
+  static std::once_flag carveout;
+  std::call_once(carveout, [] {
+    prefer_shared<false, false, true>();
+    prefer_shared<false, true, true>();
+    prefer_shared<true, false, true>();
+    prefer_shared<true, true, true>();
+    prefer_shared<false, false, false>();
+    prefer_shared<false, true, false>();
+    prefer_shared<true, false, false>();
+    prefer_shared<true, true, false>();
+  });
   const size_t smem = (size_t)warps * sizeof(WarpQ);
   if (p.keep > kKeepMax) p.keep = kKeepMax;
   if (p.keep < 0) p.keep = 0;
