@@ -226,6 +226,19 @@ rt_status rt_debug_hold_task(rt_graph_t g, int32_t task, int32_t extra);
 rt_status rt_batch_create(const rt_graph_t* graphs, int32_t n_graphs, void* stream,
                           rt_batch_t* out);
 
+/* A batch from ONE analysed graph whose tasks [task_off[k], task_off[k+1])
+ * form graph k (task_off: host int32[n_graphs+1], from 0 to the graph's task
+ * count). The caller places the graphs in disjoint parts of the domain (for
+ * instance stacked bands), so that one analysis captures all of them; the
+ * batch then runs each graph and replays it independently, as rt_batch_create
+ * does. A body sees its graph's own tasks (ids from 0); state-carrying bodies
+ * share the graph's state buffer, in which the graphs' parts are disjoint.
+ * The graph must outlive the batch. Errors: RT_ERR_STATE (not analyzed),
+ * RT_ERR_INVALID (bad offsets, or an edge joins two graphs: checked on the
+ * device), RT_ERR_OOM, RT_ERR_CUDA. */
+rt_status rt_batch_create_stacked(rt_graph_t g, const int32_t* task_off, int32_t n_graphs, void* stream,
+                                  rt_batch_t* out);
+
 /* One persistent launch in which every graph of the batch runs `replays` times;
  * graph g's replay r+1 starts as soon as its replay r has finished,
  * independently of the other graphs. exec_blocks/exec_warps/claim/keep (0 =

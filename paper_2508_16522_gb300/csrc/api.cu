@@ -1039,6 +1039,123 @@ rt_status rt_batch_create(const rt_graph_t* graphs, int32_t n_graphs, void* stre
   return RT_OK;
 }
 
+rt_status rt_batch_create_stacked(rt_graph_t g, const int32_t* task_off, int32_t n_graphs, void* stream,
+                                  rt_batch_t* out) {
+  if (!out) return fail(RT_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!g || !task_off || n_graphs <= 0) return fail(RT_ERR_INVALID, "NULL graph, offsets or no graphs");
+  if (!g->analyzed) return fail(RT_ERR_STATE, "graph is not analyzed");
+  if (task_off[0] != 0 || task_off[n_graphs] != g->n)
+    return fail(RT_ERR_INVALID, "task_off must run from 0 to the graph's %d tasks", g->n);
+  int32_t nonempty = 0;
+  for (int32_t k = 0; k < n_graphs; ++k) {
+    if (task_off[k + 1] < task_off[k]) return fail(RT_ERR_INVALID, "task_off decreases at graph %d", k);
+    nonempty += task_off[k + 1] > task_off[k];
+  }
+  CKR(ensure_device());
+  rt_batch* b = new (std::nothrow) rt_batch();
+  if (!b) return fail(RT_ERR_OOM, "host allocation failed");
+  const int64_t T = g->n, E = g->n_edges, Rt = g->n_roots;
+  b->s = (cudaStream_t)stream;
+  b->G = n_graphs;
+  b->G_nonempty = nonempty;
+  b->T = T;
+  b->E = E;
+  b->Rtot = Rt;
+  cudaStream_t s = b->s;
+  auto bail = [&](rt_status st) {
+    rt_batch_destroy(b);
+    return st;
+  };
+  rt_status st;
+  DevBuf tmp;  // task and root starts of the graphs, the check flag
+  if ((st = b->row_ptr.reserve((size_t)(T + 1) * 4, s)) || (st = b->col.reserve((size_t)std::max<int64_t>(E, 1) * 4, s)) ||
+      (st = b->indeg.reserve((size_t)std::max<int64_t>(T, 1) * 4, s)) ||
+      (st = b->count.reserve((size_t)std::max<int64_t>(T, 1) * 4, s)) ||
+      (st = b->root_items.reserve((size_t)std::max<int64_t>(Rt, 1) * 8, s)) ||
+      (st = b->gtable.reserve((size_t)n_graphs * sizeof(ExecGraph), s)) ||
+      (st = b->done_g.reserve((size_t)n_graphs * 4, s)) || (st = b->ctrl.reserve(sizeof(ExecCtrl), s)) ||
+      (st = tmp.reserve((size_t)(n_graphs + 1) * 16 + 64, s)))
+    return bail(st);
+  if (cudaMallocHost(&b->hpin, 1024) != cudaSuccess || cudaEventCreate(&b->e0) != cudaSuccess ||
+      cudaEventCreate(&b->e1) != cudaSuccess) {
+    tmp.release(s);
+    return bail(fail(RT_ERR_CUDA, "batch host/event allocation failed"));
+  }
+  cudaStreamSynchronize(g->s);  // its analysis is complete
+  uint32_t* task_first = tmp.as<uint32_t>();
+  uint32_t* gathered = task_first + (n_graphs + 1);          // 2 words per graph start
+  uint32_t* root_first = gathered + 2 * (n_graphs + 1);
+  uint32_t* bad = root_first + (n_graphs + 1);
+  std::vector<uint32_t> h_first((size_t)n_graphs + 1), h_gath(2 * ((size_t)n_graphs + 1)), h_root((size_t)n_graphs + 1);
+  for (int32_t k = 0; k <= n_graphs; ++k) h_first[(size_t)k] = (uint32_t)task_off[k];
+  cudaError_t e = cudaMemcpyAsync(task_first, h_first.data(), h_first.size() * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, 4, s);
+  launch_check_stacked(g->row_ptr.as<int32_t>(), g->col.as<int32_t>(), T, task_first, n_graphs, bad, s);
+  launch_serve_gather(g->rootpos.as<uint32_t>(), g->row_ptr.as<int32_t>(), reinterpret_cast<const int32_t*>(task_first),
+                      n_graphs + 1, gathered, s);
+  uint32_t h_bad = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_gath.data(), gathered, h_gath.size() * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h_bad, bad, 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    tmp.release(s);
+    return bail(fail(RT_ERR_CUDA, "stacked batch: %s", cudaGetErrorString(e)));
+  }
+  if (h_bad) {
+    tmp.release(s);
+    return bail(fail(RT_ERR_INVALID, "an edge joins two graphs of the stacked batch"));
+  }
+  for (int32_t k = 0; k <= n_graphs; ++k) h_root[(size_t)k] = h_gath[2 * (size_t)k];
+  std::vector<ExecGraph> table((size_t)n_graphs);
+  for (int32_t k = 0; k < n_graphs; ++k) {
+    ExecGraph& G = table[(size_t)k];
+    const int32_t tb = task_off[k];
+    G.task_base = tb;
+    G.n_tasks = task_off[k + 1] - tb;
+    G.root_base = (int32_t)h_root[(size_t)k];
+    G.n_roots = (int32_t)(h_root[(size_t)k + 1] - h_root[(size_t)k]);
+    G.body = g->desc.body;
+    G.spin_iters = g->desc.spin_iters;
+    G.ndim = g->dims.ndim;
+    // a body sees the graph's own tasks: its launch arrays start at its first task
+    G.state = (int32_t*)g->desc.state;
+    G.out = g->desc.out ? (int32_t*)g->desc.out + tb : nullptr;
+    G.body_arg = g->has_body_arg ? g->body_arg.as<int32_t>() + tb : nullptr;
+    G.req_off = g->req_off.as<int32_t>() + tb;
+    G.lo = g->lo.as<int64_t>();
+    G.hi = g->hi.as<int64_t>();
+    G.priv = g->priv.as<uint8_t>();
+    G.dom_lo[0] = g->dims.dom_lo[0];
+    G.dom_lo[1] = g->dims.dom_lo[1];
+    G.ext[0] = g->dims.ext[0];
+    G.ext[1] = g->dims.ext[1];
+  }
+  if (g->desc.body == RT_BODY_COUNTER || g->desc.body == RT_BODY_CHECK) b->need_fence = 1;
+  if (T > 0) {
+    cudaMemcpyAsync(b->row_ptr.p, g->row_ptr.p, (size_t)(T + 1) * 4, cudaMemcpyDeviceToDevice, s);
+    if (E > 0) cudaMemcpyAsync(b->col.p, g->col.p, (size_t)E * 4, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(b->indeg.p, g->indeg.p, (size_t)T * 4, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(b->count.p, g->indeg.p, (size_t)T * 4, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(root_first, h_root.data(), h_root.size() * 4, cudaMemcpyHostToDevice, s);
+    launch_tag_roots(g->root_items.as<uint64_t>(), b->root_items.as<uint64_t>(), Rt, root_first, n_graphs, s);
+  } else {
+    cudaMemsetAsync(b->row_ptr.p, 0, 4, s);
+  }
+  if ((st = b->adj.reserve((size_t)std::max<int64_t>(T, 1) * 32, s))) {
+    tmp.release(s);
+    return bail(st);
+  }
+  launch_pack_adj(b->row_ptr.as<int32_t>(), b->col.as<int32_t>(), b->indeg.as<int32_t>(), T, b->adj.as<int4>(), s);
+  e = cudaMemcpyAsync(b->gtable.p, table.data(), table.size() * sizeof(ExecGraph), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  tmp.release(s);
+  if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return bail(fail(RT_ERR_CUDA, "batch assembly failed"));
+  b->dirty = true;  // ring not yet initialised
+  *out = b;
+  return RT_OK;
+}
+
 rt_status rt_batch_execute(rt_batch_t b, int32_t replays, int32_t exec_blocks, int32_t exec_warps, int32_t claim,
                            int32_t keep) {
   if (!b) return fail(RT_ERR_INVALID, "batch is NULL");

@@ -459,7 +459,56 @@ __global__ void k_rebase_roots(const uint64_t* src, uint64_t* dst, int32_t n, in
   int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) dst[i] = ((uint64_t)(uint32_t)graph << 32) | (uint32_t)(task_base + (int32_t)(uint32_t)src[i]);
 }
+// the last k with first[k] <= x (first[0] = 0 <= x; first is nondecreasing)
+__device__ __forceinline__ int32_t last_le(const uint32_t* first, int32_t n, uint32_t x) {
+  int32_t lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int32_t mid = (lo + hi + 1) >> 1;
+    if (first[mid] <= x) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// roots of a stacked batch: tags each with its graph (its root range's index)
+__global__ void k_tag_roots(const uint64_t* src, uint64_t* dst, int64_t n, const uint32_t* root_first, int32_t G) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t k = last_le(root_first, G, (uint32_t)i);
+  dst[i] = ((uint64_t)(uint32_t)k << 32) | (uint32_t)src[i];
+}
+
+// every edge of a stacked batch stays inside its source task's graph
+__global__ void k_check_stacked(const int32_t* row_ptr, const int32_t* col, int64_t T, const uint32_t* task_first,
+                                int32_t G, uint32_t* bad) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= T) return;
+  const int32_t k = last_le(task_first, G, (uint32_t)v);
+  const int32_t lo = (int32_t)task_first[k], hi = (int32_t)task_first[k + 1];
+  for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+    const int32_t c = col[e];
+    if (c < lo || c >= hi) {
+      atomicOr(bad, 1u);
+      return;
+    }
+  }
+}
 }  // namespace
+
+void launch_tag_roots(const uint64_t* src, uint64_t* dst, int64_t n, const uint32_t* root_first, int32_t G,
+                      cudaStream_t s) {
+  if (n > 0) {
+    count_launch();
+    k_tag_roots<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, dst, n, root_first, G);
+  }
+}
+
+void launch_check_stacked(const int32_t* row_ptr, const int32_t* col, int64_t T, const uint32_t* task_first,
+                          int32_t G, uint32_t* bad, cudaStream_t s) {
+  if (T > 0) {
+    count_launch();
+    k_check_stacked<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(row_ptr, col, T, task_first, G, bad);
+  }
+}
 
 void launch_pack_adj(const int32_t* row_ptr, const int32_t* col, const int32_t* indeg, int64_t n, int4* adj,
                      cudaStream_t s) {
@@ -549,6 +598,8 @@ void preload_exec() {
   cudaFuncGetAttributes(&a, k_seed);
   cudaFuncGetAttributes(&a, k_pack_adj);
   cudaFuncGetAttributes(&a, k_rebase_roots);
+  cudaFuncGetAttributes(&a, k_tag_roots);
+  cudaFuncGetAttributes(&a, k_check_stacked);
   cudaFuncGetAttributes(&a, k_exec<false, false, true>);
   cudaFuncGetAttributes(&a, k_exec<false, true, true>);
   cudaFuncGetAttributes(&a, k_exec<true, false, true>);

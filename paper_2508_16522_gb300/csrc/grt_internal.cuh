@@ -300,6 +300,11 @@ void preload_analysis();
 void preload_sweep();
 void preload_exec();
 void preload_serve();
+// stacked batches (rt_batch_create_stacked)
+void launch_tag_roots(const uint64_t* src, uint64_t* dst, int64_t n, const uint32_t* root_first, int32_t G,
+                      cudaStream_t s);
+void launch_check_stacked(const int32_t* row_ptr, const int32_t* col, int64_t T, const uint32_t* task_first,
+                          int32_t G, uint32_t* bad, cudaStream_t s);
 // out[2i] = rootpos[idx[i]], out[2i+1] = row_ptr[idx[i]] for i < k
 void launch_serve_gather(const uint32_t* rootpos, const int32_t* row_ptr, const int32_t* idx, int k, uint32_t* out,
                          cudaStream_t s);

@@ -33,7 +33,8 @@ EXPORTS = ["rt_graph_create", "rt_graph_destroy", "rt_graph_clear", "rt_launch_b
            "rt_batch_execute", "rt_batch_sync", "rt_batch_counters", "rt_batch_destroy", "rt_last_error", "rt_device_info",
            "rt_kernel_launches", "rt_execute_csr_static", "rt_microbench_atomics", "rt_now_ns",
            "rt_server_create", "rt_server_submit", "rt_server_poll", "rt_server_result", "rt_server_drain",
-           "rt_server_stats", "rt_server_destroy", "rt_tune_tile", "rt_tune_exec", "rt_tune_batch"]
+           "rt_server_stats", "rt_server_destroy", "rt_tune_tile", "rt_tune_exec", "rt_tune_batch",
+           "rt_batch_create_stacked"]
 
 
 class GrtError(RuntimeError):
@@ -142,6 +143,7 @@ def load(path: str = LIB_PATH):
         "rt_tune_tile": [ctypes.POINTER(rt_graph_desc), i32, P, P, P, P, ctypes.c_char_p, ctypes.POINTER(i32),
                          ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)],
         "rt_tune_exec": [P, ctypes.c_char_p, ctypes.POINTER(rt_exec_config)],
+        "rt_batch_create_stacked": [P, P, i32, P, ctypes.POINTER(P)],
         "rt_tune_batch": [P, i32, ctypes.c_char_p, ctypes.POINTER(rt_exec_config)],
     }
     for name, args in sig.items():
@@ -388,6 +390,19 @@ class Batch:
         s = None if stream is None else stream.cuda_stream
         _check(load().rt_batch_create(arr, len(self.graphs), s, ctypes.byref(h)))
         self.h = h.value
+
+    @classmethod
+    def stacked(cls, graph, task_off, stream=None):
+        """A batch of the graphs that one analysed graph holds side by side:
+        tasks [task_off[k], task_off[k+1]) are graph k."""
+        self = cls.__new__(cls)
+        self.graphs = [graph]
+        off = np.ascontiguousarray(task_off, dtype=np.int32)
+        h = ctypes.c_void_p()
+        s = None if stream is None else stream.cuda_stream
+        _check(load().rt_batch_create_stacked(graph.h, off.ctypes.data, len(off) - 1, s, ctypes.byref(h)))
+        self.h = h.value
+        return self
 
     def execute(self, replays: int = 1, blocks: int = 0, warps: int = 0, claim: int = 0, keep: int = 0):
         _check(load().rt_batch_execute(self.h, replays, blocks, warps, claim, keep))

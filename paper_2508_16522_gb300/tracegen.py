@@ -295,6 +295,32 @@ def fig6_fixture() -> Trace:
                    pred_counts=np.array([0, 1, 1, 2]), pred=np.array([0, 0, 1, 2]), name="fig6")
 
 
+def stack_bands(traces: List[Trace], name: str = "stacked"):
+    """Places 2-D traces in bands of one domain, one above the other (trace k
+    moves up by the heights of the traces before it): the launches of trace k
+    become tasks [off[k], off[k+1]) of the result, and no rectangle of one
+    trace meets another's. Returns (trace, off)."""
+    counts, los, his, pv = [], [], [], []
+    y = 0
+    width = 1
+    off = np.zeros(len(traces) + 1, dtype=np.int32)
+    for k, tr in enumerate(traces):
+        assert tr.ndim == 2
+        lo = tr.lo - tr.dom_lo
+        hi = tr.hi - tr.dom_lo
+        lo[:, 1] += y
+        hi[:, 1] += y
+        counts.append(np.diff(tr.req_off))
+        los.append(lo)
+        his.append(hi)
+        pv.append(tr.priv)
+        y += int(tr.dom_hi[1] - tr.dom_lo[1] + 1)
+        width = max(width, int(tr.dom_hi[0] - tr.dom_lo[0] + 1))
+        off[k + 1] = off[k] + tr.n
+    return _finish(2, [0, 0], [width - 1, y - 1], np.concatenate(counts), np.concatenate(los).reshape(-1),
+                   np.concatenate(his).reshape(-1), np.concatenate(pv), name=name), off
+
+
 def concat(traces: List[Trace]) -> Trace:
     """Concatenate traces over the same domain into one program (ids shift)."""
     t0 = traces[0]

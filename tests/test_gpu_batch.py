@@ -105,3 +105,65 @@ def test_batch_launch_shapes_give_same_results(shape):
     b.close()
     for g in graphs:
         g.close()
+
+
+def test_stacked_batch_equals_each_graph_alone():
+    """Graphs stacked in bands of one domain are captured by ONE analysis; the
+    batch made from it runs each graph and replays it independently. Each
+    graph's part of the CSR equals its own oracle CSR, SPIN outputs count from
+    the graph's own first task, and the CHECK state after 3 replays equals the
+    oracle's 3 sequential runs of the whole stack (the graphs share no cell)."""
+    from gpu_helpers import oracle_csr
+    trs = [tg.random_rects(grid=(40, 30), n=200 + 30 * k, rects=(1, 3), side=(1, 9), seed=200 + k) for k in range(5)]
+    trs += [tg.taskbench(32, 6 + k, tg.PATTERNS[k % 3], seed=k) for k in range(4)]
+    st, off = tg.stack_bands(trs)
+    for body, spin in ((grt.RT_BODY_SPIN, 21), (grt.RT_BODY_CHECK, 0)):
+        g = gpu_graph(st, body=body, spin_iters=spin, tile=(8, 8))
+        g.analyze()
+        rp, col, ind = g.csr()
+        for k, tr in enumerate(trs):
+            a, b = int(off[k]), int(off[k + 1])
+            rp_o, col_o, _ = oracle_csr(tr)
+            mine = rp[a:b + 1].astype(np.int64) - int(rp[a])
+            assert np.array_equal(mine, rp_o), tr.name
+            assert np.array_equal(col[rp[a]:rp[b]] - a, col_o), tr.name
+        batch = grt.Batch.stacked(g, off)
+        batch.execute(replays=3)
+        batch.sync()
+        assert batch.counters()["tasks"] == 3 * st.n
+        if body == grt.RT_BODY_SPIN:
+            out = g.out.cpu().numpy()
+            for k, tr in enumerate(trs):
+                want = np.array([oracle.spin(j, spin) for j in range(tr.n)], np.uint32).view(np.int32)
+                assert np.array_equal(out[off[k]:off[k + 1]], want), tr.name
+        else:
+            # each graph's part of the stack, with its own task ids, in the
+            # stack's domain: the bodies see their own ids and the shared cells
+            parts = []
+            for k in range(len(trs)):
+                a, b = int(off[k]), int(off[k + 1])
+                r0, r1 = int(st.req_off[a]), int(st.req_off[b])
+                parts.append(tg._finish(2, st.dom_lo, st.dom_hi, np.diff(st.req_off[a:b + 1]),
+                                        st.lo[r0:r1].reshape(-1), st.hi[r0:r1].reshape(-1), st.priv[r0:r1]))
+            s_o = np.zeros(st.n_cells, np.int32)
+            outs = [None] * len(parts)
+            for _ in range(3):
+                for k, part in enumerate(parts):
+                    s_o, outs[k] = oracle.run_bodies(part, oracle.oracle.BODY_CHECK, state=s_o)
+            assert np.array_equal(g.state.cpu().numpy(), s_o)
+            out = g.out.cpu().numpy()
+            for k in range(len(parts)):
+                assert np.array_equal(out[off[k]:off[k + 1]], outs[k][:trs[k].n]), trs[k].name
+        batch.close()
+        g.close()
+
+
+def test_stacked_batch_refuses_graphs_that_share_cells():
+    trs = [tg.random_rects(grid=(20, 20), n=60, rects=(1, 2), side=(2, 8), seed=300 + k) for k in range(2)]
+    both = tg.concat(trs)  # same cells: edges join the two
+    g = gpu_graph(both)
+    g.analyze()
+    with pytest.raises(grt.GrtError) as e:
+        grt.Batch.stacked(g, [0, trs[0].n, both.n])
+    assert e.value.status == grt.RT_ERR_INVALID
+    g.close()

@@ -130,3 +130,32 @@ def test_served_full_size_stream():
             rp_o, col_o, _ = oracle_csr(r.trace)
             assert np.array_equal(rp.astype(np.int64), rp_o) and np.array_equal(col, col_o)
     srv.close()
+
+
+def test_batched_full_size_stacked_capture():
+    """The benchmark's capture of the batched workload: all 4096 graphs stacked
+    in bands of one domain and analysed ONCE. Every graph's part of the CSR
+    passes the invariants and stays inside the graph; sampled graphs (every
+    256th and the largest) equal their own oracle CSR; the stacked batch runs
+    every task of 20 replays."""
+    ensure_built()
+    traces = tg.batch_graphs(4096, seed=0)
+    st, off = tg.stack_bands(traces, name="batch")
+    g = gpu_graph(st, tile=(8, 8), defer_check=True)
+    g.analyze()
+    rp, col, ind = g.csr()
+    src, col64 = check_csr_invariants(st.n, rp, col, ind)
+    graph_of = np.searchsorted(off, np.arange(st.n), side="right") - 1
+    assert np.array_equal(graph_of[src], graph_of[col64]), "an edge joins two graphs"
+    sampled = set(range(0, 4096, 256)) | {int(np.argmax([t.n for t in traces]))}
+    for k in sorted(sampled):
+        a, b = int(off[k]), int(off[k + 1])
+        rp_o, col_o, _ = oracle_csr(traces[k])
+        assert np.array_equal(rp[a:b + 1].astype(np.int64) - int(rp[a]), rp_o), traces[k].name
+        assert np.array_equal(col[rp[a]:rp[b]] - a, col_o), traces[k].name
+    batch = grt.Batch.stacked(g, off)
+    batch.execute(replays=20)
+    batch.sync()
+    assert batch.counters()["tasks"] == 20 * st.n
+    batch.close()
+    g.close()

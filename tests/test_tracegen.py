@@ -65,3 +65,20 @@ def test_served_stream_poisson():
     reqs = tg.served_stream(2000, rate_per_s=50_000.0, n_range=(32, 64), seed=3)
     gaps = np.diff([r.arrival_ns for r in reqs])
     assert abs(gaps.mean() / 1e9 - 1 / 50_000.0) < 0.1 / 50_000.0
+
+
+def test_stack_bands_keeps_each_trace_to_itself():
+    """The oracle on traces stacked in bands finds exactly each trace's own
+    edges, moved by its task offset: no rectangle of one meets another's."""
+    import oracle
+    trs = [tg.random_rects(grid=(30 + 7 * k, 20 + 3 * k), n=120 + 40 * k, rects=(1, 3), side=(1, 12), seed=40 + k)
+           for k in range(4)] + [tg.taskbench(16, 9, "butterfly", seed=1)]
+    st, off = tg.stack_bands(trs)
+    assert off[-1] == st.n and st.n == sum(t.n for t in trs)
+    s, d = oracle.analyze(st)
+    got = set(zip(s.tolist(), d.tolist()))
+    want = set()
+    for k, t in enumerate(trs):
+        a, b = oracle.analyze(t)
+        want |= set(zip((a + off[k]).tolist(), (b + off[k]).tolist()))
+    assert got == want
