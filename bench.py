@@ -520,10 +520,62 @@ def run_ours(args):
     value = world * n_tasks * args.steps / (total_ms * 1e-3)
     e2e_value = None if args.no_e2e else n_tasks * args.steps / (sum(e2e_ms) * 1e-3)
     avg = [{k: float(np.mean([p[i][k] for p in per])) for k in per[0][i]} for i in range(len(graphs))]
+    # the same graphs with 256-iteration integer spin bodies (configs[1]'s second
+    # body), execution only: the body adds a chain of 256 dependent multiply-adds
+    # to every wavefront step
+    spin = None
+    if world == 1:
+        spin_ms = []
+        for t, tl, st_ in zip(traces, tiles, streams):
+            out = torch.zeros(t.n, dtype=torch.int32, device="cuda")
+            gs = grt.Graph(2, t.dom_lo, t.dom_hi, body=grt.RT_BODY_SPIN, spin_iters=256, out=out, tile=tl,
+                           stream=st_, flags=grt.RT_GRAPH_PROFILE)
+            gs.launch_trace(t, defer_check=True)
+            gs.analyze()
+            gs.tune(TUNE_CACHE)
+            runs = []
+            for _ in range(4):
+                gs.execute()
+                gs.sync()
+                runs.append(gs.stats()["ms_exec_kernel"])
+            spin_ms.append(float(np.median(runs[1:])))
+            gs.close()
+        empty_ms = []  # the EMPTY graphs run alone too (the timed step overlaps them)
+        for g in graphs:
+            runs = []
+            for _ in range(4):
+                g.execute()
+                g.sync()
+                runs.append(g.stats()["ms_exec_kernel"])
+            empty_ms.append(float(np.median(runs[1:])))
+        spin = {"body": "SPIN, 256 iterations of an int32 LCG per task", "ms_exec_kernel": spin_ms,
+                "ms_exec_kernel_empty_alone": empty_ms,
+                "exec_tasks_per_s": n_tasks / (sum(spin_ms) * 1e-3),
+                "added_ns_per_wavefront_step": [round(1e6 * (a - b) / STEPS, 1) for a, b in zip(spin_ms, empty_ms)],
+                "note": "each of the 1000 wavefront steps carries one 256-long chain of dependent integer "
+                        "multiply-adds on its critical path"}
+
     peaks = measured_peaks()
     roof = roofline(avg, peaks)
     # executor kernel time over step time; above 1 when the graphs' executions overlap
     roof["share_of_step"] = (roof["avg_launch_ms"] * len(graphs)) / (total_ms / args.steps) if world == 1 else None
+    # the analysis against HBM: algorithmic bytes are the launches and
+    # rectangles read once and the CSR written once (req_off 4 B per task,
+    # 2 x ndim x 8 + 1 B per rectangle; row_ptr and indeg 8 B per task, col
+    # 4 B per edge); the intermediate traffic (binned entries, candidate pairs,
+    # both sorted) is reported beside it
+    R_per = [float(t.n_rects) for t in traces]
+    ana_alg = [4 * a["n"] + 33 * r + 8 * a["n"] + 4 * a["E"] for a, r in zip(avg, R_per)]
+    ana_inter = [2 * 12 * a["entries"] + 2 * 8 * a["pairs"] for a in avg]
+    ana_ms_tot = sum(a["ms_analyze"] for a in avg)
+    analysis_roof = {
+        "bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"] if peaks else 6800.0,
+        "algorithmic_bytes_per_step": sum(ana_alg), "intermediate_bytes_per_step": sum(ana_inter),
+        "ms_per_step": ana_ms_tot,
+        "achieved": sum(ana_alg) / (ana_ms_tot * 1e-3) / 1e9,
+        "note": "a dozen dependent phases (bin, sort, sweep, sort, CSR) with host syncs between them; the "
+                "intermediate bytes (entries and pairs written and sorted) dwarf the algorithmic ones"}
+    analysis_roof["frac"] = analysis_roof["achieved"] / analysis_roof["peak"]
     ex_ms = sum(a["ms_exec_kernel"] for a in avg)
     edges = sum(a["E"] for a in avg)
     depth = getattr(args, "graph_steps", STEPS)
@@ -557,7 +609,9 @@ def run_ours(args):
                 "sequential": {"ms_per_step": sum(seq_ms) / args.steps,
                                "value": n_tasks * args.steps / (sum(seq_ms) * 1e-3),
                                "note": "the three graphs one after another, no overlap between them"},
-                "roofline": roof, "atomic_roofline": atomic_roof, "cpu_baseline": cpu, "clocks": clk,
+                "roofline": roof, "analysis_roofline": analysis_roof, "atomic_roofline": atomic_roof,
+                "spin_bodies": spin,
+                "cpu_baseline": cpu, "clocks": clk,
                 "gpu_launches": launches,
                 "batched": batched, "served": served,
                 "wall_s_timed": wall,
