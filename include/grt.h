@@ -189,6 +189,18 @@ rt_status rt_execute(rt_graph_t g);
  * persistent launch (relaunched from a cached CUDA graph). Asynchronous. */
 rt_status rt_replay(rt_graph_t g, int32_t times);
 
+/* Runs the analysed graph once through the STANDARD, event-based executor
+ * instead of the compiled one, for comparison (the paper's generic task
+ * runtime, Fig. task-to-rt-actor reduction, against its compiled actors,
+ * Section 4.2): every run starts with fresh events; each launch registers as a
+ * waiter on its preconditions' events (built from the CSR's in-edges, as the
+ * application would state them), and a finished task triggers its event and
+ * notifies the waiters. Bodies and results are those of rt_execute.
+ * Synchronous; *ms_kernel (may be NULL) receives the kernel time. Errors:
+ * RT_ERR_STATE (not analyzed), RT_ERR_INVALID, RT_ERR_TIMEOUT (no progress for
+ * timeout_ns), RT_ERR_OOM, RT_ERR_CUDA. */
+rt_status rt_execute_events(rt_graph_t g, float* ms_kernel);
+
 /* Launch shape of this graph's executor runs (0 = library default): number of
  * persistent blocks, warps per block (1..8), how many published ring slots a
  * warp claims at once (1..32) and how many newly ready successors a warp keeps

@@ -111,7 +111,8 @@ int bits_for(uint64_t v) {  // smallest b with 2^b > v
   return b;
 }
 
-enum { EV_A0 = 0, EV_BIN, EV_SORTE, EV_SWEEP, EV_SORTP, EV_CSR, EV_X0, EV_XK0, EV_XK1, EV_SW0, EV_SW1, EV_COUNT };
+enum { EV_A0 = 0, EV_BIN, EV_SORTE, EV_SWEEP, EV_SORTP, EV_CSR, EV_X0, EV_XK0, EV_XK1, EV_SW0, EV_SW1, EV_E0, EV_E1,
+       EV_COUNT };
 
 }  // namespace
 
@@ -130,6 +131,9 @@ struct rt_graph {
   DevBuf rect_task, cnt, keys, keys_alt, pay, pay_alt, seg_b, seg_e, pairs, pairs_alt, flags, upos;
   DevBuf col, row_ptr, indeg, count, rootpos, root_items, ws, misc, adj;
   DevBuf tflags;  // per tile: dropped a pair in the first sweep / in the rerun
+  // the event-based executor (rt_execute_events): in-edges, events, waiter nodes
+  DevBuf ev_pred_off, ev_pred, ev_head, ev_pending, ev_nodes, ev_ring, ev_ctrl;
+  bool ev_preds = false;  // in-edges built for the current analysis
   // execution
   DevBuf ring, ctrl, gtable, done_g, tickets;
   uint32_t* hpin = nullptr;  // pinned readback area (64 words)
@@ -278,7 +282,9 @@ rt_status rt_graph_destroy(rt_graph_t g) {
                     &g->err, &g->rect_task, &g->cnt, &g->keys, &g->keys_alt, &g->pay, &g->pay_alt,
                     &g->seg_b, &g->seg_e, &g->pairs, &g->pairs_alt, &g->flags, &g->upos, &g->col,
                     &g->row_ptr, &g->indeg, &g->count, &g->rootpos, &g->root_items, &g->ws, &g->misc, &g->adj,
-                    &g->ring, &g->ctrl, &g->gtable, &g->done_g, &g->tickets, &g->tflags};
+                    &g->ring, &g->ctrl, &g->gtable, &g->done_g, &g->tickets, &g->tflags,
+                    &g->ev_pred_off, &g->ev_pred, &g->ev_head, &g->ev_pending, &g->ev_nodes, &g->ev_ring,
+                    &g->ev_ctrl};
   for (DevBuf* b : bufs) b->release(g->s);
   cudaStreamSynchronize(g->s);
   if (g->hpin) cudaFreeHost(g->hpin);
@@ -663,6 +669,7 @@ extern "C" rt_status rt_analyze(rt_graph_t g) {
   CKR(ensure_device());
   CKR(ensure_pinned(g));
   drop_replay_graph(g);
+  g->ev_preds = false;
   if (g->n > 0) CKR(run_analysis(g));
   else g->n_edges = g->n_roots = g->n_entries = g->n_pairs = 0;
   g->analyzed = true;
@@ -837,6 +844,80 @@ extern "C" {
 rt_status rt_execute(rt_graph_t g) { return start_run(g, 1); }
 
 rt_status rt_replay(rt_graph_t g, int32_t times) { return start_run(g, times); }
+
+rt_status rt_execute_events(rt_graph_t g, float* ms_kernel) {
+  if (!g) return fail(RT_ERR_INVALID, "graph is NULL");
+  if (!g->analyzed) return fail(RT_ERR_STATE, "graph not analyzed");
+  if (ms_kernel) *ms_kernel = 0.f;
+  if (g->n == 0) return RT_OK;
+  const int body = g->desc.body;
+  if ((body == RT_BODY_SPIN || body == RT_BODY_CHECK) && (!g->desc.out || g->desc.out_elems < g->n))
+    return fail(RT_ERR_INVALID, "SPIN/CHECK bodies need `out` with one int32 per task");
+  CKR(ensure_device());
+  CKR(ensure_pinned(g));
+  cudaStream_t s = g->s;
+  const int32_t n = g->n;
+  const int64_t E = g->n_edges;
+  if (!g->ev_preds) {  // the launches' preconditions, as the application would state them
+    CKR(g->ev_pred_off.reserve((size_t)(n + 1) * 4, s));
+    CKR(g->ev_pred.reserve((size_t)std::max<int64_t>(E, 1) * 4, s));
+    CKR(g->ev_pending.reserve((size_t)n * 4, s));
+    CKR(reserve_ws(g, scan_ws_elems<uint32_t>(n + 1) * 4));
+    CK(cudaMemcpyAsync(g->ev_pred_off.p, g->indeg.p, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+    scan_exclusive<uint32_t>(g->ev_pred_off.as<uint32_t>(), g->ev_pred_off.as<uint32_t>(), n, g->ws.as<uint32_t>(), s);
+    CK(cudaMemsetAsync(g->ev_pending.p, 0, (size_t)n * 4, s));  // cursors for the transpose
+    launch_ev_transpose(g->row_ptr.as<int32_t>(), g->col.as<int32_t>(), n, g->ev_pred_off.as<int32_t>(),
+                        g->ev_pending.as<int32_t>(), g->ev_pred.as<int32_t>(), s);
+    g->ev_preds = true;
+  }
+  const uint32_t ring_cap = (uint32_t)n + 64u;
+  CKR(g->ev_head.reserve((size_t)n * 4, s));
+  CKR(g->ev_pending.reserve((size_t)n * 4, s));
+  CKR(g->ev_nodes.reserve((size_t)(E + 1) * 8, s));
+  CKR(g->ev_ring.reserve((size_t)ring_cap * 4, s));
+  CKR(g->ev_ctrl.reserve(sizeof(EvCtrl), s));
+  CK(cudaMemsetAsync(g->ev_ctrl.p, 0, sizeof(EvCtrl), s));
+  EvParams p{};
+  p.pred_off = g->ev_pred_off.as<int32_t>();
+  p.pred = g->ev_pred.as<int32_t>();
+  p.n = n;
+  p.ring_cap = ring_cap;
+  p.head = g->ev_head.as<uint32_t>();
+  p.pending = g->ev_pending.as<int32_t>();
+  p.node_task = g->ev_nodes.as<uint32_t>();
+  p.node_next = g->ev_nodes.as<uint32_t>() + (E + 1);
+  p.ring = g->ev_ring.as<uint32_t>();
+  p.ctrl = g->ev_ctrl.as<EvCtrl>();
+  ExecGraph& G = p.G;
+  G.n_tasks = n;
+  G.body = body;
+  G.spin_iters = g->desc.spin_iters;
+  G.ndim = g->dims.ndim;
+  G.state = (int32_t*)g->desc.state;
+  G.out = (int32_t*)g->desc.out;
+  G.body_arg = g->body_arg.as<int32_t>();
+  G.req_off = g->req_off.as<int32_t>();
+  G.lo = g->lo.as<int64_t>();
+  G.hi = g->hi.as<int64_t>();
+  G.priv = g->priv.as<uint8_t>();
+  G.dom_lo[0] = g->dims.dom_lo[0];
+  G.dom_lo[1] = g->dims.dom_lo[1];
+  G.ext[0] = g->dims.ext[0];
+  G.ext[1] = g->dims.ext[1];
+  p.timeout_ns = g->desc.timeout_ns > 0 ? g->desc.timeout_ns : 2000000000ll;
+  CKR(graph_events(g));
+  CK(cudaEventRecord(g->ev[EV_E0], s));
+  launch_events(p, g_dev.num_sms * 2, s);
+  CK(cudaEventRecord(g->ev[EV_E1], s));
+  CK(cudaMemcpyAsync(g->hpin + kStatusWord, &p.ctrl->status, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  if (ms_kernel) cudaEventElapsedTime(ms_kernel, g->ev[EV_E0], g->ev[EV_E1]);
+  const uint32_t st = g->hpin[kStatusWord];
+  if (st == (uint32_t)RT_ERR_TIMEOUT) return fail(RT_ERR_TIMEOUT, "event executor made no progress");
+  if (st == (uint32_t)RT_ERR_OOM) return fail(RT_ERR_OOM, "event executor ring overflow");
+  return RT_OK;
+}
 
 rt_status rt_sync(rt_graph_t g) {
   if (!g) return fail(RT_ERR_INVALID, "graph is NULL");

@@ -20,6 +20,7 @@
 // counter for timeout_ns sets status TIMEOUT and returns.
 #include <mutex>
 
+#include "bodies.cuh"
 #include "grt_internal.cuh"
 
 namespace grt {
@@ -56,84 +57,6 @@ __global__ void k_seed(ExecParams p, int64_t ring_clear) {
   }
 }
 
-__device__ __forceinline__ uint32_t cell_index(const ExecGraph& G, int64_t x, int64_t y) {
-  return (uint32_t)((y - G.dom_lo[1]) * G.ext[0] + (x - G.dom_lo[0]));
-}
-
-// CHECK body (order-sensitive): see grt.h. Lane-serial; meant for test sizes.
-__device__ void check_body(const ExecGraph& G, int j) {
-  const int r0 = G.req_off[j], r1 = G.req_off[j + 1];
-  const int D = G.ndim;
-  uint32_t acc = 0;
-  for (int pass = 0; pass < 2; ++pass) {
-    uint32_t sum = 0;
-    for (int e = r0; e < r1; ++e) {
-      const int64_t x0 = G.lo[(int64_t)e * D], x1 = G.hi[(int64_t)e * D];
-      const int64_t y0 = D == 2 ? G.lo[(int64_t)e * 2 + 1] : G.dom_lo[1];
-      const int64_t y1 = D == 2 ? G.hi[(int64_t)e * 2 + 1] : G.dom_lo[1];
-      for (int64_t y = y0; y <= y1; ++y) {
-        for (int64_t x = x0; x <= x1; ++x) {
-          bool seen = false;
-          for (int f = r0; f < e && !seen; ++f) {
-            const int64_t fx0 = G.lo[(int64_t)f * D], fx1 = G.hi[(int64_t)f * D];
-            const int64_t fy0 = D == 2 ? G.lo[(int64_t)f * 2 + 1] : y, fy1 = D == 2 ? G.hi[(int64_t)f * 2 + 1] : y;
-            seen = fx0 <= x && x <= fx1 && fy0 <= y && y <= fy1;
-          }
-          if (seen) continue;  // the first rectangle covering the cell handles it
-          uint32_t comb = G.priv[e];
-          for (int f = e + 1; f < r1; ++f) {
-            const int64_t fx0 = G.lo[(int64_t)f * D], fx1 = G.hi[(int64_t)f * D];
-            const int64_t fy0 = D == 2 ? G.lo[(int64_t)f * 2 + 1] : y, fy1 = D == 2 ? G.hi[(int64_t)f * 2 + 1] : y;
-            if (fx0 <= x && x <= fx1 && fy0 <= y && y <= fy1) comb = combine_priv(comb, G.priv[f]);
-          }
-          const uint32_t c = cell_index(G, x, y);
-          if (pass == 0) {
-            if (comb == (uint32_t)kKindRead) sum += (uint32_t)__ldcg(G.state + c);
-          } else if (comb == (uint32_t)kKindWrite) {
-            __stcg(G.state + c, (int32_t)mix32(acc, c));
-          } else if (comb == (uint32_t)kKindReduce) {
-            atomicAdd(reinterpret_cast<unsigned*>(G.state) + c, mix32((uint32_t)j, c));
-          }
-        }
-      }
-    }
-    if (pass == 0) acc = mix32((uint32_t)j, sum);
-  }
-  G.out[j] = (int32_t)acc;
-}
-
-// FENCE = false: the launch only has bodies that read nothing written by
-// other tasks (EMPTY, SPIN), so the order-sensitive bodies are compiled out.
-template <bool FENCE>
-__device__ __forceinline__ void run_body(const ExecGraph& G, int j) {
-  if (!FENCE) {
-    if (G.body == RT_BODY_SPIN) {
-      uint32_t x = (uint32_t)j;
-      for (int k = 0; k < G.spin_iters; ++k) x = x * 1664525u + 1013904223u;
-      G.out[j] = (int32_t)x;
-    }
-    return;
-  }
-  switch (G.body) {
-    case RT_BODY_SPIN: {
-      uint32_t x = (uint32_t)j;
-      for (int k = 0; k < G.spin_iters; ++k) x = x * 1664525u + 1013904223u;
-      G.out[j] = (int32_t)x;
-      break;
-    }
-    case RT_BODY_COUNTER: {
-      const int k = G.body_arg[j];
-      const int32_t v = __ldcg(G.state + k);
-      __stcg(G.state + k, (int32_t)((uint32_t)v + 1u));
-      break;
-    }
-    case RT_BODY_CHECK:
-      check_body(G, j);
-      break;
-    default:
-      break;
-  }
-}
 
 // pushes graph g's roots into the ring for its next run (warp-cooperative)
 __device__ void push_roots(const ExecParams& p, int g, int lane) {

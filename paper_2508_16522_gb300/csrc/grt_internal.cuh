@@ -300,6 +300,33 @@ void preload_analysis();
 void preload_sweep();
 void preload_exec();
 void preload_serve();
+// the event-based executor (rt_execute_events)
+struct EvCtrl {  // hot words on separate 128-byte lines
+  uint32_t reg, pad0[31];    // launches registered (claims of 32)
+  uint32_t pool, pad1[31];   // waiter nodes allocated
+  uint32_t rhead, pad2[31];  // ring tickets claimed
+  uint32_t rtail, pad3[31];  // ring slots filled
+  uint32_t done, pad4[31];   // tasks executed
+  uint32_t status, pad5[31];
+};
+struct EvParams {
+  const int32_t* pred_off;  // in-edges: pred[pred_off[v] .. pred_off[v+1])
+  const int32_t* pred;
+  int32_t n;
+  uint32_t ring_cap;
+  uint32_t* head;           // per task's completion event: its waiter list (or nil / triggered)
+  int32_t* pending;         // per task: events not yet triggered (+1 while registering)
+  uint32_t* node_task;      // waiter nodes
+  uint32_t* node_next;
+  uint32_t* ring;           // ready tasks
+  EvCtrl* ctrl;
+  ExecGraph G;
+  int64_t timeout_ns;
+};
+void launch_ev_transpose(const int32_t* row_ptr, const int32_t* col, int32_t n, const int32_t* pred_off,
+                         int32_t* cursor, int32_t* pred, cudaStream_t s);
+void launch_events(const EvParams& p, int blocks, cudaStream_t s);
+void preload_events();
 // stacked batches (rt_batch_create_stacked)
 void launch_tag_roots(const uint64_t* src, uint64_t* dst, int64_t n, const uint32_t* root_first, int32_t G,
                       cudaStream_t s);
