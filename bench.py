@@ -129,6 +129,63 @@ SERVE_SLOTS, SERVE_WORKERS, SERVE_MAX_BATCH = 512, 4, 64
 SERVE_EXEC_WARPS = 2  # serving kernel warps per SM: leaves room for 3 sweep blocks beside it
 
 
+METG_ITERS = [0, 16, 64, 256, 1024, 4096, 16384, 65536]
+METG_STEPS = 1000
+
+
+def run_metg(grt, torch):
+    """Task Bench's minimum effective task granularity, METG(50) (the paper's
+    overhead metric): stencil graphs of width 8 and 32, 1000 steps, whose task
+    bodies spin a chain of `iters` dependent integer multiply-adds on one lane.
+    Efficiency = (steps x body time) / run time, the body time per iteration
+    calibrated from the two largest counts; granularity = run time per step
+    (per task on its lane); METG(50) = the granularity where efficiency
+    crosses 1/2, for the compiled and the event-based executor."""
+    res = {"iters": METG_ITERS, "steps": METG_STEPS,
+           "body": "SPIN: a chain of `iters` dependent mad.lo.u32 on one lane per task",
+           "calibration": "each executor's body time per iteration is its own slope between the two largest "
+                          "counts; the event-based one's is about 2x the compiled one's because its ring tickets "
+                          "bind several ready tasks of a step to one warp, which runs their bodies one after "
+                          "another: that is counted as body time here, so METG(50) compares per-step overheads"}
+    for width in (8, 32):
+        tr = tg.taskbench(width, METG_STEPS, "stencil", seed=0)
+        for kind in ("compiled", "events"):
+            walls = []
+            for it in METG_ITERS:
+                out = torch.zeros(tr.n, dtype=torch.int32, device="cuda")
+                g = grt.Graph(2, tr.dom_lo, tr.dom_hi, body=grt.RT_BODY_SPIN, spin_iters=it, out=out,
+                              flags=grt.RT_GRAPH_PROFILE)
+                g.launch_trace(tr)
+                g.analyze()
+                runs = []
+                for _ in range(3):
+                    if kind == "compiled":
+                        g.execute()
+                        g.sync()
+                        runs.append(g.stats()["ms_exec_kernel"])
+                    else:
+                        runs.append(g.execute_events())
+                walls.append(float(np.median(runs)))
+                g.close()
+            c = (walls[-1] - walls[-2]) / (METG_STEPS * (METG_ITERS[-1] - METG_ITERS[-2]))  # ms per iteration
+            eff = [METG_STEPS * it * c / w for it, w in zip(METG_ITERS, walls)]
+            gran = [1e3 * w / METG_STEPS for w in walls]  # us per step = per task on its lane
+            metg = None
+            for k in range(1, len(eff)):
+                if eff[k - 1] < 0.5 <= eff[k]:
+                    t = (0.5 - eff[k - 1]) / (eff[k] - eff[k - 1])
+                    metg = float(np.exp(np.log(gran[k - 1]) + t * (np.log(gran[k]) - np.log(gran[k - 1]))))
+                    break
+            res[f"width{width}_{kind}"] = {"ms_per_run": [round(w, 3) for w in walls],
+                                          "efficiency": [round(e, 3) for e in eff],
+                                          "granularity_us": [round(x, 3) for x in gran],
+                                          "ns_per_iteration": round(c * 1e6, 3), "metg50_us": metg}
+    for width in (8, 32):
+        a, b = res[f"width{width}_events"]["metg50_us"], res[f"width{width}_compiled"]["metg50_us"]
+        res[f"width{width}_metg_ratio_events_over_compiled"] = round(a / b, 2) if a and b else None
+    return res
+
+
 def stacked_batch(traces, max_batch, band=1024):
     """Requests as the server analyses a batch of them: request j's rectangles
     move j bands along the last dimension of a domain max_batch bands long."""
@@ -505,6 +562,9 @@ def run_ours(args):
     batched = None
     if world == 1 and not args.no_batched:
         batched = run_batched(grt, torch, flush, max(1, min(args.steps, 3)))
+    metg = None
+    if world == 1 and not args.no_metg:
+        metg = run_metg(grt, torch)
     served = None
     if world == 1 and not args.no_served:
         served = run_served(grt)
@@ -625,7 +685,7 @@ def run_ours(args):
                 "spin_bodies": spin, "event_executor": events,
                 "cpu_baseline": cpu, "clocks": clk,
                 "gpu_launches": launches,
-                "batched": batched, "served": served,
+                "batched": batched, "served": served, "metg": metg,
                 "wall_s_timed": wall,
                 "phases_ms_per_graph": [{k: round(v, 4) for k, v in a.items()} for a in avg]}
         print(json.dumps(line), flush=True)
@@ -647,6 +707,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--no-metg", action="store_true")
     ap.add_argument("--graph-steps", type=int, default=STEPS, help="profiling only: fewer steps per graph")
     ap.add_argument("--patterns", default=",".join(tg.PATTERNS), help="profiling only: subset of patterns")
     ap.add_argument("--case", default=None, choices=["served-batch"],

@@ -6,6 +6,17 @@
 namespace grt {
 namespace {
 
+// The SPIN body: `iters` steps of the 32-bit LCG x <- a x + c (a = 1664525,
+// c = 1013904223) from x = the task's id: a chain of `iters` dependent integer
+// multiply-adds. Each step is one hand-written mad.lo.u32, so that the
+// compiler cannot fold the recurrence (it would in some kernels and not in
+// others): the body costs the same `iters` dependent operations in every
+// executor, which is what its granularity stands for.
+__device__ __forceinline__ uint32_t spin_body(uint32_t x, int iters) {
+  for (int k = 0; k < iters; ++k) asm volatile("mad.lo.u32 %0, %0, 1664525, 1013904223;" : "+r"(x));
+  return x;
+}
+
 __device__ __forceinline__ uint32_t cell_index(const ExecGraph& G, int64_t x, int64_t y) {
   return (uint32_t)((y - G.dom_lo[1]) * G.ext[0] + (x - G.dom_lo[0]));
 }
@@ -58,17 +69,13 @@ template <bool FENCE>
 __device__ __forceinline__ void run_body(const ExecGraph& G, int j) {
   if (!FENCE) {
     if (G.body == RT_BODY_SPIN) {
-      uint32_t x = (uint32_t)j;
-      for (int k = 0; k < G.spin_iters; ++k) x = x * 1664525u + 1013904223u;
-      G.out[j] = (int32_t)x;
+      G.out[j] = (int32_t)spin_body((uint32_t)j, G.spin_iters);
     }
     return;
   }
   switch (G.body) {
     case RT_BODY_SPIN: {
-      uint32_t x = (uint32_t)j;
-      for (int k = 0; k < G.spin_iters; ++k) x = x * 1664525u + 1013904223u;
-      G.out[j] = (int32_t)x;
+      G.out[j] = (int32_t)spin_body((uint32_t)j, G.spin_iters);
       break;
     }
     case RT_BODY_COUNTER: {

@@ -16,7 +16,8 @@
 // already or pushes a waiter node onto the event's list (an atomic push that
 // fails once the event has triggered). A task's pending count starts at 1 (a
 // guard released when its registration ends), so it cannot fire before it is
-// fully registered. Then warps take ready tasks from a ring, run the body,
+// fully registered. Then warps take ready tasks from a ring (each lane claims
+// the next ticket and waits for its slot), run the body,
 // trigger the event (an atomic exchange that returns the waiter list) and
 // walk the list, decrementing each waiter's pending count. Per edge that is
 // a node allocation, a pending increment, a list push and a pending decrement
@@ -154,7 +155,11 @@ __global__ void __launch_bounds__(256) k_events(EvParams p) {
     idle_since = 0;
     if (item != kFree) {
       fence_acq_rel_gpu();  // the predecessors' effects before the body
-      run_body<true>(p.G, (int)item);
+      if (p.G.body == RT_BODY_SPIN) {
+        p.G.out[item] = (int32_t)spin_body(item, p.G.spin_iters);
+      } else {
+        run_body<true>(p.G, (int)item);
+      }
       fence_acq_rel_gpu();  // the body's effects before the trigger
       // TASK_DONE: trigger the event and notify its waiters
       uint32_t x = atomicExch(p.head + item, kTrig);

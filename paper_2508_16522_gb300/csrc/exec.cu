@@ -223,9 +223,7 @@ __global__ void __launch_bounds__(256, 1) k_exec(ExecParams p) {
       if (TICKETS) p.tickets[2 * (int64_t)v] = (int32_t)atomicAdd(&ctrl->ticket, 1u);
       if (SINGLE && !FENCE) {
         if (body0 == RT_BODY_SPIN) {  // the one graph's fields live in registers
-          uint32_t x = (uint32_t)v;
-          for (int k = 0; k < spin0; ++k) x = x * 1664525u + 1013904223u;
-          out0[v] = (int32_t)x;
+          out0[v] = (int32_t)spin_body((uint32_t)v, spin0);
         }
       } else {
         const ExecGraph& G = p.graphs[g];

@@ -18,6 +18,7 @@
 // slots as the admitted graphs have tasks, so producers do not wait on
 // consumers. All waits are bounded; a stall longer than the timeout while
 // graphs are admitted ends the kernel with status TIMEOUT.
+#include "bodies.cuh"
 #include "grt_internal.cuh"
 
 namespace grt {
@@ -271,9 +272,7 @@ __global__ void __launch_bounds__(256, 1) k_serve(ServeParams p) {
     if (has) {
       // (no counter re-arm: every served request is analysed afresh)
       if (S.body == RT_BODY_SPIN && S.out) {
-        uint32_t x = (uint32_t)(v - S.base);  // the task's id within its request
-        for (int k = 0; k < S.spin_iters; ++k) x = x * 1664525u + 1013904223u;
-        S.out[v] = (int32_t)x;
+        S.out[v] = (int32_t)spin_body((uint32_t)(v - S.base), S.spin_iters);  // id within its request
         wrote = true;
       }
     }
