@@ -584,7 +584,7 @@ def run_ours(args):
     # body), execution only: the body adds a chain of 256 dependent multiply-adds
     # to every wavefront step
     spin = events = None
-    if world == 1:
+    if world == 1 and not args.no_extras:
         spin_ms = []
         for t, tl, st_ in zip(traces, tiles, streams):
             out = torch.zeros(t.n, dtype=torch.int32, device="cuda")
@@ -708,6 +708,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-metg", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the SPIN-body and event-executor comparisons")
     ap.add_argument("--graph-steps", type=int, default=STEPS, help="profiling only: fewer steps per graph")
     ap.add_argument("--patterns", default=",".join(tg.PATTERNS), help="profiling only: subset of patterns")
     ap.add_argument("--case", default=None, choices=["served-batch"],
