@@ -186,6 +186,33 @@ def run_metg(grt, torch):
     return res
 
 
+def run_async_nodes(grt, torch):
+    """Tasks whose bodies are whole kernels (Section 4.3): the same Task Bench
+    stencil DAG (100 steps, width 8 and 32) with one 128-thread kernel per task,
+    run lifted (the host launches a task once it has polled its predecessors'
+    events), with async edges (every launch enqueued up front, predicated on
+    events) and as one CUDA graph; the persistent executor runs the same DAG
+    with its bodies in place, for context."""
+    res = {"steps": 100, "threads_per_task_kernel": 128}
+    for width in (8, 32):
+        tr = tg.taskbench(width, 100, "stencil", seed=0)
+        out = torch.zeros(tr.n, dtype=torch.int32, device="cuda")
+        g = grt.Graph(2, tr.dom_lo, tr.dom_hi, body=grt.RT_BODY_SPIN, spin_iters=0, out=out,
+                      flags=grt.RT_GRAPH_PROFILE)
+        g.launch_trace(tr)
+        g.analyze()
+        for iters in (0, 4096):
+            row = {}
+            for mode in ("lifted", "async", "graph"):
+                g.execute_kernels(mode, iters=iters, threads=128)  # warm-up (builds the CUDA graph)
+                row[mode + "_ms"] = round(float(np.median([g.execute_kernels(mode, iters=iters, threads=128)
+                                                           for _ in range(3)])), 3)
+            row["us_per_task"] = {m: round(1e3 * row[m + "_ms"] / tr.n, 3) for m in ("lifted", "async", "graph")}
+            res[f"width{width}_iters{iters}"] = row
+        g.close()
+    return res
+
+
 def stacked_batch(traces, max_batch, band=1024):
     """Requests as the server analyses a batch of them: request j's rectangles
     move j bands along the last dimension of a domain max_batch bands long."""
@@ -565,6 +592,9 @@ def run_ours(args):
     metg = None
     if world == 1 and not args.no_metg:
         metg = run_metg(grt, torch)
+    async_nodes = None
+    if world == 1 and not args.no_extras:
+        async_nodes = run_async_nodes(grt, torch)
     served = None
     if world == 1 and not args.no_served:
         served = run_served(grt)
@@ -685,7 +715,7 @@ def run_ours(args):
                 "spin_bodies": spin, "event_executor": events,
                 "cpu_baseline": cpu, "clocks": clk,
                 "gpu_launches": launches,
-                "batched": batched, "served": served, "metg": metg,
+                "batched": batched, "served": served, "metg": metg, "async_nodes": async_nodes,
                 "wall_s_timed": wall,
                 "phases_ms_per_graph": [{k: round(v, 4) for k, v in a.items()} for a in avg]}
         print(json.dumps(line), flush=True)

@@ -201,6 +201,21 @@ rt_status rt_replay(rt_graph_t g, int32_t times);
  * timeout_ns), RT_ERR_OOM, RT_ERR_CUDA. */
 rt_status rt_execute_events(rt_graph_t g, float* ms_kernel);
 
+/* Runs the analysed graph with every task as its own GPU kernel (Section
+ * 4.3, optimisations for accelerators): one block of `threads` threads
+ * (32..1024), each running `iters` dependent FMAs, after which the task writes
+ * out[v] = 1 + the largest out[] of its predecessors (its depth, right only if
+ * every predecessor finished first). mode 0 = lifted: the host launches a task
+ * once it has seen, by polling, its predecessors' completion events; 1 = async
+ * edges: every kernel enqueued up front on a pool of streams, predicated on its
+ * predecessors' events; 2 = a CUDA graph of kernel nodes with the DAG's edges,
+ * instantiated once per (iters, threads) and relaunched. Needs `out` (one
+ * int32 per task), at most 131072 tasks. Synchronous; *ms (may be NULL)
+ * receives the host wall time of the run. Errors: RT_ERR_STATE, RT_ERR_INVALID,
+ * RT_ERR_TIMEOUT (mode 0 saw no completion for timeout_ns, default 10 s),
+ * RT_ERR_CUDA. */
+rt_status rt_execute_kernels(rt_graph_t g, int32_t mode, int32_t iters, int32_t threads, float* ms);
+
 /* Launch shape of this graph's executor runs (0 = library default): number of
  * persistent blocks, warps per block (1..8), how many published ring slots a
  * warp claims at once (1..32) and how many newly ready successors a warp keeps

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cstdarg>
 #include <mutex>
 #include <cstdio>
@@ -134,6 +135,15 @@ struct rt_graph {
   // the event-based executor (rt_execute_events): in-edges, events, waiter nodes
   DevBuf ev_pred_off, ev_pred, ev_head, ev_pending, ev_nodes, ev_ring, ev_ctrl;
   bool ev_preds = false;  // in-edges built for the current analysis
+  // rt_execute_kernels: the DAG on the host, events and streams, the CUDA graph
+  std::vector<int32_t> kh_rp, kh_col, kh_poff, kh_pred;
+  bool kh_valid = false;
+  std::vector<cudaEvent_t> kevents;
+  std::vector<cudaStream_t> kstreams;
+  cudaGraph_t kg = nullptr;
+  cudaGraphExec_t kg_exec = nullptr;
+  int32_t kg_iters = -1, kg_threads = -1;
+  DevBuf ksink;
   // execution
   DevBuf ring, ctrl, gtable, done_g, tickets;
   uint32_t* hpin = nullptr;  // pinned readback area (64 words)
@@ -175,6 +185,14 @@ void drop_replay_graph(rt_graph* g) {
   if (g->replay_exec) cudaGraphExecDestroy(g->replay_exec);
   g->replay_exec = nullptr;
   g->replay_times = 0;
+}
+
+void drop_kernel_graph(rt_graph* g) {
+  if (g->kg_exec) cudaGraphExecDestroy(g->kg_exec);
+  if (g->kg) cudaGraphDestroy(g->kg);
+  g->kg_exec = nullptr;
+  g->kg = nullptr;
+  g->kg_iters = g->kg_threads = -1;
 }
 
 rt_status check_desc(const rt_graph_desc* d, AnalysisDims* out, int64_t* ncells) {
@@ -278,6 +296,13 @@ rt_status rt_graph_destroy(rt_graph_t g) {
   if (!g) return RT_OK;
   if (g->ev_ok || g->ring.p || g->req_off.p) cudaStreamSynchronize(g->s);
   drop_replay_graph(g);
+  drop_kernel_graph(g);
+  for (cudaStream_t st : g->kstreams) {
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  }
+  for (cudaEvent_t e : g->kevents) cudaEventDestroy(e);
+  g->ksink.release(g->s);
   DevBuf* bufs[] = {&g->req_off, &g->lo, &g->hi, &g->priv, &g->pred_off, &g->pred, &g->body_arg,
                     &g->err, &g->rect_task, &g->cnt, &g->keys, &g->keys_alt, &g->pay, &g->pay_alt,
                     &g->seg_b, &g->seg_e, &g->pairs, &g->pairs_alt, &g->flags, &g->upos, &g->col,
@@ -670,6 +695,8 @@ extern "C" rt_status rt_analyze(rt_graph_t g) {
   CKR(ensure_pinned(g));
   drop_replay_graph(g);
   g->ev_preds = false;
+  g->kh_valid = false;
+  drop_kernel_graph(g);
   if (g->n > 0) CKR(run_analysis(g));
   else g->n_edges = g->n_roots = g->n_entries = g->n_pairs = 0;
   g->analyzed = true;
@@ -695,7 +722,9 @@ extern "C" rt_status rt_get_csr(rt_graph_t g, const int32_t** row_ptr, const int
 // ---------------------------------------------------------------------------
 namespace {
 
-constexpr int kStatusWord = 40;     // hpin word receiving the executor status
+constexpr int kStatusWord = 40;
+constexpr int32_t kMaxKernelTasks = 1 << 17;  // rt_execute_kernels: one event per task
+constexpr int kKernelStreams = 16;     // hpin word receiving the executor status
 constexpr int kCountersByte = 512;  // hpin byte offset of the executor's diagnostic counters
 
 rt_status prepare_run(rt_graph* g, int32_t replays, ExecParams* out, int64_t* ring_clear) {
@@ -845,6 +874,160 @@ rt_status rt_execute(rt_graph_t g) { return start_run(g, 1); }
 
 rt_status rt_replay(rt_graph_t g, int32_t times) { return start_run(g, times); }
 
+}  // extern "C"
+
+namespace grt {
+// The analysed graph's in-edges (each task's preconditions, as the application
+// would state them at launch): pred[pred_off[v] .. pred_off[v+1]), built once
+// per analysis on the device.
+rt_status ensure_in_edges(rt_graph* g) {
+  if (g->ev_preds) return RT_OK;
+  cudaStream_t s = g->s;
+  const int32_t n = g->n;
+  const int64_t E = g->n_edges;
+  CKR(g->ev_pred_off.reserve((size_t)(n + 1) * 4, s));
+  CKR(g->ev_pred.reserve((size_t)std::max<int64_t>(E, 1) * 4, s));
+  CKR(g->ev_pending.reserve((size_t)std::max<int32_t>(n, 1) * 4, s));
+  CKR(reserve_ws(g, scan_ws_elems<uint32_t>(n + 1) * 4));
+  CK(cudaMemcpyAsync(g->ev_pred_off.p, g->indeg.p, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+  scan_exclusive<uint32_t>(g->ev_pred_off.as<uint32_t>(), g->ev_pred_off.as<uint32_t>(), n, g->ws.as<uint32_t>(), s);
+  CK(cudaMemsetAsync(g->ev_pending.p, 0, (size_t)n * 4, s));  // cursors for the transpose
+  launch_ev_transpose(g->row_ptr.as<int32_t>(), g->col.as<int32_t>(), n, g->ev_pred_off.as<int32_t>(),
+                      g->ev_pending.as<int32_t>(), g->ev_pred.as<int32_t>(), s);
+  g->ev_preds = true;
+  return RT_OK;
+}
+}  // namespace grt
+
+extern "C" {
+
+rt_status rt_execute_kernels(rt_graph_t g, int32_t mode, int32_t iters, int32_t threads, float* ms) {
+  if (!g) return fail(RT_ERR_INVALID, "graph is NULL");
+  if (!g->analyzed) return fail(RT_ERR_STATE, "graph not analyzed");
+  if (mode < 0 || mode > 2) return fail(RT_ERR_INVALID, "mode must be 0 (lifted), 1 (async edges) or 2 (CUDA graph)");
+  if (iters < 0 || threads < 32 || threads > 1024) return fail(RT_ERR_INVALID, "iters >= 0, threads in 32..1024");
+  if (g->n > kMaxKernelTasks) return fail(RT_ERR_INVALID, "at most %d tasks run as kernels", kMaxKernelTasks);
+  if (!g->desc.out || g->desc.out_elems < g->n) return fail(RT_ERR_INVALID, "needs `out` with one int32 per task");
+  if (ms) *ms = 0.f;
+  const int32_t n = g->n;
+  if (n == 0) return RT_OK;
+  CKR(ensure_device());
+  cudaStream_t s = g->s;
+  CKR(ensure_in_edges(g));
+  if (!g->kh_valid) {
+    g->kh_rp.resize((size_t)n + 1);
+    g->kh_col.resize((size_t)std::max<int64_t>(g->n_edges, 1));
+    g->kh_poff.resize((size_t)n + 1);
+    g->kh_pred.resize((size_t)std::max<int64_t>(g->n_edges, 1));
+    CK(cudaMemcpyAsync(g->kh_rp.data(), g->row_ptr.p, ((size_t)n + 1) * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(g->kh_col.data(), g->col.p, (size_t)g->n_edges * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(g->kh_poff.data(), g->ev_pred_off.p, ((size_t)n + 1) * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(g->kh_pred.data(), g->ev_pred.p, (size_t)g->n_edges * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    g->kh_valid = true;
+  }
+  while ((int32_t)g->kevents.size() < n) {
+    cudaEvent_t e;
+    CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    g->kevents.push_back(e);
+  }
+  while (g->kstreams.size() < (size_t)kKernelStreams) {
+    cudaStream_t st;
+    CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    g->kstreams.push_back(st);
+  }
+  CKR(g->ksink.reserve(4096, s));
+  int32_t* depth = (int32_t*)g->desc.out;
+  const int32_t* poff = g->ev_pred_off.as<int32_t>();
+  const int32_t* pred = g->ev_pred.as<int32_t>();
+  float* sink = g->ksink.as<float>();
+  if (mode == 2 && (!g->kg_exec || g->kg_iters != iters || g->kg_threads != threads)) {
+    // one kernel node per task, its dependencies the nodes of its predecessors
+    drop_kernel_graph(g);
+    CK(cudaGraphCreate(&g->kg, 0));
+    std::vector<cudaGraphNode_t> nodes((size_t)n);
+    std::vector<cudaGraphNode_t> deps;
+    for (int32_t v = 0; v < n; ++v) {
+      deps.clear();
+      for (int32_t k = g->kh_poff[(size_t)v]; k < g->kh_poff[(size_t)v + 1]; ++k)
+        deps.push_back(nodes[(size_t)g->kh_pred[(size_t)k]]);
+      int32_t vv = v, it = iters;
+      void* args[] = {&vv, (void*)&poff, (void*)&pred, &depth, &sink, &it};
+      cudaKernelNodeParams kp{};
+      kp.func = task_kernel_fn();
+      kp.gridDim = dim3(1);
+      kp.blockDim = dim3((unsigned)threads);
+      kp.kernelParams = args;
+      CK(cudaGraphAddKernelNode(&nodes[(size_t)v], g->kg, deps.data(), deps.size(), &kp));
+    }
+    CK(cudaGraphInstantiate(&g->kg_exec, g->kg, 0));
+    g->kg_iters = iters;
+    g->kg_threads = threads;
+  }
+  // depths start at 0, so a task run before a predecessor shows
+  CK(cudaMemsetAsync(depth, 0, (size_t)n * 4, s));
+  CK(cudaStreamSynchronize(s));
+  const auto t0 = std::chrono::steady_clock::now();
+  if (mode == 2) {
+    count_launch(n);
+    CK(cudaGraphLaunch(g->kg_exec, s));
+    CK(cudaStreamSynchronize(s));
+  } else if (mode == 1) {
+    // async edges: every launch enqueued now, each predicated on its
+    // predecessors' events (program order is a topological order)
+    for (int32_t v = 0; v < n; ++v) {
+      cudaStream_t st = g->kstreams[(size_t)v % kKernelStreams];
+      for (int32_t k = g->kh_poff[(size_t)v]; k < g->kh_poff[(size_t)v + 1]; ++k)
+        CK(cudaStreamWaitEvent(st, g->kevents[(size_t)g->kh_pred[(size_t)k]], 0));
+      launch_task_kernel(v, poff, pred, depth, sink, iters, threads, st);
+      CK(cudaEventRecord(g->kevents[(size_t)v], st));
+    }
+    for (cudaStream_t st : g->kstreams) CK(cudaStreamSynchronize(st));
+  } else {
+    // lifted: the host launches a task once it has seen, by polling, that the
+    // events of all its predecessors have completed
+    std::vector<int32_t> pending((size_t)n);
+    std::vector<int32_t> ready, flight;
+    for (int32_t v = 0; v < n; ++v) {
+      pending[(size_t)v] = g->kh_poff[(size_t)v + 1] - g->kh_poff[(size_t)v];
+      if (pending[(size_t)v] == 0) ready.push_back(v);
+    }
+    const int64_t limit = g->desc.timeout_ns > 0 ? g->desc.timeout_ns : 10000000000ll;
+    int32_t done = 0;
+    auto last = std::chrono::steady_clock::now();
+    while (done < n) {
+      for (int32_t v : ready) {
+        cudaStream_t st = g->kstreams[(size_t)v % kKernelStreams];
+        launch_task_kernel(v, poff, pred, depth, sink, iters, threads, st);
+        CK(cudaEventRecord(g->kevents[(size_t)v], st));
+        flight.push_back(v);
+      }
+      ready.clear();
+      for (size_t i = 0; i < flight.size();) {
+        const int32_t v = flight[i];
+        const cudaError_t q = cudaEventQuery(g->kevents[(size_t)v]);
+        if (q == cudaErrorNotReady) {
+          ++i;
+          continue;
+        }
+        if (q != cudaSuccess) return fail(RT_ERR_CUDA, "task kernel: %s", cudaGetErrorString(q));
+        flight[i] = flight.back();
+        flight.pop_back();
+        ++done;
+        last = std::chrono::steady_clock::now();
+        for (int32_t e = g->kh_rp[(size_t)v]; e < g->kh_rp[(size_t)v + 1]; ++e)
+          if (--pending[(size_t)g->kh_col[(size_t)e]] == 0) ready.push_back(g->kh_col[(size_t)e]);
+      }
+      if (std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now() - last).count() >
+          limit)
+        return fail(RT_ERR_TIMEOUT, "task kernels made no progress");
+    }
+  }
+  CK(cudaGetLastError());
+  if (ms) *ms = (float)std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return RT_OK;
+}
+
 rt_status rt_execute_events(rt_graph_t g, float* ms_kernel) {
   if (!g) return fail(RT_ERR_INVALID, "graph is NULL");
   if (!g->analyzed) return fail(RT_ERR_STATE, "graph not analyzed");
@@ -858,18 +1041,7 @@ rt_status rt_execute_events(rt_graph_t g, float* ms_kernel) {
   cudaStream_t s = g->s;
   const int32_t n = g->n;
   const int64_t E = g->n_edges;
-  if (!g->ev_preds) {  // the launches' preconditions, as the application would state them
-    CKR(g->ev_pred_off.reserve((size_t)(n + 1) * 4, s));
-    CKR(g->ev_pred.reserve((size_t)std::max<int64_t>(E, 1) * 4, s));
-    CKR(g->ev_pending.reserve((size_t)n * 4, s));
-    CKR(reserve_ws(g, scan_ws_elems<uint32_t>(n + 1) * 4));
-    CK(cudaMemcpyAsync(g->ev_pred_off.p, g->indeg.p, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
-    scan_exclusive<uint32_t>(g->ev_pred_off.as<uint32_t>(), g->ev_pred_off.as<uint32_t>(), n, g->ws.as<uint32_t>(), s);
-    CK(cudaMemsetAsync(g->ev_pending.p, 0, (size_t)n * 4, s));  // cursors for the transpose
-    launch_ev_transpose(g->row_ptr.as<int32_t>(), g->col.as<int32_t>(), n, g->ev_pred_off.as<int32_t>(),
-                        g->ev_pending.as<int32_t>(), g->ev_pred.as<int32_t>(), s);
-    g->ev_preds = true;
-  }
+  CKR(ensure_in_edges(g));
   const uint32_t ring_cap = (uint32_t)n + 64u;
   CKR(g->ev_head.reserve((size_t)n * 4, s));
   CKR(g->ev_pending.reserve((size_t)n * 4, s));

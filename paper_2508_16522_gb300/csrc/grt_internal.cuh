@@ -327,6 +327,11 @@ void launch_ev_transpose(const int32_t* row_ptr, const int32_t* col, int32_t n, 
                          int32_t* cursor, int32_t* pred, cudaStream_t s);
 void launch_events(const EvParams& p, int blocks, cudaStream_t s);
 void preload_events();
+// tasks as whole kernels (rt_execute_kernels)
+void* task_kernel_fn();
+void launch_task_kernel(int32_t v, const int32_t* pred_off, const int32_t* pred, int32_t* depth, float* sink,
+                        int32_t iters, int threads, cudaStream_t s);
+void preload_task_kernel();
 // stacked batches (rt_batch_create_stacked)
 void launch_tag_roots(const uint64_t* src, uint64_t* dst, int64_t n, const uint32_t* root_first, int32_t G,
                       cudaStream_t s);

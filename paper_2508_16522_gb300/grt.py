@@ -34,7 +34,7 @@ EXPORTS = ["rt_graph_create", "rt_graph_destroy", "rt_graph_clear", "rt_launch_b
            "rt_kernel_launches", "rt_execute_csr_static", "rt_microbench_atomics", "rt_now_ns",
            "rt_server_create", "rt_server_submit", "rt_server_poll", "rt_server_result", "rt_server_drain",
            "rt_server_stats", "rt_server_destroy", "rt_tune_tile", "rt_tune_exec", "rt_tune_batch",
-           "rt_batch_create_stacked", "rt_execute_events"]
+           "rt_batch_create_stacked", "rt_execute_events", "rt_execute_kernels"]
 
 
 class GrtError(RuntimeError):
@@ -145,6 +145,7 @@ def load(path: str = LIB_PATH):
         "rt_tune_exec": [P, ctypes.c_char_p, ctypes.POINTER(rt_exec_config)],
         "rt_batch_create_stacked": [P, P, i32, P, ctypes.POINTER(P)],
         "rt_execute_events": [P, ctypes.POINTER(ctypes.c_float)],
+        "rt_execute_kernels": [P, i32, i32, i32, ctypes.POINTER(ctypes.c_float)],
         "rt_tune_batch": [P, i32, ctypes.c_char_p, ctypes.POINTER(rt_exec_config)],
     }
     for name, args in sig.items():
@@ -351,6 +352,14 @@ class Graph:
 
     def replay(self, times: int):
         rt_replay(self.h, times)
+
+    KERNEL_MODES = {"lifted": 0, "async": 1, "graph": 2}
+
+    def execute_kernels(self, mode: str, iters: int = 0, threads: int = 128) -> float:
+        """Every task as its own kernel (mode: lifted, async or graph); wall ms."""
+        ms = ctypes.c_float()
+        _check(load().rt_execute_kernels(self.h, self.KERNEL_MODES[mode], iters, threads, ctypes.byref(ms)))
+        return ms.value
 
     def execute_events(self) -> float:
         """One run through the standard, event-based executor; its kernel ms."""
