@@ -8,8 +8,12 @@
 //  4. sweep (sweep.cu): one warp per tile walks the candidates in program
 //     order, keeps per-cell run state in shared memory and emits (src, dst)
 //     pairs deduplicated per task within the tile
+//     (tiles whose pairs overflowed the buffer are swept again, alone, into a
+//     larger one)
 //  5. radix sort of the 64-bit pair keys, unique, CSR by source: row counts
 //     and in-degrees by warp-aggregated atomics, row_ptr by a device scan
+//  6. countdown counters (the in-degrees) and the compacted root list; the
+//     executor's trigger records are packed from the CSR (exec.cu)
 //
 // The edge rule is the per-cell run reading of "infer the DAG from the data
 // usage of tasks" (Section 2.2, Section 5): a task's rectangles combine into

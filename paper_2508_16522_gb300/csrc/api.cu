@@ -3,7 +3,8 @@
 // Owns every library buffer, validates inputs, sequences the analysis and
 // execution kernels on the graph's stream, caches CUDA graphs for replays and
 // builds batches. Nothing here computes the method's results: all of that
-// runs in the kernels of analysis.cu, sweep.cu, primitives.cu and exec.cu.
+// runs in the kernels of analysis.cu, sweep.cu, primitives.cu, exec.cu,
+// static_exec.cu, events.cu, kernels.cu and serve.cu.
 #include <cuda_runtime.h>
 
 #include <algorithm>

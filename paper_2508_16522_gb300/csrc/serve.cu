@@ -1,10 +1,11 @@
 // serve.cu -- the device-resident serving executor.
 //
 // A persistent kernel that runs for the whole life of a server (rt_server_*).
-// Host worker threads analyse arriving requests on their own streams; each
-// analysed graph is written into a slot of a device table and *posted* through
-// a host-mapped mailbox. Idle warps of this kernel take posted activations,
-// seed the graph's roots, and from then on its tasks are executed exactly as in
+// Host worker threads analyse arriving requests in batches on their own
+// streams (server.cu); each request gets a slot of a device table, pointing
+// into its batch's graph, and is *posted* through a host-mapped mailbox. Idle
+// warps of this kernel take posted activations, seed the request's roots, and
+// from then on its tasks are executed exactly as in
 // the batch executor (countdown counters, one atomic decrement per edge, kept
 // successors, a ring for the rest), interleaved with every other admitted
 // graph: new requests join while others are running (continuous batching).

@@ -26,12 +26,24 @@
 // cells: a rectangle covering the whole tile costs one class, not tw x th
 // cells, and the predecessor sets are the same.
 //
-// Lanes split the cells of the task's rectangle; predecessors found by
-// several lanes are merged with match_any, and the survivors go through a
-// per-warp shared-memory hash set, so each (src, dst) pair leaves the tile once
-// per task. Pairs are appended to per-warp chunks of a global buffer (one
-// atomic per 512 pairs); unused chunk tails are filled with a sentinel key that
-// the later sort moves to the end.
+// A class grid larger than the 1024 cells a warp keeps is swept in strips of
+// class rows. Three ways to apply candidates (segment mode is chosen per tile,
+// the other two per window of candidates):
+//   * lane-parallel: small boxes whose overlaps chain at most 16 deep, one
+//     candidate per lane, overlapping ones ordered by conflict levels;
+//   * cell-parallel: the warp's lanes split the cells of one candidate's box;
+//   * segment mode (tiles whose candidates cover 8+ class cells each on
+//     average): each class row is kept as segments of equal run state, one
+//     lane per row of the box, so a candidate costs its rows' segments, not
+//     its cells.
+// Predecessors found by several lanes are merged with match_any, and the
+// survivors go through a per-warp shared-memory hash set, so each (src, dst)
+// pair leaves the tile once per task. Pairs are appended to per-warp chunks of
+// a global buffer (one atomic per chunk; a flush that does not fit continues
+// in fresh chunks, so only a warp's last chunk keeps holes, filled with a
+// sentinel key that the later sort moves to the end). A tile that drops pairs
+// past the buffer's end is flagged with its pair count, for a rerun of just the
+// flagged tiles.
 #include "grt_internal.cuh"
 
 namespace grt {
