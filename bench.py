@@ -213,6 +213,40 @@ def run_async_nodes(grt, torch):
     return res
 
 
+def run_stitched(grt, torch):
+    """Stitched replay (external pre/post-condition vertices, Section 4.1 and
+    Section 5): 20 replays of a 100-step Task Bench graph of width 1024 in one
+    persistent launch, once with a barrier between replays (rt_replay) and once
+    joined by the edges between two copies of the trace (rt_execute_stitched),
+    so that replay r + 1 starts where its own predecessors in replay r are
+    done. EMPTY bodies, the executor's default launch shape for both; times
+    include the counter reset and seeding."""
+    R = 20
+    res = {"replays": R, "steps_per_replay": 100, "width": 1024}
+    for pat in ("stencil", "random"):
+        T = tg.taskbench(1024, 100, pat, seed=0)
+        g = grt.Graph(2, T.dom_lo, T.dom_hi, flags=grt.RT_GRAPH_PROFILE)
+        g.launch_trace(T)
+        g.analyze()
+        bar = []
+        for _ in range(4):
+            g.replay(R)
+            g.sync()
+            bar.append(g.stats()["ms_execute"])
+        g.close()
+        g2 = grt.Graph(2, T.dom_lo, T.dom_hi, flags=grt.RT_GRAPH_PROFILE)
+        g2.launch_trace(tg.concat([T, T]))
+        g2.analyze()
+        ana = g2.stats()["ms_analyze"]
+        st = [g2.execute_stitched(R) for _ in range(4)]
+        g2.close()
+        b, s_ = float(np.median(bar[1:])), float(np.median(st[1:]))
+        res[pat] = {"barrier_ms": round(b, 3), "stitched_ms": round(s_, 3), "speedup": round(b / s_, 2),
+                    "barrier_tasks_per_s": R * T.n / (b * 1e-3), "stitched_tasks_per_s": R * T.n / (s_ * 1e-3),
+                    "ms_analyze_two_copies": round(ana, 3)}
+    return res
+
+
 def stacked_batch(traces, max_batch, band=1024):
     """Requests as the server analyses a batch of them: request j's rectangles
     move j bands along the last dimension of a domain max_batch bands long."""
@@ -592,9 +626,10 @@ def run_ours(args):
     metg = None
     if world == 1 and not args.no_metg:
         metg = run_metg(grt, torch)
-    async_nodes = None
+    async_nodes = stitched = None
     if world == 1 and not args.no_extras:
         async_nodes = run_async_nodes(grt, torch)
+        stitched = run_stitched(grt, torch)
     served = None
     if world == 1 and not args.no_served:
         served = run_served(grt)
@@ -715,7 +750,7 @@ def run_ours(args):
                 "spin_bodies": spin, "event_executor": events,
                 "cpu_baseline": cpu, "clocks": clk,
                 "gpu_launches": launches,
-                "batched": batched, "served": served, "metg": metg, "async_nodes": async_nodes,
+                "batched": batched, "served": served, "metg": metg, "async_nodes": async_nodes, "stitched": stitched,
                 "wall_s_timed": wall,
                 "phases_ms_per_graph": [{k: round(v, 4) for k, v in a.items()} for a in avg]}
         print(json.dumps(line), flush=True)

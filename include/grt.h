@@ -201,6 +201,32 @@ rt_status rt_replay(rt_graph_t g, int32_t times);
  * timeout_ns), RT_ERR_OOM, RT_ERR_CUDA. */
 rt_status rt_execute_events(rt_graph_t g, float* ms_kernel);
 
+/* Stitched replay (Section 4.1's external pre/post-condition vertices, which
+ * join a compiled graph to the work around it; Section 5 joins the graphs of a
+ * sharded trace with them). `g` holds one trace launched TWICE in a row (2n
+ * tasks, analysed; the second copy must repeat the first's rectangles, and
+ * any explicit predecessors shifted by n). Edges inside the first copy are
+ * the compiled graph; edges from the first copy to the second are the
+ * conditions that join replay r to replay r + 1. Runs `replays` replays of
+ * the trace in one persistent launch with no barrier between them: a task of
+ * replay r + 1 starts once its predecessors in replays r and r + 1 are done.
+ * Task (r, v) writes out[r * n + v] (SPIN: the SPIN value of v; CHECK: its
+ * output word, the state evolving as if the trace ran `replays` times in
+ * program order; `out` must hold replays * n int32 for those bodies); COUNTER
+ * bodies act on state as in rt_execute. With RT_GRAPH_TICKETS the start and
+ * end tickets of (r, v) are kept for rt_copy_stitched_tickets. Synchronous;
+ * *ms_kernel (may be NULL) receives the launch's time (counter init plus the
+ * executor). Errors: RT_ERR_STATE (not analyzed), RT_ERR_INVALID (odd task
+ * count, halves that differ in rectangles or internal edges, replays < 1,
+ * replays * n >= 2^31 - 16, missing `out`), RT_ERR_TIMEOUT (no progress for
+ * timeout_ns, default 2 s), RT_ERR_OOM, RT_ERR_CUDA. */
+rt_status rt_execute_stitched(rt_graph_t g, int32_t replays, float* ms_kernel);
+
+/* Copies the tickets of the last stitched run made with RT_GRAPH_TICKETS:
+ * int32[replays][n][2] (start, end), into host or device memory. Synchronous.
+ * RT_ERR_STATE if there is none. */
+rt_status rt_copy_stitched_tickets(rt_graph_t g, int32_t* out);
+
 /* Runs the analysed graph with every task as its own GPU kernel (Section
  * 4.3, optimisations for accelerators): one block of `threads` threads
  * (32..1024), each running `iters` dependent FMAs, after which the task writes

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(HERE, "_lib")
 SO = os.path.join(LIBDIR, "libgrt.so")
-SOURCES = ["primitives.cu", "analysis.cu", "sweep.cu", "exec.cu", "static_exec.cu", "microbench.cu", "serve.cu", "server.cu", "tune.cu", "events.cu", "kernels.cu", "api.cu"]
+SOURCES = ["primitives.cu", "analysis.cu", "sweep.cu", "exec.cu", "static_exec.cu", "microbench.cu", "serve.cu", "server.cu", "tune.cu", "events.cu", "kernels.cu", "stitch.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

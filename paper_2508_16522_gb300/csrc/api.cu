@@ -145,6 +145,9 @@ struct rt_graph {
   cudaGraphExec_t kg_exec = nullptr;
   int32_t kg_iters = -1, kg_threads = -1;
   DevBuf ksink;
+  // rt_execute_stitched: per-replay counters, ready ring, control, tickets
+  DevBuf st_count, st_ring, st_ctrl, st_tickets, st_err;
+  int32_t st_R = 0;  // replays of the last stitched run with tickets
   // execution
   DevBuf ring, ctrl, gtable, done_g, tickets;
   uint32_t* hpin = nullptr;  // pinned readback area (64 words)
@@ -1089,6 +1092,99 @@ rt_status rt_execute_events(rt_graph_t g, float* ms_kernel) {
   const uint32_t st = g->hpin[kStatusWord];
   if (st == (uint32_t)RT_ERR_TIMEOUT) return fail(RT_ERR_TIMEOUT, "event executor made no progress");
   if (st == (uint32_t)RT_ERR_OOM) return fail(RT_ERR_OOM, "event executor ring overflow");
+  return RT_OK;
+}
+
+rt_status rt_execute_stitched(rt_graph_t g, int32_t replays, float* ms_kernel) {
+  if (!g) return fail(RT_ERR_INVALID, "graph is NULL");
+  if (!g->analyzed) return fail(RT_ERR_STATE, "graph not analyzed");
+  if (ms_kernel) *ms_kernel = 0.f;
+  if (replays < 1) return fail(RT_ERR_INVALID, "replays must be positive (got %d)", replays);
+  if (g->n % 2 != 0)
+    return fail(RT_ERR_INVALID, "a stitched graph holds two copies of one trace (got %d tasks)", g->n);
+  const int32_t n = g->n / 2;
+  if (n == 0) return RT_OK;
+  const int64_t total = (int64_t)replays * n;
+  if (total > 0x7FFFFFF0ll) return fail(RT_ERR_INVALID, "replays x tasks = %lld (limit 2^31 - 16)", (long long)total);
+  const int body = g->desc.body;
+  if ((body == RT_BODY_SPIN || body == RT_BODY_CHECK) && (!g->desc.out || g->desc.out_elems < total))
+    return fail(RT_ERR_INVALID, "SPIN/CHECK bodies need `out` with one int32 per task and replay (%lld)",
+                (long long)total);
+  CKR(ensure_device());
+  CKR(ensure_pinned(g));
+  cudaStream_t s = g->s;
+  // the second copy must repeat the first
+  CKR(g->st_err.reserve(4, s));
+  CK(cudaMemsetAsync(g->st_err.p, 0, 4, s));
+  launch_stitch_check(g->req_off.as<int32_t>(), g->lo.as<int64_t>(), g->hi.as<int64_t>(), g->priv.as<uint8_t>(),
+                      g->dims.ndim, g->row_ptr.as<int32_t>(), g->col.as<int32_t>(), n, g->st_err.as<uint32_t>(), s);
+  CK(cudaMemcpyAsync(g->hpin + kStatusWord, g->st_err.p, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  if (g->hpin[kStatusWord] & 1u)
+    return fail(RT_ERR_INVALID, "the graph's second half does not repeat the first one's rectangles");
+  if (g->hpin[kStatusWord] & 2u)
+    return fail(RT_ERR_INVALID, "the graph's two halves have different internal edges");
+  const bool tickets = (g->desc.flags & RT_GRAPH_TICKETS) != 0;
+  CKR(g->st_count.reserve((size_t)total * 4, s));
+  CKR(g->st_ring.reserve((size_t)total * 8, s));
+  CKR(g->st_ctrl.reserve(sizeof(ExecCtrl), s));
+  if (tickets) CKR(g->st_tickets.reserve((size_t)total * 8, s));
+  StitchParams p{};
+  p.adj = g->adj.as<int4>();
+  p.col = g->col.as<int32_t>();
+  p.count = g->st_count.as<int32_t>();
+  p.ring = g->st_ring.as<uint64_t>();
+  p.ring_cap = (uint32_t)total;
+  p.n = n;
+  p.R = replays;
+  p.claim = std::min(g->cfg_claim > 0 ? g->cfg_claim : 8, 32);
+  p.keep = std::min(g->cfg_keep > 0 ? g->cfg_keep : 16, 64);  // the kernel keeps at most 64 per warp
+  p.total = total;
+  p.ctrl = g->st_ctrl.as<ExecCtrl>();
+  p.tickets = tickets ? g->st_tickets.as<int32_t>() : nullptr;
+  ExecGraph& G = p.G;
+  G.n_tasks = n;
+  G.body = body;
+  G.spin_iters = g->desc.spin_iters;
+  G.ndim = g->dims.ndim;
+  G.state = (int32_t*)g->desc.state;
+  G.out = (int32_t*)g->desc.out;
+  G.body_arg = g->body_arg.as<int32_t>();
+  G.req_off = g->req_off.as<int32_t>();
+  G.lo = g->lo.as<int64_t>();
+  G.hi = g->hi.as<int64_t>();
+  G.priv = g->priv.as<uint8_t>();
+  G.dom_lo[0] = g->dims.dom_lo[0];
+  G.dom_lo[1] = g->dims.dom_lo[1];
+  G.ext[0] = g->dims.ext[0];
+  G.ext[1] = g->dims.ext[1];
+  p.timeout_ns = g->desc.timeout_ns > 0 ? g->desc.timeout_ns : 2000000000ll;
+  const int warps = std::min(g->cfg_warps > 0 ? g->cfg_warps : 2, 8);
+  const int blocks = g->cfg_blocks > 0 ? g->cfg_blocks : g_dev.num_sms;
+  CK(cudaMemsetAsync(p.ring, 0xFF, (size_t)total * 8, s));
+  CK(cudaMemsetAsync(p.ctrl, 0, sizeof(ExecCtrl), s));
+  CKR(graph_events(g));
+  CK(cudaEventRecord(g->ev[EV_E0], s));
+  launch_stitch(p, g->indeg.as<int32_t>(), g->root_items.as<uint64_t>(), g->rootpos.as<uint32_t>(), blocks, warps,
+                tickets, body == RT_BODY_CHECK || body == RT_BODY_COUNTER, s);
+  CK(cudaEventRecord(g->ev[EV_E1], s));
+  CK(cudaMemcpyAsync(g->hpin + kStatusWord, &p.ctrl->status, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  if (ms_kernel) cudaEventElapsedTime(ms_kernel, g->ev[EV_E0], g->ev[EV_E1]);
+  g->st_R = tickets ? replays : 0;
+  const uint32_t st = g->hpin[kStatusWord];
+  if (st == (uint32_t)RT_ERR_TIMEOUT) return fail(RT_ERR_TIMEOUT, "stitched replay made no progress");
+  if (st == (uint32_t)RT_ERR_OOM) return fail(RT_ERR_OOM, "stitched replay ring overflow");
+  return RT_OK;
+}
+
+rt_status rt_copy_stitched_tickets(rt_graph_t g, int32_t* out) {
+  if (!g) return fail(RT_ERR_INVALID, "graph is NULL");
+  if (!out) return fail(RT_ERR_INVALID, "out is NULL");
+  if (g->st_R == 0) return fail(RT_ERR_STATE, "no stitched run with RT_GRAPH_TICKETS yet");
+  CK(cudaMemcpy(out, g->st_tickets.p, (size_t)g->st_R * (g->n / 2) * 8, cudaMemcpyDefault));
   return RT_OK;
 }
 

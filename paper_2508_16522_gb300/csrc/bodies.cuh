@@ -1,5 +1,6 @@
-// bodies.cuh -- the task bodies, shared by the compiled executor (exec.cu)
-// and the event-based one (events.cu).
+// bodies.cuh -- the task bodies, shared by the compiled executor (exec.cu),
+// the event-based one (events.cu), the serving kernel (serve.cu) and stitched
+// replay (stitch.cu).
 #pragma once
 #include "grt_internal.cuh"
 
@@ -22,7 +23,8 @@ __device__ __forceinline__ uint32_t cell_index(const ExecGraph& G, int64_t x, in
 }
 
 // CHECK body (order-sensitive): see grt.h. Lane-serial; meant for test sizes.
-__device__ void check_body(const ExecGraph& G, int j) {
+// Applies task j's accesses to the state and returns its output word.
+__device__ uint32_t check_apply(const ExecGraph& G, int j) {
   const int r0 = G.req_off[j], r1 = G.req_off[j + 1];
   const int D = G.ndim;
   uint32_t acc = 0;
@@ -60,8 +62,10 @@ __device__ void check_body(const ExecGraph& G, int j) {
     }
     if (pass == 0) acc = mix32((uint32_t)j, sum);
   }
-  G.out[j] = (int32_t)acc;
+  return acc;
 }
+
+__device__ __forceinline__ void check_body(const ExecGraph& G, int j) { G.out[j] = (int32_t)check_apply(G, j); }
 
 // FENCE = false: the launch only has bodies that read nothing written by
 // other tasks (EMPTY, SPIN), so the order-sensitive bodies are compiled out.

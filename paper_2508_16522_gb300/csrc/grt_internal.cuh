@@ -327,6 +327,26 @@ void launch_ev_transpose(const int32_t* row_ptr, const int32_t* col, int32_t n, 
                          int32_t* cursor, int32_t* pred, cudaStream_t s);
 void launch_events(const EvParams& p, int blocks, cudaStream_t s);
 void preload_events();
+// stitched replay (rt_execute_stitched): R replays of one trace, joined by
+// the edges from one copy of it to the next
+struct StitchParams {
+  const int4* adj;     // trigger records of the two-copy graph (the first copy's are used)
+  const int32_t* col;  // its CSR targets (>= n: task target - n of the next replay)
+  int32_t* count;      // [R][n] countdown counters
+  uint64_t* ring;      // ready items (replay << 32 | task), R * n slots
+  uint32_t ring_cap;
+  int32_t n, R;        // tasks per replay, replays
+  int32_t claim, keep;
+  int64_t total;       // R * n
+  ExecCtrl* ctrl;
+  int32_t* tickets;    // [R][n][2] start / end tickets, or null
+  ExecGraph G;         // bodies of the first copy; out indexed by replay * n + task
+  int64_t timeout_ns;
+};
+void launch_stitch_check(const int32_t* req_off, const int64_t* lo, const int64_t* hi, const uint8_t* priv, int D,
+                         const int32_t* row_ptr, const int32_t* col, int32_t n, uint32_t* err, cudaStream_t s);
+void launch_stitch(const StitchParams& p, const int32_t* indeg, const uint64_t* root_items, const uint32_t* rootpos,
+                   int blocks, int warps, bool tickets, bool fence, cudaStream_t s);
 // tasks as whole kernels (rt_execute_kernels)
 void* task_kernel_fn();
 void launch_task_kernel(int32_t v, const int32_t* pred_off, const int32_t* pred, int32_t* depth, float* sink,

@@ -34,7 +34,8 @@ EXPORTS = ["rt_graph_create", "rt_graph_destroy", "rt_graph_clear", "rt_launch_b
            "rt_kernel_launches", "rt_execute_csr_static", "rt_microbench_atomics", "rt_now_ns",
            "rt_server_create", "rt_server_submit", "rt_server_poll", "rt_server_result", "rt_server_drain",
            "rt_server_stats", "rt_server_destroy", "rt_tune_tile", "rt_tune_exec", "rt_tune_batch",
-           "rt_batch_create_stacked", "rt_execute_events", "rt_execute_kernels"]
+           "rt_batch_create_stacked", "rt_execute_events", "rt_execute_kernels",
+           "rt_execute_stitched", "rt_copy_stitched_tickets"]
 
 
 class GrtError(RuntimeError):
@@ -146,6 +147,8 @@ def load(path: str = LIB_PATH):
         "rt_batch_create_stacked": [P, P, i32, P, ctypes.POINTER(P)],
         "rt_execute_events": [P, ctypes.POINTER(ctypes.c_float)],
         "rt_execute_kernels": [P, i32, i32, i32, ctypes.POINTER(ctypes.c_float)],
+        "rt_execute_stitched": [P, i32, ctypes.POINTER(ctypes.c_float)],
+        "rt_copy_stitched_tickets": [P, P],
         "rt_tune_batch": [P, i32, ctypes.c_char_p, ctypes.POINTER(rt_exec_config)],
     }
     for name, args in sig.items():
@@ -360,6 +363,20 @@ class Graph:
         ms = ctypes.c_float()
         _check(load().rt_execute_kernels(self.h, self.KERNEL_MODES[mode], iters, threads, ctypes.byref(ms)))
         return ms.value
+
+    def execute_stitched(self, replays: int) -> float:
+        """`replays` replays of the trace this graph holds twice, joined by the
+        edges between its two copies, in one launch; its time in ms."""
+        ms = ctypes.c_float()
+        _check(load().rt_execute_stitched(self.h, replays, ctypes.byref(ms)))
+        return ms.value
+
+    def stitched_tickets(self, replays: int):
+        """(start, end) tickets of the last stitched run: int32[replays, n, 2]."""
+        n = self.stats()["n_tasks"] // 2
+        t = np.empty((replays, n, 2), np.int32)
+        _check(load().rt_copy_stitched_tickets(self.h, t.ctypes.data))
+        return t
 
     def execute_events(self) -> float:
         """One run through the standard, event-based executor; its kernel ms."""
