@@ -44,6 +44,9 @@
 // sentinel key that the later sort moves to the end). A tile that drops pairs
 // past the buffer's end is flagged with its pair count, for a rerun of just the
 // flagged tiles.
+#include <map>
+#include <mutex>
+
 #include "grt_internal.cuh"
 
 namespace grt {
@@ -841,7 +844,22 @@ void launch_sweep(const uint64_t* payload, const uint32_t* seg_begin, const uint
                   AnalysisDims d, SweepOut o, int blocks, cudaStream_t s) {
   const int warps = sweep_warps_per_block(d.tw, d.th);
   const size_t bytes = sweep_smem_bytes(d.tw, d.th, warps);
-  cudaFuncSetAttribute(k_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  // The shared-memory limit is one attribute of the kernel per device, shared
+  // by every thread of the process. It only ever grows, under a lock, so an
+  // analysis on another thread with a smaller tile never lowers it below what
+  // a launch in flight here needs.
+  {
+    static std::mutex mu;
+    static std::map<int, size_t> limit;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    size_t& cur = limit[dev];
+    if (bytes > cur) {
+      cudaFuncSetAttribute(k_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      cur = bytes;
+    }
+  }
   count_launch();
   k_sweep<<<blocks, warps * 32, bytes, s>>>(payload, seg_begin, seg_end, d, o);
 }

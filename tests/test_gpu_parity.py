@@ -324,3 +324,37 @@ def test_microbench_reports_plausible_rooflines():
     assert 50 < mb["dep_l2_load_ns"] < 20000
     for k in ("scatter_atomic_gops", "scatter_red_gops", "contended_atomic_gops", "contended_warp_agg_gops"):
         assert 0.01 < mb[k] < 10000, (k, mb[k])
+
+
+def test_concurrent_analyses_with_different_tiles():
+    """Graphs analysed at the same time from several host threads, each on its
+    own stream with its own tile (so its own shared-memory need), give the
+    oracle's CSR: per-kernel launch limits set by one thread must not fail
+    another's launch."""
+    import threading
+    import torch
+    trs = [tg.random_rects(grid=(256, 192), n=3000, rects=(1, 4), side=(1, 40), seed=s) for s in range(4)]
+    refs = [oracle_csr(t) for t in trs]
+    tiles = [(8, 8), (32, 32), (16, 16), (64, 16)]
+    streams = [torch.cuda.Stream() for _ in trs]
+    graphs = [gpu_graph(t, tile=tl, stream=st) for t, tl, st in zip(trs, tiles, streams)]
+    errors = []
+
+    def work(i):
+        try:
+            for _ in range(5):
+                graphs[i].clear()
+                graphs[i].launch_trace(trs[i])
+                graphs[i].analyze()
+        except Exception as e:  # surfaced below
+            errors.append(repr(e))
+
+    th = [threading.Thread(target=work, args=(i,)) for i in range(len(trs))]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert not errors, errors
+    for g, t, ref in zip(graphs, trs, refs):
+        assert_csr_equal(g, t, ref)
+        g.close()
