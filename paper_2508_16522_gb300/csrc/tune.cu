@@ -11,7 +11,8 @@
 //                     configures it with the fastest;
 //   rt_tune_batch  -- the same for a batch launch with its replay count.
 // The executor search is coordinate descent: (warps, blocks per SM) jointly,
-// then the claim width, then the keep width, each trial the best of two runs.
+// then the claim width, then the keep width, then (warps, blocks per SM)
+// again, each trial the best of two runs.
 // Results go to an optional plain-text cache, one line per workload key
 // (device, SM count, kind, sizes, an input hash), so a later call with the
 // same workload answers without running anything.
@@ -120,22 +121,27 @@ rt_status search(int sms, Shape start, Run run, Shape* best, float* best_ms, int
   rt_status st = trial(cur, &cur_ms);
   if (st != RT_OK) return st;
   const int warps_c[] = {2, 4, 8};
-  for (int w : warps_c) {
-    const int maxb = std::max(exec_max_blocks_per_sm(w), 1);
-    for (int b = 1; b <= std::min(maxb, 3); ++b) {
-      Shape s = cur;
-      s.warps = w;
-      s.bps = b;
-      if (s.warps == cur.warps && s.bps == cur.bps) continue;
-      double ms = 0;
-      if ((st = trial(s, &ms)) != RT_OK) return st;
-      if (ms < cur_ms) {
-        cur = s;
-        cur_ms = ms;
+  auto shape_pass = [&]() -> rt_status {
+    for (int w : warps_c) {
+      const int maxb = std::max(exec_max_blocks_per_sm(w), 1);
+      for (int b = 1; b <= std::min(maxb, 3); ++b) {
+        Shape s = cur;
+        s.warps = w;
+        s.bps = b;
+        if (s.warps == cur.warps && s.bps == cur.bps) continue;
+        double ms = 0;
+        rt_status r = trial(s, &ms);
+        if (r != RT_OK) return r;
+        if (ms < cur_ms) {
+          cur = s;
+          cur_ms = ms;
+        }
       }
     }
-  }
-  const int claim_c[] = {4, 8, 16, 32};
+    return RT_OK;
+  };
+  if ((st = shape_pass()) != RT_OK) return st;
+  const int claim_c[] = {1, 2, 4, 8, 16, 32};
   const Shape after_shape = cur;
   for (int c : claim_c) {
     if (c == after_shape.claim) continue;
@@ -148,7 +154,7 @@ rt_status search(int sms, Shape start, Run run, Shape* best, float* best_ms, int
       cur_ms = ms;
     }
   }
-  const int keep_c[] = {8, 16, 32, 64};
+  const int keep_c[] = {2, 4, 8, 16, 32, 64};
   const Shape after_claim = cur;
   for (int k : keep_c) {
     if (k == after_claim.keep) continue;
@@ -161,6 +167,8 @@ rt_status search(int sms, Shape start, Run run, Shape* best, float* best_ms, int
       cur_ms = ms;
     }
   }
+  // the best grid can move with the widths: one more pass over it
+  if ((st = shape_pass()) != RT_OK) return st;
   (void)sms;
   *best = cur;
   *best_ms = (float)cur_ms;

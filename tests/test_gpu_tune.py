@@ -38,8 +38,8 @@ def test_exec_tuner_configures_the_graph_and_results_hold(tmp_path):
     g = gpu_graph(tr, body=grt.RT_BODY_SPIN, spin_iters=9)
     g.analyze()
     c = g.tune(cache)
-    assert c["trials"] >= 10 and c["warps"] in (2, 4, 8) and c["claim"] in (4, 8, 16, 32)
-    assert c["keep"] in (8, 16, 32, 64) and c["blocks"] > 0 and c["ms"] > 0
+    assert c["trials"] >= 10 and c["warps"] in (2, 4, 8) and c["claim"] in (1, 2, 4, 8, 16, 32)
+    assert c["keep"] in (2, 4, 8, 16, 32, 64) and c["blocks"] > 0 and c["ms"] > 0
     g.out.zero_()
     g.execute()
     g.sync()
