@@ -219,8 +219,8 @@ def run_stitched(grt, torch):
     persistent launch, once with a barrier between replays (rt_replay) and once
     joined by the edges between two copies of the trace (rt_execute_stitched),
     so that replay r + 1 starts where its own predecessors in replay r are
-    done. EMPTY bodies, the executor's default launch shape for both; times
-    include the counter reset and seeding."""
+    done. EMPTY bodies; both runs use the launch shape the autotuner picks for
+    one execution of the trace; times include the counter reset and seeding."""
     R = 20
     res = {"replays": R, "steps_per_replay": 100, "width": 1024}
     for pat in ("stencil", "random"):
@@ -228,6 +228,9 @@ def run_stitched(grt, torch):
         g = grt.Graph(2, T.dom_lo, T.dom_hi, flags=grt.RT_GRAPH_PROFILE)
         g.launch_trace(T)
         g.analyze()
+        shape = g.tune(TUNE_CACHE)
+        launch = (shape["blocks"], shape["warps"], shape["claim"], shape["keep"])
+        g.exec_config(*launch)
         bar = []
         for _ in range(4):
             g.replay(R)
@@ -237,11 +240,12 @@ def run_stitched(grt, torch):
         g2 = grt.Graph(2, T.dom_lo, T.dom_hi, flags=grt.RT_GRAPH_PROFILE)
         g2.launch_trace(tg.concat([T, T]))
         g2.analyze()
+        g2.exec_config(*launch)
         ana = g2.stats()["ms_analyze"]
         st = [g2.execute_stitched(R) for _ in range(4)]
         g2.close()
         b, s_ = float(np.median(bar[1:])), float(np.median(st[1:]))
-        res[pat] = {"barrier_ms": round(b, 3), "stitched_ms": round(s_, 3), "speedup": round(b / s_, 2),
+        res[pat] = {"launch": launch, "barrier_ms": round(b, 3), "stitched_ms": round(s_, 3), "speedup": round(b / s_, 2),
                     "barrier_tasks_per_s": R * T.n / (b * 1e-3), "stitched_tasks_per_s": R * T.n / (s_ * 1e-3),
                     "ms_analyze_two_copies": round(ana, 3)}
     return res
