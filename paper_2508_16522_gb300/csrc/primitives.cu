@@ -7,7 +7,12 @@
 // Radix sort: 8-bit digits, least significant first. Per pass: a per-block
 // digit histogram, an exclusive scan of the digit-major histogram matrix, and
 // a scatter whose in-block ranks are computed warp by warp with match_any (so
-// the sort is stable: keys keep their input order within a digit).
+// the sort is stable: keys keep their input order within a digit); the block
+// reorders its keys by digit in shared memory before writing them, so each
+// digit's run goes out in coalesced writes.
+
+#include <mutex>
+#include <set>
 
 #include "grt_internal.cuh"
 
@@ -167,13 +172,30 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_hist(const K* keys, int
   hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
 }
 
+// dynamic shared memory of one scatter block: its keys (and values) in
+// block-sorted order
+template <typename K, bool HAS_V>
+constexpr size_t scatter_smem_bytes() {
+  return (size_t)kRadixTile * (sizeof(K) + (HAS_V ? sizeof(uint64_t) : 0));
+}
+
+// One pass of the LSD radix sort over a block of kRadixTile keys: every key is
+// ranked within its warp and digit (match_any), the ranks become positions in
+// the block's digit-sorted order, the keys are reordered in shared memory, and
+// consecutive threads then write consecutive keys of each digit run to the
+// run's global offset, so the global writes are coalesced. Stable.
 template <typename K, bool HAS_V>
 __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(
     const K* __restrict__ keys, const uint64_t* __restrict__ vals, K* __restrict__ keys_out,
     uint64_t* __restrict__ vals_out, int64_t n, int shift, uint32_t mask,
     const uint32_t* __restrict__ offs, int64_t nblocks) {
   __shared__ uint32_t wcnt[kRadixWarps][256];
-  __shared__ uint32_t boff[256];
+  __shared__ uint32_t boff[256];    // the digit's first position in the output
+  __shared__ uint32_t bstart[257];  // the digit's first position in the block's sorted order
+  __shared__ uint32_t wsum[kRadixWarps];
+  extern __shared__ __align__(16) unsigned char rsmem[];
+  K* sk = reinterpret_cast<K*>(rsmem);
+  uint64_t* sv = reinterpret_cast<uint64_t*>(rsmem + (size_t)kRadixTile * sizeof(K));
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int w = 0; w < kRadixWarps; ++w) wcnt[w][threadIdx.x] = 0;
@@ -201,26 +223,70 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(
     rk[r] = base + before;
   }
   __syncthreads();
-  {
-    uint32_t run = 0;
+  // per digit (thread d): warp prefixes, and the digit's block total
+  uint32_t tot = 0;
 #pragma unroll
-    for (int w = 0; w < kRadixWarps; ++w) {
-      uint32_t t = wcnt[w][threadIdx.x];
-      wcnt[w][threadIdx.x] = run;
-      run += t;
-    }
+  for (int w = 0; w < kRadixWarps; ++w) {
+    uint32_t t = wcnt[w][threadIdx.x];
+    wcnt[w][threadIdx.x] = tot;
+    tot += t;
   }
+  // exclusive scan of the totals over the 256 digits (warp scans, then warps)
+  uint32_t incl = tot;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  uint32_t wpre = 0;
+#pragma unroll
+  for (int w = 0; w < kRadixWarps; ++w) wpre += w < warp ? wsum[w] : 0u;
+  bstart[threadIdx.x] = wpre + incl - tot;
+  if (threadIdx.x == kRadixThreads - 1) bstart[256] = wpre + incl;
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < kRadixIpt; ++r) {
     int64_t idx = wbase + r * 32 + lane;
     if (idx < n) {
-      uint32_t d = (uint32_t)(kv[r] >> shift) & mask;
-      uint32_t dst = boff[d] + wcnt[warp][d] + rk[r];
-      keys_out[dst] = kv[r];
-      if (HAS_V) vals_out[dst] = vv[HAS_V ? r : 0];
+      const uint32_t d = (uint32_t)(kv[r] >> shift) & mask;
+      const uint32_t lp = bstart[d] + wcnt[warp][d] + rk[r];
+      sk[lp] = kv[r];
+      if (HAS_V) sv[lp] = vv[HAS_V ? r : 0];
     }
   }
+  __syncthreads();
+  const uint32_t nvalid = bstart[256];
+  for (uint32_t i = threadIdx.x; i < nvalid; i += kRadixThreads) {
+    const K k = sk[i];
+    const uint32_t d = (uint32_t)(k >> shift) & mask;
+    const uint32_t dst = boff[d] + (i - bstart[d]);
+    keys_out[dst] = k;
+    if (HAS_V) vals_out[dst] = sv[i];
+  }
+}
+
+template <typename K, bool HAS_V>
+void launch_scatter(const K* kin, const uint64_t* vin, K* kout, uint64_t* vout, int64_t n, int shift, uint32_t mask,
+                    const uint32_t* offs, int64_t nb, cudaStream_t s) {
+  // above the default 48 KB of dynamic shared memory for some instantiations:
+  // one fixed size per instantiation, set once per device
+  static std::mutex mu;
+  static std::set<int> done;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!done.count(dev)) {
+      cudaFuncSetAttribute(k_radix_scatter<K, HAS_V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)scatter_smem_bytes<K, HAS_V>());
+      done.insert(dev);
+    }
+  }
+  count_launch();
+  k_radix_scatter<K, HAS_V><<<(unsigned)nb, kRadixThreads, scatter_smem_bytes<K, HAS_V>(), s>>>(
+      kin, vin, kout, vout, n, shift, mask, offs, nb);
 }
 }  // namespace
 
@@ -251,14 +317,9 @@ int radix_sort(K* keys, K* keys_alt, uint64_t* vals, uint64_t* vals_alt, int64_t
     k_radix_hist<K><<<(unsigned)nb, kRadixThreads, 0, s>>>(kin, n, shift, mask, hist, nb);
     scan_exclusive<uint32_t>(hist, offs, h, sws, s);
     if (vals) {
-      count_launch();
-      k_radix_scatter<K, true><<<(unsigned)nb, kRadixThreads, 0, s>>>(kin, vin, kout, vout, n, shift,
-                                                                     mask, offs, nb);
-    }
-    else {
-      count_launch();
-      k_radix_scatter<K, false><<<(unsigned)nb, kRadixThreads, 0, s>>>(kin, nullptr, kout, nullptr, n,
-                                                                      shift, mask, offs, nb);
+      launch_scatter<K, true>(kin, vin, kout, vout, n, shift, mask, offs, nb, s);
+    } else {
+      launch_scatter<K, false>(kin, nullptr, kout, nullptr, n, shift, mask, offs, nb, s);
     }
     K* t = kin;
     kin = kout;
