@@ -39,7 +39,8 @@ def _flags(verbose: bool):
 def _stale(obj: str, src: str) -> bool:
     if not os.path.exists(obj):
         return True
-    deps = [src, os.path.join(CSRC, "grt_internal.cuh"), os.path.join(INCLUDE, "grt.h")]
+    deps = [src, os.path.join(INCLUDE, "grt.h")] + [os.path.join(CSRC, h) for h in os.listdir(CSRC)
+                                                      if h.endswith(".cuh")]
     return any(os.path.getmtime(d) > os.path.getmtime(obj) for d in deps)
 
 

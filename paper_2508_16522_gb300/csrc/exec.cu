@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(256, 1) k_exec(ExecParams p) {
   unsigned long long seen = 0;
   uint32_t backoff = 32;
   uint32_t my_t = kNoTicket;     // this lane's claimed ring ticket
-  unsigned long long cnt[kCntCount];  // diagnostics (lane 0's copy is flushed at exit)
+  uint32_t cnt[kCntCount];  // diagnostics, per warp (lane 0's copy is added to the totals at exit)
 #pragma unroll
   for (int k = 0; k < kCntCount; ++k) cnt[k] = 0;
 
@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(256, 1) k_exec(ExecParams p) {
   if (lane == 0) {
 #pragma unroll
     for (int k = 0; k < kCntCount; ++k)
-      if (cnt[k]) atomicAdd(&ctrl->counters[k], cnt[k]);
+      if (cnt[k]) atomicAdd(&ctrl->counters[k], (unsigned long long)cnt[k]);
   }
 }
 
