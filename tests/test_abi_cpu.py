@@ -151,3 +151,17 @@ def test_product_package_does_not_import_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "liboracle" not in txt and "oracle.c" not in txt, f
+
+
+def test_stitched_calls_refuse_before_any_gpu_work(lib):
+    """rt_execute_stitched and rt_copy_stitched_tickets check their state on
+    the host: no graph, an unanalysed graph, no stitched run to copy from."""
+    l = grt.load()
+    f = ctypes.c_float()
+    assert l.rt_execute_stitched(None, 2, ctypes.byref(f)) == grt.RT_ERR_INVALID
+    h = grt.rt_graph_create(desc())
+    assert l.rt_execute_stitched(h, 2, ctypes.byref(f)) == grt.RT_ERR_STATE
+    out = np.zeros(8, np.int32)
+    assert l.rt_copy_stitched_tickets(h, None) == grt.RT_ERR_INVALID
+    assert l.rt_copy_stitched_tickets(h, out.ctypes.data) == grt.RT_ERR_STATE
+    grt.rt_graph_destroy(h)
