@@ -407,8 +407,10 @@ __device__ bool stage_lanes(Ctx& x, const WarpSmem& w, const SweepOut& o, unsign
 #pragma unroll
   for (int o2 = 16; o2 >= 1; o2 >>= 1) maxl = max(maxl, __shfl_xor_sync(kFull, maxl, o2));
   if (maxl >= kMaxRounds) return false;  // nothing applied yet: the warp-wide path takes the window
+  // each lane runs in one round (its level) and buffers its candidate's
+  // predecessors; the buffers are written out once, after the last round
+  int nb = 0;
   for (int r = 0; r <= maxl; ++r) {
-    int nb = 0;
     if (mine && level == r) {
       const int bw = b.x1 - b.x0 + 1;
       for (int i = 0; i < cells; ++i) {
@@ -425,23 +427,24 @@ __device__ bool stage_lanes(Ctx& x, const WarpSmem& w, const SweepOut& o, unsign
         }
       }
     }
-    // emit every lane's buffer into the warp's chunk
-    int incl = nb;
-#pragma unroll
-    for (int o2 = 1; o2 < 32; o2 <<= 1) {
-      const int y = __shfl_up_sync(kFull, incl, o2);
-      if (lane >= o2) incl += y;
-    }
-    const int total = __shfl_sync(kFull, incl, 31);
-    if (total > 0) {
-      const PairDst pd = reserve_pairs(x, o, (uint32_t)total);
-      if (lane == 0) atomicAdd(w.npairs, total);
-      const int base = incl - nb;
-      for (int k = 0; k < nb; ++k)
-        put_pair(w, o, pair_pos(pd, (uint32_t)(base + k)), pair_key(w.lbuf[lane * kLaneBuf + k], b.task, o.key_bits));
-    }
-    __syncwarp();
+    __syncwarp();  // this round's cell updates before the next round reads them
   }
+  // emit every lane's buffer into the warp's chunk
+  int incl = nb;
+#pragma unroll
+  for (int o2 = 1; o2 < 32; o2 <<= 1) {
+    const int y = __shfl_up_sync(kFull, incl, o2);
+    if (lane >= o2) incl += y;
+  }
+  const int total = __shfl_sync(kFull, incl, 31);
+  if (total > 0) {
+    const PairDst pd = reserve_pairs(x, o, (uint32_t)total);
+    if (lane == 0) atomicAdd(w.npairs, total);
+    const int base = incl - nb;
+    for (int k = 0; k < nb; ++k)
+      put_pair(w, o, pair_pos(pd, (uint32_t)(base + k)), pair_key(w.lbuf[lane * kLaneBuf + k], b.task, o.key_bits));
+  }
+  __syncwarp();
   return true;
 }
 
