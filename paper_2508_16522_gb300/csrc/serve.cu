@@ -269,12 +269,10 @@ __global__ void __launch_bounds__(256, 1) k_serve(ServeParams p) {
     const int deg = has ? a0.y : 0;
     q.bat[lane][0] = a0;
     q.bat[lane][1] = a1;
-    bool wrote = false;
     if (has) {
       // (no counter re-arm: every served request is analysed afresh)
       if (S.body == RT_BODY_SPIN && S.out) {
         S.out[v] = (int32_t)spin_body((uint32_t)(v - S.base), S.spin_iters);  // id within its request
-        wrote = true;
       }
     }
     __syncwarp();
@@ -355,7 +353,6 @@ __global__ void __launch_bounds__(256, 1) k_serve(ServeParams p) {
     // completion accounting per graph: outputs and decrements are released
     // before the count, so a completed graph's buffers are final when the host
     // sees its completion
-    (void)wrote;
     fence_acq_rel_gpu();
     const int gkey = has ? slot : -1;
     const unsigned peers = __match_any_sync(kFullS, gkey);
