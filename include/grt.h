@@ -103,7 +103,9 @@ typedef struct {
   int64_t out_elems;
   void* stream;                   /* cudaStream_t; NULL = legacy default stream */
   int32_t tile_w, tile_h;         /* analysis tile in cells; 0 = library default */
-  int64_t timeout_ns;             /* executor no-progress limit; 0 = 2 s */
+  int64_t timeout_ns;             /* executor no-progress limit; 0 = 2 s. Warps report progress
+                                     in batches (up to 4096 tasks each), so a serial chain of
+                                     very long bodies needs a limit above their total time */
   int32_t flags;                  /* RT_GRAPH_* */
 } rt_graph_desc;
 
