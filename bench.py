@@ -64,7 +64,7 @@ BATCH_GRAPHS, BATCH_REPLAYS = 4096, 20
 
 
 def run_batched(grt, torch, flush, steps):
-    """configs[3]: 4096 independent Task Bench graphs (sizes log-uniform
+    """The batched form: 4096 independent Task Bench graphs (sizes log-uniform
     64..65536, patterns mixed), captured once (analysis), then 20 replays of
     every graph in one persistent launch per step."""
     t0 = time.perf_counter()
@@ -268,7 +268,7 @@ def stacked_batch(traces, max_batch, band=1024):
 
 
 def run_served(grt, n_requests=SERVE_REQUESTS, rate=SERVE_RATE):
-    """configs[4]: Poisson arrivals (mean 50k graphs/s) of graphs with task
+    """The served form: Poisson arrivals (mean 50k graphs/s) of graphs with task
     counts log-uniform 32..16384, 1-4 rects per launch on a 1024^2 grid (sides
     log-uniform 4..256), admitted under an 8 GB device-memory budget. Requests
     are submitted when due and stamped with their due time, so submission lag
@@ -660,8 +660,8 @@ def run_ours(args):
     value = world * n_tasks * args.steps / (total_ms * 1e-3)
     e2e_value = None if args.no_e2e else n_tasks * args.steps / (sum(e2e_ms) * 1e-3)
     avg = [{k: float(np.mean([p[i][k] for p in per])) for k in per[0][i]} for i in range(len(graphs))]
-    # the same graphs with 256-iteration integer spin bodies (configs[1]'s second
-    # body), execution only: the body adds a chain of 256 dependent multiply-adds
+    # the same graphs with 256-iteration integer spin bodies (the Task Bench
+    # workload's second body), execution only: the body adds a chain of 256 dependent multiply-adds
     # to every wavefront step
     spin = events = None
     if world == 1 and not args.no_extras:
