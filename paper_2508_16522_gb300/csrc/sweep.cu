@@ -427,7 +427,7 @@ __device__ bool stage_lanes(Ctx& x, const WarpSmem& w, const SweepOut& o, unsign
         }
       }
     }
-    __syncwarp();  // this round's cell updates before the next round reads them
+    __syncwarp();  // this level's cell updates before the next level reads them
   }
   // emit every lane's buffer into the warp's chunk
   int incl = nb;
