@@ -1513,13 +1513,18 @@ rt_status rt_batch_execute(rt_batch_t b, int32_t replays, int32_t exec_blocks, i
   const int warps = exec_warps > 0 ? std::min(exec_warps, 8) : 4;
   const uint64_t cap = (uint64_t)b->T * (uint64_t)replays + 64;
   if (cap >= 0xFFFFFFF0ull) return fail(RT_ERR_INVALID, "tasks x replays must stay below 2^32 per launch");
+  const int max_blocks = g_dev.num_sms * exec_bps_for(warps);
+  if (exec_blocks > max_blocks) return fail(RT_ERR_INVALID, "more persistent blocks than can be resident");
+  const int blocks = exec_blocks > 0 ? exec_blocks : g_dev.num_sms * std::min(exec_bps_for(warps), 3);
   cudaStream_t s = b->s;
   bool clear = b->dirty;
   if (cap * 8 > b->ring.cap) {
     CKR(b->ring.reserve((size_t)cap * 8, s));
     clear = true;
   }
-  if (b->dirty) launch_reset_counts(b->count.as<int32_t>(), b->indeg.as<int32_t>(), b->T, -1, 0, s);
+  // the launch's INIT: a batch's counters count up from 0 across its replays
+  CK(cudaEventRecord(b->e0, s));
+  CK(cudaMemsetAsync(b->count.p, 0, (size_t)b->T * 4, s));
   ExecParams p{};
   p.adj = b->adj.as<int4>();
   p.row_ptr = b->row_ptr.as<int32_t>();
@@ -1542,10 +1547,6 @@ rt_status rt_batch_execute(rt_batch_t b, int32_t replays, int32_t exec_blocks, i
   p.total_roots = (int32_t)b->Rtot;
   p.need_fence = b->need_fence;
   launch_seed(p, clear ? (int64_t)(b->ring.cap / 8) : 0, s);
-  const int max_blocks = g_dev.num_sms * exec_bps_for(warps);
-  if (exec_blocks > max_blocks) return fail(RT_ERR_INVALID, "more persistent blocks than can be resident");
-  const int blocks = exec_blocks > 0 ? exec_blocks : g_dev.num_sms * std::min(exec_bps_for(warps), 3);
-  CK(cudaEventRecord(b->e0, s));
   launch_exec(p, blocks, warps, s);
   CK(cudaEventRecord(b->e1, s));
   CK(cudaMemcpyAsync(b->hpin, &p.ctrl->status, 4, cudaMemcpyDeviceToHost, s));

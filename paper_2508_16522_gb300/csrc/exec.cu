@@ -15,7 +15,12 @@
 //    the tail, publish by store-release per slot).
 // Replays: a per-graph completion counter; the warp whose increment completes
 // graph g's run r seeds g's roots again for run r+1 (graphs in a batch advance
-// independently), until `replays` runs are done.
+// independently), until `replays` runs are done. A single graph's counters
+// count down and each task re-arms its own; a batch's counters start at 0 and
+// count up across the replays, a task being ready when its counter reaches a
+// multiple of its in-degree. Run r+1's increments of a counter cannot
+// overtake run r's (the task ran in run r only after all of them), so a batch
+// needs no re-arm and no release of it before the completion count.
 // Every wait is bounded: a warp that sees no progress of the global executed
 // counter for timeout_ns sets status TIMEOUT and returns.
 #include <mutex>
@@ -219,7 +224,7 @@ __global__ void __launch_bounds__(256, 1) k_exec(ExecParams p) {
     q.bat[lane][0] = a0;
     q.bat[lane][1] = a1;
     if (has) {
-      p.count[v] = a0.z;  // INIT's reset, done by the task itself for the next run
+      if (SINGLE) p.count[v] = a0.z;  // INIT's reset, done by the task itself for the next run
       if (TICKETS) p.tickets[2 * (int64_t)v] = (int32_t)atomicAdd(&ctrl->ticket, 1u);
       if (SINGLE && !FENCE) {
         if (body0 == RT_BODY_SPIN) {  // the one graph's fields live in registers
@@ -280,7 +285,8 @@ __global__ void __launch_bounds__(256, 1) k_exec(ExecParams p) {
       for (int k = 0; k < kEdgeRound; ++k) {
         old[k] = 0;
         if (succ[k] >= 0) {
-          old[k] = atomicSub(&p.count[succ[k]], 1);
+          old[k] = SINGLE ? atomicSub(&p.count[succ[k]], 1)
+                          : (int)atomicAdd(reinterpret_cast<unsigned*>(p.count) + succ[k], 1u);
           r0[k] = __ldg(p.adj + 2 * (int64_t)succ[k]);
           r1[k] = __ldg(p.adj + 2 * (int64_t)succ[k] + 1);
         }
@@ -288,7 +294,10 @@ __global__ void __launch_bounds__(256, 1) k_exec(ExecParams p) {
 #pragma unroll
       for (int k = 0; k < kEdgeRound; ++k) {
         if (e0 + k * 32 >= D) break;  // warp-uniform
-        const bool ready = succ[k] >= 0 && old[k] == 1;
+        // one graph counts down and re-arms; a batch's counters count up across
+        // its replays (the successor's in-degree is in its speculative record)
+        const bool ready =
+            succ[k] >= 0 && (SINGLE ? old[k] == 1 : ((uint32_t)old[k] + 1u) % (uint32_t)r0[k].z == 0u);
         const unsigned rm = __ballot_sync(kFull, ready);
         if (!rm) continue;
         const uint64_t nit = ((uint64_t)gsel[k] << 32) | (uint32_t)succ[k];
@@ -333,7 +342,9 @@ __global__ void __launch_bounds__(256, 1) k_exec(ExecParams p) {
       const unsigned peers = __match_any_sync(kFull, gkey);
       bool cross = false;
       uint32_t runs_done = 0;
-      if (hm) fence_acq_rel_gpu();  // release: re-armed counters before the count
+      // release: the bodies' effects before the count (a finished run starts the
+      // next one); the counters need none, as they are never re-armed here
+      if ((FENCE || TICKETS) && hm) fence_acq_rel_gpu();
       if (has && (peers & lt) == 0) {
         const uint32_t c = (uint32_t)__popc(peers);
         const uint32_t ng = (uint32_t)p.graphs[g].n_tasks;
