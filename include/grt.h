@@ -276,8 +276,9 @@ rt_status rt_debug_hold_task(rt_graph_t g, int32_t task, int32_t extra);
  * and roots are copied into batch-owned buffers (the captured traces), with
  * task ids shifted so graph g's tasks follow graph g-1's. The batch still
  * refers to each graph's body buffers (state/out) and launch data (CHECK
- * body), so the graphs must outlive it. Errors: RT_ERR_STATE if a graph is not
- * analyzed, RT_ERR_INVALID, RT_ERR_OOM, RT_ERR_CUDA. */
+ * body), so the graphs must outlive it. At most 2^20 - 1 graphs. Errors:
+ * RT_ERR_STATE if a graph is not analyzed, RT_ERR_INVALID, RT_ERR_OOM,
+ * RT_ERR_CUDA. */
 rt_status rt_batch_create(const rt_graph_t* graphs, int32_t n_graphs, void* stream,
                           rt_batch_t* out);
 
@@ -294,10 +295,11 @@ rt_status rt_batch_create(const rt_graph_t* graphs, int32_t n_graphs, void* stre
 rt_status rt_batch_create_stacked(rt_graph_t g, const int32_t* task_off, int32_t n_graphs, void* stream,
                                   rt_batch_t* out);
 
-/* One persistent launch in which every graph of the batch runs `replays` times;
- * graph g's replay r+1 starts as soon as its replay r has finished,
+/* One persistent launch in which every graph of the batch runs `replays` times
+ * (1..4096); graph g's replay r+1 starts as soon as its replay r has finished,
  * independently of the other graphs. exec_blocks/exec_warps/claim/keep (0 =
- * default) are the launch shape of rt_graph_exec_config. Asynchronous. */
+ * default) are the launch shape of rt_graph_exec_config. The batch's counters
+ * are reset at the start of every launch. Asynchronous. */
 rt_status rt_batch_execute(rt_batch_t b, int32_t replays, int32_t exec_blocks, int32_t exec_warps,
                            int32_t claim, int32_t keep);
 

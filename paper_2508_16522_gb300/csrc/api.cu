@@ -1298,6 +1298,7 @@ rt_status rt_batch_create(const rt_graph_t* graphs, int32_t n_graphs, void* stre
   if (!out) return fail(RT_ERR_INVALID, "out is NULL");
   *out = nullptr;
   if (!graphs || n_graphs <= 0) return fail(RT_ERR_INVALID, "no graphs");
+  if (n_graphs >= (1 << 20)) return fail(RT_ERR_INVALID, "a batch holds fewer than 2^20 graphs (got %d)", n_graphs);
   int64_t T = 0, E = 0, Rt = 0;
   int32_t nonempty = 0;
   for (int32_t i = 0; i < n_graphs; ++i) {
@@ -1394,6 +1395,7 @@ rt_status rt_batch_create_stacked(rt_graph_t g, const int32_t* task_off, int32_t
   if (!out) return fail(RT_ERR_INVALID, "out is NULL");
   *out = nullptr;
   if (!g || !task_off || n_graphs <= 0) return fail(RT_ERR_INVALID, "NULL graph, offsets or no graphs");
+  if (n_graphs >= (1 << 20)) return fail(RT_ERR_INVALID, "a batch holds fewer than 2^20 graphs (got %d)", n_graphs);
   if (!g->analyzed) return fail(RT_ERR_STATE, "graph is not analyzed");
   if (task_off[0] != 0 || task_off[n_graphs] != g->n)
     return fail(RT_ERR_INVALID, "task_off must run from 0 to the graph's %d tasks", g->n);
@@ -1509,7 +1511,7 @@ rt_status rt_batch_create_stacked(rt_graph_t g, const int32_t* task_off, int32_t
 rt_status rt_batch_execute(rt_batch_t b, int32_t replays, int32_t exec_blocks, int32_t exec_warps, int32_t claim,
                            int32_t keep) {
   if (!b) return fail(RT_ERR_INVALID, "batch is NULL");
-  if (replays <= 0) return fail(RT_ERR_INVALID, "replays must be positive");
+  if (replays <= 0 || replays > 4096) return fail(RT_ERR_INVALID, "a batch runs 1 to 4096 replays (got %d)", replays);
   const int warps = exec_warps > 0 ? std::min(exec_warps, 8) : 4;
   const uint64_t cap = (uint64_t)b->T * (uint64_t)replays + 64;
   if (cap >= 0xFFFFFFF0ull) return fail(RT_ERR_INVALID, "tasks x replays must stay below 2^32 per launch");

@@ -17,8 +17,9 @@
 // graph g's run r seeds g's roots again for run r+1 (graphs in a batch advance
 // independently), until `replays` runs are done. A single graph's counters
 // count down and each task re-arms its own; a batch's counters start at 0 and
-// count up across the replays, a task being ready when its counter reaches a
-// multiple of its in-degree. Run r+1's increments of a counter cannot
+// count up across the replays, a task being ready in run r when its counter
+// reaches (r + 1) times its in-degree (each ready item carries its run, so the
+// test is one multiply). Run r+1's increments of a counter cannot
 // overtake run r's (the task ran in run r only after all of them), so a batch
 // needs no re-arm and no release of it before the completion count.
 // Every wait is bounded: a warp that sees no progress of the global executed
@@ -34,6 +35,8 @@ namespace {
 constexpr int kKeepMax = 64;
 constexpr uint32_t kNoTicket = 0xFFFFFFFFu;
 constexpr int kEdgeRound = 4;  // 32-edge groups whose decrements are in flight together
+// a batch's ready item: run << 52 | graph << 32 | task (graphs < 2^20, runs < 2^12)
+constexpr uint64_t kGraphMask = 0xFFFFFull;
 constexpr unsigned kFull = 0xffffffffu;
 
 __global__ void k_reset_counts(int32_t* count, const int32_t* indeg, int64_t n, int32_t hold_task,
@@ -64,7 +67,7 @@ __global__ void k_seed(ExecParams p, int64_t ring_clear) {
 
 
 // pushes graph g's roots into the ring for its next run (warp-cooperative)
-__device__ void push_roots(const ExecParams& p, int g, int lane) {
+__device__ void push_roots(const ExecParams& p, int g, int lane, uint64_t tag) {
   const ExecGraph& G = p.graphs[g];
   uint32_t base = 0;
   if (lane == 0) base = atomicAdd(&p.ctrl->tail, (uint32_t)G.n_roots);
@@ -73,14 +76,15 @@ __device__ void push_roots(const ExecParams& p, int g, int lane) {
     if (lane == 0) atomicCAS(&p.ctrl->status, 0u, (uint32_t)RT_ERR_OOM);
     return;
   }
-  for (int k = lane; k < G.n_roots; k += 32) st_release_u64(p.ring + base + k, p.root_items[G.root_base + k]);
+  for (int k = lane; k < G.n_roots; k += 32) st_release_u64(p.ring + base + k, p.root_items[G.root_base + k] | tag);
 }
 
 // the warp whose count completed a run of graph g: next run or graph finished
-__device__ void on_run_complete(const ExecParams& p, int g, uint32_t runs_done, int lane) {
+// (tag: the bits a batch's items carry for the run they belong to)
+__device__ void on_run_complete(const ExecParams& p, int g, uint32_t runs_done, int lane, uint64_t tag) {
   fence_acq_rel_gpu();  // acquire every re-armed counter of the finished run
   if ((int)runs_done < p.replays)
-    push_roots(p, g, lane);
+    push_roots(p, g, lane, tag);
   else if (lane == 0)
     atomicAdd(&p.ctrl->graphs_done, 1u);
 }
@@ -89,7 +93,7 @@ __device__ void on_run_complete(const ExecParams& p, int g, uint32_t runs_done, 
 struct WarpQ {
   int4 adj[kKeepMax][2];  // trigger records of the kept ready tasks
   int4 bat[32][2];        // trigger records of the current batch, one per lane
-  uint64_t item[kKeepMax];  // kept ready tasks (graph << 32 | task)
+  uint64_t item[kKeepMax];  // kept ready tasks (task | graph << 32; a batch's also run << 52)
 };
 
 template <bool TICKETS, bool FENCE, bool SINGLE>
@@ -121,7 +125,7 @@ __global__ void __launch_bounds__(256, 1) k_exec(ExecParams p) {
       uint32_t now = 0;
       if (lane == 0) now = atomicAdd(&p.done_g[0], pend) + pend;
       now = __shfl_sync(kFull, now, 0);
-      if (now % n0 == 0u) on_run_complete(p, 0, now / n0, lane);
+      if (now % n0 == 0u) on_run_complete(p, 0, now / n0, lane, 0ull);
     } else if (lane == 0) {
       atomicAdd(&ctrl->executed, (unsigned long long)pend);
     }
@@ -214,7 +218,7 @@ __global__ void __launch_bounds__(256, 1) k_exec(ExecParams p) {
     if (FENCE) fence_acq_rel_gpu();  // acquire: predecessors' effects visible to the bodies
     const bool has = item != kEmpty64;
     const int v = (int)(uint32_t)item;
-    const int g = SINGLE ? 0 : (has ? (int)(item >> 32) : -1);
+    const int g = SINGLE ? 0 : (has ? (int)((item >> 32) & kGraphMask) : -1);
     if (has && !have_rec) {
       a0 = __ldg(p.adj + 2 * (int64_t)v);
       a1 = __ldg(p.adj + 2 * (int64_t)v + 1);
@@ -295,9 +299,10 @@ __global__ void __launch_bounds__(256, 1) k_exec(ExecParams p) {
       for (int k = 0; k < kEdgeRound; ++k) {
         if (e0 + k * 32 >= D) break;  // warp-uniform
         // one graph counts down and re-arms; a batch's counters count up across
-        // its replays (the successor's in-degree is in its speculative record)
-        const bool ready =
-            succ[k] >= 0 && (SINGLE ? old[k] == 1 : ((uint32_t)old[k] + 1u) % (uint32_t)r0[k].z == 0u);
+        // its replays (the successor's in-degree is in its speculative record,
+        // the run in the item's high bits)
+        const bool ready = succ[k] >= 0 && (SINGLE ? old[k] == 1
+                                                   : (uint32_t)old[k] + 1u == ((gsel[k] >> 20) + 1u) * (uint32_t)r0[k].z);
         const unsigned rm = __ballot_sync(kFull, ready);
         if (!rm) continue;
         const uint64_t nit = ((uint64_t)gsel[k] << 32) | (uint32_t)succ[k];
@@ -361,7 +366,8 @@ __global__ void __launch_bounds__(256, 1) k_exec(ExecParams p) {
       while (cm) {
         const int L = __ffs((int)cm) - 1;
         cm &= cm - 1;
-        on_run_complete(p, __shfl_sync(kFull, g, L), __shfl_sync(kFull, runs_done, L), lane);
+        const uint32_t rd = __shfl_sync(kFull, runs_done, L);
+        on_run_complete(p, __shfl_sync(kFull, g, L), rd, lane, (uint64_t)rd << 52);
       }
     }
   }
