@@ -1,8 +1,14 @@
-"""ctypes wrapper around oracle.c (TEST INFRASTRUCTURE ONLY).
+"""ctypes wrapper around the C oracle (TEST INFRASTRUCTURE ONLY).
 
-The C file is compiled with the host gcc into ``oracle/_lib/liboracle.so``
-(``build()``; also done on first use). All arithmetic lives in oracle.c; this
-module only marshals numpy arrays.
+The C files are compiled with the host gcc into ``oracle/_lib/liboracle.so``
+(``build()``; also done on first use):
+
+* oracle.c    per-cell dependence analysis, Kahn order, sequential bodies
+* interval.c  the same analysis over interval maps of run state, threaded
+              over rows (for traces too large for the per-cell walk)
+* alg1.c      Algorithm 1's countdown executor on host threads
+
+All arithmetic lives in the C files; this module only marshals numpy arrays.
 """
 from __future__ import annotations
 
@@ -14,7 +20,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "oracle.c")
+_SRCS = [os.path.join(_HERE, f) for f in ("oracle.c", "interval.c", "alg1.c")]
 _LIBDIR = os.path.join(_HERE, "_lib")
 _SO = os.path.join(_LIBDIR, "liboracle.so")
 _lock = threading.Lock()
@@ -24,11 +30,11 @@ BODY_EMPTY, BODY_SPIN, BODY_COUNTER, BODY_CHECK = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c with gcc (plain C99, no target-specific flags)."""
+    """Compile the oracle with gcc (plain C11 + pthreads, no target-specific flags)."""
     os.makedirs(_LIBDIR, exist_ok=True)
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_SO) or any(os.path.getmtime(_SO) < os.path.getmtime(s) for s in _SRCS):
         tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread", "-o", tmp] + _SRCS)
         os.replace(tmp, _SO)
     return _SO
 
@@ -59,6 +65,17 @@ def _load(path: str = None):
         lib.orc_mix32.argtypes = [u32, u32]
         lib.orc_spin.restype = u32
         lib.orc_spin.argtypes = [u32, i32]
+        if hasattr(lib, "orc_b3_analyze"):  # absent from a single-file build of oracle.c
+            lib.orc_b3_analyze.restype = P
+            lib.orc_b3_analyze.argtypes = [i32, P, P, i32, P, P, P, P, P, P, i32]
+            lib.orc_b3_edges.restype = i64
+            lib.orc_b3_edges.argtypes = [P]
+            lib.orc_b3_copy.restype = None
+            lib.orc_b3_copy.argtypes = [P, P, P]
+            lib.orc_b3_free.restype = None
+            lib.orc_b3_free.argtypes = [P]
+            lib.orc_alg1_run.restype = i32
+            lib.orc_alg1_run.argtypes = [i32, P, P, i32, i32, i32, P, P, P, P, P]
         if path is None:
             _lib = lib
         return lib
@@ -93,6 +110,50 @@ def analyze(tr, lib_path: str = None):
     finally:
         lib.orc_result_free(h)
     return src, dst
+
+
+def analyze_intervals(tr, threads: int = 1, lib_path: str = None):
+    """The same edges as ``analyze`` computed over interval maps of run state,
+    rows split over `threads` host threads: canonical CSR (row_ptr int64[n+1],
+    col int32[E])."""
+    lib = _load(lib_path)
+    req_off = _c(tr.req_off, np.int32)
+    lo, hi = _c(tr.lo, np.int64), _c(tr.hi, np.int64)
+    priv = _c(tr.priv, np.uint8)
+    po, pr = _c(tr.pred_off, np.int32), _c(tr.pred, np.int32)
+    dlo, dhi = _c(tr.dom_lo, np.int64), _c(tr.dom_hi, np.int64)
+    h = lib.orc_b3_analyze(tr.ndim, _p(dlo), _p(dhi), tr.n, _p(req_off), _p(lo), _p(hi), _p(priv),
+                           _p(po), _p(pr), int(threads))
+    if not h:
+        raise MemoryError("interval analysis failed to allocate")
+    try:
+        e = lib.orc_b3_edges(h)
+        row_ptr = np.empty(tr.n + 1, np.int64)
+        col = np.empty(e, np.int32)
+        lib.orc_b3_copy(h, _p(row_ptr), _p(col))
+    finally:
+        lib.orc_b3_free(h)
+    return row_ptr, col
+
+
+def alg1_run(n: int, row_ptr, col, threads: int, body: int = BODY_EMPTY, spin_iters: int = 0,
+             body_arg=None, state=None, tickets: bool = False):
+    """Runs the CSR once with Algorithm 1's countdowns on `threads` host
+    threads (bodies EMPTY, SPIN or COUNTER). Returns (state, out, tickets or
+    None, ns from INIT to the last completion)."""
+    lib = _load()
+    rp = _c(row_ptr, np.int64)
+    cl = _c(col, np.int32)
+    out = np.zeros(max(n, 1), np.int32)
+    st = np.ascontiguousarray(state if state is not None else np.zeros(1, np.int32), np.int32)
+    ba = _c(body_arg, np.int32)
+    tk = np.full(2 * max(n, 1), -1, np.int32) if tickets else None
+    ns = np.zeros(1, np.int64)
+    rc = lib.orc_alg1_run(n, _p(rp), _p(cl), int(threads), int(body), int(spin_iters), _p(ba), _p(st),
+                          _p(out), _p(tk), _p(ns))
+    if rc:
+        raise MemoryError("alg1 executor failed to allocate")
+    return st, out, tk, int(ns[0])
 
 
 def csr_from_pairs(n: int, src: np.ndarray, dst: np.ndarray):
