@@ -255,16 +255,28 @@ def batch_graph_shape(n_target: int):
     return w, steps
 
 
-def batch_graphs(n_graphs: int = 4096, n_range=(64, 65536), seed: int = 0,
-                 encode: str = "region") -> List[Trace]:
+def batch_graph_specs(n_graphs: int = 4096, n_range=(64, 65536), seed: int = 0):
+    """(width, steps, pattern, seed) of every graph of a batch: sizes
+    log-uniform, patterns uniform. Any one graph can be rebuilt from its spec
+    (``batch_graph``) without generating the others."""
     rng = np.random.Generator(np.random.PCG64(seed))
     sizes = loguniform_int(rng, n_range[0], n_range[1], n_graphs)
     pats = rng.integers(0, 3, size=n_graphs)
     out = []
     for g in range(n_graphs):
         w, steps = batch_graph_shape(int(sizes[g]))
-        out.append(taskbench(w, steps, PATTERNS[int(pats[g])], seed=seed * 100003 + g, encode=encode))
+        out.append((w, steps, PATTERNS[int(pats[g])], seed * 100003 + g))
     return out
+
+
+def batch_graph(spec, encode: str = "region") -> Trace:
+    w, steps, pattern, gseed = spec
+    return taskbench(w, steps, pattern, seed=gseed, encode=encode)
+
+
+def batch_graphs(n_graphs: int = 4096, n_range=(64, 65536), seed: int = 0,
+                 encode: str = "region") -> List[Trace]:
+    return [batch_graph(sp, encode) for sp in batch_graph_specs(n_graphs, n_range, seed)]
 
 
 @dataclasses.dataclass

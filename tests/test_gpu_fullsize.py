@@ -1,9 +1,11 @@
 """Parity at the full sizes of the workloads, in the launch configurations
-the benchmark uses. The oracle cannot take these whole, so each test checks
-what it can compute one by one (windows of the grid, sampled graphs, the
-smallest requests) element by element, and properties that hold at any
-size on everything (edges point forward in program order, rows sorted and
-unique, in-degrees equal column counts, every task of every replay ran)."""
+the benchmark uses: whole results against the oracle where it can take them
+(the 1M-launch trace through the threaded interval-map oracle), element by
+element on what it computes one by one elsewhere, and properties that hold
+at any size on everything (edges point forward in program order, rows sorted
+and unique, in-degrees equal column counts, every task of every replay ran)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -11,8 +13,8 @@ import oracle
 from paper_2508_16522_gb300 import grt
 from paper_2508_16522_gb300 import tracegen as tg
 
-from gpu_helpers import ensure_built, gpu_graph, oracle_csr
-from windows import clip_to_window
+import oracle_pool
+from gpu_helpers import ensure_built, gpu_graph
 
 pytestmark = pytest.mark.gpu
 
@@ -29,58 +31,53 @@ def check_csr_invariants(n, rp, col, ind):
     return src, col
 
 
-def test_random_rects_4096_full_size_windows():
-    """1M launches of 1-4 rects (sides log-uniform 16..1024) on 4096^2, the
-    library's default tiling. Three 64x64 windows: every edge the oracle finds
-    in a window is in the GPU graph, and tasks wholly inside a window have
-    exactly the oracle's in- and out-edges."""
-    ensure_built()
+@pytest.fixture(scope="module")
+def rects_4096():
+    """The 1M-launch 4096^2 trace and its CSR from the interval-map oracle, which
+    runs the per-cell rule row by row on every host core (pinned on the CPU to
+    the per-cell oracle on downsized traces of this workload)."""
     tr = tg.random_rects(grid=(4096, 4096), n=1_000_000, seed=0)
-    g = gpu_graph(tr, defer_check=True)
+    return tr, oracle.analyze_intervals(tr, os.cpu_count() or 1)
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (32, 32)])
+def test_random_rects_4096_full_size_whole_csr(rects_4096, tile):
+    """1M launches of 1-4 rects (sides log-uniform 16..1024) on 4096^2, at the
+    library's default tile and at the one the benchmark uses: the WHOLE CSR
+    (row_ptr, all 24,051,083 columns, in-degrees) equals the oracle's byte for
+    byte."""
+    ensure_built()
+    tr, (rp_o, col_o) = rects_4096
+    g = gpu_graph(tr, tile=tile, defer_check=True)
     g.analyze()
     rp, col, ind = g.csr()
     g.close()
-    n = tr.n
-    src, col = check_csr_invariants(n, rp, col, ind)
-    assert 10_000_000 <= len(col) <= 40_000_000
-    keys = src * n + col  # ascending: rows in order, columns ascending
-    by_dst = np.argsort(col, kind="stable")
-    col_sorted = col[by_dst]
-    rng = np.random.default_rng(0)
-    inside_checked = 0
-    for _ in range(3):
-        wx, wy = (int(v) for v in rng.integers(0, 4096 - 64, 2))
-        sub, ids, inside = clip_to_window(tr, [wx, wy], [wx + 63, wy + 63])
-        s, d = oracle.analyze(sub)
-        wkeys = ids[s].astype(np.int64) * n + ids[d]
-        pos = np.searchsorted(keys, wkeys)
-        assert np.all(pos < len(keys)) and np.array_equal(keys[np.minimum(pos, len(keys) - 1)], wkeys)
-        for k in np.nonzero(inside)[0]:
-            t = int(ids[k])
-            mine = d == k
-            want_in = np.sort(ids[s[mine]])
-            a, b = np.searchsorted(col_sorted, [t, t + 1])
-            assert np.array_equal(np.sort(src[by_dst[a:b]]), want_in), t
-            want_out = np.sort(ids[d[s == k]])
-            assert np.array_equal(col[rp[t]:rp[t + 1]], want_out), t
-            inside_checked += 1
-    assert inside_checked >= 3
+    check_csr_invariants(tr.n, rp, col, ind)
+    assert len(col) == len(col_o) == 24_051_083
+    assert np.array_equal(rp.astype(np.int64), rp_o)
+    assert np.array_equal(col, col_o)
+    assert np.array_equal(ind.astype(np.int64), np.bincount(col_o, minlength=tr.n))
 
 
-def test_batched_full_size_sampled_graphs():
+@pytest.fixture(scope="module")
+def batch_digests():
+    """The oracle's CSR and its CHECK state and outputs after 20 sequential runs,
+    as digests, for every graph of the 4096-graph batch (spawned processes over
+    the host's cores)."""
+    return oracle_pool.batch_check_digests(4096, seed=0, runs=20)
+
+
+def test_batched_full_size_every_graph(batch_digests):
     """4096 Task Bench graphs (sizes log-uniform 64..65536) in one persistent
-    launch with 20 replays, as the benchmark runs them. Every 128th graph runs
-    the order-sensitive CHECK body and must end in the oracle's state after
-    20 sequential runs; every graph's CSR is checked for the invariants, the
-    sampled ones against the oracle, and the launch must have run every task
-    of every replay."""
+    launch with 20 replays, as the benchmark runs them, every graph on the
+    order-sensitive CHECK body: every graph's CSR equals the oracle's, and its
+    state and outputs after the launch equal the oracle's after 20 sequential
+    runs; the launch ran every task of every replay."""
     ensure_built()
     traces = tg.batch_graphs(4096, seed=0)
-    sampled = set(range(0, 4096, 128)) | {int(np.argmax([t.n for t in traces]))}
     graphs = []
-    for k, tr in enumerate(traces):
-        body = grt.RT_BODY_CHECK if k in sampled else grt.RT_BODY_EMPTY
-        g = gpu_graph(tr, body=body)
+    for tr in traces:
+        g = gpu_graph(tr, body=grt.RT_BODY_CHECK)
         g.analyze()
         graphs.append(g)
     batch = grt.Batch(graphs)
@@ -92,14 +89,11 @@ def test_batched_full_size_sampled_graphs():
     for k, (tr, g) in enumerate(zip(traces, graphs)):
         rp, col, ind = g.csr()
         check_csr_invariants(tr.n, rp, col, ind)
-        if k in sampled:
-            rp_o, col_o, _ = oracle_csr(tr)
-            assert np.array_equal(rp.astype(np.int64), rp_o) and np.array_equal(col, col_o), tr.name
-            st = out = None
-            for _ in range(20):
-                st, out = oracle.run_bodies(tr, oracle.oracle.BODY_CHECK, state=st)
-            assert np.array_equal(g.state.cpu().numpy(), st), tr.name
-            assert np.array_equal(g.out.cpu().numpy(), out), tr.name
+        want_csr, want_body = batch_digests[k]
+        assert oracle_pool.csr_digest(rp, col) == want_csr, tr.name
+        st = g.state.cpu().numpy()[:tr.n_cells]
+        out = g.out.cpu().numpy()[:tr.n]
+        assert oracle_pool.digest(st, out) == want_body, tr.name
     batch.close()
     for g in graphs:
         g.close()
@@ -108,8 +102,9 @@ def test_batched_full_size_sampled_graphs():
 def test_served_full_size_stream():
     """2000 requests of the served workload (Poisson at 50k graphs/s, sizes
     log-uniform 32..16384, dense rects on 1024^2) through the server as the
-    benchmark configures it, results kept. All complete; every result passes
-    the invariants; the smallest requests match the oracle exactly."""
+    benchmark configures it, results kept. All complete; every request's CSR
+    equals the interval-map oracle's for that request alone, and its SPIN
+    outputs are those of its own task ids."""
     ensure_built()
     reqs = tg.served_stream(2000, rate_per_s=50_000.0, seed=0)
     srv = grt.Server(2, [0, 0], [1023, 1023], body=grt.RT_BODY_SPIN, spin_iters=5, budget_bytes=8 << 30,
@@ -118,26 +113,22 @@ def test_served_full_size_stream():
     srv.drain(600_000_000_000)
     infos = [srv.poll(t) for t in tickets]
     assert all(i["state"] == 3 for i in infos)
-    order = np.argsort([r.trace.n for r in reqs])
-    exact = set(order[:6].tolist())
     # a SPIN output depends only on the task's id within its request
     spin_all = np.array([oracle.spin(j, 5) for j in range(16384)], np.uint32).view(np.int32)
-    for k, (r, t, i) in enumerate(zip(reqs, tickets, infos)):
+    threads = os.cpu_count() or 1
+    for r, t, i in zip(reqs, tickets, infos):
         rp, col, out = srv.result(t, i["n_tasks"], i["n_edges"], with_out=True)
-        check_csr_invariants(r.trace.n, rp, col, np.bincount(col, minlength=r.trace.n))
         assert np.array_equal(out, spin_all[:r.trace.n])
-        if k in exact:
-            rp_o, col_o, _ = oracle_csr(r.trace)
-            assert np.array_equal(rp.astype(np.int64), rp_o) and np.array_equal(col, col_o)
+        rp_o, col_o = oracle.analyze_intervals(r.trace, threads)
+        assert np.array_equal(rp.astype(np.int64), rp_o) and np.array_equal(col, col_o), r.trace.name
     srv.close()
 
 
-def test_batched_full_size_stacked_capture():
+def test_batched_full_size_stacked_capture(batch_digests):
     """The benchmark's capture of the batched workload: all 4096 graphs stacked
     in bands of one domain and analysed ONCE. Every graph's part of the CSR
-    passes the invariants and stays inside the graph; sampled graphs (every
-    256th and the largest) equal their own oracle CSR; the stacked batch runs
-    every task of 20 replays."""
+    stays inside the graph and equals the graph's own oracle CSR; the stacked
+    batch runs every task of 20 replays."""
     ensure_built()
     traces = tg.batch_graphs(4096, seed=0)
     st, off = tg.stack_bands(traces, name="batch")
@@ -147,12 +138,10 @@ def test_batched_full_size_stacked_capture():
     src, col64 = check_csr_invariants(st.n, rp, col, ind)
     graph_of = np.searchsorted(off, np.arange(st.n), side="right") - 1
     assert np.array_equal(graph_of[src], graph_of[col64]), "an edge joins two graphs"
-    sampled = set(range(0, 4096, 256)) | {int(np.argmax([t.n for t in traces]))}
-    for k in sorted(sampled):
+    for k in range(len(traces)):
         a, b = int(off[k]), int(off[k + 1])
-        rp_o, col_o, _ = oracle_csr(traces[k])
-        assert np.array_equal(rp[a:b + 1].astype(np.int64) - int(rp[a]), rp_o), traces[k].name
-        assert np.array_equal(col[rp[a]:rp[b]] - a, col_o), traces[k].name
+        got = oracle_pool.csr_digest(rp[a:b + 1].astype(np.int64) - int(rp[a]), col[rp[a]:rp[b]] - a)
+        assert got == batch_digests[k][0], traces[k].name
     batch = grt.Batch.stacked(g, off)
     batch.execute(replays=20)
     batch.sync()
