@@ -133,27 +133,45 @@ METG_ITERS = [0, 16, 64, 256, 1024, 4096, 16384, 65536]
 METG_STEPS = 1000
 
 
-def run_metg(grt, torch):
+def metg50(gran, eff):
+    """Task Bench's METG(50) from a sweep of task granularities (ascending) and
+    the efficiency measured at each: the granularity at which efficiency first
+    reaches 1/2, interpolated linearly in efficiency and geometrically in
+    granularity between the two samples that straddle it. The first
+    granularity if efficiency is already 1/2 there; None if it never gets there."""
+    if not gran:
+        return None
+    if eff[0] >= 0.5:
+        return float(gran[0])
+    for k in range(1, len(eff)):
+        if eff[k - 1] < 0.5 <= eff[k]:
+            t = (0.5 - eff[k - 1]) / (eff[k] - eff[k - 1])
+            return float(np.exp(np.log(gran[k - 1]) + t * (np.log(gran[k]) - np.log(gran[k - 1]))))
+    return None
+
+
+def run_metg(grt, torch, ns_per_iter):
     """Task Bench's minimum effective task granularity, METG(50) (the paper's
-    overhead metric): stencil graphs of width 8 and 32, 1000 steps, whose task
-    bodies spin a chain of `iters` dependent integer multiply-adds on one lane.
-    Efficiency = (steps x body time) / run time, the body time per iteration
-    calibrated from the two largest counts; granularity = run time per step
-    (per task on its lane); METG(50) = the granularity where efficiency
-    crosses 1/2, for the compiled and the event-based executor."""
+    overhead metric, Section 6): stencil graphs of width 8 and 32, 1000 steps,
+    whose task bodies run Task Bench's floating-point loop, `iters` dependent
+    binary32 FMAs on one lane. Efficiency = useful time / run time, where the
+    useful time of a run is steps x iters x the body's time per iteration
+    measured ALONE on this GPU (one warp running nothing but the loop): one
+    denominator for the box, shared by both executors, so that any time an
+    executor adds to a body counts as overhead. Granularity = run time per
+    step (per task on its lane); METG(50) = the granularity where efficiency
+    reaches 1/2, for the compiled and the event-based executor."""
     res = {"iters": METG_ITERS, "steps": METG_STEPS,
-           "body": "SPIN: a chain of `iters` dependent mad.lo.u32 on one lane per task",
-           "calibration": "each executor's body time per iteration is its own slope between the two largest "
-                          "counts; the event-based one's is about 2x the compiled one's because its ring tickets "
-                          "bind several ready tasks of a step to one warp, which runs their bodies one after "
-                          "another: that is counted as body time here, so METG(50) compares per-step overheads"}
+           "body": "FMA: `iters` dependent fma.rn.f32 (x = x * 0.999f + 0.25f) on one lane per task",
+           "ns_per_iteration_alone": ns_per_iter,
+           "efficiency": "steps x iters x ns_per_iteration_alone / run time (one denominator per box)"}
     for width in (8, 32):
         tr = tg.taskbench(width, METG_STEPS, "stencil", seed=0)
         for kind in ("compiled", "events"):
             walls = []
             for it in METG_ITERS:
                 out = torch.zeros(tr.n, dtype=torch.int32, device="cuda")
-                g = grt.Graph(2, tr.dom_lo, tr.dom_hi, body=grt.RT_BODY_SPIN, spin_iters=it, out=out,
+                g = grt.Graph(2, tr.dom_lo, tr.dom_hi, body=grt.RT_BODY_FMA, spin_iters=it, out=out,
                               flags=grt.RT_GRAPH_PROFILE)
                 g.launch_trace(tr)
                 g.analyze()
@@ -167,19 +185,12 @@ def run_metg(grt, torch):
                         runs.append(g.execute_events())
                 walls.append(float(np.median(runs)))
                 g.close()
-            c = (walls[-1] - walls[-2]) / (METG_STEPS * (METG_ITERS[-1] - METG_ITERS[-2]))  # ms per iteration
-            eff = [METG_STEPS * it * c / w for it, w in zip(METG_ITERS, walls)]
+            eff = [METG_STEPS * it * ns_per_iter * 1e-6 / w for it, w in zip(METG_ITERS, walls)]
             gran = [1e3 * w / METG_STEPS for w in walls]  # us per step = per task on its lane
-            metg = None
-            for k in range(1, len(eff)):
-                if eff[k - 1] < 0.5 <= eff[k]:
-                    t = (0.5 - eff[k - 1]) / (eff[k] - eff[k - 1])
-                    metg = float(np.exp(np.log(gran[k - 1]) + t * (np.log(gran[k]) - np.log(gran[k - 1]))))
-                    break
             res[f"width{width}_{kind}"] = {"ms_per_run": [round(w, 3) for w in walls],
                                           "efficiency": [round(e, 3) for e in eff],
                                           "granularity_us": [round(x, 3) for x in gran],
-                                          "ns_per_iteration": round(c * 1e6, 3), "metg50_us": metg}
+                                          "metg50_us": metg50(gran, eff)}
     for width in (8, 32):
         a, b = res[f"width{width}_events"]["metg50_us"], res[f"width{width}_compiled"]["metg50_us"]
         res[f"width{width}_metg_ratio_events_over_compiled"] = round(a / b, 2) if a and b else None
@@ -324,9 +335,161 @@ def run_served(grt, n_requests=SERVE_REQUESTS, rate=SERVE_RATE):
             "generate_s": gen_s}
 
 
+def run_stencil1d(grt, torch, reps=200):
+    """The 1-D stencil trace (16 pieces x 100 steps = 1600 launches; task (i, t)
+    reads pieces i-1..i+1 and writes piece i, 1024 cells a piece; COUNTER body,
+    seed 0): the latency-bound case, where the overhead per task is all there
+    is. Timed end to end through the C ABI from pinned host arrays (ingest,
+    analysis, one execution and the status read-back, host clock), from inputs
+    already on the device, and as a trace replay (no re-analysis)."""
+    tr = tg.stencil_1d(16, 100)
+    stream = torch.cuda.Stream()
+    state = torch.zeros(16, dtype=torch.int32, device="cuda")
+    host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in
+            (tr.req_off, tr.lo, tr.hi, tr.priv, tr.body_arg)]
+    dev = [a.cuda() for a in host]
+    g = grt.Graph(1, tr.dom_lo, tr.dom_hi, body=grt.RT_BODY_COUNTER, state=state, stream=stream,
+                  flags=grt.RT_GRAPH_PROFILE)
+
+    def one(inp):
+        g.clear()
+        g.launch(*inp[:4], body_arg=inp[4])
+        g.analyze()
+        g.execute()
+        g.sync()
+
+    for _ in range(10):
+        one(host)
+    walls, ana, exe = {}, [], []
+    for name, inp in (("host", host), ("device", dev)):
+        w = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            one(inp)
+            w.append(time.perf_counter() - t0)
+            st = g.stats()
+            ana.append(st["ms_analyze"])
+            exe.append(st["ms_execute"])
+        walls[name] = float(np.median(w))
+    rep_w = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        g.replay(1)
+        g.sync()
+        rep_w.append(time.perf_counter() - t0)
+    n, E = tr.n, g.stats()["n_edges"]
+    g.close()
+    us = lambda x: round(x * 1e6, 2)
+    return {"workload": "1-D stencil, 16 pieces x 100 steps = 1600 launches (reads pieces i-1..i+1, writes piece "
+                        "i; 1024 cells a piece), COUNTER body, one graph at a time", "tasks": n, "edges": E,
+            "us_per_graph_e2e_host": us(walls["host"]), "us_per_graph_device_inputs": us(walls["device"]),
+            "us_per_replay": us(float(np.median(rep_w))),
+            "ns_per_task_e2e_host": round(walls["host"] * 1e9 / n, 1),
+            "ns_per_task_replay": round(float(np.median(rep_w)) * 1e9 / n, 1),
+            "tasks_per_s_e2e_host": n / walls["host"],
+            "kernel_ms": {"analysis": round(float(np.median(ana)), 4), "execution": round(float(np.median(exe)), 4)},
+            "timing": f"host clock around each call sequence, median of {reps}; the graph is 100 steps deep, "
+                      "so execution is a chain of 100+ dependent wavefront steps"}
+
+
+def run_rects_1m(grt, torch, flush, peaks, reps=3):
+    """The implicit-analysis throughput case: 1M launches of 1-4 rectangles on a
+    4096^2 grid (sides log-uniform 16..1024, read/write/reduce 60/30/10 %,
+    seed 0), inputs resident on the device, analysed at the tuned tile.
+    Algorithmic bytes: each launch's offset (4 B) and rectangles (2 x 2 x 8 +
+    1 B each) read once, the CSR written once (row_ptr and in-degree 8 B per
+    task, 4 B per edge)."""
+    t0 = time.perf_counter()
+    tr = tg.random_rects(grid=(4096, 4096), n=1_000_000, seed=0)
+    gen_s = time.perf_counter() - t0
+    tile = list(grt.rt_tune_tile(tr, TUNE_CACHE)[:2])
+    stream = torch.cuda.Stream()
+    dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (tr.req_off, tr.lo, tr.hi, tr.priv)]
+    host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (tr.req_off, tr.lo, tr.hi, tr.priv)]
+    g = grt.Graph(2, tr.dom_lo, tr.dom_hi, tile=tile, stream=stream, flags=grt.RT_GRAPH_PROFILE)
+    runs, walls, e2e = [], [], []
+    for k in range(reps + 1):  # the first run grows the buffers
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 255)
+        stream.synchronize()
+        t0 = time.perf_counter()
+        g.clear()
+        g.launch(*dev, defer_check=True)
+        g.analyze()
+        stream.synchronize()
+        if k:
+            walls.append(time.perf_counter() - t0)
+            runs.append(g.stats())
+    for k in range(reps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 255)
+        stream.synchronize()
+        t0 = time.perf_counter()
+        g.clear()
+        g.launch(*host, defer_check=True)
+        g.analyze()
+        stream.synchronize()
+        e2e.append(time.perf_counter() - t0)
+    g.close()
+    st = runs[-1]
+    n, R, E = tr.n, tr.n_rects, st["n_edges"]
+    ms = float(np.median([r["ms_analyze"] for r in runs]))
+    algo = 4 * n + 33 * R + 8 * n + 4 * E
+    inter = 2 * 12 * st["n_entries"] + 2 * 8 * st["n_pairs"]
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    med = lambda key: round(float(np.median([r[key] for r in runs])), 3)
+    return {"workload": "1M launches of 1-4 rectangles on 4096^2 (sides log-uniform 16..1024, read/write/reduce "
+                        "60/30/10 %), seed 0; inputs on the device; analysis only", "tasks": n, "rects": R,
+            "edges": E, "entries": st["n_entries"], "pairs": st["n_pairs"],
+            "pairs_per_edge": round(st["n_pairs"] / max(E, 1), 2), "tile": tile,
+            "ms_analyze": round(ms, 3), "launches_per_s": n / (ms * 1e-3), "ns_per_launch": round(ms * 1e6 / n, 2),
+            "wall_ms_device_inputs": round(1e3 * float(np.median(walls)), 3),
+            "wall_ms_e2e_host": round(1e3 * float(np.median(e2e)), 3),
+            "phases_ms": {k: med(k) for k in ("ms_bin", "ms_sort_entries", "ms_sweep", "ms_sort_pairs", "ms_csr")},
+            "hbm": {"algorithmic_bytes": algo, "intermediate_bytes": inter, "achieved_gbs": algo / (ms * 1e-3) / 1e9,
+                    "peak_gbs": peak, "frac": algo / (ms * 1e-3) / 1e9 / peak},
+            "generate_s": round(gen_s, 2), "timed_runs": reps,
+            "l2": "flushed before each run (512 MB write)"}
+
+
 # ---------------------------------------------------------------------------
 # the oracle, timed on host cores (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
+def host_info():
+    """The host the CPU numbers were taken on: core count and CPU model."""
+    info = {"nproc": os.cpu_count(), "arch": os.uname().machine}
+    try:
+        info["affinity_cpus"] = len(os.sched_getaffinity(0))
+    except Exception:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            k, _, v = line.partition(":")
+            if k.strip() in ("Model name", "Vendor ID", "CPU(s)", "Thread(s) per core", "Core(s) per socket",
+                             "Socket(s)", "CPU max MHz"):
+                info["lscpu_" + k.strip().lower().replace(" ", "_").replace("(s)", "s")] = v.strip()
+    except Exception:
+        pass
+    return info
+
+
+def oracle_threaded_step(traces, threads):
+    """The oracle on `threads` host threads: interval-map analysis (rows split
+    across threads) and Algorithm 1's countdown executor (shared ready queue),
+    EMPTY bodies. Returns (analysis s, execution s)."""
+    import oracle
+    ta = te = 0.0
+    for tr in traces:
+        t0 = time.perf_counter()
+        rp, col = oracle.analyze_intervals(tr, threads)
+        ta += time.perf_counter() - t0
+        t0 = time.perf_counter()
+        oracle.alg1_run(tr.n, rp, col, threads)
+        te += time.perf_counter() - t0
+    return ta, te
+
+
 def oracle_step(traces):
     import oracle
     t0 = time.perf_counter()
@@ -375,17 +538,20 @@ def run_reference(args):
         return 0
     traces = load_traces(args)
     n_tasks = sum(t.n for t in traces)
+    cores = os.cpu_count() or 1
     for _ in range(args.warmup):
-        oracle_step(traces)
-    times = [oracle_step(traces) for _ in range(args.steps)]
+        oracle_threaded_step(traces, cores)
+    times = [sum(oracle_threaded_step(traces, cores)) for _ in range(args.steps)]
     total = sum(times)
     value = n_tasks * args.steps / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "ns_per_task": 1e9 / value, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int32", "data": "synthetic", "config": config(n_tasks, args),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "each step = the full workload: per-cell oracle analysis + Kahn order"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "each step = the full workload: interval-map oracle analysis and "
+                                       "Algorithm 1's countdown executor (shared ready queue), both on every "
+                                       "host core", "host": host_info()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -476,6 +642,25 @@ def committed_traffic(name):
     except Exception:
         return None
     return d["bytes_per_launch"] if d.get("source_sha") == kernel_source_sha(name) else None
+
+
+def atomic_roofline_line(per_graph, mb):
+    """The dominant kernel, the persistent executor, against the measured atomic
+    roofline: algorithmic atomics per launch = E (one countdown decrement per
+    edge) + 2 N / 32 (one ring reservation and one claim per 32-task warp
+    batch), divided by the kernel's CUDA-event time, against the measured rate
+    of scattered atomicSub on distinct addresses with the result used."""
+    t_exec = sum(g["ms_exec_kernel"] for g in per_graph)
+    atoms = sum(g["E"] + 2.0 * g["n"] / 32.0 for g in per_graph)
+    launches = len(per_graph)
+    achieved = (atoms / launches) / (t_exec / launches * 1e-3) / 1e9
+    peak = mb["scatter_atomic_gops"]
+    return {"kernel": "k_exec (persistent executor)", "bound": "atomic", "achieved": achieved, "peak": peak,
+            "unit": "Gatomic/s", "frac": achieved / peak, "traffic": committed_traffic("exec"),
+            "traffic_unit": "DRAM bytes per launch (ncu)",
+            "algorithmic_atomics_per_launch": atoms / launches, "avg_launch_ms": t_exec / launches,
+            "peak_source": "measured in this run: scattered int32 atomicSub on distinct addresses, result used "
+                           "(rt_microbench_atomics)", "share_of_step": None}
 
 
 def roofline(per_graph, peaks):
@@ -638,9 +823,12 @@ def run_ours(args):
     batched = None
     if world == 1 and not args.no_batched:
         batched = run_batched(grt, torch, flush, max(1, min(args.steps, 3)))
+    # the executor's own rooflines (dependent atomic latency, scattered atomics)
+    # and the FMA body's rate alone
+    mb = grt.rt_microbench_atomics()
     metg = None
     if world == 1 and not args.no_metg:
-        metg = run_metg(grt, torch)
+        metg = run_metg(grt, torch, mb["fma_body_ns_per_iter"])
     async_nodes = stitched = None
     if world == 1 and not args.no_extras:
         async_nodes = run_async_nodes(grt, torch)
@@ -655,8 +843,6 @@ def run_ours(args):
             k: calm[k] for k in ("offered_graphs_per_s", "achieved_graphs_per_s", "tasks_per_s", "latency_ms",
                                  "service_ms", "analysis_ms", "mean_batch")}
 
-    # the executor's own rooflines (dependent atomic latency, scattered atomics)
-    mb = grt.rt_microbench_atomics()
     value = world * n_tasks * args.steps / (total_ms * 1e-3)
     e2e_value = None if args.no_e2e else n_tasks * args.steps / (sum(e2e_ms) * 1e-3)
     avg = [{k: float(np.mean([p[i][k] for p in per])) for k in per[0][i]} for i in range(len(graphs))]
@@ -708,9 +894,15 @@ def run_ours(args):
                         "multiply-adds on its critical path"}
 
     peaks = measured_peaks()
-    roof = roofline(avg, peaks)
+    roof_hbm = roofline(avg, peaks)
+    roof = atomic_roofline_line(avg, mb)
     # executor kernel time over step time; above 1 when the graphs' executions overlap
-    roof["share_of_step"] = (roof["avg_launch_ms"] * len(graphs)) / (total_ms / args.steps) if world == 1 else None
+    for r in (roof, roof_hbm):
+        r["share_of_step"] = (r["avg_launch_ms"] * len(graphs)) / (total_ms / args.steps) if world == 1 else None
+    stencil1d = rects_1m = None
+    if world == 1 and not args.no_extras:
+        stencil1d = run_stencil1d(grt, torch)
+        rects_1m = run_rects_1m(grt, torch, flush, peaks)
     # the analysis against HBM: algorithmic bytes are the launches and
     # rectangles read once and the CSR written once (req_off 4 B per task,
     # 2 x ndim x 8 + 1 B per rectangle; row_ptr and indeg 8 B per task, col
@@ -745,10 +937,23 @@ def run_ours(args):
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
+            cores = os.cpu_count() or 1
+            ta, te = oracle_threaded_step(traces, cores)
+            t1a, t1e = oracle_threaded_step(traces, 1)
             secs = oracle_step(traces)
-            cpu = {"value": n_tasks / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": "one pass of the full workload (3 graphs, 3.07M tasks): per-cell oracle analysis "
-                             "+ Kahn order, single thread", "seconds": secs}
+            cpu = {"value": n_tasks / (ta + te), "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": "one pass of the full workload (3 graphs, 3.07M tasks, EMPTY bodies): interval-map "
+                             "oracle analysis (rows split over every host core) + Algorithm 1's countdown "
+                             "executor (atomic countdowns, one shared ready queue, every host core)",
+                   "analysis_s": round(ta, 3), "execution_s": round(te, 3),
+                   "analysis_tasks_per_s": n_tasks / ta, "execution_tasks_per_s": n_tasks / te,
+                   "one_thread": {"analysis_s": round(t1a, 3), "execution_s": round(t1e, 3),
+                                  "value": n_tasks / (t1a + t1e)},
+                   "per_cell_oracle_one_thread": {"value": n_tasks / secs, "seconds": round(secs, 3),
+                                                  "what": "per-cell oracle analysis + Kahn order"},
+                   "note": "with EMPTY bodies the threaded executor is slower than one thread: every decrement "
+                           "moves a counter's cache line between cores",
+                   "host": host_info()}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "ns_per_task": 1e9 / value * world,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
@@ -761,7 +966,8 @@ def run_ours(args):
                 "sequential": {"ms_per_step": sum(seq_ms) / args.steps,
                                "value": n_tasks * args.steps / (sum(seq_ms) * 1e-3),
                                "note": "the three graphs one after another, no overlap between them"},
-                "roofline": roof, "analysis_roofline": analysis_roof, "atomic_roofline": atomic_roof,
+                "roofline": roof, "roofline_hbm": roof_hbm, "analysis_roofline": analysis_roof,
+                "atomic_roofline": atomic_roof, "stencil_1d": stencil1d, "rects_1m": rects_1m,
                 "spin_bodies": spin, "event_executor": events,
                 "cpu_baseline": cpu, "clocks": clk,
                 "gpu_launches": launches,

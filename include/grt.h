@@ -66,16 +66,19 @@ typedef enum {
 /* privileges of a region requirement */
 enum { RT_READ = 0, RT_WRITE = 1, RT_REDUCE_SUM = 2 };
 
-/* task bodies run in place by the executor (all integer, sums wrap mod 2^32)
+/* task bodies run in place by the executor (integer sums wrap mod 2^32)
  *  EMPTY   nothing (pure runtime overhead)
  *  SPIN    x = task id; spin_iters times x = x*1664525 + 1013904223; out[task] = x
+ *  FMA     x = (float)task id; spin_iters times x = fma(x, 0.999f, 0.25f) in IEEE
+ *          binary32, round to nearest even; out[task] = the bits of x (the
+ *          floating-point loop of Task Bench's compute-bound kernel)
  *  COUNTER state[body_arg[task]] += 1 (plain, non-atomic read-modify-write)
  *  CHECK   acc = mix32(task, sum of state over the task's read cells);
  *          state[c] = mix32(acc, c) on its write cells;
  *          state[c] += mix32(task, c) on its reduce cells (atomic);
  *          out[task] = acc.  mix32(a, b) = fmix32(a ^ (b * 0x9E3779B1)),
  *          fmix32 = murmur3's finaliser; c = row-major cell index.            */
-enum { RT_BODY_EMPTY = 0, RT_BODY_SPIN = 1, RT_BODY_COUNTER = 2, RT_BODY_CHECK = 3 };
+enum { RT_BODY_EMPTY = 0, RT_BODY_SPIN = 1, RT_BODY_COUNTER = 2, RT_BODY_CHECK = 3, RT_BODY_FMA = 4 };
 
 /* rt_launch_batch flags */
 enum {
@@ -95,11 +98,11 @@ typedef struct {
   int32_t ndim;                   /* 1 or 2 */
   int64_t dom_lo[2], dom_hi[2];   /* inclusive domain bounds (index 1 unused for 1-D) */
   int32_t body;                   /* RT_BODY_* */
-  int32_t spin_iters;             /* SPIN: iteration count (>= 0) */
+  int32_t spin_iters;             /* SPIN, FMA: iteration count (>= 0) */
   void* state;                    /* int32 device buffer, caller-owned: one per cell
                                      (CHECK, row-major) or per counter (COUNTER) */
   int64_t state_elems;
-  void* out;                      /* int32 device buffer, one per task (SPIN, CHECK) */
+  void* out;                      /* int32 device buffer, one per task (SPIN, FMA, CHECK) */
   int64_t out_elems;
   void* stream;                   /* cudaStream_t; NULL = legacy default stream */
   int32_t tile_w, tile_h;         /* analysis tile in cells; 0 = library default */
@@ -361,9 +364,16 @@ typedef struct {
   int32_t ndim;                  /* every request shares this domain and tiling */
   int64_t dom_lo[2], dom_hi[2];
   int32_t tile_w, tile_h;        /* 0 = library default */
-  int32_t body;                  /* RT_BODY_EMPTY or RT_BODY_SPIN */
+  int32_t body;                  /* RT_BODY_EMPTY, RT_BODY_SPIN or RT_BODY_CHECK. A served body
+                                    sees its request alone: task ids from 0 within the request
+                                    and, for CHECK, the request's own zeroed state (one int32
+                                    per cell of this domain, row-major), so every result equals
+                                    that of the request run by itself */
   int32_t spin_iters;
-  int64_t budget_bytes;          /* device memory admitted requests may hold at once */
+  int64_t budget_bytes;          /* device memory the analysed requests' graphs may hold at
+                                    once, retained buffers included (the fixed pool allocated
+                                    at creation is apart): each batch graph grows under a cap
+                                    that keeps the sum within it */
   int32_t max_inflight;          /* graphs admitted at once, 1..1024 */
   int32_t max_tasks;             /* tasks of the largest request accepted */
   int32_t workers;               /* host threads analysing requests, 1..64 */
@@ -402,10 +412,19 @@ rt_status rt_server_submit(rt_server_t s, int32_t n, const int32_t* req_off, con
 rt_status rt_server_poll(rt_server_t s, int64_t ticket, rt_request_info* info);
 
 /* With keep_results: copies a finished request's canonical CSR (row_ptr
- * int32[n+1], col int32[E]) and, for SPIN, its outputs (int32[n]) into host
- * buffers (any may be NULL). RT_ERR_STATE if it is not done; a request that
- * failed returns its own status, with the reason in rt_last_error(). */
+ * int32[n+1], col int32[E]) and, for SPIN and CHECK, its outputs (int32[n])
+ * into host buffers (any may be NULL). RT_ERR_STATE if it is not done; a
+ * request that failed returns its own status, with the reason in
+ * rt_last_error(). */
 rt_status rt_server_result(rt_server_t s, int64_t ticket, int32_t* row_ptr, int32_t* col, int32_t* out);
+
+/* With keep_results and the CHECK body: copies a finished request's final
+ * state (int32, one per cell of the server's domain, row-major) into a host
+ * buffer. The order-sensitive CHECK body makes this the proof that the
+ * request's edges were respected while it ran beside others (Algorithm 1:
+ * a task runs only after all its predecessors). Errors as rt_server_result;
+ * RT_ERR_STATE if the server does not run CHECK bodies or keep results. */
+rt_status rt_server_result_state(rt_server_t s, int64_t ticket, int32_t* state);
 
 /* Waits until every submitted request is done or failed (or timeout_ns
  * passes: RT_ERR_TIMEOUT), or the serving kernel reported a stall. */
@@ -414,7 +433,13 @@ rt_status rt_server_drain(rt_server_t s, int64_t timeout_ns);
 /* Diagnostics: out[0] activations posted, [1] taken by the kernel, [2]
  * finished, [3] kernel status, [4] tasks executed, [5] requests queued, [6]
  * analysing, [7] running, [8] 1 while the serving kernel runs, [9] batches
- * analysed, [10] requests in them. */
+ * analysed, [10] requests in them; the memory budget: [11] bytes the batch
+ * graphs may hold now (caps of batches in analysis, retained buffers of the
+ * others; never above budget_bytes), [12] its peak, [13] bytes the batch
+ * graphs hold after their last analyses, [14] its peak, [15] bytes of the
+ * fixed pool allocated at creation (ring, slot table, per-batch outputs and
+ * CHECK states: not request memory), [16] retained graphs trimmed to make
+ * room, [17] batches that outgrew their cap and were admitted again. */
 rt_status rt_server_stats(rt_server_t s, int64_t* out, int32_t n);
 
 /* Drains (30 s at most), asks the serving kernel to stop once idle (forcing it
@@ -442,26 +467,33 @@ rt_status rt_device_info(int32_t* num_sms, int32_t* exec_blocks_per_sm);
  *          be a later task id (src < dst) and indeg must match the columns
  *  out     int32[n_tasks] device buffer: the SPIN body's result per task
  *          (x = task id; spin_iters times x = x*1664525 + 1013904223)
+ *  tickets NULL, or an int32[2*n_tasks] device buffer, caller-owned: task v's
+ *          start and finish tickets at [2v] and [2v+1], drawn from one counter,
+ *          so the caller can check that every edge's source finished first
  *  stream  cudaStream_t (NULL = legacy default stream)
  * Synchronous: validates the CSR on the device (RT_ERR_INVALID if it is
- * malformed), runs it once and returns the executor's status. n_tasks may be
- * at most 262144 (2^18); larger graphs get RT_ERR_INVALID. No cudaMalloc,
- * cudaFree or allocating library call is made. The first call on a device looks
- * up the array's device address once; make that first call before capturing
- * any stream. All calls share the one array and it keeps the previous call's
- * contents (each call re-initialises what it needs), so calls whose GPU work
- * overlaps -- from several streams or host threads -- race and corrupt each
- * other: the caller must serialise them. */
+ * malformed), runs it once and returns the executor's status; it reads flags
+ * back into host memory, so it must not be called on a stream that is being
+ * captured (RT_ERR_STATE). A CUDA error already pending when it is called is
+ * reported as RT_ERR_CUDA before anything is launched. n_tasks may be at most
+ * 262144 (2^18); larger graphs get RT_ERR_INVALID. No cudaMalloc, cudaFree or
+ * allocating library call is made. The first call on a device looks up the
+ * array's device address once. All calls share the one array and it keeps the
+ * previous call's contents (each call re-initialises what it needs), so calls
+ * whose GPU work overlaps -- from several streams or host threads -- race and
+ * corrupt each other: the caller must serialise them. */
 rt_status rt_execute_csr_static(const int32_t* row_ptr, const int32_t* col, const int32_t* indeg,
                                 int32_t n_tasks, int64_t n_edges, int32_t spin_iters, int32_t* out,
-                                void* stream);
+                                int32_t* tickets, void* stream);
 
 /* The executor's rooflines, measured on the current device (synchronous,
  * allocates a 64 MB scratch array): out[0] dependent atomic latency (ns),
  * out[1] dependent L2 load latency (ns), out[2] scattered atomicSub throughput
  * with the result used (G ops/s), out[3] the same without using the result,
  * out[4] contended single-address atomicAdd (G ops/s), out[5] the same
- * warp-aggregated (G thread-ops/s). n = how many of the six to return. */
+ * warp-aggregated (G thread-ops/s), out[6] the FMA body alone: ns per
+ * dependent iteration on one warp (Task Bench's peak for its efficiency).
+ * n = how many of the seven to return. */
 rt_status rt_microbench_atomics(double* out, int32_t n, void* stream);
 
 /* Total number of kernels this library has launched in the process (for

@@ -7,12 +7,14 @@ from .oracle import (  # noqa: F401
     BODY_CHECK,
     BODY_COUNTER,
     BODY_EMPTY,
+    BODY_FMA,
     BODY_SPIN,
     alg1_run,
     analyze,
     analyze_intervals,
     build,
     csr_from_pairs,
+    fma_bits,
     mix32,
     run_bodies,
     spin,

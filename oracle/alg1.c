@@ -15,13 +15,14 @@
  *  - COMPLETED_EDGE: for each out-edge the worker atomically decrements the
  *    successor's countdown; the decrement that finds 1 (the last pending
  *    edge) queues the successor.
- * The queue is an array of n slots: producers reserve a slot with one atomic
- * add on the tail and publish the task with a release store; consumers claim
- * the next slot with a compare-and-swap on the head (never past n) and wait
- * for it to be published. Every task is queued exactly once, so the run ends
- * when all n slots have been claimed and executed. Waiting cannot deadlock on
- * an acyclic graph: while tasks remain, some queued task is unclaimed or
- * running, and its completion publishes the next ones.
+ * A worker that makes successors ready keeps the first of them and runs it
+ * next (Algorithm 1's EXECUTE_OP message a worker sends itself); the others
+ * go to the shared queue, an array of n slots: producers reserve a slot with
+ * one atomic add on the tail and publish the task with a release store;
+ * consumers claim the next reserved slot with a compare-and-swap on the head
+ * (never past the tail) and wait for the producer's store, which follows its
+ * reservation at once. A worker adds the tasks it ran to the shared completion
+ * count when it finds no work, and every worker leaves once that count is n.
  *
  * Bodies: EMPTY (nothing), SPIN (out[v] = the LCG x = 1664525 x + 1013904223
  * iterated spin_iters times from x = v), COUNTER (state[body_arg[v]] += 1,
@@ -46,7 +47,7 @@ typedef struct {
   const int32_t* col;
   atomic_int* count;
   atomic_int* slot;
-  atomic_int head, tail, ticket;
+  atomic_int head, tail, ticket, done;
   int32_t body, spin_iters;
   const int32_t* body_arg;
   int32_t* state;
@@ -65,16 +66,30 @@ static void* a1_worker(void* arg) {
   unsigned wait = 0;
   while (!atomic_load_explicit(&J->go, memory_order_acquire))
     if (++wait > 256) sched_yield();
+  int local = -1; /* a ready successor this worker runs next */
+  int ran = 0;    /* tasks run, not yet added to the completion count */
+  unsigned idle = 0;
   for (;;) {
-    int h = atomic_load_explicit(&J->head, memory_order_relaxed);
-    if (h >= J->n) break;
-    if (!atomic_compare_exchange_weak_explicit(&J->head, &h, h + 1, memory_order_relaxed,
-                                               memory_order_relaxed))
-      continue;
-    int v;
-    unsigned spins = 0;
-    while ((v = atomic_load_explicit(&J->slot[h], memory_order_acquire)) < 0)
-      if (++spins > 256) sched_yield();
+    int v = local;
+    local = -1;
+    if (v < 0) {
+      int h = atomic_load_explicit(&J->head, memory_order_relaxed);
+      if (h >= atomic_load_explicit(&J->tail, memory_order_relaxed)) {
+        if (ran) {
+          atomic_fetch_add_explicit(&J->done, ran, memory_order_relaxed);
+          ran = 0;
+        }
+        if (atomic_load_explicit(&J->done, memory_order_relaxed) >= J->n) break;
+        if (++idle > 64) sched_yield();
+        continue;
+      }
+      if (!atomic_compare_exchange_weak_explicit(&J->head, &h, h + 1, memory_order_relaxed,
+                                                 memory_order_relaxed))
+        continue;
+      while ((v = atomic_load_explicit(&J->slot[h], memory_order_acquire)) < 0) {
+      }
+    }
+    idle = 0;
     if (J->tickets) J->tickets[2 * (int64_t)v] = atomic_fetch_add(&J->ticket, 1);
     if (J->body == A1_SPIN) {
       J->out[v] = (int32_t)a1_spin((uint32_t)v, J->spin_iters);
@@ -83,11 +98,16 @@ static void* a1_worker(void* arg) {
       J->state[k] = (int32_t)((uint32_t)J->state[k] + 1u);
     }
     if (J->tickets) J->tickets[2 * (int64_t)v + 1] = atomic_fetch_add(&J->ticket, 1);
+    ++ran;
     for (int64_t e = J->row_ptr[v]; e < J->row_ptr[v + 1]; ++e) {
       const int s = J->col[e];
       if (atomic_fetch_sub_explicit(&J->count[s], 1, memory_order_acq_rel) == 1) {
-        const int t = atomic_fetch_add_explicit(&J->tail, 1, memory_order_relaxed);
-        atomic_store_explicit(&J->slot[t], s, memory_order_release);
+        if (local < 0) {
+          local = s;
+        } else {
+          const int t = atomic_fetch_add_explicit(&J->tail, 1, memory_order_relaxed);
+          atomic_store_explicit(&J->slot[t], s, memory_order_release);
+        }
       }
     }
   }
@@ -148,6 +168,7 @@ int32_t orc_alg1_run(int32_t n, const int64_t* row_ptr, const int32_t* col, int3
   atomic_init(&J.head, 0);
   atomic_init(&J.tail, roots);
   atomic_init(&J.ticket, 0);
+  atomic_init(&J.done, 0);
   atomic_store_explicit(&J.go, 1, memory_order_release);
   if (started == 0) a1_worker(&J); /* no thread could start: run on the caller's */
   for (int t = 0; t < started; ++t) pthread_join(tid[t], NULL);

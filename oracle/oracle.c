@@ -31,7 +31,9 @@
  *                 every node without incoming edges, COMPLETED_EDGE releases a
  *                 node when its last incoming edge is removed).
  *  orc_run        executes the task bodies in a given order (NULL = program
- *                 order, i.e. sequential semantics).
+ *                 order, i.e. sequential semantics): EMPTY, SPIN (integer
+ *                 LCG), FMA (Section 6's floating-point task loop), COUNTER
+ *                 and the order-sensitive CHECK.
  *
  * Parity: O1/O2 themselves are a reading of the paper, pinned by brute force
  * (pairwise run-boundary count, interference soundness and completeness) and
@@ -39,6 +41,7 @@
  * four-task DAG and by "execution in any topological order equals program
  * order" properties.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -339,6 +342,7 @@ int64_t orc_topo_order(int32_t n, const int64_t* row_ptr, const int32_t* col, in
 #define BODY_SPIN 1
 #define BODY_COUNTER 2
 #define BODY_CHECK 3
+#define BODY_FMA 4
 
 /* murmur3's 32-bit finaliser */
 static uint32_t orc_fmix32(uint32_t h) {
@@ -355,6 +359,17 @@ uint32_t orc_mix32(uint32_t a, uint32_t b) { return orc_fmix32(a ^ (b * 0x9E3779
 uint32_t orc_spin(uint32_t x, int32_t iters) {
   for (int32_t k = 0; k < iters; ++k) x = x * 1664525u + 1013904223u;
   return x;
+}
+
+/* The floating-point loop of a compute-bound Task Bench kernel (Section 6):
+ * x = (float)task, then `iters` fused multiply-adds x = x * 0.999f + 0.25f in
+ * binary32, each rounded once to nearest even (C99 fmaf). Returns x's bits. */
+uint32_t orc_fma(uint32_t task, int32_t iters) {
+  float x = (float)task;
+  for (int32_t k = 0; k < iters; ++k) x = fmaf(x, 0.999f, 0.25f);
+  uint32_t bits;
+  memcpy(&bits, &x, 4);
+  return bits;
 }
 
 /* Runs the bodies of tasks order[0..count) (order == NULL: 0..n-1).
@@ -384,6 +399,8 @@ int32_t orc_run(int32_t ndim, const int64_t* dom_lo, const int64_t* dom_hi, int3
     int32_t j = order ? order[q] : (int32_t)q;
     if (body == BODY_SPIN) {
       out[j] = (int32_t)orc_spin((uint32_t)j, spin_iters);
+    } else if (body == BODY_FMA) {
+      out[j] = (int32_t)orc_fma((uint32_t)j, spin_iters);
     } else if (body == BODY_COUNTER) {
       int32_t k = body_arg[j];
       state[k] = (int32_t)((uint32_t)state[k] + 1u);

@@ -26,7 +26,7 @@ _SO = os.path.join(_LIBDIR, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-BODY_EMPTY, BODY_SPIN, BODY_COUNTER, BODY_CHECK = 0, 1, 2, 3
+BODY_EMPTY, BODY_SPIN, BODY_COUNTER, BODY_CHECK, BODY_FMA = 0, 1, 2, 3, 4
 
 
 def build(force: bool = False) -> str:
@@ -34,7 +34,7 @@ def build(force: bool = False) -> str:
     os.makedirs(_LIBDIR, exist_ok=True)
     if force or not os.path.exists(_SO) or any(os.path.getmtime(_SO) < os.path.getmtime(s) for s in _SRCS):
         tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread", "-o", tmp] + _SRCS)
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread", "-o", tmp] + _SRCS + ["-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -65,6 +65,8 @@ def _load(path: str = None):
         lib.orc_mix32.argtypes = [u32, u32]
         lib.orc_spin.restype = u32
         lib.orc_spin.argtypes = [u32, i32]
+        lib.orc_fma.restype = u32
+        lib.orc_fma.argtypes = [u32, i32]
         if hasattr(lib, "orc_b3_analyze"):  # absent from a single-file build of oracle.c
             lib.orc_b3_analyze.restype = P
             lib.orc_b3_analyze.argtypes = [i32, P, P, i32, P, P, P, P, P, P, i32]
@@ -200,3 +202,8 @@ def mix32(a: int, b: int) -> int:
 
 def spin(x: int, iters: int) -> int:
     return int(_load().orc_spin(x & 0xffffffff, iters))
+
+
+def fma_bits(task: int, iters: int) -> int:
+    """Bits of the FMA body's result for this task (binary32)."""
+    return int(_load().orc_fma(task & 0xffffffff, iters))

@@ -48,6 +48,13 @@ rt_status fail(rt_status s, const char* fmt, ...) {
     if (r_ != RT_OK) return r_;             \
   } while (0)
 
+// A graph whose device bytes are capped (the server gives each batch graph a
+// share of its memory budget): while a call grows that graph's buffers on this
+// thread, every growth that would take the graph past its cap fails with
+// RT_ERR_BUDGET instead of allocating. Null: no cap applies.
+thread_local const rt_graph* t_capped = nullptr;
+bool over_cap(size_t grow_by);  // defined after rt_graph
+
 // grow-only device buffer, allocated stream-ordered on its owner's stream:
 // cudaMallocAsync / cudaFreeAsync never wait for work on other streams (a
 // plain cudaFree would wait for the whole device, including a serving kernel
@@ -59,6 +66,10 @@ struct DevBuf {
     if (bytes <= cap && p) return RT_OK;
     size_t nc = std::max<size_t>(bytes, keep ? cap * 2 : bytes);
     nc = std::max<size_t>(nc, 256);
+    // the old buffer is freed only after the new one exists (and, with `keep`,
+    // after the copy), so the graph briefly holds both
+    if (t_capped && over_cap(nc))
+      return fail(RT_ERR_BUDGET, "growing a buffer to %zu bytes would pass the graph's memory cap", nc);
     void* np = nullptr;
     cudaError_t e = cudaMallocAsync(&np, nc, s);
     if (e != cudaSuccess) {
@@ -163,7 +174,39 @@ struct rt_graph {
   bool gt_valid = false;
   int exec_blocks = 0, exec_warps = 8;
   int cfg_blocks = 0, cfg_warps = 0, cfg_claim = 0, cfg_keep = 0;  // rt_graph_exec_config
+  size_t mem_cap = 0;  // device bytes the graph may hold while it grows (0 = no cap; set by a server)
 };
+
+namespace {
+// every device buffer a graph holds (its footprint is the sum of their capacities)
+template <class G, class F>
+void for_each_buf(G* g, F f) {
+  auto bufs = {&g->req_off, &g->lo, &g->hi, &g->priv, &g->pred_off, &g->pred, &g->body_arg, &g->err,
+                &g->rect_task, &g->cnt, &g->keys, &g->keys_alt, &g->pay, &g->pay_alt, &g->seg_b, &g->seg_e,
+                &g->pairs, &g->pairs_alt, &g->flags, &g->upos, &g->col, &g->row_ptr, &g->indeg, &g->count,
+                &g->rootpos, &g->root_items, &g->ws, &g->misc, &g->adj, &g->ring, &g->ctrl, &g->gtable,
+                &g->done_g, &g->tickets, &g->tflags, &g->ev_pred_off, &g->ev_pred, &g->ev_head, &g->ev_pending,
+                &g->ev_nodes, &g->ev_ring, &g->ev_ctrl, &g->ksink, &g->st_count, &g->st_ring, &g->st_ctrl,
+                &g->st_tickets, &g->st_err};
+  for (auto* b : bufs) f(*b);
+}
+
+size_t footprint_of(const rt_graph* g) {
+  size_t f = 0;
+  for_each_buf(g, [&](const DevBuf& b) { f += b.cap; });
+  return f;
+}
+
+bool over_cap(size_t grow_by) { return footprint_of(t_capped) + grow_by > t_capped->mem_cap; }
+
+// applies the graph's memory cap to the buffers this thread grows until the
+// scope ends
+struct CapScope {
+  const rt_graph* saved;
+  explicit CapScope(const rt_graph* g) : saved(t_capped) { t_capped = g->mem_cap ? g : nullptr; }
+  ~CapScope() { t_capped = saved; }
+};
+}  // namespace
 
 struct rt_batch {
   cudaStream_t s = nullptr;
@@ -215,7 +258,7 @@ rt_status check_desc(const rt_graph_desc* d, AnalysisDims* out, int64_t* ncells)
       a.ext[k] = 1;
     }
   }
-  if (d->body < RT_BODY_EMPTY || d->body > RT_BODY_CHECK) return fail(RT_ERR_INVALID, "unknown body %d", d->body);
+  if (d->body < RT_BODY_EMPTY || d->body > RT_BODY_FMA) return fail(RT_ERR_INVALID, "unknown body %d", d->body);
   if (d->spin_iters < 0) return fail(RT_ERR_INVALID, "spin_iters < 0");
   if (d->state_elems < 0 || d->out_elems < 0 || d->timeout_ns < 0)
     return fail(RT_ERR_INVALID, "negative size");
@@ -306,15 +349,7 @@ rt_status rt_graph_destroy(rt_graph_t g) {
     cudaStreamDestroy(st);
   }
   for (cudaEvent_t e : g->kevents) cudaEventDestroy(e);
-  g->ksink.release(g->s);
-  DevBuf* bufs[] = {&g->req_off, &g->lo, &g->hi, &g->priv, &g->pred_off, &g->pred, &g->body_arg,
-                    &g->err, &g->rect_task, &g->cnt, &g->keys, &g->keys_alt, &g->pay, &g->pay_alt,
-                    &g->seg_b, &g->seg_e, &g->pairs, &g->pairs_alt, &g->flags, &g->upos, &g->col,
-                    &g->row_ptr, &g->indeg, &g->count, &g->rootpos, &g->root_items, &g->ws, &g->misc, &g->adj,
-                    &g->ring, &g->ctrl, &g->gtable, &g->done_g, &g->tickets, &g->tflags,
-                    &g->ev_pred_off, &g->ev_pred, &g->ev_head, &g->ev_pending, &g->ev_nodes, &g->ev_ring,
-                    &g->ev_ctrl};
-  for (DevBuf* b : bufs) b->release(g->s);
+  for_each_buf(g, [&](DevBuf& b) { b.release(g->s); });
   cudaStreamSynchronize(g->s);
   if (g->hpin) cudaFreeHost(g->hpin);
   if (g->ev_ok)
@@ -384,6 +419,7 @@ extern "C" rt_status rt_launch_batch(rt_graph_t g, int32_t n, const int32_t* req
   if (!g) return fail(RT_ERR_INVALID, "graph is NULL");
   if (g->analyzed) return fail(RT_ERR_STATE, "graph already analyzed; call rt_graph_clear first");
   if (n < 0) return fail(RT_ERR_INVALID, "n < 0");
+  CapScope cap_scope(g);
   if (n == 0) return RT_OK;
   if (!req_off) return fail(RT_ERR_INVALID, "req_off is NULL");
   if ((pred_off == nullptr) != (pred == nullptr))
@@ -691,9 +727,10 @@ rt_status run_analysis(rt_graph* g) {
 extern "C" rt_status rt_analyze(rt_graph_t g) {
   if (!g) return fail(RT_ERR_INVALID, "graph is NULL");
   if (g->analyzed) return RT_OK;
+  CapScope cap_scope(g);
   const int body = g->desc.body;
-  if ((body == RT_BODY_SPIN || body == RT_BODY_CHECK) && (!g->desc.out || g->desc.out_elems < g->n))
-    return fail(RT_ERR_INVALID, "SPIN/CHECK bodies need `out` with one int32 per task (%d)", g->n);
+  if ((body == RT_BODY_SPIN || body == RT_BODY_FMA || body == RT_BODY_CHECK) && (!g->desc.out || g->desc.out_elems < g->n))
+    return fail(RT_ERR_INVALID, "SPIN/FMA/CHECK bodies need `out` with one int32 per task (%d)", g->n);
   if (g->n > 0 && body == RT_BODY_COUNTER && !g->has_body_arg) return fail(RT_ERR_INVALID, "COUNTER needs body_arg");
   CKR(ensure_device());
   CKR(ensure_pinned(g));
@@ -1038,7 +1075,7 @@ rt_status rt_execute_events(rt_graph_t g, float* ms_kernel) {
   if (ms_kernel) *ms_kernel = 0.f;
   if (g->n == 0) return RT_OK;
   const int body = g->desc.body;
-  if ((body == RT_BODY_SPIN || body == RT_BODY_CHECK) && (!g->desc.out || g->desc.out_elems < g->n))
+  if ((body == RT_BODY_SPIN || body == RT_BODY_FMA || body == RT_BODY_CHECK) && (!g->desc.out || g->desc.out_elems < g->n))
     return fail(RT_ERR_INVALID, "SPIN/CHECK bodies need `out` with one int32 per task");
   CKR(ensure_device());
   CKR(ensure_pinned(g));
@@ -1107,7 +1144,7 @@ rt_status rt_execute_stitched(rt_graph_t g, int32_t replays, float* ms_kernel) {
   const int64_t total = (int64_t)replays * n;
   if (total > 0x7FFFFFF0ll) return fail(RT_ERR_INVALID, "replays x tasks = %lld (limit 2^31 - 16)", (long long)total);
   const int body = g->desc.body;
-  if ((body == RT_BODY_SPIN || body == RT_BODY_CHECK) && (!g->desc.out || g->desc.out_elems < total))
+  if ((body == RT_BODY_SPIN || body == RT_BODY_FMA || body == RT_BODY_CHECK) && (!g->desc.out || g->desc.out_elems < total))
     return fail(RT_ERR_INVALID, "SPIN/CHECK bodies need `out` with one int32 per task and replay (%lld)",
                 (long long)total);
   CKR(ensure_device());
@@ -1628,7 +1665,7 @@ extern "C" rt_status rt_kernel_launches(int64_t* count) {
 
 extern "C" rt_status rt_execute_csr_static(const int32_t* row_ptr, const int32_t* col, const int32_t* indeg,
                                            int32_t n_tasks, int64_t n_edges, int32_t spin_iters, int32_t* out,
-                                           void* stream) {
+                                           int32_t* tickets, void* stream) {
   if (n_tasks < 0 || n_edges < 0 || spin_iters < 0) return fail(RT_ERR_INVALID, "negative size");
   if (n_tasks > grt::static_max_tasks())
     return fail(RT_ERR_INVALID, "rt_execute_csr_static handles at most %d tasks (got %d); use rt_execute",
@@ -1637,7 +1674,7 @@ extern "C" rt_status rt_execute_csr_static(const int32_t* row_ptr, const int32_t
   if (n_tasks == 0) return RT_OK;
   if (!row_ptr || !indeg || !out || (n_edges > 0 && !col)) return fail(RT_ERR_INVALID, "NULL array");
   const char* why = "";
-  rt_status st = grt::static_execute(row_ptr, col, indeg, n_tasks, n_edges, spin_iters, out,
+  rt_status st = grt::static_execute(row_ptr, col, indeg, n_tasks, n_edges, spin_iters, out, tickets,
                                      (cudaStream_t)stream, 2000000000ll, &why);
   if (st != RT_OK) return fail(st, "rt_execute_csr_static: %s", why);
   return RT_OK;
@@ -1686,6 +1723,10 @@ rt_status batch_shape(rt_batch_t b, int64_t* graphs, int64_t* tasks, int64_t* ed
 rt_status graph_view(rt_graph_t g, GraphView* v) {
   if (!g || !v) return fail(RT_ERR_INVALID, "NULL argument");
   if (!g->analyzed) return fail(RT_ERR_STATE, "graph not analyzed");
+  v->req_off = g->req_off.as<int32_t>();
+  v->lo = g->lo.as<int64_t>();
+  v->hi = g->hi.as<int64_t>();
+  v->priv = g->priv.as<uint8_t>();
   v->adj = g->adj.as<int4>();
   v->col = g->col.as<int32_t>();
   v->row_ptr = g->row_ptr.as<int32_t>();
@@ -1695,14 +1736,22 @@ rt_status graph_view(rt_graph_t g, GraphView* v) {
   v->n = g->n;
   v->n_roots = (int32_t)g->n_roots;
   v->n_edges = g->n_edges;
-  size_t f = 0;
-  const DevBuf* bufs[] = {&g->req_off, &g->lo, &g->hi, &g->priv, &g->pred_off, &g->pred, &g->body_arg, &g->err,
-                          &g->rect_task, &g->cnt, &g->keys, &g->keys_alt, &g->pay, &g->pay_alt, &g->seg_b,
-                          &g->seg_e, &g->pairs, &g->pairs_alt, &g->flags, &g->upos, &g->col, &g->row_ptr,
-                          &g->indeg, &g->count, &g->rootpos, &g->root_items, &g->ws, &g->misc, &g->adj,
-                          &g->ring, &g->ctrl, &g->gtable, &g->done_g, &g->tickets, &g->tflags};
-  for (const DevBuf* b : bufs) f += b->cap;
-  v->footprint = f;
+  v->footprint = footprint_of(g);
+  return RT_OK;
+}
+
+size_t graph_footprint(rt_graph_t g) { return g ? footprint_of(g) : 0; }
+
+void graph_set_mem_cap(rt_graph_t g, size_t cap) {
+  if (g) g->mem_cap = cap;
+}
+
+rt_status graph_trim(rt_graph_t g) {
+  if (!g) return fail(RT_ERR_INVALID, "graph is NULL");
+  rt_graph_clear(g);
+  drop_kernel_graph(g);
+  for_each_buf(g, [&](DevBuf& b) { b.release(g->s); });
+  g->gt_valid = false;
   return RT_OK;
 }
 }  // namespace grt

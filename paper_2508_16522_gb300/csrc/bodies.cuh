@@ -18,13 +18,25 @@ __device__ __forceinline__ uint32_t spin_body(uint32_t x, int iters) {
   return x;
 }
 
+// The FMA body: `iters` dependent single-precision fused multiply-adds
+// x <- x * 0.999f + 0.25f from x = the task's id (rounded to float), each one
+// hand-written fma.rn.f32 (IEEE, round to nearest even): the floating-point
+// loop of a compute-bound Task Bench kernel, on one lane. Its result's bits go
+// to out[task].
+__device__ __forceinline__ int32_t fma_body(uint32_t task, int iters) {
+  float x = (float)task;
+  for (int k = 0; k < iters; ++k) asm volatile("fma.rn.f32 %0, %0, %1, %2;" : "+f"(x) : "f"(0.999f), "f"(0.25f));
+  return __float_as_int(x);
+}
+
 __device__ __forceinline__ uint32_t cell_index(const ExecGraph& G, int64_t x, int64_t y) {
   return (uint32_t)((y - G.dom_lo[1]) * G.ext[0] + (x - G.dom_lo[0]));
 }
 
 // CHECK body (order-sensitive): see grt.h. Lane-serial; meant for test sizes.
-// Applies task j's accesses to the state and returns its output word.
-__device__ uint32_t check_apply(const ExecGraph& G, int j) {
+// Applies task j's accesses to the state and returns its output word; `id` is
+// the task id the body mixes in (j itself, or j's id within its own request).
+__device__ uint32_t check_apply(const ExecGraph& G, int j, uint32_t id) {
   const int r0 = G.req_off[j], r1 = G.req_off[j + 1];
   const int D = G.ndim;
   uint32_t acc = 0;
@@ -55,25 +67,27 @@ __device__ uint32_t check_apply(const ExecGraph& G, int j) {
           } else if (comb == (uint32_t)kKindWrite) {
             __stcg(G.state + c, (int32_t)mix32(acc, c));
           } else if (comb == (uint32_t)kKindReduce) {
-            atomicAdd(reinterpret_cast<unsigned*>(G.state) + c, mix32((uint32_t)j, c));
+            atomicAdd(reinterpret_cast<unsigned*>(G.state) + c, mix32(id, c));
           }
         }
       }
     }
-    if (pass == 0) acc = mix32((uint32_t)j, sum);
+    if (pass == 0) acc = mix32(id, sum);
   }
   return acc;
 }
 
-__device__ __forceinline__ void check_body(const ExecGraph& G, int j) { G.out[j] = (int32_t)check_apply(G, j); }
+__device__ __forceinline__ void check_body(const ExecGraph& G, int j) { G.out[j] = (int32_t)check_apply(G, j, (uint32_t)j); }
 
 // FENCE = false: the launch only has bodies that read nothing written by
-// other tasks (EMPTY, SPIN), so the order-sensitive bodies are compiled out.
+// other tasks (EMPTY, SPIN, FMA), so the order-sensitive bodies are compiled out.
 template <bool FENCE>
 __device__ __forceinline__ void run_body(const ExecGraph& G, int j) {
   if (!FENCE) {
     if (G.body == RT_BODY_SPIN) {
       G.out[j] = (int32_t)spin_body((uint32_t)j, G.spin_iters);
+    } else if (G.body == RT_BODY_FMA) {
+      G.out[j] = fma_body((uint32_t)j, G.spin_iters);
     }
     return;
   }
@@ -82,6 +96,9 @@ __device__ __forceinline__ void run_body(const ExecGraph& G, int j) {
       G.out[j] = (int32_t)spin_body((uint32_t)j, G.spin_iters);
       break;
     }
+    case RT_BODY_FMA:
+      G.out[j] = fma_body((uint32_t)j, G.spin_iters);
+      break;
     case RT_BODY_COUNTER: {
       const int k = G.body_arg[j];
       const int32_t v = __ldcg(G.state + k);

@@ -233,6 +233,8 @@ __global__ void __launch_bounds__(256, 1) k_exec(ExecParams p) {
       if (SINGLE && !FENCE) {
         if (body0 == RT_BODY_SPIN) {  // the one graph's fields live in registers
           out0[v] = (int32_t)spin_body((uint32_t)v, spin0);
+        } else if (body0 == RT_BODY_FMA) {
+          out0[v] = fma_body((uint32_t)v, spin0);
         }
       } else {
         const ExecGraph& G = p.graphs[g];

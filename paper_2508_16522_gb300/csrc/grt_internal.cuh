@@ -183,11 +183,22 @@ struct ServeSlot {         // device table entry of one admitted request
   const int32_t* col;      // that graph's CSR columns (successors past the inline ones)
   int32_t* count;          // that graph's countdown counters
   const uint64_t* roots;   // the request's roots (low 32 bits: task id in that graph)
-  int32_t* out;            // SPIN results, one per task of that graph (null for EMPTY)
+  int32_t* out;            // SPIN/CHECK results, one per task of that graph (null for EMPTY)
   int32_t n_tasks, n_roots, body, spin_iters;
   uint32_t gen;            // activation number, echoed at completion
   int32_t base;            // the request's first task in that graph
   uint32_t pad[2];
+  // CHECK body only: the batch graph's launch arrays (indexed by batch task
+  // id), the request's own state (one int32 per cell of its domain) and the
+  // origin of its band in the batch's stacked domain
+  const int32_t* req_off;
+  const int64_t* lo;
+  const int64_t* hi;
+  const uint8_t* priv;
+  int32_t* state;
+  int64_t band_lo[2];
+  int64_t ext0;
+  int32_t ndim, pad1;
 };
 
 struct ServeMailbox {      // host-mapped: written by the host, read by the kernel
@@ -365,6 +376,10 @@ void launch_serve(ServeParams p, int blocks, int warps, cudaStream_t s);
 
 // what the serving host code needs to know about an analysed graph
 struct GraphView {
+  const int32_t* req_off;   // the launches as appended (device)
+  const int64_t* lo;
+  const int64_t* hi;
+  const uint8_t* priv;
   const int4* adj;
   const int32_t* col;
   const int32_t* row_ptr;   // int32[n+1]
@@ -376,10 +391,17 @@ struct GraphView {
   size_t footprint;  // bytes of device memory the graph object holds
 };
 rt_status graph_view(rt_graph_t g, GraphView* v);
+// device bytes the graph's buffers hold (the sum of their capacities)
+size_t graph_footprint(rt_graph_t g);
+// caps the device bytes the graph may hold while its buffers grow (0 = none):
+// a growth past the cap fails with RT_ERR_BUDGET and allocates nothing
+void graph_set_mem_cap(rt_graph_t g, size_t cap);
+// releases every device buffer of the graph (stream-ordered) and clears it
+rt_status graph_trim(rt_graph_t g);
 rt_status batch_shape(rt_batch_t b, int64_t* graphs, int64_t* tasks, int64_t* edges);
 int32_t static_max_tasks();
 rt_status static_execute(const int32_t* row_ptr, const int32_t* col, const int32_t* indeg, int32_t n,
-                         int64_t n_edges, int32_t spin_iters, int32_t* out, cudaStream_t s,
+                         int64_t n_edges, int32_t spin_iters, int32_t* out, int32_t* tickets, cudaStream_t s,
                          int64_t timeout_ns, const char** why);
 
 }  // namespace grt

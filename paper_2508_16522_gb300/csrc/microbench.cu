@@ -13,6 +13,10 @@
 //   [3] the same without using the result (fire-and-forget reductions)
 //   [4] contended atomicAdd on one address by every thread (G ops/s)
 //   [5] the same, warp-aggregated (one atomic per warp; G thread-ops/s)
+//   [6] the FMA task body alone: ns per dependent iteration on one warp (one
+//       task per lane), the body's peak rate that Task Bench's efficiency is
+//       measured against
+#include "bodies.cuh"
 #include "grt_internal.cuh"
 
 namespace grt {
@@ -53,6 +57,11 @@ __global__ void k_mb_distinct(uint32_t* a, int64_t n, int iters, uint32_t* sink)
   if (USE && acc == 0xFFFFFFFFu) *sink = acc;
 }
 
+__global__ void k_mb_fma(int iters, int32_t* sink) {
+  const int32_t x = fma_body(threadIdx.x, iters);
+  if (x == 0x7fffffff) *sink = x;  // keeps the chain live
+}
+
 template <bool AGG>
 __global__ void k_mb_contended(uint32_t* a, int iters) {
   for (int k = 0; k < iters; ++k) {
@@ -77,7 +86,7 @@ rt_status microbench(double* out, int n_out, cudaStream_t s, const char** why) {
   int dev = 0, sms = 0;
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  double r[6] = {0, 0, 0, 0, 0, 0};
+  double r[7] = {0, 0, 0, 0, 0, 0, 0};
   auto timed = [&](auto launch) -> double {
     launch();  // warm-up
     cudaEventRecord(e0, s);
@@ -103,6 +112,9 @@ rt_status microbench(double* out, int n_out, cudaStream_t s, const char** why) {
     r[3] = total / (timed([&] { k_mb_distinct<false><<<blocks, threads, 0, s>>>(a, kMbWords, iters, sink); }) * 1e6);
     r[4] = total / (timed([&] { k_mb_contended<false><<<blocks, threads, 0, s>>>(sink, iters); }) * 1e6);
     r[5] = total / (timed([&] { k_mb_contended<true><<<blocks, threads, 0, s>>>(sink, iters); }) * 1e6);
+    const int fma_iters = 1 << 20;
+    count_launch(2);
+    r[6] = timed([&] { k_mb_fma<<<1, 32, 0, s>>>(fma_iters, reinterpret_cast<int32_t*>(sink)); }) * 1e6 / fma_iters;
     e = cudaGetLastError();
   }
   if (a) cudaFree(a);
@@ -113,7 +125,7 @@ rt_status microbench(double* out, int n_out, cudaStream_t s, const char** why) {
     *why = cudaGetErrorString(e);
     return RT_ERR_CUDA;
   }
-  for (int k = 0; k < n_out && k < 6; ++k) out[k] = r[k];
+  for (int k = 0; k < n_out && k < 7; ++k) out[k] = r[k];
   return RT_OK;
 }
 

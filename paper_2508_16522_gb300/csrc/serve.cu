@@ -134,6 +134,25 @@ struct SlotView {
   uint32_t gen;
 };
 
+// the CHECK body's view of a request: the batch graph's launches, and the
+// request's own state and band origin, so that cell indices and task ids are
+// those of the request alone
+__device__ ExecGraph check_view(const ServeParams& p, int slot) {
+  const ServeSlot* S = p.slots + slot;
+  ExecGraph G{};
+  G.req_off = reinterpret_cast<const int32_t*>(__ldcg(reinterpret_cast<const unsigned long long*>(&S->req_off)));
+  G.lo = reinterpret_cast<const int64_t*>(__ldcg(reinterpret_cast<const unsigned long long*>(&S->lo)));
+  G.hi = reinterpret_cast<const int64_t*>(__ldcg(reinterpret_cast<const unsigned long long*>(&S->hi)));
+  G.priv = reinterpret_cast<const uint8_t*>(__ldcg(reinterpret_cast<const unsigned long long*>(&S->priv)));
+  G.state = reinterpret_cast<int32_t*>(__ldcg(reinterpret_cast<const unsigned long long*>(&S->state)));
+  G.dom_lo[0] = __ldcg(reinterpret_cast<const long long*>(&S->band_lo[0]));
+  G.dom_lo[1] = __ldcg(reinterpret_cast<const long long*>(&S->band_lo[1]));
+  G.ext[0] = __ldcg(reinterpret_cast<const long long*>(&S->ext0));
+  G.ext[1] = 1;
+  G.ndim = __ldcg(&S->ndim);
+  return G;
+}
+
 __device__ __forceinline__ SlotView slot_view(const ServeParams& p, int slot) {
   const ServeSlot* S = p.slots + slot;
   const unsigned long long* w = reinterpret_cast<const unsigned long long*>(S);
@@ -269,12 +288,20 @@ __global__ void __launch_bounds__(256, 1) k_serve(ServeParams p) {
     const int deg = has ? a0.y : 0;
     q.bat[lane][0] = a0;
     q.bat[lane][1] = a1;
+    // an order-sensitive body reads what its predecessors wrote: acquire their
+    // effects before it runs and release its own before the decrements
+    const bool chk = __any_sync(kFullS, has && S.body == RT_BODY_CHECK);
+    if (chk) fence_acq_rel_gpu();
     if (has) {
       // (no counter re-arm: every served request is analysed afresh)
       if (S.body == RT_BODY_SPIN && S.out) {
         S.out[v] = (int32_t)spin_body((uint32_t)(v - S.base), S.spin_iters);  // id within its request
+      } else if (S.body == RT_BODY_CHECK) {
+        const ExecGraph G = check_view(p, slot);
+        S.out[v] = (int32_t)check_apply(G, v, (uint32_t)(v - S.base));
       }
     }
+    if (chk) fence_acq_rel_gpu();
     __syncwarp();
 
     int incl = deg;

@@ -56,8 +56,10 @@ struct Request {
   int64_t estimate = 0, footprint = 0, n_edges = 0;
   int state = 0, status = 0, slot = -1, batch = -1;
   int32_t toff = 0;                        // first task in the batch graph
+  int32_t band = 0;                        // its band (position) in the batch
   int64_t eoff = 0;                        // first edge in the batch graph's CSR
   std::vector<int32_t> row_ptr, col, out;  // results (keep_results)
+  std::vector<int32_t> cells;              // CHECK: final state of its domain (keep_results)
   std::string error;                       // why it failed (state 4)
 };
 
@@ -77,7 +79,8 @@ struct HostBuf {
 struct Batch {     // a pooled graph that analyses one batch of requests
   rt_graph_t g = nullptr;
   cudaStream_t stream = nullptr;
-  int32_t* out = nullptr;    // SPIN outputs of the whole batch (device)
+  int32_t* out = nullptr;    // SPIN/CHECK outputs of the whole batch (device)
+  int32_t* state = nullptr;  // CHECK: one domain's state per band (device)
   int32_t* gidx = nullptr;   // task offsets of the batch's requests (device)
   uint32_t* gout = nullptr;  // gathered root and edge offsets (device)
   int32_t* hidx = nullptr;   // pinned mirrors of the two
@@ -100,6 +103,7 @@ struct rt_server {
   int device = 0;
   int stack_dim = 0;               // requests are stacked along this dimension
   int64_t band = 0;                // extent of one request's domain along it
+  int64_t cells = 0;               // cells of one request's domain (CHECK state)
   std::vector<Slot> slots;
   std::vector<int> free_slots;
   std::vector<Batch> batches;
@@ -127,7 +131,17 @@ struct rt_server {
   std::deque<Request*> pending;
   std::unordered_map<int64_t, std::unique_ptr<Request>> reqs;
   int64_t next_ticket = 1;
-  int64_t budget_used = 0;
+  // Device-memory budget. Every batch graph has a ledger entry: the bytes it
+  // may hold. While a batch is analysed that is its cap (the graph cannot grow
+  // past it); otherwise it is what the graph holds, retained for reuse. The
+  // entries always sum to at most budget_bytes, so the bytes the graphs hold
+  // never exceed the budget; free batch graphs are trimmed to make room.
+  std::vector<int64_t> ledger;
+  int64_t ledger_sum = 0, ledger_peak = 0;
+  std::vector<int64_t> held;            // per batch graph: bytes it held after its last analysis
+  int64_t held_sum = 0, held_peak = 0;
+  int64_t fixed_bytes = 0;              // the pool allocated at creation (not request memory)
+  int64_t n_trims = 0, n_retries = 0;
   int64_t outstanding = 0;         // submitted, not yet done or failed
   int64_t n_batches = 0, n_batched = 0;
   std::mutex post_mu;              // serialises mailbox posts
@@ -200,14 +214,38 @@ rt_status build_union(rt_server* s, Batch& b, const std::vector<Request*>& rs, i
       }
     std::memcpy(pv + roff, r->priv.data(), (size_t)R);
     roff += R;
-    // the request's own copy of its launches is no longer needed
-    std::vector<int32_t>().swap(r->req_off);
-    std::vector<int64_t>().swap(r->lo);
-    std::vector<int64_t>().swap(r->hi);
-    std::vector<uint8_t>().swap(r->priv);
   }
   ro[n_tot] = (int32_t)R_tot;
   return RT_OK;
+}
+
+void set_ledger(rt_server* s, int bi, int64_t bytes) {
+  s->ledger_sum += bytes - s->ledger[(size_t)bi];
+  s->ledger[(size_t)bi] = bytes;
+  s->ledger_peak = std::max(s->ledger_peak, s->ledger_sum);
+}
+
+// batch bi's graph now holds `bytes` (measured by the thread that owns it)
+void set_held(rt_server* s, int bi, int64_t bytes) {
+  s->held_sum += bytes - s->held[(size_t)bi];
+  s->held[(size_t)bi] = bytes;
+  s->held_peak = std::max(s->held_peak, s->held_sum);
+}
+
+// Room for batch bi to hold `need` bytes (its ledger entry included)? Trims
+// the other free batch graphs' retained buffers when that makes the room.
+// Called with s->mu held.
+bool make_room(rt_server* s, int bi, int64_t need) {
+  const int64_t others = s->ledger_sum - s->ledger[(size_t)bi];
+  if (others + need <= s->desc.budget_bytes) return true;
+  for (int f : s->free_batches) {
+    if (f == bi || s->ledger[(size_t)f] == 0) continue;
+    graph_trim(s->batches[(size_t)f].g);
+    set_ledger(s, f, 0);
+    set_held(s, f, 0);
+    ++s->n_trims;
+  }
+  return s->ledger_sum - s->ledger[(size_t)bi] + need <= s->desc.budget_bytes;
 }
 
 void worker_main(rt_server* s) {
@@ -222,26 +260,34 @@ void worker_main(rt_server* s) {
       s->cv.wait(lk, [&] {
         if (s->quit) return true;
         if (s->pending.empty() || s->free_slots.empty() || s->free_batches.empty()) return false;
-        return s->budget_used + s->pending.front()->estimate <= s->desc.budget_bytes;
+        const int f = s->free_batches.back();
+        return make_room(s, f, std::max(s->ledger[(size_t)f], s->pending.front()->estimate));
       });
       if (s->quit) return;
       bi = s->free_batches.back();
       s->free_batches.pop_back();
       const int64_t t = now_ns();
-      // admit in arrival order: everything waiting that fits, up to max_batch
+      const int64_t others = s->ledger_sum - s->ledger[(size_t)bi];
+      const int64_t room = s->desc.budget_bytes - others;
+      // admit in arrival order: everything waiting whose estimates fit, up to max_batch
       while (!s->pending.empty() && (int)rs.size() < s->desc.max_batch && !s->free_slots.empty() &&
-             s->budget_used + s->pending.front()->estimate <= s->desc.budget_bytes) {
+             est + s->pending.front()->estimate <= room) {
         Request* r = s->pending.front();
         s->pending.pop_front();
         r->slot = s->free_slots.back();
         s->free_slots.pop_back();
-        s->budget_used += r->estimate;
         est += r->estimate;
         r->batch = bi;
         r->state = 1;
         r->admit = t;
         rs.push_back(r);
       }
+      // the batch graph may grow to twice the estimate (never past the room
+      // left): estimates are not bounds, and a graph that would pass its cap
+      // fails cleanly and its requests are admitted again with larger ones
+      const int64_t cap = std::min<int64_t>(room, std::max<int64_t>(std::max<int64_t>(2 * est, est + ((int64_t)64 << 20)), s->ledger[(size_t)bi]));
+      set_ledger(s, bi, cap);
+      graph_set_mem_cap(s->batches[(size_t)bi].g, (size_t)cap);
     }
     Batch& b = s->batches[(size_t)bi];
     trace("worker: batch admitted");
@@ -299,30 +345,80 @@ void worker_main(rt_server* s) {
           e.spin_iters = s->desc.spin_iters;
           e.gen = ++s->slots[(size_t)r->slot].gen;
           e.base = r->toff;
+          r->band = j;
+          if (s->desc.body == RT_BODY_CHECK) {
+            e.req_off = v.req_off;
+            e.lo = v.lo;
+            e.hi = v.hi;
+            e.priv = v.priv;
+            e.state = b.state + (size_t)j * (size_t)s->cells;
+            e.band_lo[0] = s->desc.dom_lo[0];
+            e.band_lo[1] = s->desc.ndim == 2 ? s->desc.dom_lo[1] : 0;
+            e.band_lo[s->stack_dim] += (int64_t)j * s->band;
+            e.ext0 = s->desc.dom_hi[0] - s->desc.dom_lo[0] + 1;
+            e.ndim = s->desc.ndim;
+          }
           s->table_h[r->slot] = e;
           if (cudaMemcpyAsync(s->table + r->slot, s->table_h + r->slot, sizeof e, cudaMemcpyHostToDevice,
                               b.stream) != cudaSuccess)
             st = RT_ERR_CUDA;
         }
+        // CHECK: every request of the batch starts from a zero state
+        if (st == RT_OK && s->desc.body == RT_BODY_CHECK &&
+            cudaMemsetAsync(b.state, 0, (size_t)B * (size_t)s->cells * 4, b.stream) != cudaSuccess)
+          st = RT_ERR_CUDA;
         if (st == RT_OK && cudaStreamSynchronize(b.stream) != cudaSuccess) st = RT_ERR_CUDA;
         if (st != RT_OK) why = "slot table write";
         trace("worker: table written");
       }
     }
     std::vector<int> post;
+    const int64_t fp = (int64_t)graph_footprint(b.g);  // this worker owns the graph until it is posted
     {
       std::lock_guard<std::mutex> lk(s->mu);
-      s->budget_used -= est;
-      if (st != RT_OK) {
+      if (st == RT_ERR_BUDGET) {
+        // the batch outgrew its cap: release what the graph holds and admit its
+        // requests again, first in line, with twice their estimates (a request
+        // that failed with the whole budget as its estimate can never fit)
+        graph_trim(b.g);
+        set_ledger(s, bi, 0);
+        set_held(s, bi, 0);
+        ++s->n_retries;
+        for (size_t j = rs.size(); j-- > 0;) {
+          Request* r = rs[j];
+          s->free_slots.push_back(r->slot);
+          r->slot = -1;
+          r->batch = -1;
+          if (r->estimate >= s->desc.budget_bytes) {
+            fail_request(r, RT_ERR_BUDGET, "request does not fit the memory budget: " + why);
+            --s->outstanding;
+          } else {
+            r->estimate = std::min(2 * r->estimate, s->desc.budget_bytes);
+            r->state = 0;
+            s->pending.push_front(r);
+          }
+        }
+        s->free_batches.push_back(bi);
+      } else if (st != RT_OK) {
         for (Request* r : rs) {
           fail_request(r, st, why);
           s->free_slots.push_back(r->slot);
           --s->outstanding;
         }
+        set_ledger(s, bi, fp);
+        set_held(s, bi, fp);
         s->free_batches.push_back(bi);
       } else {
-        b.footprint = n_tot > 0 ? (int64_t)v.footprint : 0;
-        s->budget_used += b.footprint;
+        // the graph keeps what it holds (at most its cap) for the next batch
+        b.footprint = fp;
+        set_ledger(s, bi, fp);
+        set_held(s, bi, fp);
+        for (Request* r : rs) {  // the batch has its own copy of the launches now
+          std::vector<int32_t>().swap(r->req_off);
+          std::vector<int64_t>().swap(r->lo);
+          std::vector<int64_t>().swap(r->hi);
+          std::vector<uint8_t>().swap(r->priv);
+        }
         ++s->n_batches;
         s->n_batched += B;
         b.live = 0;
@@ -347,10 +443,7 @@ void worker_main(rt_server* s) {
           post.push_back(r->slot);
           ++b.live;
         }
-        if (b.live == 0) {
-          s->budget_used -= b.footprint;
-          s->free_batches.push_back(bi);
-        }
+        if (b.live == 0) s->free_batches.push_back(bi);
       }
       s->cv.notify_all();
       s->cv_done.notify_all();
@@ -378,9 +471,14 @@ void copy_results(rt_server* s, Request* r) {
                   s->copy_stream);
   if (r->n_edges)
     cudaMemcpyAsync(r->col.data(), v.col + r->eoff, (size_t)r->n_edges * 4, cudaMemcpyDeviceToHost, s->copy_stream);
-  if (s->desc.body == RT_BODY_SPIN) {
+  if (s->desc.body == RT_BODY_SPIN || s->desc.body == RT_BODY_CHECK) {
     r->out.resize((size_t)r->n);
     cudaMemcpyAsync(r->out.data(), b.out + r->toff, (size_t)r->n * 4, cudaMemcpyDeviceToHost, s->copy_stream);
+  }
+  if (s->desc.body == RT_BODY_CHECK) {
+    r->cells.resize((size_t)s->cells);
+    cudaMemcpyAsync(r->cells.data(), b.state + (size_t)r->band * (size_t)s->cells, (size_t)s->cells * 4,
+                    cudaMemcpyDeviceToHost, s->copy_stream);
   }
   cudaStreamSynchronize(s->copy_stream);
   const int32_t e0 = r->row_ptr[0];
@@ -417,10 +515,7 @@ void completer_main(rt_server* s) {
       s->free_slots.push_back(slot);
       --s->outstanding;
       Batch& b = s->batches[(size_t)r->batch];
-      if (--b.live == 0) {  // the batch's last request: its graph is free again
-        s->budget_used -= b.footprint;
-        s->free_batches.push_back(r->batch);
-      }
+      if (--b.live == 0) s->free_batches.push_back(r->batch);  // its graph is free again (buffers retained)
     }
     if (!done_slots.empty()) {
       std::lock_guard<std::mutex> lk(s->mu);
@@ -460,6 +555,7 @@ void free_server(rt_server* s) {
     if (b.g) rt_graph_destroy(b.g);
     if (b.stream) cudaStreamDestroy(b.stream);
     if (b.out) cudaFree(b.out);
+    if (b.state) cudaFree(b.state);
     if (b.gidx) cudaFree(b.gidx);
     if (b.gout) cudaFree(b.gout);
     if (b.hidx) cudaFreeHost(b.hidx);
@@ -492,8 +588,8 @@ int64_t rt_now_ns(void) { return now_ns(); }
 rt_status rt_server_create(const rt_server_desc* d, rt_server_t* out) {
   if (!d || !out) return sfail(RT_ERR_INVALID, "NULL argument");
   *out = nullptr;
-  if (d->body != RT_BODY_EMPTY && d->body != RT_BODY_SPIN)
-    return sfail(RT_ERR_INVALID, "serving supports EMPTY and SPIN bodies");
+  if (d->body != RT_BODY_EMPTY && d->body != RT_BODY_SPIN && d->body != RT_BODY_CHECK)
+    return sfail(RT_ERR_INVALID, "serving supports EMPTY, SPIN and CHECK bodies");
   if (d->ndim < 1 || d->ndim > 2 || d->max_inflight < 1 || d->max_inflight > 1024 || d->workers < 1 ||
       d->workers > 64 || d->max_tasks < 1 || d->budget_bytes <= 0 || d->spin_iters < 0 || d->exec_warps < 0 ||
       d->exec_warps > 8 || d->exec_blocks < 0 || d->max_batch < 0 || d->max_batch > 1024)
@@ -512,6 +608,11 @@ rt_status rt_server_create(const rt_server_desc* d, rt_server_t* out) {
   s->desc.max_batch = mb;
   s->stack_dim = sd;
   s->band = band;
+  s->cells = (d->dom_hi[0] - d->dom_lo[0] + 1) * (d->ndim == 2 ? d->dom_hi[1] - d->dom_lo[1] + 1 : 1);
+  if (d->body == RT_BODY_CHECK && (s->cells > ((int64_t)1 << 31) || s->cells * mb > ((int64_t)1 << 36))) {
+    delete s;
+    return sfail(RT_ERR_INVALID, "CHECK serving: the domain's state is too large for max_batch bands");
+  }
   if (s->desc.timeout_ns == 0) s->desc.timeout_ns = 2000000000ll;
   auto bail = [&](rt_status st, const std::string& m) {
     free_server(s);
@@ -528,7 +629,9 @@ rt_status rt_server_create(const rt_server_desc* d, rt_server_t* out) {
     Batch& b = s->batches[(size_t)i];
     if (cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking) != cudaSuccess)
       return bail(RT_ERR_CUDA, "streams");
-    if ((d->body == RT_BODY_SPIN && cudaMalloc(&b.out, (size_t)mb * d->max_tasks * 4) != cudaSuccess) ||
+    if (((d->body == RT_BODY_SPIN || d->body == RT_BODY_CHECK) &&
+         cudaMalloc(&b.out, (size_t)mb * d->max_tasks * 4) != cudaSuccess) ||
+        (d->body == RT_BODY_CHECK && cudaMalloc(&b.state, (size_t)mb * (size_t)s->cells * 4) != cudaSuccess) ||
         cudaMalloc(&b.gidx, (size_t)(mb + 1) * 4) != cudaSuccess ||
         cudaMalloc(&b.gout, (size_t)(mb + 1) * 8) != cudaSuccess ||
         cudaHostAlloc(&b.hidx, (size_t)(mb + 1) * 4, cudaHostAllocDefault) != cudaSuccess ||
@@ -600,6 +703,24 @@ rt_status rt_server_create(const rt_server_desc* d, rt_server_t* out) {
     }
   }
   if (cudaDeviceSynchronize() != cudaSuccess) return bail(RT_ERR_CUDA, "kernel preload");
+  // the batch graphs' warm-up buffers are the first entries of the budget's ledger
+  s->ledger.assign((size_t)P, 0);
+  s->held.assign((size_t)P, 0);
+  for (int i = 0; i < P; ++i) {
+    const int64_t fp = (int64_t)graph_footprint(s->batches[(size_t)i].g);
+    if (s->ledger_sum + fp > d->budget_bytes) {
+      graph_trim(s->batches[(size_t)i].g);
+      continue;
+    }
+    set_ledger(s, i, fp);
+    set_held(s, i, fp);
+  }
+  s->fixed_bytes = (int64_t)M * (int64_t)(sizeof(ServeSlot) + 4) + (int64_t)sizeof(ServeCtrl) + (int64_t)s->cap * 16;
+  for (Batch& b : s->batches) {
+    s->fixed_bytes += (int64_t)(mb + 1) * 12;
+    if (b.out) s->fixed_bytes += (int64_t)mb * d->max_tasks * 4;
+    if (b.state) s->fixed_bytes += (int64_t)mb * s->cells * 4;
+  }
   launch_serve_init(p, s->exec_stream);
   // Two warps per SM by default: the kernel stays resident beside the workers'
   // analysis, and with more warps its registers would leave room for only two
@@ -688,6 +809,21 @@ rt_status rt_server_result(rt_server_t s, int64_t ticket, int32_t* row_ptr, int3
   return RT_OK;
 }
 
+rt_status rt_server_result_state(rt_server_t s, int64_t ticket, int32_t* state) {
+  if (!s || !state) return sfail(RT_ERR_INVALID, "NULL argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return sfail(RT_ERR_INVALID, "unknown ticket");
+  const Request* r = it->second.get();
+  if (r->state == 4) return sfail((rt_status)r->status, "request failed: " + r->error);
+  if (r->state != 3) return sfail(RT_ERR_STATE, "request is not done");
+  if (!s->desc.keep_results || s->desc.body != RT_BODY_CHECK)
+    return sfail(RT_ERR_STATE, "server does not keep CHECK states");
+  if (r->cells.empty()) memset(state, 0, (size_t)s->cells * 4);  // an empty request
+  else memcpy(state, r->cells.data(), r->cells.size() * 4);
+  return RT_OK;
+}
+
 rt_status rt_server_drain(rt_server_t s, int64_t timeout_ns) {
   if (!s) return sfail(RT_ERR_INVALID, "NULL server");
   const int64_t until = now_ns() + (timeout_ns > 0 ? timeout_ns : (int64_t)3600 * 1000000000ll);
@@ -742,7 +878,7 @@ rt_status rt_server_stats(rt_server_t s, int64_t* out, int32_t n) {
   cudaMemcpyAsync(&w[2], &s->ctrl->status, 4, cudaMemcpyDeviceToHost, s->copy_stream);
   cudaMemcpyAsync(&ex, &s->ctrl->executed, 8, cudaMemcpyDeviceToHost, s->copy_stream);
   if (cudaStreamSynchronize(s->copy_stream) != cudaSuccess) return sfail(RT_ERR_CUDA, "stats copy");
-  int64_t v[11];
+  int64_t v[18];
   v[0] = s->mail->posted;
   v[1] = w[0];
   v[2] = w[1];
@@ -754,12 +890,19 @@ rt_status rt_server_stats(rt_server_t s, int64_t* out, int32_t n) {
     for (auto& kv : s->reqs) by_state[std::min(std::max(kv.second->state, 0), 4)]++;
     v[9] = s->n_batches;
     v[10] = s->n_batched;
+    v[11] = s->ledger_sum;
+    v[12] = s->ledger_peak;
+    v[13] = s->held_sum;
+    v[14] = s->held_peak;
+    v[15] = s->fixed_bytes;
+    v[16] = s->n_trims;
+    v[17] = s->n_retries;
   }
   v[5] = by_state[0];
   v[6] = by_state[1];
   v[7] = by_state[2];
   v[8] = cudaStreamQuery(s->exec_stream) == cudaErrorNotReady ? 1 : 0;
-  for (int k = 0; k < n && k < 11; ++k) out[k] = v[k];
+  for (int k = 0; k < n && k < 18; ++k) out[k] = v[k];
   return RT_OK;
 }
 rt_status rt_server_destroy(rt_server_t s) {

@@ -10,6 +10,10 @@
 // trigger records, control block, graph table) in one file-scope device array
 // instead of library-allocated buffers.
 //
+// With a caller-owned tickets buffer the executor also records each task's
+// start and finish ticket (one global counter), so that a caller can check
+// that every edge was respected.
+//
 // Limits and sharing: the array holds kStaticMaxTasks tasks worth of scratch
 // (about 11 MB) and stays resident on every device that loads the library until
 // the process exits. All calls share it and it keeps the previous call's
@@ -154,10 +158,29 @@ cudaError_t static_scratch(void** out) {
 int32_t static_max_tasks() { return kStaticMaxTasks; }
 
 rt_status static_execute(const int32_t* row_ptr, const int32_t* col, const int32_t* indeg, int32_t n,
-                         int64_t n_edges, int32_t spin_iters, int32_t* out, cudaStream_t s,
+                         int64_t n_edges, int32_t spin_iters, int32_t* out, int32_t* tickets, cudaStream_t s,
                          int64_t timeout_ns, const char** why) {
+  // an error left pending by earlier, unrelated work is reported as such (and
+  // left pending), not taken for a failure of the launches below
+  cudaError_t e = cudaPeekAtLastError();
+  if (e != cudaSuccess) {
+    *why = "a CUDA error was already pending before the call";
+    return RT_ERR_CUDA;
+  }
+  // the call reads back validation flags and the status with synchronous
+  // copies into host memory, which a stream capture cannot hold
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(s, &cap);
+  if (e != cudaSuccess) {
+    *why = cudaGetErrorString(e);
+    return RT_ERR_CUDA;
+  }
+  if (cap != cudaStreamCaptureStatusNone) {
+    *why = "the stream is being captured; this call is synchronous and cannot be captured";
+    return RT_ERR_STATE;
+  }
   void* scratch = nullptr;
-  cudaError_t e = static_scratch(&scratch);
+  e = static_scratch(&scratch);
   if (e != cudaSuccess) {
     *why = cudaGetErrorString(e);
     return RT_ERR_CUDA;
@@ -169,7 +192,8 @@ rt_status static_execute(const int32_t* row_ptr, const int32_t* col, const int32
   count_launch(2);
   k_static_clear_err<<<1, 1, 0, s>>>();
   k_static_check_rows<<<nb, 256, 0, s>>>(row_ptr, n, n_edges);
-  e = cudaMemcpyAsync(&flags, err, 4, cudaMemcpyDeviceToHost, s);
+  e = cudaGetLastError();  // the flags word is trusted only if both kernels launched
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&flags, err, 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     *why = cudaGetErrorString(e);
@@ -182,7 +206,8 @@ rt_status static_execute(const int32_t* row_ptr, const int32_t* col, const int32
   count_launch(2);
   k_static_check_cols<<<nb, 256, 0, s>>>(row_ptr, col, n);
   k_static_check_indeg<<<nb, 256, 0, s>>>(indeg, n);
-  e = cudaMemcpyAsync(&flags, err, 4, cudaMemcpyDeviceToHost, s);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&flags, err, 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     *why = cudaGetErrorString(e);
@@ -200,6 +225,11 @@ rt_status static_execute(const int32_t* row_ptr, const int32_t* col, const int32
   k_static_reset<<<256, 256, 0, s>>>(indeg, n, spin_iters, out);
   k_static_seed<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(indeg, n);
   launch_pack_adj(row_ptr, col, indeg, n, reinterpret_cast<int4*>(base + kOffAdj), s);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    *why = cudaGetErrorString(e);
+    return RT_ERR_CUDA;
+  }
   ExecParams p{};
   p.adj = reinterpret_cast<const int4*>(base + kOffAdj);
   p.row_ptr = row_ptr;
@@ -218,7 +248,7 @@ rt_status static_execute(const int32_t* row_ptr, const int32_t* col, const int32
   p.timeout_ns = timeout_ns;
   p.claim = 32;
   p.keep = 32;
-  p.tickets = nullptr;
+  p.tickets = tickets;  // caller-owned int32[2n], or null
   p.total_roots = 0;
   p.need_fence = 0;
   int dev = 0, sms = 0;

@@ -213,9 +213,11 @@ __global__ void __launch_bounds__(256, 1) k_stitch(StitchParams p) {
       const ExecGraph& G = p.G;
       if (G.body == RT_BODY_SPIN) {
         G.out[slot] = (int32_t)spin_body((uint32_t)v, G.spin_iters);
+      } else if (G.body == RT_BODY_FMA) {
+        G.out[slot] = fma_body((uint32_t)v, G.spin_iters);
       } else if (FENCE) {
         if (G.body == RT_BODY_CHECK) {
-          G.out[slot] = (int32_t)check_apply(G, v);
+          G.out[slot] = (int32_t)check_apply(G, v, (uint32_t)v);
         } else if (G.body == RT_BODY_COUNTER) {
           run_body<true>(G, v);
         }

@@ -22,7 +22,7 @@ RT_OK, RT_ERR_INVALID, RT_ERR_OOM, RT_ERR_CUDA, RT_ERR_TIMEOUT, RT_ERR_STATE, RT
 STATUS_NAMES = ["RT_OK", "RT_ERR_INVALID", "RT_ERR_OOM", "RT_ERR_CUDA", "RT_ERR_TIMEOUT", "RT_ERR_STATE",
                 "RT_ERR_BUDGET"]
 RT_READ, RT_WRITE, RT_REDUCE_SUM = 0, 1, 2
-RT_BODY_EMPTY, RT_BODY_SPIN, RT_BODY_COUNTER, RT_BODY_CHECK = 0, 1, 2, 3
+RT_BODY_EMPTY, RT_BODY_SPIN, RT_BODY_COUNTER, RT_BODY_CHECK, RT_BODY_FMA = 0, 1, 2, 3, 4
 RT_LAUNCH_HOST, RT_LAUNCH_DEVICE, RT_LAUNCH_DEFER_CHECK = 0, 1, 2
 RT_GRAPH_TICKETS, RT_GRAPH_PROFILE = 1, 2
 
@@ -32,7 +32,8 @@ EXPORTS = ["rt_graph_create", "rt_graph_destroy", "rt_graph_clear", "rt_launch_b
            "rt_get_tickets", "rt_copy_tickets", "rt_debug_hold_task", "rt_batch_create",
            "rt_batch_execute", "rt_batch_sync", "rt_batch_counters", "rt_batch_destroy", "rt_last_error", "rt_device_info",
            "rt_kernel_launches", "rt_execute_csr_static", "rt_microbench_atomics", "rt_now_ns",
-           "rt_server_create", "rt_server_submit", "rt_server_poll", "rt_server_result", "rt_server_drain",
+           "rt_server_create", "rt_server_submit", "rt_server_poll", "rt_server_result", "rt_server_result_state",
+           "rt_server_drain",
            "rt_server_stats", "rt_server_destroy", "rt_tune_tile", "rt_tune_exec", "rt_tune_batch",
            "rt_batch_create_stacked", "rt_execute_events", "rt_execute_kernels",
            "rt_execute_stitched", "rt_copy_stitched_tickets"]
@@ -132,12 +133,13 @@ def load(path: str = LIB_PATH):
         "rt_batch_counters": [P, ctypes.POINTER(i64), i32],
         "rt_device_info": [ctypes.POINTER(i32), ctypes.POINTER(i32)],
         "rt_kernel_launches": [ctypes.POINTER(i64)],
-        "rt_execute_csr_static": [P, P, P, i32, i64, i32, P, P],
+        "rt_execute_csr_static": [P, P, P, i32, i64, i32, P, P, P],
         "rt_microbench_atomics": [ctypes.POINTER(ctypes.c_double), i32, P],
         "rt_server_create": [ctypes.POINTER(rt_server_desc), ctypes.POINTER(P)],
         "rt_server_submit": [P, i32, P, P, P, P, i64, ctypes.POINTER(i64)],
         "rt_server_poll": [P, i64, ctypes.POINTER(rt_request_info)],
         "rt_server_result": [P, i64, P, P, P],
+        "rt_server_result_state": [P, i64, P],
         "rt_server_drain": [P, i64],
         "rt_server_destroy": [P],
         "rt_server_stats": [P, ctypes.POINTER(i64), i32],
@@ -227,18 +229,20 @@ def rt_kernel_launches() -> int:
     return c.value
 
 
-def rt_execute_csr_static(row_ptr, col, indeg, n_tasks: int, n_edges: int, spin_iters: int, out, stream=None):
+def rt_execute_csr_static(row_ptr, col, indeg, n_tasks: int, n_edges: int, spin_iters: int, out, tickets=None,
+                          stream=None):
     """Executes a caller-held CSR (device pointers) with SPIN bodies, allocating
-    nothing; see include/grt.h for the limits and the sharing rule."""
-    _check(load().rt_execute_csr_static(row_ptr, col, indeg, n_tasks, n_edges, spin_iters, out, stream))
+    nothing; `tickets` (device int32[2n], optional) receives each task's start
+    and finish ticket. See include/grt.h for the limits and the sharing rule."""
+    _check(load().rt_execute_csr_static(row_ptr, col, indeg, n_tasks, n_edges, spin_iters, out, tickets, stream))
 
 
 def rt_microbench_atomics(stream=None) -> dict:
     """The executor's measured rooflines (see include/grt.h)."""
-    out = (ctypes.c_double * 6)()
-    _check(load().rt_microbench_atomics(out, 6, stream))
+    out = (ctypes.c_double * 7)()
+    _check(load().rt_microbench_atomics(out, 7, stream))
     names = ("dep_atomic_ns", "dep_l2_load_ns", "scatter_atomic_gops", "scatter_red_gops",
-             "contended_atomic_gops", "contended_warp_agg_gops")
+             "contended_atomic_gops", "contended_warp_agg_gops", "fma_body_ns_per_iter")
     return dict(zip(names, list(out)))
 
 
@@ -531,11 +535,20 @@ class Server:
                                        None if out is None else out.ctypes.data))
         return rp, col[:n_edges], (None if out is None else out[:n_tasks])
 
+    def result_state(self, ticket, n_cells):
+        """Final state of a finished request (CHECK body, keep_results)."""
+        st = np.empty(max(n_cells, 1), np.int32)
+        _check(load().rt_server_result_state(self.h, ticket, st.ctypes.data))
+        return st[:n_cells]
+
+    STAT_NAMES = ("posted", "taken", "finished", "status", "executed", "queued", "analysing", "running",
+                  "kernel_running", "batches", "batched_requests", "ledger_bytes", "ledger_peak_bytes",
+                  "held_bytes", "held_peak_bytes", "fixed_bytes", "trims", "budget_retries")
+
     def stats(self) -> dict:
-        arr = (ctypes.c_int64 * 11)()
-        _check(load().rt_server_stats(self.h, arr, 11))
-        return dict(zip(("posted", "taken", "finished", "status", "executed", "queued", "analysing", "running",
-                         "kernel_running", "batches", "batched_requests"), list(arr)))
+        arr = (ctypes.c_int64 * len(self.STAT_NAMES))()
+        _check(load().rt_server_stats(self.h, arr, len(self.STAT_NAMES)))
+        return dict(zip(self.STAT_NAMES, list(arr)))
 
     def drain(self, timeout_ns=0):
         _check(load().rt_server_drain(self.h, timeout_ns))

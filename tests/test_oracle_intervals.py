@@ -163,7 +163,7 @@ def test_mutant_is_caught(name):
         open(c, "w").write(src.replace(old, new))
         # the mutant library also needs the wrapper's other entry points
         base = [os.path.join(os.path.dirname(SRC), f) for f in ("oracle.c", "alg1.c")]
-        subprocess.check_call(["gcc", "-O1", "-std=c11", "-shared", "-fPIC", "-pthread", "-o", so, c] + base)
+        subprocess.check_call(["gcc", "-O1", "-std=c11", "-shared", "-fPIC", "-pthread", "-o", so, c] + base + ["-lm"])
         cases = tiny_traces() + [tg.stencil_1d(16, 6), tg.fig6_fixture()]
         wrong = 0
         for tr in cases:

@@ -42,7 +42,7 @@ def test_mutant_is_caught(name):
         c = os.path.join(d, "mut.c")
         so = os.path.join(d, "libmut.so")
         open(c, "w").write(src.replace(old, new))
-        subprocess.check_call(["gcc", "-O1", "-std=c99", "-shared", "-fPIC", "-o", so, c])
+        subprocess.check_call(["gcc", "-O1", "-std=c99", "-shared", "-fPIC", "-o", so, c, "-lm"])
         cases = tiny_traces() + [tg.stencil_1d(16, 6), tg.fig6_fixture()]
         wrong = 0
         for tr in cases:

@@ -296,6 +296,42 @@ def test_spin_body_closed_form():
             assert oracle.spin(x0, it) == (A * x0 + C) % (1 << 32)
 
 
+def round_to_binary32(q):
+    """Bits of the binary32 value nearest to the rational q (ties to even);
+    q is positive and in the normal range."""
+    from fractions import Fraction
+    assert q > 0
+    e = q.numerator.bit_length() - q.denominator.bit_length()
+    while Fraction(2) ** e > q:
+        e -= 1
+    while Fraction(2) ** (e + 1) <= q:
+        e += 1
+    m = q / Fraction(2) ** (e - 23)  # in [2^23, 2^24)
+    fl = m.numerator // m.denominator
+    rem = m - fl
+    if rem > Fraction(1, 2) or (rem == Fraction(1, 2) and fl % 2 == 1):
+        fl += 1
+    if fl == 1 << 24:
+        fl, e = 1 << 23, e + 1
+    return ((e + 127) << 23) | (fl - (1 << 23))
+
+
+def test_fma_body_is_binary32_fused_multiply_add():
+    """The FMA body against IEEE binary32 arithmetic written out with exact
+    rationals: each step takes x * a + b exactly and rounds it once to the
+    nearest float (ties to even); a = 0.999 and b = 0.25 as binary32."""
+    from fractions import Fraction
+    a = Fraction(float(np.float32(0.999)))
+    b = Fraction(1, 4)
+    for task in (0, 1, 7, 12345, 999_999, (1 << 24) + 1):
+        x = Fraction(float(np.float32(task)))  # the task id rounded to binary32
+        for it in range(0, 41):
+            if it in (0, 1, 2, 3, 17, 40):
+                want = round_to_binary32(x) if x != 0 else 0
+                assert oracle.fma_bits(task, it) == want, (task, it)
+            x = Fraction(float(np.frombuffer(np.uint32(round_to_binary32(x * a + b)).tobytes(), np.float32)[0]))
+
+
 def test_mix32_is_a_bijection_in_its_second_argument():
     for a in (0, 1, 0xdeadbeef):
         vals = {oracle.mix32(a, b) for b in range(1 << 12)}

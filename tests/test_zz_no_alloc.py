@@ -4,7 +4,9 @@ It serves callers that may not allocate device memory when they run a graph
 (an arena that owns all device memory, a loop where cudaMalloc/cudaFree is not
 allowed). Its output must equal the regular entry point's on the same graph,
 on two calls in a row (the calls share one static scratch array, so the second
-call checks that the first call's leftovers are re-initialised)."""
+call checks that the first call's leftovers are re-initialised), and its
+tickets must show every edge respected: the SPIN output depends on the task
+alone, so the order check is what shows that the countdowns held."""
 import numpy as np
 import pytest
 
@@ -40,10 +42,21 @@ def test_static_entry_matches_regular_entry(make):
     g.sync()
     ref = g.out.cpu().numpy().copy()
     rp, col, ind, n, e = _device_csr(g, torch)
+    src = np.repeat(np.arange(n), np.diff(rp.cpu().numpy()))
+    dst = col.cpu().numpy()[:e]
     for _ in range(2):
         out = torch.full((n,), -7, dtype=torch.int32, device="cuda")
-        grt.rt_execute_csr_static(rp.data_ptr(), col.data_ptr(), ind.data_ptr(), n, e, 64, out.data_ptr())
+        tk = torch.full((2 * n,), -1, dtype=torch.int32, device="cuda")
+        grt.rt_execute_csr_static(rp.data_ptr(), col.data_ptr(), ind.data_ptr(), n, e, 64, out.data_ptr(),
+                                  tk.data_ptr())
         assert np.array_equal(out.cpu().numpy(), ref)
+        t = tk.cpu().numpy().reshape(n, 2).astype(np.int64)
+        assert np.array_equal(np.sort(t.reshape(-1)), np.arange(2 * n)), "a task did not run exactly once"
+        assert np.all(t[src, 1] < t[dst, 0]), "an edge was not respected"
+    # and without tickets
+    out = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+    grt.rt_execute_csr_static(rp.data_ptr(), col.data_ptr(), ind.data_ptr(), n, e, 64, out.data_ptr())
+    assert np.array_equal(out.cpu().numpy(), ref)
     g.close()
 
 
