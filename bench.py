@@ -10,7 +10,9 @@ dependence analysis (binning, tile sweep, CSR) and one execution of the DAG.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 --impl reference times the CPU oracle on the same workload (host cores).
-With N > 1 (torchrun) every rank runs its own replica (weak scaling).
+With N > 1 (torchrun) every rank runs its own replica of the plain step (weak
+scaling); the batched leg's 4096 graphs are split across the ranks by
+footprint (strong scaling, no exchange between GPUs).
 """
 from __future__ import annotations
 
@@ -63,39 +65,43 @@ def config(tasks_per_step, args=None, tiles=None):
 BATCH_GRAPHS, BATCH_REPLAYS = 4096, 20
 
 
-def run_batched(grt, torch, flush, steps):
+def run_batched(grt, torch, flush, steps, world=1, rank=0):
     """The batched form: 4096 independent Task Bench graphs (sizes log-uniform
     64..65536, patterns mixed), captured once (analysis), then 20 replays of
-    every graph in one persistent launch per step."""
+    every graph in one persistent launch per step. With several ranks the
+    graphs are split across them by footprint (shard.py; no exchange between
+    GPUs): each rank captures and runs its share, and the job's time is the
+    slowest rank's."""
+    from paper_2508_16522_gb300 import shard
     t0 = time.perf_counter()
-    traces = tg.batch_graphs(BATCH_GRAPHS, seed=0)
+    all_traces = tg.batch_graphs(BATCH_GRAPHS, seed=0)
     gen_s = time.perf_counter() - t0
+    share = shard.my_share([shard.footprint(t) for t in all_traces], world, rank)
+    traces = [all_traces[k] for k in share]
+    total_tasks = sum(t.n for t in all_traces)
+    cache = TUNE_CACHE if world == 1 else None  # ranks would append to one file at once
     stream = torch.cuda.Stream()
     big = max(traces, key=lambda t: t.n)
-    tile = list(grt.rt_tune_tile(big, TUNE_CACHE)[:2])  # tuned on the largest graph
-    # capture: the graphs are stacked in bands of one domain and analysed by
-    # ONE analysis; the batch takes each graph's part of the result
-    t0 = time.perf_counter()
-    st, off = tg.stack_bands(traces, name="batch")
-    stack_s = time.perf_counter() - t0
-    inputs = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (st.req_off, st.lo, st.hi, st.priv)]
+    tile = list(grt.rt_tune_tile(big, cache)[:2])  # tuned on the largest graph
+    # capture: the library places the graphs in bands of one domain and
+    # analyses them ONCE (rt_batch_capture); the inputs are each graph's own
+    # launches, concatenated, on the device
+    inputs = [torch.from_numpy(a).cuda() for a in grt.concat_inputs(traces)]
     torch.cuda.synchronize()
-    g = grt.Graph(2, st.dom_lo, st.dom_hi, tile=tile, stream=stream, flags=grt.RT_GRAPH_PROFILE)
     capture_ms = []
-    for rep in range(2):  # the first run grows the buffers
+    batch = None
+    for rep in range(2):  # the first capture loads and sizes everything
+        if batch is not None:
+            batch.close()
         t0 = time.perf_counter()
-        g.clear()
-        g.launch(*inputs, defer_check=True)
-        g.analyze()
+        batch = grt.Batch.capture(traces, tile=tile, stream=stream, flags=grt.RT_GRAPH_PROFILE, inputs=inputs)
         capture_ms.append((time.perf_counter() - t0) * 1e3)
     capture_ms = capture_ms[-1]
-    gst = g.stats()
+    gst = batch.graph_stats()
     ana_ms = gst["ms_analyze"]
-    graphs = [g]
-    T = st.n
+    T = gst["n_tasks"]
     E = gst["n_edges"]
-    batch = grt.Batch.stacked(g, off, stream=stream)
-    shape = batch.tune(replays=BATCH_REPLAYS, cache_path=TUNE_CACHE)
+    shape = batch.tune(replays=BATCH_REPLAYS, cache_path=cache)
     launch = {k: shape[k] for k in ("blocks", "warps", "claim", "keep")}
     batch.execute(replays=BATCH_REPLAYS, **launch)
     batch.sync()
@@ -106,6 +112,10 @@ def run_batched(grt, torch, flush, steps):
         batch.execute(replays=BATCH_REPLAYS, **launch)
         ms.append(batch.sync())
     kern = float(np.mean(ms))
+    if world > 1:  # the job's launch and capture take as long as the slowest rank's
+        kern = max_over_ranks(kern, "cuda")
+        capture_ms = max_over_ranks(capture_ms, "cuda")
+        T = total_tasks
     done = T * BATCH_REPLAYS
     out = {"workload": f"{BATCH_GRAPHS} Task Bench graphs, sizes log-uniform 64..65536, stencil/butterfly/random "
                        f"mixed, region-encoded, EMPTY bodies; {BATCH_REPLAYS} replays of every graph in one "
@@ -113,14 +123,16 @@ def run_batched(grt, torch, flush, steps):
            "replays": BATCH_REPLAYS, "ms_per_launch": kern, "exec_tasks_per_s": done / (kern * 1e-3),
            "exec_ns_per_task": kern * 1e6 / done, "capture_wall_ms": capture_ms,
            "capture_ns_per_task": capture_ms * 1e6 / T, "analysis_kernel_ms": ana_ms,
-           "capture": f"the {BATCH_GRAPHS} graphs stacked in bands of one {st.dom_hi[0] + 1} x {st.dom_hi[1] + 1} "
-                      f"domain ({st.n_rects} rectangles, inputs on the device), analysed once, tile {tile}",
-           "stack_s": stack_s,
+           "capture": f"rt_batch_capture: the library places the graphs' launches ({sum(t.n_rects for t in traces)} "
+                      f"rectangles, each graph in its own domain, inputs on the device) in bands of one domain and "
+                      f"analyses them once, tile {tile}; the launch itself is relaunched from a cached CUDA graph",
+           "graph_captured_launches": batch.info()["graph_launches"],
            "tasks_per_s_incl_capture": done / ((kern + capture_ms) * 1e-3), "generate_s": gen_s,
-           "timed_launches": steps, "autotune": {"tile": tile, "exec": shape}}
+           "timed_launches": steps, "autotune": {"tile": tile, "exec": shape},
+           "ranks": world, "split": "graphs placed on ranks by footprint, largest first (no exchange); time = "
+                                    "slowest rank's" if world > 1 else None,
+           "scaling": "strong" if world > 1 else None}
     batch.close()
-    for g in graphs:
-        g.close()
     return out
 
 
@@ -164,7 +176,9 @@ def run_metg(grt, torch, ns_per_iter):
     res = {"iters": METG_ITERS, "steps": METG_STEPS,
            "body": "FMA: `iters` dependent fma.rn.f32 (x = x * 0.999f + 0.25f) on one lane per task",
            "ns_per_iteration_alone": ns_per_iter,
-           "efficiency": "steps x iters x ns_per_iteration_alone / run time (one denominator per box)"}
+           "efficiency": "steps x iters x ns_per_iteration_alone / run time (one denominator per box)",
+           "launch": "both executors claim one ready task per warp at a time, so that a step's long bodies "
+                     "spread over warps instead of running one after another in one warp"}
     for width in (8, 32):
         tr = tg.taskbench(width, METG_STEPS, "stencil", seed=0)
         for kind in ("compiled", "events"):
@@ -175,6 +189,7 @@ def run_metg(grt, torch, ns_per_iter):
                               flags=grt.RT_GRAPH_PROFILE)
                 g.launch_trace(tr)
                 g.analyze()
+                g.exec_config(claim=1)  # both executors: one ready task per warp claim
                 runs = []
                 for _ in range(3):
                     if kind == "compiled":
@@ -821,8 +836,8 @@ def run_ours(args):
         e2e_ms, _ = timed(host_inputs, args.steps, defer=True)
     h2d = sum(sum(int(a.numel() * a.element_size()) for a in inp) for inp in host_inputs)
     batched = None
-    if world == 1 and not args.no_batched:
-        batched = run_batched(grt, torch, flush, max(1, min(args.steps, 3)))
+    if not args.no_batched:
+        batched = run_batched(grt, torch, flush, max(1, min(args.steps, 3)), world, rank)
     # the executor's own rooflines (dependent atomic latency, scattered atomics)
     # and the FMA body's rate alone
     mb = grt.rt_microbench_atomics()

@@ -249,9 +249,10 @@ rt_status rt_execute_kernels(rt_graph_t g, int32_t mode, int32_t iters, int32_t 
 
 /* Launch shape of this graph's executor runs (0 = library default): number of
  * persistent blocks, warps per block (1..8), how many published ring slots a
- * warp claims at once (1..32) and how many newly ready successors a warp keeps
- * for its own next batch instead of publishing them (0..64). These are the
- * autotuner's knobs; results do not depend on them. */
+ * warp claims at once (1..32; default 8) and how many newly ready successors a
+ * warp keeps for its own next batch instead of publishing them (0..64). These
+ * are the autotuner's knobs; results do not depend on them. The event-based
+ * executor (rt_execute_events) takes the same claim width. */
 rt_status rt_graph_exec_config(rt_graph_t g, int32_t blocks, int32_t warps, int32_t claim, int32_t keep);
 
 /* Waits for the graph's stream; returns RT_OK, RT_ERR_TIMEOUT (the executor
@@ -298,15 +299,50 @@ rt_status rt_batch_create(const rt_graph_t* graphs, int32_t n_graphs, void* stre
 rt_status rt_batch_create_stacked(rt_graph_t g, const int32_t* task_off, int32_t n_graphs, void* stream,
                                   rt_batch_t* out);
 
+/* Captures a batch of independent graphs with ONE analysis, placing them in
+ * bands of one domain itself (Section 4.1: each graph is then launched as one
+ * operation; Section 5: the analysis is done once and replayed). Graph k owns
+ * launches [task_off[k], task_off[k+1]) of the arrays (host task_off
+ * int32[n_graphs+1], from 0), and its rectangles are in its OWN domain
+ * [graph_lo[k], graph_hi[k]] (host int64[n_graphs][ndim], inclusive). The
+ * library stacks the domains along the last dimension -- graph k's band starts
+ * where graph k-1's ends, at 0 across the other dimension -- so that the
+ * graphs share no cell, copies the launches (req_off int32[n+1] over all
+ * launches, lo/hi int64[R][ndim], priv uint8[R], R = req_off[n]; host arrays,
+ * or device arrays with RT_LAUNCH_DEVICE), checks on the device that every
+ * rectangle lies in its own graph's domain and moves it into the graph's band,
+ * analyses the stacked graph and builds the batch as
+ * rt_batch_create_stacked does. desc gives ndim, body, spin_iters, the body
+ * buffers, stream, tile, timeout and flags (its domain is ignored): `out`
+ * holds one int32 per task of all graphs, and a CHECK body's `state` one int32
+ * per cell of the stacked domain, [0, W-1] x [0, H-1] in 2-D with W the
+ * widest graph and H the sum of the graphs' heights ([0, sum of lengths - 1]
+ * in 1-D). The batch owns the stacked graph; *graph_out (may be NULL)
+ * receives it for rt_copy_csr and rt_graph_stats, valid until the batch is
+ * destroyed. Errors: RT_ERR_INVALID (bad offsets or domains, a rectangle
+ * outside its graph's domain -- reported by the analysis), RT_ERR_OOM,
+ * RT_ERR_CUDA. */
+rt_status rt_batch_capture(const rt_graph_desc* desc, int32_t n_graphs, const int32_t* task_off,
+                           const int64_t* graph_lo, const int64_t* graph_hi, const int32_t* req_off, const int64_t* lo,
+                           const int64_t* hi, const uint8_t* priv, int32_t flags, rt_batch_t* out,
+                           rt_graph_t* graph_out);
+
 /* One persistent launch in which every graph of the batch runs `replays` times
  * (1..4096); graph g's replay r+1 starts as soon as its replay r has finished,
  * independently of the other graphs. exec_blocks/exec_warps/claim/keep (0 =
  * default) are the launch shape of rt_graph_exec_config. The batch's counters
- * are reset at the start of every launch. Asynchronous. */
+ * are reset at the start of every launch. The launch {counter reset, seed,
+ * executor, status read-back} is captured as a CUDA graph once per launch
+ * shape and relaunched from it afterwards (the first launch of a new or
+ * grown ring, which clears the whole ring, is issued directly). Asynchronous. */
 rt_status rt_batch_execute(rt_batch_t b, int32_t replays, int32_t exec_blocks, int32_t exec_warps,
                            int32_t claim, int32_t keep);
 
 rt_status rt_batch_sync(rt_batch_t b, float* ms_kernel);
+
+/* out[0] graphs, [1] tasks, [2] edges, [3] launches made from the cached CUDA
+ * graph so far (n values; no device work). */
+rt_status rt_batch_info(rt_batch_t b, int64_t* out, int32_t n);
 
 /* The first n (<= 9) diagnostic counters of the last batch launch, in the
  * order of rt_graph_stats_t.exec_counters (synchronises). */

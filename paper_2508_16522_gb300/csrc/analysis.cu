@@ -26,7 +26,39 @@ namespace grt {
 namespace {
 
 // error bits of the device-side validation
-constexpr uint32_t kErrReqOff = 1u, kErrRect = 2u, kErrPriv = 4u, kErrPred = 8u, kErrBodyArg = 16u;
+constexpr uint32_t kErrReqOff = 1u, kErrRect = 2u, kErrPriv = 4u, kErrPred = 8u, kErrBodyArg = 16u, kErrBand = 32u;
+
+// the last k in [0, n) with first[k] <= x (first[0] <= x, first nondecreasing)
+__device__ __forceinline__ int32_t last_at_most(const int32_t* first, int32_t n, int64_t x) {
+  int32_t lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int32_t mid = (lo + hi + 1) >> 1;
+    if ((int64_t)first[mid] <= x) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Band placement of a captured batch (rt_batch_capture): rectangle r belongs
+// to the task whose rectangle range holds it, which belongs to graph k; it must
+// lie in graph k's own domain (kErrBand otherwise) and moves by graph k's shift
+// into its band of the stacked domain. box[k] = {lo[D], hi[D], shift[D]}.
+__global__ void k_band_place(const int32_t* req_off, int32_t n, const int32_t* task_first, int32_t G,
+                             const int64_t* box, int D, int64_t* lo, int64_t* hi, int64_t R, uint32_t* err) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R; r += stride) {
+    const int32_t t = last_at_most(req_off, n, r);
+    const int32_t k = last_at_most(task_first, G, t);
+    const int64_t* b = box + (int64_t)k * 3 * D;
+    bool outside = false;
+    for (int d = 0; d < D; ++d) {
+      const int64_t a = lo[r * D + d], c = hi[r * D + d];
+      if (a < b[d] || c > b[D + d]) outside = true;
+      lo[r * D + d] = a + b[2 * D + d];
+      hi[r * D + d] = c + b[2 * D + d];
+    }
+    if (outside) atomicOr(err, kErrBand);
+  }
+}
 
 // Checks one appended batch whose offsets were already shifted to graph-wide
 // positions: req_off[0..n] must run from r_first to r_end without decreasing;
@@ -260,6 +292,15 @@ void launch_validate(const int32_t* req_off, int32_t n, int64_t r_first, const i
     count_launch();
     k_validate_rects<<<nblk(R, 256), 256, 0, s>>>(lo, hi, priv, R, d, err);
   }
+}
+
+void launch_band_place(const int32_t* req_off, int32_t n, const int32_t* task_first, int32_t G, const int64_t* box,
+                       int D, int64_t* lo, int64_t* hi, int64_t R, uint32_t* err, cudaStream_t s) {
+  if (R <= 0) return;
+  unsigned blocks = nblk(R, 256);
+  if (blocks > 4096) blocks = 4096;
+  count_launch();
+  k_band_place<<<blocks, 256, 0, s>>>(req_off, n, task_first, G, box, D, lo, hi, R, err);
 }
 
 void launch_add_offset(int32_t* a, int64_t n, int32_t add, cudaStream_t s) {

@@ -217,6 +217,13 @@ struct rt_batch {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   bool dirty = false;
   int need_fence = 0;
+  // the launch as a CUDA graph {counter reset, seed, executor, status
+  // read-back}, instantiated once per launch shape and relaunched
+  cudaGraphExec_t gexec = nullptr;
+  int64_t gkey[7] = {0, 0, 0, 0, 0, 0, 0};
+  cudaStream_t cap_stream = nullptr;
+  int64_t graph_launches = 0;  // launches that went through the cached CUDA graph
+  rt_graph* owned = nullptr;   // rt_batch_capture: the stacked graph it analysed
 };
 
 namespace {
@@ -413,9 +420,30 @@ rt_status ensure_pinned(rt_graph* g) {
 
 }  // namespace
 
+namespace {
+// rt_batch_capture's placement of graphs in bands, applied to the launches of
+// a fresh graph between their copy and their validation
+struct BandPlace {
+  const int32_t* task_first;  // device int32[G+1]: graph k owns tasks [task_first[k], task_first[k+1])
+  int32_t G;
+  const int64_t* box;         // device int64[G][3][ndim]: its domain's lo, hi and its shift
+};
+
+rt_status append_launches(rt_graph_t g, int32_t n, const int32_t* req_off, const int64_t* lo, const int64_t* hi,
+                          const uint8_t* priv, const int32_t* pred_off, const int32_t* pred, const int32_t* body_arg,
+                          int32_t flags, const BandPlace* bp);
+}  // namespace
+
 extern "C" rt_status rt_launch_batch(rt_graph_t g, int32_t n, const int32_t* req_off, const int64_t* lo,
                                      const int64_t* hi, const uint8_t* priv, const int32_t* pred_off,
                                      const int32_t* pred, const int32_t* body_arg, int32_t flags) {
+  return append_launches(g, n, req_off, lo, hi, priv, pred_off, pred, body_arg, flags, nullptr);
+}
+
+namespace {
+rt_status append_launches(rt_graph_t g, int32_t n, const int32_t* req_off, const int64_t* lo, const int64_t* hi,
+                          const uint8_t* priv, const int32_t* pred_off, const int32_t* pred, const int32_t* body_arg,
+                          int32_t flags, const BandPlace* bp) {
   if (!g) return fail(RT_ERR_INVALID, "graph is NULL");
   if (g->analyzed) return fail(RT_ERR_STATE, "graph already analyzed; call rt_graph_clear first");
   if (n < 0) return fail(RT_ERR_INVALID, "n < 0");
@@ -513,6 +541,9 @@ extern "C" rt_status rt_launch_batch(rt_graph_t g, int32_t n, const int32_t* req
       CKR(g->err.reserve(256, s));
       CK(cudaMemsetAsync(g->err.p, 0, 4, s));
     }
+    if (bp)  // each rectangle checked against its own graph's domain, then moved into its band
+      launch_band_place(g->req_off.as<int32_t>() + n0, n, bp->task_first, bp->G, bp->box, D,
+                        g->lo.as<int64_t>() + R0 * D, g->hi.as<int64_t>() + R0 * D, R, g->err.as<uint32_t>(), s);
     const int64_t limit = g->desc.body == RT_BODY_COUNTER ? g->desc.state_elems : -1;
     launch_validate(g->req_off.as<int32_t>() + n0, n, R0, g->lo.as<int64_t>() + R0 * D,
                     g->hi.as<int64_t>() + R0 * D, g->priv.as<uint8_t>() + R0, R,
@@ -528,6 +559,7 @@ extern "C" rt_status rt_launch_batch(rt_graph_t g, int32_t n, const int32_t* req
   g->P += Pb;
   return RT_OK;
 }
+}  // namespace
 
 // ---------------------------------------------------------------------------
 // analysis
@@ -535,6 +567,7 @@ extern "C" rt_status rt_launch_batch(rt_graph_t g, int32_t n, const int32_t* req
 namespace {
 
 const char* err_bits_text(uint32_t e) {
+  if (e & 32u) return "a rectangle lies outside its own graph's domain";
   if (e & 2u) return "a rectangle has lo > hi or lies outside the domain";
   if (e & 4u) return "a privilege is not read/write/reduce";
   if (e & 1u) return "req_off does not start at 0, decreases, or does not end at the rect count";
@@ -1091,6 +1124,7 @@ rt_status rt_execute_events(rt_graph_t g, float* ms_kernel) {
   CKR(g->ev_ctrl.reserve(sizeof(EvCtrl), s));
   CK(cudaMemsetAsync(g->ev_ctrl.p, 0, sizeof(EvCtrl), s));
   EvParams p{};
+  p.claim = std::min(std::max(g->cfg_claim > 0 ? g->cfg_claim : 8, 1), 32);  // as the compiled executor's
   p.pred_off = g->ev_pred_off.as<int32_t>();
   p.pred = g->ev_pred.as<int32_t>();
   p.n = n;
@@ -1545,6 +1579,106 @@ rt_status rt_batch_create_stacked(rt_graph_t g, const int32_t* task_off, int32_t
   return RT_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// One batch launch on stream s: the launch's INIT (a batch's counters count up
+// from 0 across its replays; the ring is cleared only when it is new or dirty),
+// the persistent executor and the status read-back.
+rt_status enqueue_batch(rt_batch* b, const ExecParams& p, int64_t ring_clear, int blocks, int warps,
+                        cudaStream_t s) {
+  CK(cudaMemsetAsync(b->count.p, 0, (size_t)b->T * 4, s));
+  launch_seed(p, ring_clear, s);
+  launch_exec(p, blocks, warps, s);
+  CK(cudaMemcpyAsync(b->hpin, &p.ctrl->status, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(reinterpret_cast<char*>(b->hpin) + 512, p.ctrl->counters, kCntCount * sizeof(unsigned long long),
+                     cudaMemcpyDeviceToHost, s));
+  return RT_OK;
+}
+
+void drop_batch_graph(rt_batch* b) {
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  b->gexec = nullptr;
+}
+}  // namespace
+
+extern "C" {
+
+rt_status rt_batch_capture(const rt_graph_desc* desc, int32_t n_graphs, const int32_t* task_off,
+                           const int64_t* graph_lo, const int64_t* graph_hi, const int32_t* req_off, const int64_t* lo,
+                           const int64_t* hi, const uint8_t* priv, int32_t flags, rt_batch_t* out,
+                           rt_graph_t* graph_out) {
+  if (!out) return fail(RT_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (graph_out) *graph_out = nullptr;
+  if (!desc || !task_off || !graph_lo || !graph_hi || !req_off)
+    return fail(RT_ERR_INVALID, "NULL descriptor, offsets, domains or req_off");
+  if (n_graphs <= 0 || n_graphs >= (1 << 20))
+    return fail(RT_ERR_INVALID, "a batch holds 1 to 2^20 - 1 graphs (got %d)", n_graphs);
+  if (desc->ndim != 1 && desc->ndim != 2) return fail(RT_ERR_INVALID, "ndim must be 1 or 2");
+  if (flags & ~(RT_LAUNCH_DEVICE | RT_LAUNCH_DEFER_CHECK)) return fail(RT_ERR_INVALID, "unknown flags");
+  const int D = desc->ndim, sd = D - 1;  // graphs are stacked along the last dimension
+  if (task_off[0] != 0) return fail(RT_ERR_INVALID, "task_off[0] must be 0");
+  // the bands: graph k's domain moves to origin 0 across the other dimension
+  // and to the sum of the earlier graphs' extents along the stacking one
+  std::vector<int64_t> box((size_t)n_graphs * 3 * D);
+  int64_t along = 0, across = 1;
+  for (int32_t k = 0; k < n_graphs; ++k) {
+    if (task_off[k + 1] < task_off[k]) return fail(RT_ERR_INVALID, "task_off decreases at graph %d", k);
+    int64_t* b = &box[(size_t)k * 3 * D];
+    for (int d = 0; d < D; ++d) {
+      const int64_t l = graph_lo[(size_t)k * D + d], h = graph_hi[(size_t)k * D + d];
+      if (l > h || h - l >= (1ll << 40)) return fail(RT_ERR_INVALID, "graph %d has an empty or huge domain", k);
+      b[d] = l;
+      b[D + d] = h;
+      b[2 * D + d] = (d == sd ? along : 0) - l;
+      if (d != sd) across = std::max<int64_t>(across, h - l + 1);
+    }
+    along += graph_hi[(size_t)k * D + sd] - graph_lo[(size_t)k * D + sd] + 1;
+    if (along >= (1ll << 40)) return fail(RT_ERR_INVALID, "the stacked domain is too long");
+  }
+  const int32_t n = task_off[n_graphs];
+  rt_graph_desc sdesc = *desc;
+  sdesc.dom_lo[0] = sdesc.dom_lo[1] = 0;
+  sdesc.dom_hi[0] = D == 2 ? across - 1 : along - 1;
+  sdesc.dom_hi[1] = D == 2 ? along - 1 : 0;
+  rt_graph_t g = nullptr;
+  CKR(rt_graph_create(&sdesc, &g));
+  auto bail = [&](rt_status st) {
+    const std::string msg = g_err;
+    rt_graph_destroy(g);
+    g_err = msg;
+    return st;
+  };
+  rt_status st = ensure_device();
+  if (st != RT_OK) return bail(st);
+  // the offsets and bands on the device, for the placement kernel
+  DevBuf place;
+  const size_t off_bytes = ((size_t)n_graphs + 1) * 4, box_off = (off_bytes + 15) / 16 * 16;
+  if ((st = place.reserve(box_off + box.size() * 8, g->s)) != RT_OK) return bail(st);
+  if (cudaMemcpyAsync(place.p, task_off, off_bytes, cudaMemcpyHostToDevice, g->s) != cudaSuccess ||
+      cudaMemcpyAsync(static_cast<char*>(place.p) + box_off, box.data(), box.size() * 8, cudaMemcpyHostToDevice,
+                      g->s) != cudaSuccess) {
+    place.release(g->s);
+    return bail(fail(RT_ERR_CUDA, "band table copy failed"));
+  }
+  BandPlace bp{place.as<int32_t>(), n_graphs,
+               reinterpret_cast<const int64_t*>(static_cast<char*>(place.p) + box_off)};
+  // host arrays are validated on the device too: their coordinates are each
+  // graph's own until the placement moves them
+  const int32_t fl = (flags & RT_LAUNCH_DEVICE) ? RT_LAUNCH_DEVICE : RT_LAUNCH_DEFER_CHECK;
+  st = append_launches(g, n, req_off, lo, hi, priv, nullptr, nullptr, nullptr, fl, &bp);
+  if (st == RT_OK) st = rt_analyze(g);
+  place.release(g->s);
+  if (st != RT_OK) return bail(st);
+  std::vector<int32_t> toff(task_off, task_off + n_graphs + 1);
+  st = rt_batch_create_stacked(g, toff.data(), n_graphs, desc->stream, out);
+  if (st != RT_OK) return bail(st);
+  (*out)->owned = g;
+  if (graph_out) *graph_out = g;
+  return RT_OK;
+}
+
 rt_status rt_batch_execute(rt_batch_t b, int32_t replays, int32_t exec_blocks, int32_t exec_warps, int32_t claim,
                            int32_t keep) {
   if (!b) return fail(RT_ERR_INVALID, "batch is NULL");
@@ -1558,12 +1692,10 @@ rt_status rt_batch_execute(rt_batch_t b, int32_t replays, int32_t exec_blocks, i
   cudaStream_t s = b->s;
   bool clear = b->dirty;
   if (cap * 8 > b->ring.cap) {
+    drop_batch_graph(b);
     CKR(b->ring.reserve((size_t)cap * 8, s));
     clear = true;
   }
-  // the launch's INIT: a batch's counters count up from 0 across its replays
-  CK(cudaEventRecord(b->e0, s));
-  CK(cudaMemsetAsync(b->count.p, 0, (size_t)b->T * 4, s));
   ExecParams p{};
   p.adj = b->adj.as<int4>();
   p.row_ptr = b->row_ptr.as<int32_t>();
@@ -1585,14 +1717,43 @@ rt_status rt_batch_execute(rt_batch_t b, int32_t replays, int32_t exec_blocks, i
   p.tickets = nullptr;
   p.total_roots = (int32_t)b->Rtot;
   p.need_fence = b->need_fence;
-  launch_seed(p, clear ? (int64_t)(b->ring.cap / 8) : 0, s);
-  launch_exec(p, blocks, warps, s);
+  CK(cudaEventRecord(b->e0, s));
+  if (clear) {
+    // a new or dirty ring is cleared whole: a direct launch
+    CKR(enqueue_batch(b, p, (int64_t)(b->ring.cap / 8), blocks, warps, s));
+  } else {
+    // the launch from a cached CUDA graph, captured once per launch shape
+    const int64_t key[7] = {replays, blocks, warps, p.claim, p.keep, (int64_t)(uintptr_t)p.ring, (int64_t)p.ring_cap};
+    if (!b->gexec || memcmp(key, b->gkey, sizeof key) != 0) {
+      drop_batch_graph(b);
+      if (!b->cap_stream) CK(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+      CK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+      rt_status st = enqueue_batch(b, p, 0, blocks, warps, b->cap_stream);
+      cudaGraph_t graph = nullptr;
+      cudaError_t e = cudaStreamEndCapture(b->cap_stream, &graph);
+      if (st != RT_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+      }
+      if (e != cudaSuccess) return fail(RT_ERR_CUDA, "batch capture: %s", cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&b->gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return fail(RT_ERR_CUDA, "batch instantiate: %s", cudaGetErrorString(e));
+      memcpy(b->gkey, key, sizeof key);
+    }
+    CK(cudaGraphLaunch(b->gexec, s));
+    ++b->graph_launches;
+  }
   CK(cudaEventRecord(b->e1, s));
-  CK(cudaMemcpyAsync(b->hpin, &p.ctrl->status, 4, cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(reinterpret_cast<char*>(b->hpin) + 512, p.ctrl->counters, kCntCount * sizeof(unsigned long long),
-                     cudaMemcpyDeviceToHost, s));
   CK(cudaGetLastError());
   b->dirty = false;
+  return RT_OK;
+}
+
+rt_status rt_batch_info(rt_batch_t b, int64_t* out, int32_t n) {
+  if (!b || !out || n < 0) return fail(RT_ERR_INVALID, "NULL argument");
+  const int64_t v[4] = {b->G, b->T, b->E, b->graph_launches};
+  for (int32_t k = 0; k < n; ++k) out[k] = k < 4 ? v[k] : 0;
   return RT_OK;
 }
 
@@ -1621,12 +1782,15 @@ rt_status rt_batch_sync(rt_batch_t b, float* ms_kernel) {
 rt_status rt_batch_destroy(rt_batch_t b) {
   if (!b) return RT_OK;
   cudaStreamSynchronize(b->s);
+  drop_batch_graph(b);
   DevBuf* bufs[] = {&b->row_ptr, &b->col, &b->indeg, &b->count, &b->root_items, &b->gtable, &b->done_g, &b->ring, &b->ctrl, &b->adj};
   for (DevBuf* x : bufs) x->release(b->s);
   cudaStreamSynchronize(b->s);
   if (b->hpin) cudaFreeHost(b->hpin);
   if (b->e0) cudaEventDestroy(b->e0);
   if (b->e1) cudaEventDestroy(b->e1);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  if (b->owned) rt_graph_destroy(b->owned);
   delete b;
   return RT_OK;
 }

@@ -17,7 +17,7 @@
 // fails once the event has triggered). A task's pending count starts at 1 (a
 // guard released when its registration ends), so it cannot fire before it is
 // fully registered. Then warps take ready tasks from a ring (each lane claims
-// the next ticket and waits for its slot), run the body,
+// one of the warp's `claim` tickets and waits for its slot), run the body,
 // trigger the event (an atomic exchange that returns the waiter list) and
 // walk the list, decrementing each waiter's pending count. Per edge that is
 // a node allocation, a pending increment, a list push and a pending decrement
@@ -126,8 +126,9 @@ __global__ void __launch_bounds__(256) k_events(EvParams p) {
     if (!__any_sync(0xffffffffu, item != kFree)) {
       if (!__any_sync(0xffffffffu, my != kNoTk)) {
         uint32_t h = 0;
-        if (lane == 0) h = atomicAdd(&p.ctrl->rhead, 32u);
-        my = __shfl_sync(0xffffffffu, h, 0) + (uint32_t)lane;
+        if (lane == 0) h = atomicAdd(&p.ctrl->rhead, (uint32_t)p.claim);
+        h = __shfl_sync(0xffffffffu, h, 0);
+        if (lane < p.claim) my = h + (uint32_t)lane;
         continue;
       }
       int stop = 0;

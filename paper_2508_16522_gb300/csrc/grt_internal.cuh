@@ -264,6 +264,10 @@ void launch_validate(const int32_t* req_off, int32_t n, int64_t r_first, const i
                      const int32_t* body_arg, int64_t body_limit, AnalysisDims d, uint32_t* err,
                      cudaStream_t s);
 void launch_add_offset(int32_t* a, int64_t n, int32_t add, cudaStream_t s);
+// rt_batch_capture: checks every rectangle against its graph's own domain and
+// moves it into the graph's band (box: int64 [G][3][ndim] = lo, hi, shift)
+void launch_band_place(const int32_t* req_off, int32_t n, const int32_t* task_first, int32_t G, const int64_t* box,
+                       int D, int64_t* lo, int64_t* hi, int64_t R, uint32_t* err, cudaStream_t s);
 void launch_bin_count(const int32_t* req_off, int32_t n, const int64_t* lo, const int64_t* hi,
                       int64_t R, AnalysisDims d, int32_t* rect_task, uint64_t* cnt, cudaStream_t s);
 void launch_bin_expand(const int32_t* rect_task, const int64_t* lo, const int64_t* hi,
@@ -333,6 +337,7 @@ struct EvParams {
   EvCtrl* ctrl;
   ExecGraph G;
   int64_t timeout_ns;
+  int32_t claim;            // ring tickets a warp claims at once (1..32), one per lane
 };
 void launch_ev_transpose(const int32_t* row_ptr, const int32_t* col, int32_t n, const int32_t* pred_off,
                          int32_t* cursor, int32_t* pred, cudaStream_t s);

@@ -36,7 +36,7 @@ EXPORTS = ["rt_graph_create", "rt_graph_destroy", "rt_graph_clear", "rt_launch_b
            "rt_server_drain",
            "rt_server_stats", "rt_server_destroy", "rt_tune_tile", "rt_tune_exec", "rt_tune_batch",
            "rt_batch_create_stacked", "rt_execute_events", "rt_execute_kernels",
-           "rt_execute_stitched", "rt_copy_stitched_tickets"]
+           "rt_execute_stitched", "rt_copy_stitched_tickets", "rt_batch_capture", "rt_batch_info"]
 
 
 class GrtError(RuntimeError):
@@ -147,6 +147,9 @@ def load(path: str = LIB_PATH):
                          ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)],
         "rt_tune_exec": [P, ctypes.c_char_p, ctypes.POINTER(rt_exec_config)],
         "rt_batch_create_stacked": [P, P, i32, P, ctypes.POINTER(P)],
+        "rt_batch_capture": [ctypes.POINTER(rt_graph_desc), i32, P, P, P, P, P, P, P, i32, ctypes.POINTER(P),
+                             ctypes.POINTER(P)],
+        "rt_batch_info": [P, ctypes.POINTER(i64), i32],
         "rt_execute_events": [P, ctypes.POINTER(ctypes.c_float)],
         "rt_execute_kernels": [P, i32, i32, i32, ctypes.POINTER(ctypes.c_float)],
         "rt_execute_stitched": [P, i32, ctypes.POINTER(ctypes.c_float)],
@@ -441,6 +444,62 @@ class Batch:
         self.h = h.value
         return self
 
+    @classmethod
+    def capture(cls, traces, body=RT_BODY_EMPTY, spin_iters=256, state=None, out=None, stream=None, tile=(0, 0),
+                flags=0, inputs=None):
+        """A batch of independent traces captured by ONE analysis, the library
+        placing them in bands of one domain (rt_batch_capture). `inputs`
+        (optional): the concatenated (req_off, lo, hi, priv) already on the
+        device, as from concat_inputs(traces)."""
+        ndim = traces[0].ndim
+        d = rt_graph_desc()
+        d.ndim = ndim
+        d.body, d.spin_iters = body, spin_iters
+        if state is not None:
+            d.state, d.state_elems = state.data_ptr(), state.numel()
+        if out is not None:
+            d.out, d.out_elems = out.data_ptr(), out.numel()
+        d.stream = None if stream is None else stream.cuda_stream
+        d.tile_w, d.tile_h = int(tile[0]), int(tile[1])
+        d.flags = flags
+        task_off = np.zeros(len(traces) + 1, np.int32)
+        np.cumsum([t.n for t in traces], out=task_off[1:])
+        glo = np.ascontiguousarray(np.stack([t.dom_lo for t in traces]), np.int64)
+        ghi = np.ascontiguousarray(np.stack([t.dom_hi for t in traces]), np.int64)
+        if inputs is None:
+            inputs = concat_inputs(traces)
+        ptrs = [_ptr(a) for a in inputs]
+        dev = any(p[1] for p in ptrs)
+        h, gh = ctypes.c_void_p(), ctypes.c_void_p()
+        _check(load().rt_batch_capture(ctypes.byref(d), len(traces), task_off.ctypes.data, glo.ctypes.data,
+                                       ghi.ctypes.data, *[p[0] for p in ptrs], RT_LAUNCH_DEVICE if dev else 0,
+                                       ctypes.byref(h), ctypes.byref(gh)))
+        self = cls.__new__(cls)
+        self.graphs = []
+        self.h = h.value
+        self.graph_h = gh.value  # owned by the batch
+        self.task_off = task_off
+        self._keep = (state, out, inputs)
+        return self
+
+    def info(self) -> dict:
+        arr = (ctypes.c_int64 * 4)()
+        _check(load().rt_batch_info(self.h, arr, 4))
+        return dict(zip(("graphs", "tasks", "edges", "graph_launches"), list(arr)))
+
+    def graph_csr(self):
+        """(row_ptr, col, indeg) of the captured stacked graph (rt_batch_capture)."""
+        st = rt_graph_stats(self.graph_h)
+        n, e = st["n_tasks"], st["n_edges"]
+        rp = np.empty(n + 1, np.int32)
+        col = np.empty(max(e, 1), np.int32)
+        ind = np.empty(max(n, 1), np.int32)
+        _check(load().rt_copy_csr(self.graph_h, rp.ctypes.data, col.ctypes.data, ind.ctypes.data))
+        return rp, col[:e], ind[:n]
+
+    def graph_stats(self) -> dict:
+        return rt_graph_stats(self.graph_h)
+
     def execute(self, replays: int = 1, blocks: int = 0, warps: int = 0, claim: int = 0, keep: int = 0):
         _check(load().rt_batch_execute(self.h, replays, blocks, warps, claim, keep))
 
@@ -473,8 +532,21 @@ class Batch:
             pass
 
 
+def concat_inputs(traces):
+    """The launches of several traces as one (req_off, lo, hi, priv) set of host
+    arrays, each trace's rectangles still in its own domain (rt_batch_capture
+    places them). Concatenation only: no coordinate is changed."""
+    counts = np.concatenate([np.diff(t.req_off) for t in traces])
+    req_off = np.zeros(len(counts) + 1, np.int32)
+    np.cumsum(counts, out=req_off[1:])
+    lo = np.ascontiguousarray(np.concatenate([t.lo for t in traces]), np.int64)
+    hi = np.ascontiguousarray(np.concatenate([t.hi for t in traces]), np.int64)
+    priv = np.ascontiguousarray(np.concatenate([t.priv for t in traces]), np.uint8)
+    return req_off, lo, hi, priv
+
+
 def body_name(b: int) -> str:
-    return ["EMPTY", "SPIN", "COUNTER", "CHECK"][b]
+    return ["EMPTY", "SPIN", "COUNTER", "CHECK", "FMA"][b]
 
 
 def describe(st: dict) -> str:

@@ -33,7 +33,7 @@ def gpu_graph(tr, body=grt.RT_BODY_EMPTY, tile=(0, 0), spin_iters=256, flags=0, 
         state = torch.zeros(max(tr.n_cells, 1), dtype=torch.int32, device="cuda")
     elif body == grt.RT_BODY_COUNTER:
         state = torch.zeros(state_elems or int(tr.body_arg.max()) + 1, dtype=torch.int32, device="cuda")
-    if body in (grt.RT_BODY_CHECK, grt.RT_BODY_SPIN):
+    if body in (grt.RT_BODY_CHECK, grt.RT_BODY_SPIN, grt.RT_BODY_FMA):
         out = torch.zeros(max(tr.n, 1), dtype=torch.int32, device="cuda")
     g = grt.Graph(tr.ndim, tr.dom_lo, tr.dom_hi, body=body, spin_iters=spin_iters, state=state, out=out,
                   tile=tile, flags=flags, timeout_ns=timeout_ns, stream=stream)

@@ -165,3 +165,30 @@ def test_stitched_calls_refuse_before_any_gpu_work(lib):
     assert l.rt_copy_stitched_tickets(h, None) == grt.RT_ERR_INVALID
     assert l.rt_copy_stitched_tickets(h, out.ctypes.data) == grt.RT_ERR_STATE
     grt.rt_graph_destroy(h)
+
+
+def test_batch_capture_refuses_bad_arguments_without_a_gpu(lib):
+    """rt_batch_capture checks its host arguments before any CUDA call."""
+    import ctypes
+    from paper_2508_16522_gb300 import grt
+    d = grt.rt_graph_desc()
+    d.ndim = 2
+    out, gout = ctypes.c_void_p(), ctypes.c_void_p()
+    toff = np.array([0, 2, 1], np.int32)  # decreasing
+    glo = np.zeros((2, 2), np.int64)
+    ghi = np.full((2, 2), 7, np.int64)
+    ro = np.array([0, 1, 2], np.int32)
+    lo = np.zeros((2, 2), np.int64)
+    pv = np.zeros(2, np.uint8)
+    args = [toff.ctypes.data, glo.ctypes.data, ghi.ctypes.data, ro.ctypes.data, lo.ctypes.data, lo.ctypes.data,
+            pv.ctypes.data, 0, ctypes.byref(out), ctypes.byref(gout)]
+    assert lib.rt_batch_capture(ctypes.byref(d), 2, *args) == grt.RT_ERR_INVALID
+    assert b"decreases" in lib.rt_last_error()
+    assert lib.rt_batch_capture(ctypes.byref(d), 0, *args) == grt.RT_ERR_INVALID
+    toff2 = np.array([0, 1, 2], np.int32)
+    empty_hi = np.array([[7, 7], [-1, 3]], np.int64)  # graph 1: hi < lo
+    args2 = [toff2.ctypes.data, glo.ctypes.data, empty_hi.ctypes.data] + args[3:]
+    assert lib.rt_batch_capture(ctypes.byref(d), 2, *args2) == grt.RT_ERR_INVALID
+    assert b"empty or huge domain" in lib.rt_last_error()
+    d.ndim = 3
+    assert lib.rt_batch_capture(ctypes.byref(d), 2, *args) == grt.RT_ERR_INVALID

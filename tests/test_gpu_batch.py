@@ -167,3 +167,94 @@ def test_stacked_batch_refuses_graphs_that_share_cells():
         grt.Batch.stacked(g, [0, trs[0].n, both.n])
     assert e.value.status == grt.RT_ERR_INVALID
     g.close()
+
+
+def test_capture_places_graphs_in_bands_itself():
+    """rt_batch_capture: graphs given in their own domains (some offset), placed
+    in bands by the library and analysed once. Each graph's part of the CSR
+    equals its own oracle CSR; with the CHECK body the batch's state and
+    outputs after 2 launches of 3 replays equal the oracle's 6 sequential runs
+    of the same graphs placed on the host (each graph's tasks numbered from 0,
+    as a batched body sees them); later launches come from the cached CUDA
+    graph."""
+    import torch
+    traces = [tg.taskbench(32, 9, "random", seed=1), tg.random_rects(grid=(40, 17), n=300, side=(1, 12), seed=4),
+              tg.taskbench(8, 30, "butterfly", seed=2), tg.random_rects(grid=(25, 31), n=200, side=(1, 9), seed=5)]
+    # give the second graph an offset domain: the library must move it to its band
+    t1 = traces[1]
+    off = np.array([-7, 100], np.int64)
+    traces[1] = tg._finish(2, t1.dom_lo + off, t1.dom_hi + off, np.diff(t1.req_off), (t1.lo + off).reshape(-1),
+                           (t1.hi + off).reshape(-1), t1.priv, name="offset")
+    host, _ = tg.stack_bands(traces)  # the same placement, on the host, for the oracle
+    T = host.n
+    state = torch.zeros(host.n_cells, dtype=torch.int32, device="cuda")
+    out = torch.zeros(T, dtype=torch.int32, device="cuda")
+    b = grt.Batch.capture(traces, body=grt.RT_BODY_CHECK, state=state, out=out, tile=(8, 8))
+    rp, col, _ = b.graph_csr()
+    toff = b.task_off
+    for k, tr in enumerate(traces):
+        a, z = int(toff[k]), int(toff[k + 1])
+        s, d = oracle.analyze(tr)
+        rp_o, col_o = oracle.csr_from_pairs(tr.n, s, d)
+        assert np.array_equal(rp[a:z + 1].astype(np.int64) - int(rp[a]), rp_o), tr.name
+        assert np.array_equal(col[rp[a]:rp[z]] - a, col_o), tr.name
+    for _ in range(2):
+        b.execute(replays=3)
+        b.sync()
+    assert b.info()["graph_launches"] >= 1
+    # a batched body sees its graph's own task ids, in the stacked domain's cells
+    st_o, out_o = _stacked_local_ids_state(traces, host, 6)
+    assert np.array_equal(state.cpu().numpy(), st_o)
+    assert np.array_equal(out.cpu().numpy(), out_o)
+    b.close()
+
+
+def _stacked_local_ids_state(traces, host, runs):
+    """The oracle's state and outputs for the stacked program when every task
+    mixes in its id within its own graph (as a batched body does): the
+    stacked program run graph by graph, each graph's launches relabelled from 0."""
+    W = int(host.dom_hi[0]) + 1
+    state = np.zeros(host.n_cells, np.int32)
+    outs = []
+    y = 0
+    for tr in traces:
+        h = int(tr.dom_hi[1] - tr.dom_lo[1]) + 1
+        lo = tr.lo - tr.dom_lo + np.array([0, y])
+        hi = tr.hi - tr.dom_lo + np.array([0, y])
+        band = tg._finish(2, [0, 0], [W - 1, int(host.dom_hi[1])], np.diff(tr.req_off), lo.reshape(-1),
+                          hi.reshape(-1), tr.priv)
+        o = None
+        for _ in range(runs):
+            state, o = oracle.run_bodies(band, oracle.oracle.BODY_CHECK, state=state)
+        outs.append(o[:tr.n])
+        y += h
+    return state, np.concatenate(outs)
+
+
+def test_capture_one_dimensional_and_refusals():
+    import torch
+    traces = [tg.random_rects(grid=(300,), n=120, side=(1, 40), seed=s, ndim=1) for s in (1, 2, 3)]
+    out = torch.zeros(sum(t.n for t in traces), dtype=torch.int32, device="cuda")
+    b = grt.Batch.capture(traces, body=grt.RT_BODY_SPIN, spin_iters=9, out=out, tile=(64, 1))
+    rp, col, _ = b.graph_csr()
+    toff = b.task_off
+    for k, tr in enumerate(traces):
+        a, z = int(toff[k]), int(toff[k + 1])
+        s, d = oracle.analyze(tr)
+        rp_o, col_o = oracle.csr_from_pairs(tr.n, s, d)
+        assert np.array_equal(rp[a:z + 1].astype(np.int64) - int(rp[a]), rp_o)
+        assert np.array_equal(col[rp[a]:rp[z]] - a, col_o)
+    b.execute(replays=2)
+    b.sync()
+    want = np.concatenate([np.array([oracle.spin(j, 9) for j in range(t.n)], np.uint32).view(np.int32)
+                           for t in traces])
+    assert np.array_equal(out.cpu().numpy(), want)
+    b.close()
+    # a rectangle outside its own graph's domain would reach the next band: refused
+    bad = traces[0]
+    hi = bad.hi.copy()
+    hi[0, 0] = 305
+    bad = tg._finish(1, bad.dom_lo, bad.dom_hi, np.diff(bad.req_off), bad.lo.reshape(-1), hi.reshape(-1), bad.priv)
+    with pytest.raises(grt.GrtError) as e:
+        grt.Batch.capture([bad, traces[1]], body=grt.RT_BODY_EMPTY)
+    assert e.value.status == grt.RT_ERR_INVALID and "its own graph's domain" in str(e.value)

@@ -1,6 +1,8 @@
-"""The multi-process path of the benchmark on CPU (gloo, world size 2): every
-rank runs its own replica and the job's time is the slowest rank's; under
-torchrun only rank 0 prints the result line."""
+"""The multi-process path on CPU (gloo, world size 2): the job's time is the
+slowest rank's; under torchrun only rank 0 prints the result line; and
+independent graphs split across ranks by footprint are each taken by exactly
+one rank, the shares are balanced, and the union of what the ranks compute
+for their shares equals what one rank computes for all of them."""
 import json
 import os
 import socket
@@ -42,6 +44,79 @@ def test_max_over_ranks_with_two_gloo_ranks():
         assert p.exitcode == 0
     got = dict(q.get(timeout=10) for _ in range(2))
     assert got == {0: 15.0, 1: 15.0}
+
+
+def _batch_rank(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    sys.path.insert(0, ROOT)
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import oracle_pool
+    from paper_2508_16522_gb300 import shard
+    from paper_2508_16522_gb300 import tracegen as tg
+    import oracle
+    traces = tg.batch_graphs(96, n_range=(64, 4096), seed=3)
+    share = shard.my_share([shard.footprint(t) for t in traces], world, rank)
+    mine = {}
+    for k in share:
+        s, d = oracle.analyze(traces[k])
+        rp, col = oracle.csr_from_pairs(traces[k].n, s, d)
+        mine[k] = oracle_pool.csr_digest(rp, col)
+    gathered = [None] * world
+    dist.all_gather_object(gathered, mine)
+    load = sum(shard.footprint(traces[k]) for k in share)
+    loads = [None] * world
+    dist.all_gather_object(loads, load)
+    q.put((rank, gathered, loads))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_batch_split_across_two_gloo_ranks():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = free_port()
+    procs = [ctx.Process(target=_batch_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(300)
+        assert p.exitcode == 0
+    got = dict((r, (g, l)) for r, g, l in (q.get(timeout=10) for _ in range(2)))
+    gathered, loads = got[0]
+    assert got[1][0] == gathered and got[1][1] == loads  # every rank sees the same union
+    sys.path.insert(0, ROOT)
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import oracle
+    import oracle_pool
+    from paper_2508_16522_gb300 import shard
+    from paper_2508_16522_gb300 import tracegen as tg
+    traces = tg.batch_graphs(96, n_range=(64, 4096), seed=3)
+    keys = [k for part in gathered for k in part]
+    assert sorted(keys) == list(range(len(traces))), "a graph was taken by no rank or by two"
+    union = {k: v for part in gathered for k, v in part.items()}
+    for k, tr in enumerate(traces):  # one rank computing everything gives the same
+        s, d = oracle.analyze(tr)
+        assert union[k] == oracle_pool.csr_digest(*oracle.csr_from_pairs(tr.n, s, d))
+    fps = [shard.footprint(t) for t in traces]
+    assert sum(loads) == sum(fps)
+    assert max(loads) - min(loads) <= max(fps)  # greedy largest-first balance
+
+
+def test_assignment_properties():
+    sys.path.insert(0, ROOT)
+    from paper_2508_16522_gb300 import shard
+    import numpy as np
+    rng = np.random.default_rng(1)
+    for world in (1, 2, 3, 4, 8):
+        fp = rng.integers(1, 10_000, size=200)
+        owner = shard.assign_by_footprint(fp, world)
+        loads = np.bincount(owner, weights=fp, minlength=world)
+        assert owner.min() >= 0 and owner.max() < world
+        assert loads.max() - loads.min() <= fp.max()
+        assert sorted(k for r in range(world) for k in shard.my_share(fp, world, r)) == list(range(200))
+        assert np.array_equal(owner, shard.assign_by_footprint(fp, world))  # deterministic
+    assert shard.assign_by_footprint([], 3).tolist() == []
 
 
 def test_reference_arm_under_torchrun_prints_once():
