@@ -88,6 +88,12 @@ enum {
   RT_LAUNCH_DEFER_CHECK = 2 /* with host pointers: validate on the device instead */
 };
 
+/* executor policies of a single graph (rt_graph_exec_policy) */
+enum {
+  RT_EXEC_RING = 0,  /* ready tasks go through a global ring that any warp claims from */
+  RT_EXEC_OWNED = 1  /* every warp owns fixed chunks of 32 consecutive tasks and polls their countdowns */
+};
+
 /* rt_graph_desc.flags */
 enum {
   RT_GRAPH_TICKETS = 1, /* record per-task (start, finish) tickets of the last run */
@@ -255,6 +261,21 @@ rt_status rt_execute_kernels(rt_graph_t g, int32_t mode, int32_t iters, int32_t 
  * executor (rt_execute_events) takes the same claim width. */
 rt_status rt_graph_exec_config(rt_graph_t g, int32_t blocks, int32_t warps, int32_t claim, int32_t keep);
 
+/* How rt_execute / rt_replay find ready tasks (Algorithm 1's EXECUTE_OP):
+ * RT_EXEC_RING (default) publishes every task made ready that its warp does
+ * not keep to a global ring that any warp claims from; RT_EXEC_OWNED gives
+ * every warp fixed chunks of 32 consecutive tasks (chunk c to warp c mod the
+ * grid's warps, taken in increasing order, one task per lane) and lets it poll
+ * their countdowns, the predecessors decrementing them with reductions that
+ * need no answer -- the operations compiled to their worker of Algorithm 1.
+ * OWNED suits graphs whose tasks become ready roughly in task order (the
+ * wavefronts of Task Bench); RING suits irregular ones. Under OWNED the claim
+ * width of rt_graph_exec_config is the number of chunks a warp holds at once
+ * (1, 2 or 4; default 1; with more, the next chunks' records and countdowns
+ * are loaded while the current one finishes) and keep is unused. Results never depend on
+ * the policy. Errors: RT_ERR_INVALID. */
+rt_status rt_graph_exec_policy(rt_graph_t g, int32_t policy);
+
 /* Waits for the graph's stream; returns RT_OK, RT_ERR_TIMEOUT (the executor
  * gave up; the next execution re-initialises the counters) or RT_ERR_CUDA. */
 rt_status rt_sync(rt_graph_t g);
@@ -361,6 +382,7 @@ typedef struct {
   int32_t blocks, warps, claim, keep;  /* launch shape (rt_graph_exec_config) */
   float ms;                            /* time of one run with it */
   int32_t trials;                      /* shapes measured (0: from the cache) */
+  int32_t policy;                      /* RT_EXEC_RING or RT_EXEC_OWNED (rt_tune_exec) */
 } rt_exec_config;
 
 /* Analyses the launches (host arrays, as rt_launch_batch) once per candidate
@@ -372,10 +394,12 @@ rt_status rt_tune_tile(const rt_graph_desc* desc, int32_t n, const int32_t* req_
                        const int64_t* hi, const uint8_t* priv, const char* cache_path, int32_t* tile_w,
                        int32_t* tile_h, float* ms);
 
-/* Runs an analysed graph under candidate launch shapes (coordinate descent:
- * warps x blocks per SM, then claim, then keep; best of two runs each) and
- * configures it with the fastest (rt_graph_exec_config). The graph's bodies run
- * once per trial: a state-changing body sees those runs. Synchronous. */
+/* Runs an analysed graph under candidate launch shapes -- the ring policy by
+ * coordinate descent (warps x blocks per SM, then claim, then keep), the
+ * owned policy over warps x blocks per SM; best of two runs each -- and
+ * configures it with the fastest policy and shape (rt_graph_exec_policy,
+ * rt_graph_exec_config). The graph's bodies run once per trial: a
+ * state-changing body sees those runs. Synchronous. */
 rt_status rt_tune_exec(rt_graph_t g, const char* cache_path, rt_exec_config* best);
 
 /* The same for a batch launch of `replays` replays; returns the shape for

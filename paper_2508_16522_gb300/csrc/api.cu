@@ -175,6 +175,7 @@ struct rt_graph {
   int exec_blocks = 0, exec_warps = 8;
   int cfg_blocks = 0, cfg_warps = 0, cfg_claim = 0, cfg_keep = 0;  // rt_graph_exec_config
   size_t mem_cap = 0;  // device bytes the graph may hold while it grows (0 = no cap; set by a server)
+  int cfg_policy = RT_EXEC_RING;  // rt_graph_exec_policy
 };
 
 namespace {
@@ -803,14 +804,15 @@ constexpr int kCountersByte = 512;  // hpin byte offset of the executor's diagno
 
 rt_status prepare_run(rt_graph* g, int32_t replays, ExecParams* out, int64_t* ring_clear) {
   cudaStream_t s = g->s;
+  const bool owned = g->cfg_policy == RT_EXEC_OWNED;  // no ring: every warp polls the countdowns it owns
   const uint64_t cap = (uint64_t)g->n * (uint64_t)replays + 64;
   if (cap >= 0xFFFFFFF0ull) return fail(RT_ERR_INVALID, "tasks x replays must stay below 2^32 per launch");
-  const bool grow = cap * 8 > g->ring.cap || !g->ring.p;
+  const bool grow = !owned && (cap * 8 > g->ring.cap || !g->ring.p);
   if (grow) {
     drop_replay_graph(g);
     CKR(g->ring.reserve((size_t)cap * 8, s));
   }
-  *ring_clear = (grow || g->dirty) ? (int64_t)(g->ring.cap / 8) : 0;
+  *ring_clear = owned ? 0 : ((grow || g->dirty) ? (int64_t)(g->ring.cap / 8) : 0);
   CKR(g->ctrl.reserve(sizeof(ExecCtrl), s));
   CKR(g->done_g.reserve(64, s));
   if (!g->gtable.p) {
@@ -859,11 +861,12 @@ rt_status prepare_run(rt_graph* g, int32_t replays, ExecParams* out, int64_t* ri
   p.replays = replays;
   p.graphs_target = 1;
   p.timeout_ns = g->desc.timeout_ns;
-  p.claim = g->cfg_claim > 0 ? g->cfg_claim : 8;
+  p.claim = g->cfg_claim > 0 ? g->cfg_claim : (owned ? 1 : 8);  // owned: chunks a warp holds at once
   p.keep = g->cfg_keep > 0 ? g->cfg_keep : 16;
   p.tickets = (g->desc.flags & RT_GRAPH_TICKETS) ? g->tickets.as<int32_t>() : nullptr;
-  p.total_roots = (int32_t)g->n_roots;
+  p.total_roots = owned ? 0 : (int32_t)g->n_roots;
   p.need_fence = g->desc.body == RT_BODY_COUNTER || g->desc.body == RT_BODY_CHECK;
+  p.policy = g->cfg_policy;
   *out = p;
   return RT_OK;
 }
@@ -1338,6 +1341,14 @@ rt_status rt_graph_exec_config(rt_graph_t g, int32_t blocks, int32_t warps, int3
   g->cfg_claim = claim;
   g->cfg_keep = keep;
   drop_replay_graph(g);
+  return RT_OK;
+}
+
+rt_status rt_graph_exec_policy(rt_graph_t g, int32_t policy) {
+  if (!g) return fail(RT_ERR_INVALID, "graph is NULL");
+  if (policy != RT_EXEC_RING && policy != RT_EXEC_OWNED) return fail(RT_ERR_INVALID, "unknown policy %d", policy);
+  if (policy != g->cfg_policy) drop_replay_graph(g);
+  g->cfg_policy = policy;
   return RT_OK;
 }
 

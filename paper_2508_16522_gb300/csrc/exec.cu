@@ -25,6 +25,7 @@
 // Every wait is bounded: a warp that sees no progress of the global executed
 // counter for timeout_ns sets status TIMEOUT and returns.
 #include <mutex>
+#include <vector>
 
 #include "bodies.cuh"
 #include "grt_internal.cuh"
@@ -109,7 +110,7 @@ __global__ void __launch_bounds__(256, 1) k_exec(ExecParams p) {
   int32_t* const out0 = SINGLE ? p.graphs[0].out : nullptr;  // task_base is 0 for a single graph
   int nl = 0;                    // kept ready tasks (warp-uniform)
   uint32_t pend = 0;             // executed but not yet counted (warp-uniform)
-  uint64_t idle_since = 0, last_check = 0;  // lane 0
+  uint64_t idle_since = 0, last_check = 0, last_status = 0;  // lane 0
   unsigned long long seen = 0;
   uint32_t backoff = 32;
   uint32_t my_t = kNoTicket;     // this lane's claimed ring ticket
@@ -185,12 +186,18 @@ __global__ void __launch_bounds__(256, 1) k_exec(ExecParams p) {
       ++cnt[kCntIdle];
       int stop = 0;
       if (lane == 0) {
-        const uint32_t st = ld_relaxed_u32(&ctrl->status);
-        const uint32_t gd = ld_relaxed_u32(&ctrl->graphs_done);
+        // the shared status words, read at most every microsecond per idle
+        // warp (all of them reading at every pass would pile onto one L2 line)
+        const uint64_t now = globaltimer_ns();
+        uint32_t st = 0u, gd = 0u;
+        if (now - last_status >= 1000u) {
+          last_status = now;
+          st = ld_relaxed_u32(&ctrl->status);
+          gd = ld_relaxed_u32(&ctrl->graphs_done);
+        }
         if (st != 0u || (int)gd >= p.graphs_target) {
           stop = 1;
         } else {
-          const uint64_t now = globaltimer_ns();
           if (idle_since == 0) {
             idle_since = last_check = now;
             seen = SINGLE ? ld_relaxed_u32(&p.done_g[0]) : ld_relaxed_u64(&ctrl->executed);
@@ -380,6 +387,249 @@ __global__ void __launch_bounds__(256, 1) k_exec(ExecParams p) {
   }
 }
 
+// The owned-chunk executor (RT_EXEC_OWNED, one graph). Algorithm 1 compiles
+// every operation to one worker; here warp w owns chunks c = w, w + W, w + 2W
+// ... of 32 consecutive tasks (W = warps of the grid) and runs them in that
+// order, one task per lane, holding K of them at once (a window: the next
+// chunks' trigger records and countdowns are already in flight while the
+// current ones finish). A lane polls its task's countdown (one coalesced
+// 128-byte load per chunk and poll) and runs the task once it reads 0; the
+// task re-arms its own countdown, runs its body in place, and decrements its
+// successors with fire-and-forget reductions (COMPLETED_EDGE needs no answer:
+// the successor's owner sees the zero when it polls): the first kAdjInline
+// straight from the lane's trigger record, the rest shared by the warp. No
+// ring, no reservation, no record load on the critical path: a wavefront step
+// costs a reduction reaching L2 and the owner's next poll.
+// Every warp takes its chunks in increasing task order and holds its oldest
+// unfinished one, and every edge points to a later task, so the smallest
+// unfinished task is always in a chunk its owner holds, with all its
+// predecessors done: no warp waits forever. Replays: a warp starts run r+1
+// once every task of run r has run (a counter of finished tasks), so a run's
+// decrements never reach a counter of the run before. Waits are bounded by
+// timeout_ns without global progress.
+constexpr uint32_t kOwnedBackoffMax = 256;  // ns between polls of a warp whose tasks are all waiting
+
+template <bool TICKETS, bool FENCE, int K>
+__global__ void __launch_bounds__(256, 1) k_exec_owned(ExecParams p) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int W = (int)(gridDim.x * (blockDim.x >> 5));
+  const int gw = (int)blockIdx.x * (int)(blockDim.x >> 5) + warp;
+  ExecCtrl* ctrl = p.ctrl;
+  const ExecGraph& G = p.graphs[0];
+  const int n = G.n_tasks;
+  const int body = G.body, spin = G.spin_iters;
+  int32_t* const out = G.out;
+  const int nchunks = (n + 31) >> 5;
+  uint32_t cnt[kCntCount];
+#pragma unroll
+  for (int k = 0; k < kCntCount; ++k) cnt[k] = 0;
+  uint64_t idle_since = 0, last_check = 0;  // lane 0
+  unsigned long long seen = 0;
+  bool stop = false;
+
+  // lane 0 of a warp that has nothing to do: is the launch over (status), or
+  // has no task anywhere run for timeout_ns? (the shared status and progress
+  // words are read at most every 2 us per warp: every waiting warp reading
+  // them at every poll would pile onto one L2 line)
+  auto idle_check = [&]() -> bool {
+    int st = 0;
+    if (lane == 0) {
+      const uint64_t now = globaltimer_ns();
+      if (idle_since == 0) {
+        idle_since = last_check = now;
+        seen = ld_relaxed_u64(&ctrl->executed);
+      } else if (now - last_check > 2000u) {
+        last_check = now;
+        const unsigned long long pr = ld_relaxed_u64(&ctrl->executed);
+        if (ld_relaxed_u32(&ctrl->status) != 0u) {
+          st = 1;
+        } else if (pr != seen) {
+          seen = pr;
+          idle_since = now;
+        } else if (now - idle_since > (uint64_t)p.timeout_ns) {
+          atomicCAS(&ctrl->status, 0u, (uint32_t)RT_ERR_TIMEOUT);
+          st = 1;
+        }
+      }
+    }
+    return __shfl_sync(kFull, st, 0) != 0;
+  };
+
+  for (int r = 0; r < p.replays && !stop; ++r) {
+    if (r > 0) {
+      // run r starts once every task of run r - 1 has run and re-armed itself
+      const uint32_t target = (uint32_t)r * (uint32_t)n;
+      for (;;) {
+        uint32_t d = 0;
+        if (lane == 0) d = ld_relaxed_u32(&p.done_g[0]);
+        d = __shfl_sync(kFull, d, 0);
+        if (d >= target) break;
+        if (idle_check()) {
+          stop = true;
+          break;
+        }
+        __nanosleep(64);
+      }
+      if (stop) break;
+      idle_since = 0;
+      fence_acq_rel_gpu();  // acquire: the counters re-armed by run r - 1
+    }
+    // the window: slot k holds chunk ck[k] (-1: none), one task per lane
+    uint32_t ran = 0;  // tasks this warp ran in run r (warp-uniform)
+    int next_c = gw;   // the next chunk this warp takes
+    int ck[K], v[K], ctasks[K];
+    int4 a0[K], a1[K];
+    int32_t polled[K];  // the lane's countdown, polled one round ahead
+    unsigned pending[K];
+    auto take = [&](int k) {
+      ck[k] = -1;
+      v[k] = 0;
+      ctasks[k] = 0;
+      pending[k] = 0u;
+      polled[k] = 1;
+      a0[k] = make_int4(0, 0, 0, -1);
+      a1[k] = make_int4(-1, -1, -1, -1);
+      if (next_c >= nchunks) return;
+      ck[k] = next_c;
+      next_c += W;
+      v[k] = ck[k] * 32 + lane;
+      const bool has = v[k] < n;
+      if (has) {
+        a0[k] = __ldg(p.adj + 2 * (int64_t)v[k]);
+        a1[k] = __ldg(p.adj + 2 * (int64_t)v[k] + 1);
+        polled[k] = ld_relaxed_s32(p.count + v[k]);
+      }
+      pending[k] = __ballot_sync(kFull, has);
+      ctasks[k] = __popc(pending[k]);
+    };
+#pragma unroll
+    for (int k = 0; k < K; ++k) take(k);
+    uint32_t backoff = 0;
+    for (;;) {
+      bool busy = false, any = false;
+      bool ready[K];
+      unsigned rm[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        busy |= pending[k] != 0u;
+        ready[k] = ((pending[k] >> lane) & 1u) && polled[k] == 0;
+        rm[k] = __ballot_sync(kFull, ready[k]);
+        any |= rm[k] != 0u;
+      }
+      if (!busy || stop) break;
+      if (!any) {
+        ++cnt[kCntIdle];
+        // the first empty polls retry at once (a stale prefetch); the launch's
+        // status and progress are watched once polls keep failing
+        if (backoff >= 64 && idle_check()) {
+          stop = true;
+          break;
+        }
+        if (backoff) __nanosleep(backoff);
+        backoff = backoff ? (backoff < kOwnedBackoffMax ? backoff * 2 : kOwnedBackoffMax) : 16;
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+          if ((pending[k] >> lane) & 1u) polled[k] = ld_relaxed_s32(p.count + v[k]);
+        continue;
+      }
+      backoff = 0;
+      idle_since = 0;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        pending[k] &= ~rm[k];
+        // the next poll is in flight during the work below; a value read
+        // before this warp's own decrements can only be late (counters only
+        // go down to 0), never early
+        if (!FENCE && !TICKETS) polled[k] = ((pending[k] >> lane) & 1u) ? ld_relaxed_s32(p.count + v[k]) : 1;
+      }
+      if (FENCE) fence_acq_rel_gpu();  // acquire: the predecessors' effects before the bodies
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        if (!ready[k]) continue;
+        const int t = v[k];
+        p.count[t] = a0[k].z;  // INIT's reset for the next run, done by the task itself
+        if (TICKETS) p.tickets[2 * (int64_t)t] = (int32_t)atomicAdd(&ctrl->ticket, 1u);
+        if (!FENCE) {
+          if (body == RT_BODY_SPIN) out[t] = (int32_t)spin_body((uint32_t)t, spin);
+          else if (body == RT_BODY_FMA) out[t] = fma_body((uint32_t)t, spin);
+        } else {
+          run_body<true>(G, t);
+        }
+        if (TICKETS) p.tickets[2 * (int64_t)t + 1] = (int32_t)atomicAdd(&ctrl->ticket, 1u);
+      }
+      if (FENCE || TICKETS) fence_acq_rel_gpu();  // release: bodies before the decrements
+      // COMPLETED_EDGE for every out-edge of the tasks that just ran: each lane
+      // its task's inline successors, straight from its record (no answer
+      // needed: reductions); the warp shares the edges past them
+      unsigned degs = 0;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int deg = ready[k] ? a0[k].y : 0;
+        degs += (unsigned)deg;
+        if (ready[k]) {
+          const int succ[kAdjInline] = {a0[k].w, a1[k].x, a1[k].y, a1[k].z, a1[k].w};
+#pragma unroll
+          for (int j = 0; j < kAdjInline; ++j)
+            if (j < deg) atomicSub(p.count + succ[j], 1);  // result unused: a reduction
+        }
+        const int extra = deg > kAdjInline ? deg - kAdjInline : 0;
+        if (__any_sync(kFull, extra > 0)) {
+          int incl = extra;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+          }
+          const int excl = incl - extra;
+          const int D = __shfl_sync(kFull, incl, 31);
+          const int rbeg = a0[k].x + kAdjInline;
+          for (int e0 = 0; e0 < D; e0 += 32) {
+            const int e = e0 + lane;
+            int owner = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+              const int cand = owner + step;
+              if (__shfl_sync(kFull, excl, cand) <= e) owner = cand;
+            }
+            const int oex = __shfl_sync(kFull, excl, owner);
+            const int orb = __shfl_sync(kFull, rbeg, owner);
+            if (e < D) atomicSub(p.count + p.col[orb + (e - oex)], 1);
+          }
+        }
+      }
+      int k_ran = 0;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        if (FENCE || TICKETS) polled[k] = ((pending[k] >> lane) & 1u) ? ld_relaxed_s32(p.count + v[k]) : 1;
+        k_ran += __popc(rm[k]);
+      }
+      cnt[kCntBatches] += 1;
+      cnt[kCntTasks] += (unsigned)k_ran;
+      cnt[kCntEdges] += __reduce_add_sync(kFull, degs);
+      ran += (uint32_t)k_ran;
+      // finished chunks: progress for the other warps' bounded waits, and the
+      // slot takes this warp's next chunk
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        if (ck[k] >= 0 && pending[k] == 0u) {
+          if (lane == 0) atomicAdd(&ctrl->executed, (unsigned long long)ctasks[k]);
+          take(k);
+        }
+      }
+    }
+    if (stop) break;
+    // release: this warp's bodies and re-armed counters before its count
+    fence_acq_rel_gpu();
+    __syncwarp();
+    if (lane == 0 && ran) atomicAdd(&p.done_g[0], ran);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < kCntCount; ++k)
+      if (cnt[k]) atomicAdd(&ctrl->counters[k], (unsigned long long)cnt[k]);
+  }
+}
+
 // trigger record of each task: {row start, out-degree, in-degree, first
 // kAdjInline successors (-1 padded)}, two int4 per task
 __global__ void k_pack_adj(const int32_t* row_ptr, const int32_t* col, const int32_t* indeg, int64_t n,
@@ -491,6 +741,14 @@ int exec_max_blocks_per_sm(int warps) {
   return nb;
 }
 
+// every instantiation of the owned-chunk executor
+std::vector<void (*)(ExecParams)> owned_kernels() {
+  return {k_exec_owned<false, false, 1>, k_exec_owned<false, false, 2>, k_exec_owned<false, false, 4>,
+          k_exec_owned<false, true, 1>,  k_exec_owned<false, true, 2>,  k_exec_owned<false, true, 4>,
+          k_exec_owned<true, false, 1>,  k_exec_owned<true, false, 2>,  k_exec_owned<true, false, 4>,
+          k_exec_owned<true, true, 1>,   k_exec_owned<true, true, 2>,   k_exec_owned<true, true, 4>};
+}
+
 template <bool T, bool F, bool S>
 void prefer_shared() {
   cudaFuncSetAttribute(k_exec<T, F, S>, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -512,6 +770,8 @@ void launch_exec(ExecParams p, int blocks, int warps, cudaStream_t s) {
     prefer_shared<false, true, false>();
     prefer_shared<true, false, false>();
     prefer_shared<true, true, false>();
+    for (auto f : owned_kernels())
+      cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   });
   const size_t smem = (size_t)warps * sizeof(WarpQ);
   if (p.keep > kKeepMax) p.keep = kKeepMax;
@@ -521,6 +781,23 @@ void launch_exec(ExecParams p, int blocks, int warps, cudaStream_t s) {
   const bool single = p.n_graphs == 1;
   const bool fence = p.need_fence != 0;
   count_launch();
+  if (single && p.policy == RT_EXEC_OWNED) {  // keeps nothing in shared memory
+    // the claim width is the window: chunks a warp holds at once (1, 2 or 4)
+    const int K = p.claim >= 4 ? 4 : (p.claim >= 2 ? 2 : 1);
+#define GRT_OWNED(T, F)                                                         \
+  do {                                                                         \
+    if (K == 4) k_exec_owned<T, F, 4><<<blocks, warps * 32, 0, s>>>(p);        \
+    else if (K == 2) k_exec_owned<T, F, 2><<<blocks, warps * 32, 0, s>>>(p);   \
+    else k_exec_owned<T, F, 1><<<blocks, warps * 32, 0, s>>>(p);               \
+  } while (0)
+    if (p.tickets) {
+      if (fence) GRT_OWNED(true, true); else GRT_OWNED(true, false);
+    } else {
+      if (fence) GRT_OWNED(false, true); else GRT_OWNED(false, false);
+    }
+#undef GRT_OWNED
+    return;
+  }
 #define GRT_EXEC(T, F, S) k_exec<T, F, S><<<blocks, warps * 32, smem, s>>>(p)
   if (p.tickets) {
     if (single) { if (fence) GRT_EXEC(true, true, true); else GRT_EXEC(true, false, true); }
@@ -548,6 +825,7 @@ void preload_exec() {
   cudaFuncGetAttributes(&a, k_exec<false, true, false>);
   cudaFuncGetAttributes(&a, k_exec<true, false, false>);
   cudaFuncGetAttributes(&a, k_exec<true, true, false>);
+  for (auto f : owned_kernels()) cudaFuncGetAttributes(&a, f);
 }
 
 }  // namespace grt

@@ -76,6 +76,11 @@ __device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t* p) {
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
+__device__ __forceinline__ int32_t ld_relaxed_s32(const int32_t* p) {
+  int32_t v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
 __device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
   uint32_t v;
   asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -173,6 +178,7 @@ struct ExecParams {
   int32_t* tickets;       // optional int32[2 * total tasks]
   int32_t total_roots;
   int32_t need_fence;     // some body reads data written by its predecessors
+  int32_t policy;         // single graph: RT_EXEC_RING (ready ring) or RT_EXEC_OWNED (owned chunks)
 };
 
 // ---------------------------------------------------------------------------

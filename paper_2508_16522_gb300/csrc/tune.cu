@@ -10,9 +10,10 @@
 //   rt_tune_exec   -- runs an analysed graph under candidate launch shapes and
 //                     configures it with the fastest;
 //   rt_tune_batch  -- the same for a batch launch with its replay count.
-// The executor search is coordinate descent: (warps, blocks per SM) jointly,
-// then the claim width, then the keep width, then (warps, blocks per SM)
-// again, each trial the best of two runs.
+// The executor search is coordinate descent for the ring policy: (warps,
+// blocks per SM) jointly, then the claim width, then the keep width, then
+// (warps, blocks per SM) again; then a pass over the grids of the owned
+// policy; each trial the best of two runs.
 // Results go to an optional plain-text cache, one line per workload key
 // (device, SM count, kind, sizes, an input hash), so a later call with the
 // same workload answers without running anything.
@@ -266,12 +267,18 @@ rt_status rt_tune_exec(rt_graph_t g, const char* cache_path, rt_exec_config* bes
   if (s != RT_OK) return s;
   int sms = 0;
   if ((s = rt_device_info(&sms, nullptr)) != RT_OK) return s;
-  const std::string key = "exec/" + device_tag() + "/" + std::to_string(st.n_tasks) + "/" +
+  // "exec5": entries that also weigh the owned policy's grids and windows
+  const std::string key = "exec5/" + device_tag() + "/" + std::to_string(st.n_tasks) + "/" +
                           std::to_string(st.n_edges) + "/" + std::to_string(st.n_roots);
+  auto apply = [&](const rt_exec_config& c) -> rt_status {
+    rt_status r = rt_graph_exec_policy(g, c.policy);
+    return r != RT_OK ? r : rt_graph_exec_config(g, c.blocks, c.warps, c.claim, c.keep);
+  };
   std::vector<double> c;
-  if (cache_get(cache_path, key, &c) && c.size() >= 5) {
-    *best = rt_exec_config{(int32_t)c[0], (int32_t)c[1], (int32_t)c[2], (int32_t)c[3], (float)c[4], 0};
-    return rt_graph_exec_config(g, best->blocks, best->warps, best->claim, best->keep);
+  if (cache_get(cache_path, key, &c) && c.size() >= 6) {
+    *best = rt_exec_config{(int32_t)c[0], (int32_t)c[1], (int32_t)c[2], (int32_t)c[3], (float)c[4], 0,
+                           (int32_t)c[5]};
+    return apply(*best);
   }
   auto run = [&](const Shape& sh) -> double {
     if (rt_graph_exec_config(g, sms * sh.bps, sh.warps, sh.claim, sh.keep) != RT_OK) return -1;
@@ -282,13 +289,53 @@ rt_status rt_tune_exec(rt_graph_t g, const char* cache_path, rt_exec_config* bes
   Shape b{};
   float ms = 0;
   int trials = 0;
+  rt_graph_exec_policy(g, RT_EXEC_RING);
   if ((s = search(sms, Shape{2, 1, 8, 16}, run, &b, &ms, &trials)) != RT_OK) {
     rt_graph_exec_config(g, 0, 0, 0, 0);
     return tfail(s, std::string("executor trial failed: ") + rt_last_error());
   }
-  *best = rt_exec_config{sms * b.bps, b.warps, b.claim, b.keep, ms, trials};
-  cache_put(cache_path, key, {(double)best->blocks, (double)b.warps, (double)b.claim, (double)b.keep, ms});
-  return rt_graph_exec_config(g, best->blocks, best->warps, best->claim, best->keep);
+  *best = rt_exec_config{sms * b.bps, b.warps, b.claim, b.keep, ms, trials, RT_EXEC_RING};
+  rt_graph_exec_policy(g, RT_EXEC_OWNED);
+  // the owned policy: grids from 32 warps (a Task Bench step's 32 chunks, each
+  // warp always on the same column of chunks) up to several warps per SM, one
+  // chunk at a time; then wider windows (chunks a warp holds) on the best grid
+  auto run_owned = [&](int blocks, int warps, int window) -> double {
+    if (rt_graph_exec_config(g, blocks, warps, window, 16) != RT_OK) return -1;
+    const auto t0 = std::chrono::steady_clock::now();
+    if (rt_execute(g) != RT_OK || rt_sync(g) != RT_OK) return -1;
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  };
+  bool failed = false;
+  auto owned_trial = [&](int blocks, int warps, int window) {
+    double t = 1e30;
+    for (int rep = 0; rep < 3 && !failed; ++rep) {
+      const double m = run_owned(blocks, warps, window);
+      if (m < 0) failed = true;
+      t = std::min(t, m);
+    }
+    ++trials;
+    if (!failed && t < best->ms)
+      *best = rt_exec_config{blocks, warps, window, 16, (float)t, trials, RT_EXEC_OWNED};
+  };
+  const int owned_c[][2] = {{32, 1}, {64, 1}, {96, 1}, {152, 1}, {152, 2}, {152, 4}, {304, 2}, {304, 4}};
+  for (const auto& bw : owned_c) {
+    const int blocks = bw[0] * sms / 152 > 0 ? bw[0] * sms / 152 : 1;  // scaled to this GPU's SM count
+    if (blocks > sms * std::max(exec_max_blocks_per_sm(bw[1]), 1)) continue;
+    owned_trial(blocks, bw[1], 1);
+  }
+  if (!failed && best->policy == RT_EXEC_OWNED) {
+    const int gb = best->blocks, gwp = best->warps;
+    for (int window : {2, 4}) owned_trial(gb, gwp, window);
+  }
+  if (failed) {
+    rt_graph_exec_policy(g, RT_EXEC_RING);
+    rt_graph_exec_config(g, 0, 0, 0, 0);
+    return tfail(RT_ERR_CUDA, std::string("executor trial failed: ") + rt_last_error());
+  }
+  best->trials = trials;
+  cache_put(cache_path, key, {(double)best->blocks, (double)best->warps, (double)best->claim, (double)best->keep,
+                              best->ms, (double)best->policy});
+  return apply(*best);
 }
 
 rt_status rt_tune_batch(rt_batch_t b, int32_t replays, const char* cache_path, rt_exec_config* best) {

@@ -25,6 +25,7 @@ RT_READ, RT_WRITE, RT_REDUCE_SUM = 0, 1, 2
 RT_BODY_EMPTY, RT_BODY_SPIN, RT_BODY_COUNTER, RT_BODY_CHECK, RT_BODY_FMA = 0, 1, 2, 3, 4
 RT_LAUNCH_HOST, RT_LAUNCH_DEVICE, RT_LAUNCH_DEFER_CHECK = 0, 1, 2
 RT_GRAPH_TICKETS, RT_GRAPH_PROFILE = 1, 2
+RT_EXEC_RING, RT_EXEC_OWNED = 0, 1
 
 # every symbol include/grt.h declares (checked by the CPU tests)
 EXPORTS = ["rt_graph_create", "rt_graph_destroy", "rt_graph_clear", "rt_launch_batch", "rt_analyze",
@@ -36,7 +37,8 @@ EXPORTS = ["rt_graph_create", "rt_graph_destroy", "rt_graph_clear", "rt_launch_b
            "rt_server_drain",
            "rt_server_stats", "rt_server_destroy", "rt_tune_tile", "rt_tune_exec", "rt_tune_batch",
            "rt_batch_create_stacked", "rt_execute_events", "rt_execute_kernels",
-           "rt_execute_stitched", "rt_copy_stitched_tickets", "rt_batch_capture", "rt_batch_info"]
+           "rt_execute_stitched", "rt_copy_stitched_tickets", "rt_batch_capture", "rt_batch_info",
+           "rt_graph_exec_policy"]
 
 
 class GrtError(RuntimeError):
@@ -64,7 +66,8 @@ class rt_server_desc(ctypes.Structure):
 
 class rt_exec_config(ctypes.Structure):
     _fields_ = [("blocks", ctypes.c_int32), ("warps", ctypes.c_int32), ("claim", ctypes.c_int32),
-                ("keep", ctypes.c_int32), ("ms", ctypes.c_float), ("trials", ctypes.c_int32)]
+                ("keep", ctypes.c_int32), ("ms", ctypes.c_float), ("trials", ctypes.c_int32),
+                ("policy", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -150,6 +153,7 @@ def load(path: str = LIB_PATH):
         "rt_batch_capture": [ctypes.POINTER(rt_graph_desc), i32, P, P, P, P, P, P, P, i32, ctypes.POINTER(P),
                              ctypes.POINTER(P)],
         "rt_batch_info": [P, ctypes.POINTER(i64), i32],
+        "rt_graph_exec_policy": [P, i32],
         "rt_execute_events": [P, ctypes.POINTER(ctypes.c_float)],
         "rt_execute_kernels": [P, i32, i32, i32, ctypes.POINTER(ctypes.c_float)],
         "rt_execute_stitched": [P, i32, ctypes.POINTER(ctypes.c_float)],
@@ -399,6 +403,9 @@ class Graph:
 
     def exec_config(self, blocks: int = 0, warps: int = 0, claim: int = 0, keep: int = 0):
         _check(load().rt_graph_exec_config(self.h, blocks, warps, claim, keep))
+
+    def exec_policy(self, policy: int):
+        _check(load().rt_graph_exec_policy(self.h, policy))
 
     def hold_task(self, task: int, extra: int = 1):
         rt_debug_hold_task(self.h, task, extra)

@@ -38,16 +38,21 @@ def test_exec_tuner_configures_the_graph_and_results_hold(tmp_path):
     g = gpu_graph(tr, body=grt.RT_BODY_SPIN, spin_iters=9)
     g.analyze()
     c = g.tune(cache)
-    assert c["trials"] >= 10 and c["warps"] in (2, 4, 8) and c["claim"] in (1, 2, 4, 8, 16, 32)
-    assert c["keep"] in (2, 4, 8, 16, 32, 64) and c["blocks"] > 0 and c["ms"] > 0
+    assert c["policy"] in (grt.RT_EXEC_RING, grt.RT_EXEC_OWNED)
+    if c["policy"] == grt.RT_EXEC_RING:
+        assert c["warps"] in (2, 4, 8) and c["claim"] in (1, 2, 4, 8, 16, 32)
+        assert c["keep"] in (2, 4, 8, 16, 32, 64)
+    else:  # owned chunks: only the grid is tuned
+        assert c["warps"] in (1, 2, 4)
+    assert c["trials"] >= 10 and c["blocks"] > 0 and c["ms"] > 0
     g.out.zero_()
     g.execute()
     g.sync()
     want = np.array([oracle.spin(j, 9) for j in range(tr.n)], np.uint32).view(np.int32)
     assert np.array_equal(g.out.cpu().numpy(), want)
     c2 = g.tune(cache)
-    assert c2["trials"] == 0 and (c2["blocks"], c2["warps"], c2["claim"], c2["keep"]) == \
-        (c["blocks"], c["warps"], c["claim"], c["keep"])
+    assert c2["trials"] == 0 and (c2["blocks"], c2["warps"], c2["claim"], c2["keep"], c2["policy"]) == \
+        (c["blocks"], c["warps"], c["claim"], c["keep"], c["policy"])
     g.close()
 
 
