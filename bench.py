@@ -659,7 +659,17 @@ def committed_traffic(name):
     return d["bytes_per_launch"] if d.get("source_sha") == kernel_source_sha(name) else None
 
 
-def atomic_roofline_line(per_graph, mb):
+def executor_name(shapes):
+    """The persistent executor kernel the graphs ran under their tuned policies."""
+    pols = {int(sh.get("policy", 0)) for sh in shapes} if shapes else {0}
+    if pols == {1}:
+        return "k_exec_owned (persistent executor, owned chunks)"
+    if pols == {0}:
+        return "k_exec (persistent executor, ready ring)"
+    return "k_exec_owned / k_exec (persistent executor, per-graph policy)"
+
+
+def atomic_roofline_line(per_graph, mb, shapes=None):
     """The dominant kernel, the persistent executor, against the measured atomic
     roofline: algorithmic atomics per launch = E (one countdown decrement per
     edge) + 2 N / 32 (one ring reservation and one claim per 32-task warp
@@ -670,7 +680,7 @@ def atomic_roofline_line(per_graph, mb):
     launches = len(per_graph)
     achieved = (atoms / launches) / (t_exec / launches * 1e-3) / 1e9
     peak = mb["scatter_atomic_gops"]
-    return {"kernel": "k_exec (persistent executor)", "bound": "atomic", "achieved": achieved, "peak": peak,
+    return {"kernel": executor_name(shapes), "bound": "atomic", "achieved": achieved, "peak": peak,
             "unit": "Gatomic/s", "frac": achieved / peak, "traffic": committed_traffic("exec"),
             "traffic_unit": "DRAM bytes per launch (ncu)",
             "algorithmic_atomics_per_launch": atoms / launches, "avg_launch_ms": t_exec / launches,
@@ -678,7 +688,7 @@ def atomic_roofline_line(per_graph, mb):
                            "(rt_microbench_atomics)", "share_of_step": None}
 
 
-def roofline(per_graph, peaks):
+def roofline(per_graph, peaks, shapes=None):
     """per_graph: list of dicts (n, E, entries, pairs, ms_exec_kernel, ms_sweep_kernel) averaged
     over the timed steps. Algorithmic bytes:
       executor: 16 B per task (row_ptr pair, indeg read, counter re-arm) + 12 B per edge
@@ -696,7 +706,7 @@ def roofline(per_graph, peaks):
     achieved = (algo / launches) / (ms / launches * 1e-3) / 1e9
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     traffic = committed_traffic(name)
-    return {"kernel": {"exec": "k_exec (persistent executor)", "sweep": "k_sweep (tile interference sweep)"}[name],
+    return {"kernel": {"exec": executor_name(shapes), "sweep": "k_sweep (tile interference sweep)"}[name],
             "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "algorithmic_bytes_per_launch": algo / launches,
             "avg_launch_ms": ms / launches, "peak_source": "measured" if peaks else "fallback",
@@ -909,8 +919,8 @@ def run_ours(args):
                         "multiply-adds on its critical path"}
 
     peaks = measured_peaks()
-    roof_hbm = roofline(avg, peaks)
-    roof = atomic_roofline_line(avg, mb)
+    roof_hbm = roofline(avg, peaks, exec_shapes)
+    roof = atomic_roofline_line(avg, mb, exec_shapes)
     # executor kernel time over step time; above 1 when the graphs' executions overlap
     for r in (roof, roof_hbm):
         r["share_of_step"] = (r["avg_launch_ms"] * len(graphs)) / (total_ms / args.steps) if world == 1 else None
