@@ -245,18 +245,20 @@ def run_stitched(grt, torch):
     persistent launch, once with a barrier between replays (rt_replay) and once
     joined by the edges between two copies of the trace (rt_execute_stitched),
     so that replay r + 1 starts where its own predecessors in replay r are
-    done. EMPTY bodies; both runs use the launch shape the autotuner picks for
-    one execution of the trace; times include the counter reset and seeding."""
+    done. EMPTY bodies; the barrier replay runs under the autotuner's policy and
+    shape for one execution of the trace, the stitched one (a ring kernel) at the
+    best of four ring shapes; times include the counter reset and seeding."""
     R = 20
-    res = {"replays": R, "steps_per_replay": 100, "width": 1024}
+    res = {"replays": R, "steps_per_replay": 100, "width": 1024,
+           "launch": "barrier replay: the autotuner's policy and shape for one execution of the trace; stitched "
+                     "replay (a ring kernel): the best of four ring shapes (blocks, warps, claim, keep)"}
+    ring_shapes = [(304, 4, 2, 8), (304, 2, 2, 4), (152, 4, 1, 4), (152, 2, 2, 8)]
     for pat in ("stencil", "random"):
         T = tg.taskbench(1024, 100, pat, seed=0)
         g = grt.Graph(2, T.dom_lo, T.dom_hi, flags=grt.RT_GRAPH_PROFILE)
         g.launch_trace(T)
         g.analyze()
         shape = g.tune(TUNE_CACHE)
-        launch = (shape["blocks"], shape["warps"], shape["claim"], shape["keep"])
-        g.exec_config(*launch)
         bar = []
         for _ in range(4):
             g.replay(R)
@@ -266,12 +268,19 @@ def run_stitched(grt, torch):
         g2 = grt.Graph(2, T.dom_lo, T.dom_hi, flags=grt.RT_GRAPH_PROFILE)
         g2.launch_trace(tg.concat([T, T]))
         g2.analyze()
-        g2.exec_config(*launch)
         ana = g2.stats()["ms_analyze"]
-        st = [g2.execute_stitched(R) for _ in range(4)]
+        best = None
+        for sh in ring_shapes:
+            g2.exec_config(*sh)
+            st = [g2.execute_stitched(R) for _ in range(4)]
+            m = float(np.median(st[1:]))
+            if best is None or m < best[1]:
+                best = (sh, m)
         g2.close()
-        b, s_ = float(np.median(bar[1:])), float(np.median(st[1:]))
-        res[pat] = {"launch": launch, "barrier_ms": round(b, 3), "stitched_ms": round(s_, 3), "speedup": round(b / s_, 2),
+        b, s_ = float(np.median(bar[1:])), best[1]
+        res[pat] = {"barrier_launch": {k: shape[k] for k in ("policy", "blocks", "warps", "claim", "keep")},
+                    "stitched_launch": best[0], "barrier_ms": round(b, 3), "stitched_ms": round(s_, 3),
+                    "speedup": round(b / s_, 2),
                     "barrier_tasks_per_s": R * T.n / (b * 1e-3), "stitched_tasks_per_s": R * T.n / (s_ * 1e-3),
                     "ms_analyze_two_copies": round(ana, 3)}
     return res
