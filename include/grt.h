@@ -132,7 +132,8 @@ typedef struct {
   float ms_exec_kernel;   /* the persistent executor kernel alone */
   int32_t exec_blocks, exec_threads;
   float ms_sweep_kernel;  /* the interference sweep kernel alone */
-  int32_t pad0;
+  int32_t csr_by_buckets; /* 1: the CSR was built from per-source buckets (every row held at most
+                             1024 candidate pairs), 0: from a radix sort of all the pairs */
   /* diagnostic counters of the last executor launch: batches, tasks, edges,
    * ring claims, failed claim CASes, items published to the ring, idle polls,
    * waits for a reserved slot, ready successors kept by their warp */

@@ -275,6 +275,145 @@ __global__ void k_roots_emit(const int32_t* indeg, const uint32_t* pos, int32_t 
   if (dg == 0) root_items[pos[v]] = ((uint64_t)(uint32_t)graph << 32) | (uint32_t)(task_base + v);
 }
 
+// ---------------------------------------------------------------------------
+// CSR by buckets (graphs whose rows hold at most kBucketMaxRow candidate
+// pairs): the pairs are counted per source, each pair's target is scattered
+// into its source's bucket, every bucket is sorted and deduplicated in place,
+// and the unique targets are compacted into the CSR. One pass over the pairs
+// and a few over the targets, where an LSD radix sort of (source, target) keys
+// makes five.
+// ---------------------------------------------------------------------------
+constexpr int kBucketSmallRow = 32;  // rows sorted by one thread
+constexpr int kBucketLanes = 32;
+
+// pairs counted per source; the pair count is read on the device (the sweep's
+// cursor, capped at the buffer) so that no host sync is needed before it
+__global__ void k_bucket_count(const uint64_t* pairs, const unsigned long long* cursor, unsigned long long cap,
+                               int key_bits, uint32_t* cnt) {
+  const unsigned long long P = *cursor < cap ? *cursor : cap;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < (int64_t)P; i0 += stride) {
+    const int64_t i = i0 + threadIdx.x;
+    const uint64_t k = i < (int64_t)P ? pairs[i] : kEmpty64;
+    const int src = k != kEmpty64 ? (int)(k >> key_bits) : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, src);
+    if (src >= 0 && (peers & lanemask_lt()) == 0) atomicAdd(cnt + src, (uint32_t)__popc(peers));
+  }
+}
+
+// the longest row (atomicMax into *out)
+__global__ void k_bucket_maxrow(const uint32_t* cnt, int32_t n, uint32_t* out) {
+  uint32_t m = 0;
+  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) m = max(m, cnt[v]);
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
+// each pair's target into its source's bucket: positions off[src] .. off[src]
+// + cnt[src] - 1, handed out by counting cnt down (it ends at 0)
+__global__ void k_bucket_scatter(const uint64_t* pairs, int64_t P, int key_bits, const uint32_t* off, uint32_t* cnt,
+                                 uint32_t* bucket) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t k = i < P ? pairs[i] : kEmpty64;
+  const int src = k != kEmpty64 ? (int)(k >> key_bits) : -1;
+  const unsigned peers = __match_any_sync(0xffffffffu, src);
+  const int leader = __ffs((int)peers) - 1;
+  uint32_t old = 0;
+  if (src >= 0 && (peers & lanemask_lt()) == 0) old = atomicSub(cnt + src, (uint32_t)__popc(peers));
+  old = __shfl_sync(0xffffffffu, old, leader);
+  if (src >= 0) {
+    const uint32_t rank = (uint32_t)__popc(peers & lanemask_lt());
+    bucket[off[src] + old - 1u - rank] = (uint32_t)(k & ((1ull << key_bits) - 1ull));
+  }
+}
+
+// rows of at most kBucketSmallRow pairs: one thread sorts its row in place
+// (insertion sort) and keeps the distinct targets at its front; longer rows are
+// listed for k_bucket_sort_large
+__global__ void k_bucket_sort_small(const uint32_t* off, int32_t n, uint32_t* bucket, uint32_t* ucnt, uint32_t* big,
+                                    uint32_t* nbig) {
+  const int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  const uint32_t a = off[v], len = off[v + 1] - a;
+  if (len > (uint32_t)kBucketSmallRow) {
+    big[atomicAdd(nbig, 1u)] = (uint32_t)v;
+    return;
+  }
+  uint32_t* b = bucket + a;
+  for (uint32_t i = 1; i < len; ++i) {
+    const uint32_t x = b[i];
+    int j = (int)i - 1;
+    while (j >= 0 && b[j] > x) {
+      b[j + 1] = b[j];
+      --j;
+    }
+    b[j + 1] = x;
+  }
+  uint32_t u = 0;
+  for (uint32_t i = 0; i < len; ++i)
+    if (u == 0 || b[i] != b[u - 1]) b[u++] = b[i];
+  ucnt[v] = u;
+}
+
+// the listed long rows (at most kBucketMaxRow pairs): one warp each, a bitonic
+// sort in shared memory padded with ~0, then the distinct targets written back
+// to the row's front
+__global__ void __launch_bounds__(128) k_bucket_sort_large(const uint32_t* off, uint32_t* bucket, uint32_t* ucnt,
+                                                           const uint32_t* big, const uint32_t* nbig) {
+  __shared__ uint32_t buf[4][kBucketMaxRow];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t* s = buf[warp];
+  const uint32_t nb = *nbig;
+  for (uint32_t r = blockIdx.x * 4 + warp; r < nb; r += gridDim.x * 4) {
+    const uint32_t v = big[r];
+    const uint32_t a = off[v], len = off[v + 1] - a;
+    uint32_t N = 64;
+    while (N < len) N <<= 1;
+    for (uint32_t i = lane; i < N; i += 32) s[i] = i < len ? bucket[a + i] : 0xFFFFFFFFu;
+    __syncwarp();
+    for (uint32_t k = 2; k <= N; k <<= 1) {
+      for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+        for (uint32_t i = lane; i < N; i += 32) {
+          const uint32_t p = i ^ j;
+          if (p > i) {
+            const uint32_t x = s[i], y = s[p];
+            const bool up = (i & k) == 0;
+            if ((x > y) == up) {
+              s[i] = y;
+              s[p] = x;
+            }
+          }
+        }
+        __syncwarp();
+      }
+    }
+    uint32_t u = 0;
+    for (uint32_t i0 = 0; i0 < len; i0 += 32) {
+      const uint32_t i = i0 + lane;
+      const bool keep = i < len && (i == 0 || s[i] != s[i - 1]);
+      const unsigned m = __ballot_sync(0xffffffffu, keep);
+      if (keep) bucket[a + u + (uint32_t)__popc(m & lanemask_lt())] = s[i];
+      u += (uint32_t)__popc(m);
+    }
+    if (lane == 0) ucnt[v] = u;
+    __syncwarp();
+  }
+}
+
+// the distinct targets of every row into the CSR's columns, and in-degrees
+__global__ void k_bucket_compact(const uint32_t* off, const uint32_t* row_ptr, int32_t n, const uint32_t* bucket,
+                                 int32_t* col, int32_t* indeg) {
+  const int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  const uint32_t a = off[v], o = row_ptr[v], u = row_ptr[v + 1] - o;
+  for (uint32_t i = 0; i < u; ++i) {
+    const uint32_t t = bucket[a + i];
+    col[o + i] = (int32_t)t;
+    atomicAdd(indeg + t, 1);
+  }
+}
+
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -349,6 +488,40 @@ void launch_unique_flags(const uint64_t* keys, int64_t P, uint32_t* flags, cudaS
     count_launch();
     k_unique_flags<<<nblk(P, 256), 256, 0, s>>>(keys, P, flags);
   }
+}
+
+void launch_bucket_count(const uint64_t* pairs, const unsigned long long* cursor, unsigned long long cap,
+                         int key_bits, uint32_t* cnt, int32_t n, uint32_t* maxrow, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  count_launch(2);
+  k_bucket_count<<<(unsigned)(sms > 0 ? sms * 8 : 1024), 256, 0, s>>>(pairs, cursor, cap, key_bits, cnt);
+  unsigned mb = nblk(n, 256);
+  if (mb > 1024) mb = 1024;
+  if (mb < 1) mb = 1;
+  k_bucket_maxrow<<<mb, 256, 0, s>>>(cnt, n, maxrow);
+}
+
+void launch_bucket_build(const uint64_t* pairs, int64_t P, int key_bits, int32_t n, uint32_t* cnt, uint32_t* off,
+                         uint32_t* ucnt, uint32_t* big, uint32_t* nbig, uint32_t* bucket, uint32_t* row_ptr,
+                         uint32_t* scan_ws, int32_t* col, int32_t* indeg, cudaStream_t s) {
+  scan_exclusive<uint32_t>(cnt, off, n, scan_ws, s);
+  if (P > 0) {
+    count_launch();
+    k_bucket_scatter<<<nblk(P, 256), 256, 0, s>>>(pairs, P, key_bits, off, cnt, bucket);
+  }
+  cudaMemsetAsync(nbig, 0, 4, s);
+  count_launch(2);
+  k_bucket_sort_small<<<nblk(n, 256), 256, 0, s>>>(off, n, bucket, ucnt, big, nbig);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  k_bucket_sort_large<<<(unsigned)(sms > 0 ? sms * 4 : 512), 128, 0, s>>>(off, bucket, ucnt, big, nbig);
+  scan_exclusive<uint32_t>(ucnt, row_ptr, n, scan_ws, s);
+  cudaMemsetAsync(indeg, 0, (size_t)n * 4, s);
+  count_launch();
+  k_bucket_compact<<<nblk(n, 256), 256, 0, s>>>(off, row_ptr, n, bucket, col, indeg);
 }
 
 void launch_emit_csr(const uint64_t* keys, const uint32_t* flags, const uint32_t* upos, int64_t P,

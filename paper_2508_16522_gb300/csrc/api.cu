@@ -144,6 +144,7 @@ struct rt_graph {
   DevBuf rect_task, cnt, keys, keys_alt, pay, pay_alt, seg_b, seg_e, pairs, pairs_alt, flags, upos;
   DevBuf col, row_ptr, indeg, count, rootpos, root_items, ws, misc, adj;
   DevBuf tflags;  // per tile: dropped a pair in the first sweep / in the rerun
+  DevBuf bucket;  // CSR by buckets: per-task counts, offsets, distinct counts, long-row list, control words
   // the event-based executor (rt_execute_events): in-edges, events, waiter nodes
   DevBuf ev_pred_off, ev_pred, ev_head, ev_pending, ev_nodes, ev_ring, ev_ctrl;
   bool ev_preds = false;  // in-edges built for the current analysis
@@ -176,6 +177,7 @@ struct rt_graph {
   int cfg_blocks = 0, cfg_warps = 0, cfg_claim = 0, cfg_keep = 0;  // rt_graph_exec_config
   size_t mem_cap = 0;  // device bytes the graph may hold while it grows (0 = no cap; set by a server)
   int cfg_policy = RT_EXEC_RING;  // rt_graph_exec_policy
+  bool csr_by_buckets = false;    // the last analysis built its CSR from buckets, not the pair sort
 };
 
 namespace {
@@ -185,7 +187,7 @@ void for_each_buf(G* g, F f) {
   auto bufs = {&g->req_off, &g->lo, &g->hi, &g->priv, &g->pred_off, &g->pred, &g->body_arg, &g->err,
                 &g->rect_task, &g->cnt, &g->keys, &g->keys_alt, &g->pay, &g->pay_alt, &g->seg_b, &g->seg_e,
                 &g->pairs, &g->pairs_alt, &g->flags, &g->upos, &g->col, &g->row_ptr, &g->indeg, &g->count,
-                &g->rootpos, &g->root_items, &g->ws, &g->misc, &g->adj, &g->ring, &g->ctrl, &g->gtable,
+                &g->rootpos, &g->root_items, &g->ws, &g->misc, &g->adj, &g->bucket, &g->ring, &g->ctrl, &g->gtable,
                 &g->done_g, &g->tickets, &g->tflags, &g->ev_pred_off, &g->ev_pred, &g->ev_head, &g->ev_pending,
                 &g->ev_nodes, &g->ev_ring, &g->ev_ctrl, &g->ksink, &g->st_count, &g->st_ring, &g->st_ctrl,
                 &g->st_tickets, &g->st_err};
@@ -673,6 +675,17 @@ rt_status run_analysis(rt_graph* g) {
   if (Pe > 0)
     launch_explicit_pairs(g->pred_off.as<int32_t>(), g->pred.as<int32_t>(), n, B, g->pairs.as<uint64_t>(), s);
   int64_t Ptot = Pe;
+  // CSR by buckets: counts [n+1], offsets [n+1], distinct counts [n+1], long
+  // rows [n+1], the longest row and the long-row count
+  CKR(g->bucket.reserve(((size_t)4 * (n + 1) + 64) * 4, s));
+  uint32_t* bcnt = g->bucket.as<uint32_t>();
+  uint32_t* boff = bcnt + (n + 1);
+  uint32_t* bucnt = boff + (n + 1);
+  uint32_t* bbig = bucnt + (n + 1);
+  uint32_t* bmax = bbig + (n + 1);
+  uint32_t* bnbig = bmax + 16;
+  const bool counted = M > 0;  // the sweep's pairs are counted per source before its sync
+  h64[6] = 0;
   if (M > 0) {
     unsigned long long* rerun = reinterpret_cast<unsigned long long*>(g->misc.as<char>() + 128);
     CKR(g->tflags.reserve((size_t)ntiles * 2, s));
@@ -689,6 +702,12 @@ rt_status run_analysis(rt_graph* g) {
     if (prof) CK(cudaEventRecord(g->ev[EV_SW1], s));
     CK(cudaGetLastError());
     trace("analyze: sweep enqueued");
+    // the pairs per source and the longest row, before the sync the sweep
+    // needs anyway: they decide between the bucket CSR and the pair sort
+    CK(cudaMemsetAsync(bcnt, 0, (size_t)(n + 1) * 4, s));
+    CK(cudaMemsetAsync(bmax, 0, 4, s));
+    launch_bucket_count(g->pairs.as<uint64_t>(), cursor, cap, B, bcnt, n, bmax, s);
+    CK(cudaMemcpyAsync((void*)&h64[6], bmax, 4, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync((void*)&h64[3], cursor, 8, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync((void*)&h64[5], rerun, 8, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -704,6 +723,11 @@ rt_status run_analysis(rt_graph* g) {
       launch_sweep(spay, g->seg_b.as<uint32_t>(), g->seg_e.as<uint32_t>(), d, o2, sweep_blocks, s);
       if (prof) CK(cudaEventRecord(g->ev[EV_SW1], s));
       CK(cudaGetLastError());
+      // the rerun appended pairs: count again
+      CK(cudaMemsetAsync(bcnt, 0, (size_t)(n + 1) * 4, s));
+      CK(cudaMemsetAsync(bmax, 0, 4, s));
+      launch_bucket_count(g->pairs.as<uint64_t>(), cursor, cap, B, bcnt, n, bmax, s);
+      CK(cudaMemcpyAsync((void*)&h64[6], bmax, 4, cudaMemcpyDeviceToHost, s));
       CK(cudaMemcpyAsync((void*)&h64[3], cursor, 8, cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
       Ptot = (int64_t)h64[3];
@@ -726,17 +750,31 @@ rt_status run_analysis(rt_graph* g) {
   CKR(g->root_items.reserve((size_t)n * 8, s));
   CKR(reserve_ws(g, std::max(radix_ws_bytes(Ptot),
                              scan_ws_elems<uint32_t>(std::max<int64_t>(Ptot, n) + 1) * 4)));
-  const int flip = radix_sort<uint64_t>(g->pairs.as<uint64_t>(), g->pairs_alt.as<uint64_t>(), nullptr,
-                                        nullptr, Ptot, 2 * B, g->ws.p, s);
-  const uint64_t* sp = flip ? g->pairs_alt.as<uint64_t>() : g->pairs.as<uint64_t>();
-  if (prof) CK(cudaEventRecord(g->ev[EV_SORTP], s));
-  launch_unique_flags(sp, Ptot, g->flags.as<uint32_t>(), s);
-  scan_exclusive<uint32_t>(g->flags.as<uint32_t>(), g->upos.as<uint32_t>(), Ptot, g->ws.as<uint32_t>(), s);
-  CK(cudaMemsetAsync(g->row_ptr.p, 0, (size_t)(n + 1) * 4, s));
-  CK(cudaMemsetAsync(g->indeg.p, 0, (size_t)n * 4, s));
-  launch_emit_csr(sp, g->flags.as<uint32_t>(), g->upos.as<uint32_t>(), Ptot, B, g->col.as<int32_t>(),
-                  g->row_ptr.as<int32_t>(), g->indeg.as<int32_t>(), s);
-  scan_exclusive<uint32_t>(g->row_ptr.as<uint32_t>(), g->row_ptr.as<uint32_t>(), n, g->ws.as<uint32_t>(), s);
+  // rows of at most kBucketMaxRow pairs: buckets per source, each sorted and
+  // deduplicated in place; longer rows: an LSD radix sort of all the pairs
+  const bool by_buckets = counted && (uint32_t)(h64[6] & 0xffffffffull) <= (uint32_t)kBucketMaxRow;
+  const uint32_t* n_edges_at;
+  if (by_buckets) {
+    launch_bucket_build(g->pairs.as<uint64_t>(), Ptot, B, n, bcnt, boff, bucnt, bbig, bnbig, g->flags.as<uint32_t>(),
+                        g->row_ptr.as<uint32_t>(), g->ws.as<uint32_t>(), g->col.as<int32_t>(), g->indeg.as<int32_t>(),
+                        s);
+    if (prof) CK(cudaEventRecord(g->ev[EV_SORTP], s));
+    n_edges_at = g->row_ptr.as<uint32_t>() + n;
+  } else {
+    const int flip = radix_sort<uint64_t>(g->pairs.as<uint64_t>(), g->pairs_alt.as<uint64_t>(), nullptr,
+                                          nullptr, Ptot, 2 * B, g->ws.p, s);
+    const uint64_t* sp = flip ? g->pairs_alt.as<uint64_t>() : g->pairs.as<uint64_t>();
+    if (prof) CK(cudaEventRecord(g->ev[EV_SORTP], s));
+    launch_unique_flags(sp, Ptot, g->flags.as<uint32_t>(), s);
+    scan_exclusive<uint32_t>(g->flags.as<uint32_t>(), g->upos.as<uint32_t>(), Ptot, g->ws.as<uint32_t>(), s);
+    CK(cudaMemsetAsync(g->row_ptr.p, 0, (size_t)(n + 1) * 4, s));
+    CK(cudaMemsetAsync(g->indeg.p, 0, (size_t)n * 4, s));
+    launch_emit_csr(sp, g->flags.as<uint32_t>(), g->upos.as<uint32_t>(), Ptot, B, g->col.as<int32_t>(),
+                    g->row_ptr.as<int32_t>(), g->indeg.as<int32_t>(), s);
+    scan_exclusive<uint32_t>(g->row_ptr.as<uint32_t>(), g->row_ptr.as<uint32_t>(), n, g->ws.as<uint32_t>(), s);
+    n_edges_at = g->upos.as<uint32_t>() + Ptot;
+  }
+  g->csr_by_buckets = by_buckets;
   launch_roots(g->indeg.as<int32_t>(), n, g->rootpos.as<uint32_t>(), s);
   scan_exclusive<uint32_t>(g->rootpos.as<uint32_t>(), g->rootpos.as<uint32_t>(), n, g->ws.as<uint32_t>(), s);
   launch_roots_emit(g->indeg.as<int32_t>(), g->rootpos.as<uint32_t>(), n, 0, 0, g->root_items.as<uint64_t>(),
@@ -744,7 +782,7 @@ rt_status run_analysis(rt_graph* g) {
   CKR(g->adj.reserve((size_t)n * 32, s));
   launch_pack_adj(g->row_ptr.as<int32_t>(), g->col.as<int32_t>(), g->indeg.as<int32_t>(), n, g->adj.as<int4>(), s);
   if (prof) CK(cudaEventRecord(g->ev[EV_CSR], s));
-  CK(cudaMemcpyAsync(g->hpin + 8, g->upos.as<uint32_t>() + Ptot, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(g->hpin + 8, n_edges_at, 4, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(g->hpin + 9, g->rootpos.as<uint32_t>() + n, 4, cudaMemcpyDeviceToHost, s));
   trace("analyze: csr enqueued");
   CK(cudaStreamSynchronize(s));
@@ -1291,6 +1329,7 @@ rt_status rt_graph_stats(rt_graph_t g, rt_graph_stats_t* out) {
   out->n_preds = g->P;
   out->n_entries = g->n_entries;
   out->n_pairs = g->n_pairs;
+  out->csr_by_buckets = g->csr_by_buckets ? 1 : 0;
   out->n_edges = g->n_edges;
   out->n_roots = g->n_roots;
   out->tile_w = g->dims.tw;

@@ -301,6 +301,17 @@ void launch_explicit_pairs(const int32_t* pred_off, const int32_t* pred, int32_t
 void launch_unique_flags(const uint64_t* keys, int64_t P, uint32_t* flags, cudaStream_t s);
 void launch_emit_csr(const uint64_t* keys, const uint32_t* flags, const uint32_t* upos, int64_t P,
                      int key_bits, int32_t* col, int32_t* rowcnt, int32_t* indeg, cudaStream_t s);
+// CSR by buckets (rows of at most kBucketMaxRow candidate pairs): pairs
+// counted per source and the longest row found (count reads the pair count on
+// the device); then scatter into per-source buckets, sort and deduplicate
+// every bucket, compact into col[] and in-degrees, row_ptr = scan of the
+// distinct counts
+constexpr int kBucketMaxRow = 1024;
+void launch_bucket_count(const uint64_t* pairs, const unsigned long long* cursor, unsigned long long cap,
+                         int key_bits, uint32_t* cnt, int32_t n, uint32_t* maxrow, cudaStream_t s);
+void launch_bucket_build(const uint64_t* pairs, int64_t P, int key_bits, int32_t n, uint32_t* cnt, uint32_t* off,
+                         uint32_t* ucnt, uint32_t* big, uint32_t* nbig, uint32_t* bucket, uint32_t* row_ptr,
+                         uint32_t* scan_ws, int32_t* col, int32_t* indeg, cudaStream_t s);
 void launch_roots(const int32_t* indeg, int32_t n, uint32_t* flags, cudaStream_t s);
 void launch_roots_emit(const int32_t* indeg, const uint32_t* pos, int32_t n, int32_t task_base,
                        int32_t graph, uint64_t* root_items, int32_t* count, cudaStream_t s);

@@ -90,13 +90,13 @@ class rt_graph_stats_t(ctypes.Structure):
                 ("ms_sweep", ctypes.c_float), ("ms_sort_pairs", ctypes.c_float), ("ms_csr", ctypes.c_float),
                 ("ms_execute", ctypes.c_float), ("ms_exec_kernel", ctypes.c_float),
                 ("exec_blocks", ctypes.c_int32), ("exec_threads", ctypes.c_int32),
-                ("ms_sweep_kernel", ctypes.c_float), ("pad0", ctypes.c_int32),
+                ("ms_sweep_kernel", ctypes.c_float), ("csr_by_buckets", ctypes.c_int32),
                 ("exec_counters", ctypes.c_int64 * 9)]
 
     COUNTER_NAMES = ("batches", "tasks", "edges", "claims", "cas_fail", "pushed", "idle", "slot_wait", "kept")
 
     def as_dict(self):
-        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("pad0", "exec_counters")}
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "exec_counters"}
         d["exec_counters"] = dict(zip(self.COUNTER_NAMES, list(self.exec_counters)))
         return d
 

@@ -358,3 +358,28 @@ def test_concurrent_analyses_with_different_tiles():
     for g, t, ref in zip(graphs, trs, refs):
         assert_csr_equal(g, t, ref)
         g.close()
+
+
+@pytest.mark.parametrize("readers", [5, 300, 1024, 1500])
+def test_csr_by_buckets_and_by_pair_sort(readers):
+    """A write of one cell followed by `readers` reads of it: the writer's row
+    holds `readers` candidate pairs. Rows of at most 32 pairs are sorted by one
+    thread, up to 1024 by a warp in shared memory, longer ones send the whole
+    graph to the radix sort of all pairs; every path gives the oracle's CSR,
+    with a Task Bench graph (short rows) on the bucket path too."""
+    n = readers + 2
+    lo = np.zeros(n, np.int64)
+    lo[-1] = 1  # an unrelated task on another cell
+    pv = np.array([1] + [0] * readers + [1], np.uint8)
+    tr = tg._finish(1, [0], [7], np.ones(n), lo, lo, pv, name=f"fanout{readers}")
+    g = gpu_graph(tr, tile=(8, 1))
+    g.analyze()
+    assert_csr_equal(g, tr)
+    assert g.stats()["csr_by_buckets"] == (1 if readers <= 1024 else 0)
+    g.close()
+    tb = tg.taskbench(128, 40, "random", seed=readers)
+    g = gpu_graph(tb)
+    g.analyze()
+    assert_csr_equal(g, tb)
+    assert g.stats()["csr_by_buckets"] == 1
+    g.close()
