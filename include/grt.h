@@ -91,7 +91,7 @@ enum {
 /* executor policies of a single graph (rt_graph_exec_policy) */
 enum {
   RT_EXEC_RING = 0,  /* ready tasks go through a global ring that any warp claims from */
-  RT_EXEC_OWNED = 1  /* every warp owns fixed chunks of 32 consecutive tasks and polls their countdowns */
+  RT_EXEC_OWNED = 1  /* every warp owns fixed chunks of consecutive tasks and polls their countdowns */
 };
 
 /* rt_graph_desc.flags */
@@ -265,16 +265,18 @@ rt_status rt_graph_exec_config(rt_graph_t g, int32_t blocks, int32_t warps, int3
 /* How rt_execute / rt_replay find ready tasks (Algorithm 1's EXECUTE_OP):
  * RT_EXEC_RING (default) publishes every task made ready that its warp does
  * not keep to a global ring that any warp claims from; RT_EXEC_OWNED gives
- * every warp fixed chunks of 32 consecutive tasks (chunk c to warp c mod the
- * grid's warps, taken in increasing order, one task per lane) and lets it poll
- * their countdowns, the predecessors decrementing them with reductions that
- * need no answer -- the operations compiled to their worker of Algorithm 1.
- * OWNED suits graphs whose tasks become ready roughly in task order (the
- * wavefronts of Task Bench); RING suits irregular ones. Under OWNED the claim
- * width of rt_graph_exec_config is the number of chunks a warp holds at once
- * (1, 2 or 4; default 1; with more, the next chunks' records and countdowns
- * are loaded while the current one finishes) and keep is unused. Results never depend on
- * the policy. Errors: RT_ERR_INVALID. */
+ * every warp fixed chunks of consecutive tasks (chunk c to warp c mod the
+ * grid's warps, taken in increasing order) and lets it poll their countdowns,
+ * the predecessors decrementing them with reductions that need no answer --
+ * the operations compiled to their worker of Algorithm 1. OWNED suits graphs
+ * whose tasks become ready roughly in task order (the wavefronts of Task
+ * Bench); RING suits irregular ones. Under OWNED the claim width of
+ * rt_graph_exec_config is the number of lanes that hold one task (1, 2 or 4;
+ * default 1; a chunk is 32 / that many tasks, and the task's successors are
+ * split between its lanes) and keep is unused. The first OWNED run after an
+ * analysis of a graph with a task of more than 5 successors builds 32 more
+ * bytes of trigger record per task (successors 6 to 13 inline). Results never
+ * depend on the policy. Errors: RT_ERR_INVALID. */
 rt_status rt_graph_exec_policy(rt_graph_t g, int32_t policy);
 
 /* Waits for the graph's stream; returns RT_OK, RT_ERR_TIMEOUT (the executor
@@ -396,8 +398,9 @@ rt_status rt_tune_tile(const rt_graph_desc* desc, int32_t n, const int32_t* req_
                        int32_t* tile_h, float* ms);
 
 /* Runs an analysed graph under candidate launch shapes -- the ring policy by
- * coordinate descent (warps x blocks per SM, then claim, then keep), the
- * owned policy over warps x blocks per SM; best of two runs each -- and
+ * coordinate descent (warps x blocks per SM, then claim, then keep; best of
+ * two runs each), the owned policy over its grids and then lanes per task
+ * (best of three) -- and
  * configures it with the fastest policy and shape (rt_graph_exec_policy,
  * rt_graph_exec_config). The graph's bodies run once per trial: a
  * state-changing body sees those runs. Synchronous. */

@@ -143,6 +143,9 @@ struct rt_graph {
   // analysis
   DevBuf rect_task, cnt, keys, keys_alt, pay, pay_alt, seg_b, seg_e, pairs, pairs_alt, flags, upos;
   DevBuf col, row_ptr, indeg, count, rootpos, root_items, ws, misc, adj;
+  DevBuf adjx;          // the owned executor's extension records, built on its first run after an analysis
+  bool adjx_ok = false;
+  int32_t max_outdeg = 0;  // largest out-degree of the analysed graph
   DevBuf tflags;  // per tile: dropped a pair in the first sweep / in the rerun
   DevBuf bucket;  // CSR by buckets: per-task counts, offsets, distinct counts, long-row list, control words
   // the event-based executor (rt_execute_events): in-edges, events, waiter nodes
@@ -187,10 +190,10 @@ void for_each_buf(G* g, F f) {
   auto bufs = {&g->req_off, &g->lo, &g->hi, &g->priv, &g->pred_off, &g->pred, &g->body_arg, &g->err,
                 &g->rect_task, &g->cnt, &g->keys, &g->keys_alt, &g->pay, &g->pay_alt, &g->seg_b, &g->seg_e,
                 &g->pairs, &g->pairs_alt, &g->flags, &g->upos, &g->col, &g->row_ptr, &g->indeg, &g->count,
-                &g->rootpos, &g->root_items, &g->ws, &g->misc, &g->adj, &g->bucket, &g->ring, &g->ctrl, &g->gtable,
-                &g->done_g, &g->tickets, &g->tflags, &g->ev_pred_off, &g->ev_pred, &g->ev_head, &g->ev_pending,
-                &g->ev_nodes, &g->ev_ring, &g->ev_ctrl, &g->ksink, &g->st_count, &g->st_ring, &g->st_ctrl,
-                &g->st_tickets, &g->st_err};
+                &g->rootpos, &g->root_items, &g->ws, &g->misc, &g->adj, &g->adjx, &g->bucket, &g->ring, &g->ctrl,
+                &g->gtable, &g->done_g, &g->tickets, &g->tflags, &g->ev_pred_off, &g->ev_pred, &g->ev_head,
+                &g->ev_pending, &g->ev_nodes, &g->ev_ring, &g->ev_ctrl, &g->ksink, &g->st_count, &g->st_ring,
+                &g->st_ctrl, &g->st_tickets, &g->st_err};
   for (auto* b : bufs) f(*b);
 }
 
@@ -780,16 +783,22 @@ rt_status run_analysis(rt_graph* g) {
   launch_roots_emit(g->indeg.as<int32_t>(), g->rootpos.as<uint32_t>(), n, 0, 0, g->root_items.as<uint64_t>(),
                     g->count.as<int32_t>(), s);
   CKR(g->adj.reserve((size_t)n * 32, s));
-  launch_pack_adj(g->row_ptr.as<int32_t>(), g->col.as<int32_t>(), g->indeg.as<int32_t>(), n, g->adj.as<int4>(), s);
+  uint32_t* maxdeg = reinterpret_cast<uint32_t*>(g->misc.as<char>() + 192);
+  CK(cudaMemsetAsync(maxdeg, 0, 4, s));
+  launch_pack_adj(g->row_ptr.as<int32_t>(), g->col.as<int32_t>(), g->indeg.as<int32_t>(), n, g->adj.as<int4>(),
+                  maxdeg, s);
+  g->adjx_ok = false;
   if (prof) CK(cudaEventRecord(g->ev[EV_CSR], s));
   CK(cudaMemcpyAsync(g->hpin + 8, n_edges_at, 4, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(g->hpin + 9, g->rootpos.as<uint32_t>() + n, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(g->hpin + 10, maxdeg, 4, cudaMemcpyDeviceToHost, s));
   trace("analyze: csr enqueued");
   CK(cudaStreamSynchronize(s));
   trace("analyze: csr synced");
   CK(cudaGetLastError());
   g->n_edges = g->hpin[8];
   g->n_roots = g->hpin[9];
+  g->max_outdeg = (int32_t)g->hpin[10];
   g->analyze_timed = prof;
   return RT_OK;
 }
@@ -853,6 +862,12 @@ rt_status prepare_run(rt_graph* g, int32_t replays, ExecParams* out, int64_t* ri
   *ring_clear = owned ? 0 : ((grow || g->dirty) ? (int64_t)(g->ring.cap / 8) : 0);
   CKR(g->ctrl.reserve(sizeof(ExecCtrl), s));
   CKR(g->done_g.reserve(64, s));
+  const bool wide = owned && g->max_outdeg > kAdjInline;  // some task has successors past its record
+  if (wide && !g->adjx_ok) {
+    CKR(g->adjx.reserve((size_t)g->n * 32, s));
+    launch_pack_adjx(g->row_ptr.as<int32_t>(), g->col.as<int32_t>(), g->n, g->adjx.as<int4>(), s);
+    g->adjx_ok = true;
+  }
   if (!g->gtable.p) {
     CKR(g->gtable.reserve(sizeof(ExecGraph), s));
   }
@@ -885,6 +900,7 @@ rt_status prepare_run(rt_graph* g, int32_t replays, ExecParams* out, int64_t* ri
   if (g->desc.flags & RT_GRAPH_TICKETS) CKR(g->tickets.reserve((size_t)g->n * 8, s));
   ExecParams p{};
   p.adj = g->adj.as<int4>();
+  p.adjx = wide ? g->adjx.as<int4>() : nullptr;
   p.row_ptr = g->row_ptr.as<int32_t>();
   p.col = g->col.as<int32_t>();
   p.indeg = g->indeg.as<int32_t>();
@@ -1501,7 +1517,8 @@ rt_status rt_batch_create(const rt_graph_t* graphs, int32_t n_graphs, void* stre
     rb += g->n_roots;
   }
   if ((st = b->adj.reserve((size_t)std::max<int64_t>(T, 1) * 32, s))) return bail(st);
-  launch_pack_adj(b->row_ptr.as<int32_t>(), b->col.as<int32_t>(), b->indeg.as<int32_t>(), T, b->adj.as<int4>(), s);
+  launch_pack_adj(b->row_ptr.as<int32_t>(), b->col.as<int32_t>(), b->indeg.as<int32_t>(), T, b->adj.as<int4>(),
+                  nullptr, s);
   if (cudaMemcpyAsync(b->gtable.p, table.data(), table.size() * sizeof(ExecGraph), cudaMemcpyHostToDevice, s) !=
           cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess)
@@ -1619,7 +1636,8 @@ rt_status rt_batch_create_stacked(rt_graph_t g, const int32_t* task_off, int32_t
     tmp.release(s);
     return bail(st);
   }
-  launch_pack_adj(b->row_ptr.as<int32_t>(), b->col.as<int32_t>(), b->indeg.as<int32_t>(), T, b->adj.as<int4>(), s);
+  launch_pack_adj(b->row_ptr.as<int32_t>(), b->col.as<int32_t>(), b->indeg.as<int32_t>(), T, b->adj.as<int4>(),
+                  nullptr, s);
   e = cudaMemcpyAsync(b->gtable.p, table.data(), table.size() * sizeof(ExecGraph), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   tmp.release(s);
@@ -1966,6 +1984,7 @@ rt_status graph_trim(rt_graph_t g) {
   drop_kernel_graph(g);
   for_each_buf(g, [&](DevBuf& b) { b.release(g->s); });
   g->gt_valid = false;
+  g->adjx_ok = false;
   return RT_OK;
 }
 }  // namespace grt

@@ -389,17 +389,25 @@ __global__ void __launch_bounds__(256, 1) k_exec(ExecParams p) {
 
 // The owned-chunk executor (RT_EXEC_OWNED, one graph). Algorithm 1 compiles
 // every operation to one worker; here warp w owns chunks c = w, w + W, w + 2W
-// ... of 32 consecutive tasks (W = warps of the grid) and runs them in that
-// order, one task per lane, holding K of them at once (a window: the next
-// chunks' trigger records and countdowns are already in flight while the
-// current ones finish). A lane polls its task's countdown (one coalesced
-// 128-byte load per chunk and poll) and runs the task once it reads 0; the
-// task re-arms its own countdown, runs its body in place, and decrements its
-// successors with fire-and-forget reductions (COMPLETED_EDGE needs no answer:
-// the successor's owner sees the zero when it polls): the first kAdjInline
-// straight from the lane's trigger record, the rest shared by the warp. No
-// ring, no reservation, no record load on the critical path: a wavefront step
-// costs a reduction reaching L2 and the owner's next poll.
+// ... of C consecutive tasks (W = warps of the grid) and runs them in that
+// order. Each task of a chunk is held by a group of L consecutive lanes
+// (C = 32 / L). Every lane of a group polls the task's countdown (one
+// coalesced load per chunk and poll; the group reads one word in one load, so
+// its lanes agree on readiness), and once it reads 0 the group runs the task:
+// its head lane re-arms the countdown (INIT for the next run) and runs the
+// body in place, and every lane decrements the successors held in its part
+// of the task's trigger record with fire-and-forget reductions
+// (COMPLETED_EDGE needs no answer: the successor's owner sees the zero when
+// it polls). A record is R = 2 int4 per task (kAdjInline successors inline)
+// or, when some task has more, R = 4 (the extension record adds successors
+// up to kAdjWide); lane h of a group holds record int4s [h R / L,
+// (h + 1) R / L). A warp alone on its SM hides no instruction latency, and a
+// predicated reduction slot costs about the same whether or not its lanes
+// are active, so spreading a record over L lanes cuts the slots one wave
+// issues from 4R to 4R / L. Successors past the record take the warp-shared
+// path through the CSR's columns. No ring, no reservation, no record load on
+// the critical path: a wavefront step costs a reduction reaching L2 and the
+// owner's next poll (issued before the wave's bodies run, and read after).
 // Every warp takes its chunks in increasing task order and holds its oldest
 // unfinished one, and every edge points to a later task, so the smallest
 // unfinished task is always in a chunk its owner holds, with all its
@@ -409,9 +417,12 @@ __global__ void __launch_bounds__(256, 1) k_exec(ExecParams p) {
 // timeout_ns without global progress.
 constexpr uint32_t kOwnedBackoffMax = 256;  // ns between polls of a warp whose tasks are all waiting
 
-template <bool TICKETS, bool FENCE, int K>
+template <bool TICKETS, bool FENCE, int L>
 __global__ void __launch_bounds__(256, 1) k_exec_owned(ExecParams p) {
+  constexpr int C = 32 / L;   // tasks per chunk
+  constexpr int QM = 4 / L;   // record int4s one lane holds at most
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = lane / L, h = lane % L;  // the lane's task in the chunk, its part of the record
   const int W = (int)(gridDim.x * (blockDim.x >> 5));
   const int gw = (int)blockIdx.x * (int)(blockDim.x >> 5) + warp;
   ExecCtrl* ctrl = p.ctrl;
@@ -419,7 +430,15 @@ __global__ void __launch_bounds__(256, 1) k_exec_owned(ExecParams p) {
   const int n = G.n_tasks;
   const int body = G.body, spin = G.spin_iters;
   int32_t* const out = G.out;
-  const int nchunks = (n + 31) >> 5;
+  const int nchunks = (n + C - 1) / C;
+  const int R = p.adjx != nullptr ? 4 : 2;              // int4s per trigger record
+  const int inl = 4 * R - 3;                            // successors a record holds
+  const int g0 = h * R / L, nq = (h + 1) * R / L - g0;  // this lane's record int4s [g0, g0 + nq)
+  const int head = (L + R - 1) / R - 1;                 // the group's lane holding int4 0
+  const bool is_head = h == head;
+  const int head_lane = grp * L + head;
+  const unsigned heads = __ballot_sync(kFull, is_head);
+  uint32_t edges = 0;  // out-edges of the tasks this lane ran as head (diagnostics)
   uint32_t cnt[kCntCount];
 #pragma unroll
   for (int k = 0; k < kCntCount; ++k) cnt[k] = 0;
@@ -474,50 +493,44 @@ __global__ void __launch_bounds__(256, 1) k_exec_owned(ExecParams p) {
       idle_since = 0;
       fence_acq_rel_gpu();  // acquire: the counters re-armed by run r - 1
     }
-    // the window: slot k holds chunk ck[k] (-1: none), one task per lane
     uint32_t ran = 0;  // tasks this warp ran in run r (warp-uniform)
     int next_c = gw;   // the next chunk this warp takes
-    int ck[K], v[K], ctasks[K];
-    int4 a0[K], a1[K];
-    int32_t polled[K];  // the lane's countdown, polled one round ahead
-    unsigned pending[K];
-    auto take = [&](int k) {
-      ck[k] = -1;
-      v[k] = 0;
-      ctasks[k] = 0;
-      pending[k] = 0u;
-      polled[k] = 1;
-      a0[k] = make_int4(0, 0, 0, -1);
-      a1[k] = make_int4(-1, -1, -1, -1);
+    int ck = -1, v = 0, ctasks = 0, deg = 0, dmax = 0;
+    int4 q[QM];        // this lane's part of its task's trigger record
+    int32_t polled = 1;  // the lane's countdown, polled one round ahead
+    unsigned pending = 0u;
+    auto take = [&]() {
+      ck = -1;
+      ctasks = 0;
+      pending = 0u;
+      polled = 1;
+      deg = 0;
+      dmax = 0;
       if (next_c >= nchunks) return;
-      ck[k] = next_c;
+      ck = next_c;
       next_c += W;
-      v[k] = ck[k] * 32 + lane;
-      const bool has = v[k] < n;
-      if (has) {
-        a0[k] = __ldg(p.adj + 2 * (int64_t)v[k]);
-        a1[k] = __ldg(p.adj + 2 * (int64_t)v[k] + 1);
-        polled[k] = ld_relaxed_s32(p.count + v[k]);
-      }
-      pending[k] = __ballot_sync(kFull, has);
-      ctasks[k] = __popc(pending[k]);
-    };
+      v = ck * C + grp;
+      const bool has = v < n;
 #pragma unroll
-    for (int k = 0; k < K; ++k) take(k);
+      for (int k = 0; k < QM; ++k) {
+        const int g = g0 + k;
+        q[k] = make_int4(-1, -1, -1, -1);
+        if (k < nq && has) q[k] = __ldg(g < 2 ? p.adj + 2 * (int64_t)v + g : p.adjx + 2 * (int64_t)v + (g - 2));
+      }
+      if (has) polled = ld_relaxed_s32(p.count + v);
+      pending = __ballot_sync(kFull, has);
+      ctasks = __popc(pending & heads);
+      deg = __shfl_sync(kFull, q[0].y, head_lane);  // the head's int4 0: {row start, degree, in-degree, s0}
+      if (!has) deg = 0;
+      dmax = (int)__reduce_max_sync(kFull, (unsigned)deg);  // record slots past it stay unissued
+    };
+    take();
     uint32_t backoff = 0;
     for (;;) {
-      bool busy = false, any = false;
-      bool ready[K];
-      unsigned rm[K];
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        busy |= pending[k] != 0u;
-        ready[k] = ((pending[k] >> lane) & 1u) && polled[k] == 0;
-        rm[k] = __ballot_sync(kFull, ready[k]);
-        any |= rm[k] != 0u;
-      }
-      if (!busy || stop) break;
-      if (!any) {
+      if (pending == 0u || stop) break;
+      const bool ready = ((pending >> lane) & 1u) && polled == 0;
+      const unsigned rm = __ballot_sync(kFull, ready);
+      if (!rm) {
         ++cnt[kCntIdle];
         // the first empty polls retry at once (a stale prefetch); the launch's
         // status and progress are watched once polls keep failing
@@ -527,94 +540,88 @@ __global__ void __launch_bounds__(256, 1) k_exec_owned(ExecParams p) {
         }
         if (backoff) __nanosleep(backoff);
         backoff = backoff ? (backoff < kOwnedBackoffMax ? backoff * 2 : kOwnedBackoffMax) : 16;
-#pragma unroll
-        for (int k = 0; k < K; ++k)
-          if ((pending[k] >> lane) & 1u) polled[k] = ld_relaxed_s32(p.count + v[k]);
+        if ((pending >> lane) & 1u) polled = ld_relaxed_s32(p.count + v);
         continue;
       }
       backoff = 0;
       idle_since = 0;
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        pending[k] &= ~rm[k];
-        // the next poll is in flight during the work below; a value read
-        // before this warp's own decrements can only be late (counters only
-        // go down to 0), never early
-        if (!FENCE && !TICKETS) polled[k] = ((pending[k] >> lane) & 1u) ? ld_relaxed_s32(p.count + v[k]) : 1;
-      }
+      pending &= ~rm;
+      // the next poll is in flight during the work below; a value read before
+      // this warp's own decrements can only be late (counters only go down to
+      // 0), never early
+      if (!FENCE && !TICKETS) polled = ((pending >> lane) & 1u) ? ld_relaxed_s32(p.count + v) : 1;
       if (FENCE) fence_acq_rel_gpu();  // acquire: the predecessors' effects before the bodies
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        if (!ready[k]) continue;
-        const int t = v[k];
-        p.count[t] = a0[k].z;  // INIT's reset for the next run, done by the task itself
-        if (TICKETS) p.tickets[2 * (int64_t)t] = (int32_t)atomicAdd(&ctrl->ticket, 1u);
+      if (ready && is_head) {
+        p.count[v] = q[0].z;  // INIT's reset for the next run, done by the task itself
+        if (TICKETS) p.tickets[2 * (int64_t)v] = (int32_t)atomicAdd(&ctrl->ticket, 1u);
         if (!FENCE) {
-          if (body == RT_BODY_SPIN) out[t] = (int32_t)spin_body((uint32_t)t, spin);
-          else if (body == RT_BODY_FMA) out[t] = fma_body((uint32_t)t, spin);
+          if (body == RT_BODY_SPIN) out[v] = (int32_t)spin_body((uint32_t)v, spin);
+          else if (body == RT_BODY_FMA) out[v] = fma_body((uint32_t)v, spin);
         } else {
-          run_body<true>(G, t);
+          run_body<true>(G, v);
         }
-        if (TICKETS) p.tickets[2 * (int64_t)t + 1] = (int32_t)atomicAdd(&ctrl->ticket, 1u);
+        if (TICKETS) p.tickets[2 * (int64_t)v + 1] = (int32_t)atomicAdd(&ctrl->ticket, 1u);
       }
-      if (FENCE || TICKETS) fence_acq_rel_gpu();  // release: bodies before the decrements
-      // COMPLETED_EDGE for every out-edge of the tasks that just ran: each lane
-      // its task's inline successors, straight from its record (no answer
-      // needed: reductions); the warp shares the edges past them
-      unsigned degs = 0;
+      if (FENCE || TICKETS) {
+        // release: bodies before the decrements. A task's body ran in its head
+        // lane and its decrements come from every lane of its group, so the
+        // warp synchronizes first: the head's writes then precede each lane's
+        // fence, which releases them with that lane's reductions
+        if (L > 1) __syncwarp();
+        fence_acq_rel_gpu();
+      }
+      // COMPLETED_EDGE for every out-edge of the tasks that just ran: each
+      // lane the successors in its part of the record (int4 g holds successors
+      // 4g - 3 .. 4g; int4 0 only successor 0), as reductions; the warp shares
+      // the edges past the record
+      if (ready) {
 #pragma unroll
-      for (int k = 0; k < K; ++k) {
-        const int deg = ready[k] ? a0[k].y : 0;
-        degs += (unsigned)deg;
-        if (ready[k]) {
-          const int succ[kAdjInline] = {a0[k].w, a1[k].x, a1[k].y, a1[k].z, a1[k].w};
-#pragma unroll
-          for (int j = 0; j < kAdjInline; ++j)
-            if (j < deg) atomicSub(p.count + succ[j], 1);  // result unused: a reduction
-        }
-        const int extra = deg > kAdjInline ? deg - kAdjInline : 0;
-        if (__any_sync(kFull, extra > 0)) {
-          int incl = extra;
-#pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += y;
-          }
-          const int excl = incl - extra;
-          const int D = __shfl_sync(kFull, incl, 31);
-          const int rbeg = a0[k].x + kAdjInline;
-          for (int e0 = 0; e0 < D; e0 += 32) {
-            const int e = e0 + lane;
-            int owner = 0;
-#pragma unroll
-            for (int step = 16; step >= 1; step >>= 1) {
-              const int cand = owner + step;
-              if (__shfl_sync(kFull, excl, cand) <= e) owner = cand;
-            }
-            const int oex = __shfl_sync(kFull, excl, owner);
-            const int orb = __shfl_sync(kFull, rbeg, owner);
-            if (e < D) atomicSub(p.count + p.col[orb + (e - oex)], 1);
+        for (int k = 0; k < QM; ++k) {
+          if (k < nq && 4 * (g0 + k) - 3 < dmax) {  // uniform when L = 1: the chunk's largest degree
+            const int j = 4 * (g0 + k) - 3;  // successor index of q[k].x
+            if (j >= 0 && j < deg) atomicSub(p.count + q[k].x, 1);  // result unused: a reduction
+            if (j + 1 >= 0 && j + 1 < deg) atomicSub(p.count + q[k].y, 1);
+            if (j + 2 >= 0 && j + 2 < deg) atomicSub(p.count + q[k].z, 1);
+            if (j + 3 < deg) atomicSub(p.count + q[k].w, 1);
           }
         }
       }
-      int k_ran = 0;
+      const bool ran_head = ready && is_head;
+      if (ran_head) edges += (uint32_t)deg;
+      const int extra = ran_head && deg > inl ? deg - inl : 0;
+      if (__any_sync(kFull, extra > 0)) {
+        int incl = extra;
 #pragma unroll
-      for (int k = 0; k < K; ++k) {
-        if (FENCE || TICKETS) polled[k] = ((pending[k] >> lane) & 1u) ? ld_relaxed_s32(p.count + v[k]) : 1;
-        k_ran += __popc(rm[k]);
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(kFull, incl, o);
+          if (lane >= o) incl += y;
+        }
+        const int excl = incl - extra;
+        const int D = __shfl_sync(kFull, incl, 31);
+        const int rbeg = is_head ? q[0].x + inl : 0;
+        for (int e0 = 0; e0 < D; e0 += 32) {
+          const int e = e0 + lane;
+          int owner = 0;
+#pragma unroll
+          for (int step = 16; step >= 1; step >>= 1) {
+            const int cand = owner + step;
+            if (__shfl_sync(kFull, excl, cand) <= e) owner = cand;
+          }
+          const int oex = __shfl_sync(kFull, excl, owner);
+          const int orb = __shfl_sync(kFull, rbeg, owner);
+          if (e < D) atomicSub(p.count + p.col[orb + (e - oex)], 1);
+        }
       }
+      if (FENCE || TICKETS) polled = ((pending >> lane) & 1u) ? ld_relaxed_s32(p.count + v) : 1;
+      const int k_ran = __popc(rm & heads);
       cnt[kCntBatches] += 1;
       cnt[kCntTasks] += (unsigned)k_ran;
-      cnt[kCntEdges] += __reduce_add_sync(kFull, degs);
       ran += (uint32_t)k_ran;
-      // finished chunks: progress for the other warps' bounded waits, and the
-      // slot takes this warp's next chunk
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        if (ck[k] >= 0 && pending[k] == 0u) {
-          if (lane == 0) atomicAdd(&ctrl->executed, (unsigned long long)ctasks[k]);
-          take(k);
-        }
+      // a finished chunk: progress for the other warps' bounded waits, and the
+      // warp takes its next chunk
+      if (ck >= 0 && pending == 0u) {
+        if (lane == 0) atomicAdd(&ctrl->executed, (unsigned long long)ctasks);
+        take();
       }
     }
     if (stop) break;
@@ -623,6 +630,7 @@ __global__ void __launch_bounds__(256, 1) k_exec_owned(ExecParams p) {
     __syncwarp();
     if (lane == 0 && ran) atomicAdd(&p.done_g[0], ran);
   }
+  cnt[kCntEdges] = __reduce_add_sync(kFull, edges);
   if (lane == 0) {
 #pragma unroll
     for (int k = 0; k < kCntCount; ++k)
@@ -631,10 +639,15 @@ __global__ void __launch_bounds__(256, 1) k_exec_owned(ExecParams p) {
 }
 
 // trigger record of each task: {row start, out-degree, in-degree, first
-// kAdjInline successors (-1 padded)}, two int4 per task
+// kAdjInline successors (-1 padded)}, two int4 per task; optionally the
+// largest out-degree (atomicMax into *maxdeg)
 __global__ void k_pack_adj(const int32_t* row_ptr, const int32_t* col, const int32_t* indeg, int64_t n,
-                           int4* adj) {
+                           int4* adj, uint32_t* maxdeg) {
   const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (maxdeg) {  // uniform over the grid: every lane of a warp reaches the reduction
+    const uint32_t m = __reduce_max_sync(0xffffffffu, v < n ? (uint32_t)(row_ptr[v + 1] - row_ptr[v]) : 0u);
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(maxdeg, m);
+  }
   if (v >= n) return;
   const int b = row_ptr[v], d = row_ptr[v + 1] - b;
   int c[kAdjInline];
@@ -642,6 +655,19 @@ __global__ void k_pack_adj(const int32_t* row_ptr, const int32_t* col, const int
   for (int j = 0; j < kAdjInline; ++j) c[j] = j < d ? col[b + j] : -1;
   adj[2 * v] = make_int4(b, d, indeg[v], c[0]);
   adj[2 * v + 1] = make_int4(c[1], c[2], c[3], c[4]);
+}
+
+// extension record of each task for the owned-chunk executor: successors
+// kAdjInline .. kAdjWide - 1 (-1 padded), two int4 per task
+__global__ void k_pack_adjx(const int32_t* row_ptr, const int32_t* col, int64_t n, int4* adjx) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  const int b = row_ptr[v], d = row_ptr[v + 1] - b;
+  int c[kAdjWide - kAdjInline];
+#pragma unroll
+  for (int j = 0; j < kAdjWide - kAdjInline; ++j) c[j] = kAdjInline + j < d ? col[b + kAdjInline + j] : -1;
+  adjx[2 * v] = make_int4(c[0], c[1], c[2], c[3]);
+  adjx[2 * v + 1] = make_int4(c[4], c[5], c[6], c[7]);
 }
 
 __global__ void k_rebase_roots(const uint64_t* src, uint64_t* dst, int32_t n, int32_t graph,
@@ -701,10 +727,17 @@ void launch_check_stacked(const int32_t* row_ptr, const int32_t* col, int64_t T,
 }
 
 void launch_pack_adj(const int32_t* row_ptr, const int32_t* col, const int32_t* indeg, int64_t n, int4* adj,
-                     cudaStream_t s) {
+                     uint32_t* maxdeg, cudaStream_t s) {
   if (n > 0) {
     count_launch();
-    k_pack_adj<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(row_ptr, col, indeg, n, adj);
+    k_pack_adj<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(row_ptr, col, indeg, n, adj, maxdeg);
+  }
+}
+
+void launch_pack_adjx(const int32_t* row_ptr, const int32_t* col, int64_t n, int4* adjx, cudaStream_t s) {
+  if (n > 0) {
+    count_launch();
+    k_pack_adjx<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(row_ptr, col, n, adjx);
   }
 }
 
@@ -782,12 +815,12 @@ void launch_exec(ExecParams p, int blocks, int warps, cudaStream_t s) {
   const bool fence = p.need_fence != 0;
   count_launch();
   if (single && p.policy == RT_EXEC_OWNED) {  // keeps nothing in shared memory
-    // the claim width is the window: chunks a warp holds at once (1, 2 or 4)
-    const int K = p.claim >= 4 ? 4 : (p.claim >= 2 ? 2 : 1);
+    // the claim width is the group size: lanes per task (1, 2 or 4)
+    const int Lg = p.claim >= 4 ? 4 : (p.claim >= 2 ? 2 : 1);
 #define GRT_OWNED(T, F)                                                         \
   do {                                                                         \
-    if (K == 4) k_exec_owned<T, F, 4><<<blocks, warps * 32, 0, s>>>(p);        \
-    else if (K == 2) k_exec_owned<T, F, 2><<<blocks, warps * 32, 0, s>>>(p);   \
+    if (Lg == 4) k_exec_owned<T, F, 4><<<blocks, warps * 32, 0, s>>>(p);        \
+    else if (Lg == 2) k_exec_owned<T, F, 2><<<blocks, warps * 32, 0, s>>>(p);   \
     else k_exec_owned<T, F, 1><<<blocks, warps * 32, 0, s>>>(p);               \
   } while (0)
     if (p.tickets) {

@@ -156,9 +156,14 @@ enum { kCntBatches = 0, kCntTasks, kCntEdges, kCntClaims, kCntCasFail, kCntPushe
 // packed trigger record of one task (two int4): {row start, out-degree,
 // in-degree, first 5 successors (-1 padded)}
 constexpr int kAdjInline = 5;
+// the owned-chunk executor's extension record (two more int4 per task):
+// successors kAdjInline .. kAdjWide - 1 (-1 padded), so that a task with up to
+// kAdjWide successors decrements them all without reading the CSR's columns
+constexpr int kAdjWide = 13;
 
 struct ExecParams {
   const int4* adj;        // 2 x int4 per task: packed trigger records
+  const int4* adjx;       // optional (owned policy): 2 x int4 per task, successors kAdjInline .. kAdjWide - 1
   const int32_t* row_ptr;
   const int32_t* col;
   const int32_t* indeg;
@@ -316,8 +321,10 @@ void launch_roots(const int32_t* indeg, int32_t n, uint32_t* flags, cudaStream_t
 void launch_roots_emit(const int32_t* indeg, const uint32_t* pos, int32_t n, int32_t task_base,
                        int32_t graph, uint64_t* root_items, int32_t* count, cudaStream_t s);
 
+// maxdeg (nullable, zeroed by the caller): receives the largest out-degree
 void launch_pack_adj(const int32_t* row_ptr, const int32_t* col, const int32_t* indeg, int64_t n, int4* adj,
-                     cudaStream_t s);
+                     uint32_t* maxdeg, cudaStream_t s);
+void launch_pack_adjx(const int32_t* row_ptr, const int32_t* col, int64_t n, int4* adjx, cudaStream_t s);
 void launch_reset_counts(int32_t* count, const int32_t* indeg, int64_t n, int32_t hold_task,
                          int32_t hold_extra, cudaStream_t s);
 void launch_rebase_roots(const uint64_t* src, uint64_t* dst, int32_t n, int32_t graph, int32_t task_base,

@@ -224,7 +224,7 @@ rt_status static_execute(const int32_t* row_ptr, const int32_t* col, const int32
   count_launch(2);
   k_static_reset<<<256, 256, 0, s>>>(indeg, n, spin_iters, out);
   k_static_seed<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(indeg, n);
-  launch_pack_adj(row_ptr, col, indeg, n, reinterpret_cast<int4*>(base + kOffAdj), s);
+  launch_pack_adj(row_ptr, col, indeg, n, reinterpret_cast<int4*>(base + kOffAdj), nullptr, s);
   e = cudaGetLastError();
   if (e != cudaSuccess) {
     *why = cudaGetErrorString(e);

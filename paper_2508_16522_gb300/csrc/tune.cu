@@ -13,7 +13,8 @@
 // The executor search is coordinate descent for the ring policy: (warps,
 // blocks per SM) jointly, then the claim width, then the keep width, then
 // (warps, blocks per SM) again; then a pass over the grids of the owned
-// policy; each trial the best of two runs.
+// policy, and its group sizes (lanes per task) on the best grid; each ring
+// trial the best of two runs, each owned trial the best of three.
 // Results go to an optional plain-text cache, one line per workload key
 // (device, SM count, kind, sizes, an input hash), so a later call with the
 // same workload answers without running anything.
@@ -267,8 +268,8 @@ rt_status rt_tune_exec(rt_graph_t g, const char* cache_path, rt_exec_config* bes
   if (s != RT_OK) return s;
   int sms = 0;
   if ((s = rt_device_info(&sms, nullptr)) != RT_OK) return s;
-  // "exec5": entries that also weigh the owned policy's grids and windows
-  const std::string key = "exec5/" + device_tag() + "/" + std::to_string(st.n_tasks) + "/" +
+  // "exec6": entries that also weigh the owned policy's grids and group sizes
+  const std::string key = "exec6/" + device_tag() + "/" + std::to_string(st.n_tasks) + "/" +
                           std::to_string(st.n_edges) + "/" + std::to_string(st.n_roots);
   auto apply = [&](const rt_exec_config& c) -> rt_status {
     rt_status r = rt_graph_exec_policy(g, c.policy);
@@ -298,26 +299,27 @@ rt_status rt_tune_exec(rt_graph_t g, const char* cache_path, rt_exec_config* bes
   rt_graph_exec_policy(g, RT_EXEC_OWNED);
   // the owned policy: grids from 32 warps (a Task Bench step's 32 chunks, each
   // warp always on the same column of chunks) up to several warps per SM, one
-  // chunk at a time; then wider windows (chunks a warp holds) on the best grid
-  auto run_owned = [&](int blocks, int warps, int window) -> double {
-    if (rt_graph_exec_config(g, blocks, warps, window, 16) != RT_OK) return -1;
+  // lane per task; then groups of 2 and 4 lanes per task (chunks of 16 and 8
+  // tasks) on the best grid and on one that many times wider
+  auto run_owned = [&](int blocks, int warps, int group) -> double {
+    if (rt_graph_exec_config(g, blocks, warps, group, 16) != RT_OK) return -1;
     const auto t0 = std::chrono::steady_clock::now();
     if (rt_execute(g) != RT_OK || rt_sync(g) != RT_OK) return -1;
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   };
   bool failed = false;
-  auto owned_trial = [&](int blocks, int warps, int window) {
+  auto owned_trial = [&](int blocks, int warps, int group) {
     double t = 1e30;
     for (int rep = 0; rep < 3 && !failed; ++rep) {
-      const double m = run_owned(blocks, warps, window);
+      const double m = run_owned(blocks, warps, group);
       if (m < 0) failed = true;
       t = std::min(t, m);
     }
     ++trials;
     if (!failed && t < best->ms)
-      *best = rt_exec_config{blocks, warps, window, 16, (float)t, trials, RT_EXEC_OWNED};
+      *best = rt_exec_config{blocks, warps, group, 16, (float)t, trials, RT_EXEC_OWNED};
   };
-  const int owned_c[][2] = {{32, 1}, {64, 1}, {96, 1}, {152, 1}, {152, 2}, {152, 4}, {304, 2}, {304, 4}};
+  const int owned_c[][2] = {{32, 1}, {64, 1}, {96, 1}, {128, 1}, {152, 1}, {152, 2}, {152, 4}, {304, 2}};
   for (const auto& bw : owned_c) {
     const int blocks = bw[0] * sms / 152 > 0 ? bw[0] * sms / 152 : 1;  // scaled to this GPU's SM count
     if (blocks > sms * std::max(exec_max_blocks_per_sm(bw[1]), 1)) continue;
@@ -325,7 +327,11 @@ rt_status rt_tune_exec(rt_graph_t g, const char* cache_path, rt_exec_config* bes
   }
   if (!failed && best->policy == RT_EXEC_OWNED) {
     const int gb = best->blocks, gwp = best->warps;
-    for (int window : {2, 4}) owned_trial(gb, gwp, window);
+    for (int group : {2, 4}) {
+      owned_trial(gb, gwp, group);
+      const int wider = std::min(gb * group, sms * std::max(exec_max_blocks_per_sm(gwp), 1));
+      if (wider > gb) owned_trial(wider, gwp, group);
+    }
   }
   if (failed) {
     rt_graph_exec_policy(g, RT_EXEC_RING);

@@ -1,9 +1,12 @@
 """The owned-chunk executor policy (RT_EXEC_OWNED): every warp owns fixed
-chunks of 32 consecutive tasks and polls their countdowns. Results must be
-those of the ring policy and of the oracle: order-sensitive CHECK and COUNTER
-bodies equal sequential execution, replays equal repeated runs, tickets order
-every edge, a held task ends the run with a bounded wait, and launch shapes
-down to one warp (which owns every chunk) give the same results."""
+chunks of consecutive tasks (32 / L of them, L lanes per task) and polls their
+countdowns. Results must be those of the ring policy and of the oracle:
+order-sensitive CHECK and COUNTER bodies equal sequential execution, replays
+equal repeated runs, tickets order every edge, a held task ends the run with a
+bounded wait, and launch shapes down to one warp (which owns every chunk) and
+every group size give the same results -- also for out-degrees on both sides
+of what the trigger records hold inline (5, and 13 with the extension
+record)."""
 import numpy as np
 import pytest
 
@@ -11,11 +14,12 @@ import oracle
 from paper_2508_16522_gb300 import grt
 from paper_2508_16522_gb300 import tracegen as tg
 
-from gpu_helpers import gpu_graph
+from gpu_helpers import gpu_graph, oracle_csr
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(0, 0), (1, 1), (3, 2), (152, 4)]  # (blocks, warps); (0, 0) = default
+# (blocks, warps, lanes per task); 0 = default
+SHAPES = [(0, 0, 0), (1, 1, 1), (3, 2, 2), (152, 4, 4), (7, 1, 4), (64, 1, 2)]
 
 
 def traces():
@@ -30,7 +34,7 @@ def test_check_body_and_replays(shape):
         g = gpu_graph(tr, body=grt.RT_BODY_CHECK, tile=(8, 8) if tr.ndim == 2 else (64, 1))
         g.analyze()
         g.exec_policy(grt.RT_EXEC_OWNED)
-        g.exec_config(shape[0], shape[1])
+        g.exec_config(shape[0], shape[1], shape[2])
         g.execute()
         g.sync()
         st, out = oracle.run_bodies(tr, oracle.BODY_CHECK)
@@ -66,14 +70,14 @@ def test_counter_and_fma_bodies():
     g.close()
 
 
-@pytest.mark.parametrize("shape", [(0, 0), (1, 1), (304, 2)])
+@pytest.mark.parametrize("shape", [(0, 0, 0), (1, 1, 1), (304, 2, 2), (128, 1, 4)])
 def test_tickets_order_every_edge(shape):
     for tr in [tg.taskbench(1024, 200, "random"), tg.taskbench(1024, 200, "stencil"),
                tg.random_rects(grid=(64, 64), n=3000, side=(2, 24), seed=5)]:
         g = gpu_graph(tr, flags=grt.RT_GRAPH_TICKETS)
         g.analyze()
         g.exec_policy(grt.RT_EXEC_OWNED)
-        g.exec_config(shape[0], shape[1])
+        g.exec_config(shape[0], shape[1], shape[2])
         g.execute()
         g.sync()
         t = g.tickets()
@@ -84,6 +88,50 @@ def test_tickets_order_every_edge(shape):
         st = g.stats()
         assert st["exec_counters"]["tasks"] == tr.n and st["exec_counters"]["edges"] == len(col)
         g.close()
+
+
+def hub_trace(ks=(4, 5, 6, 12, 13, 14, 40)):
+    """1-D hubs: for each k, a task writes k cells, k tasks read one cell each
+    (the writer's out-degree is k), and a task writes the k cells again (its
+    in-degree is k)."""
+    lo, hi, priv = [], [], []
+    base = 0
+    for k in ks:
+        lo.append(base); hi.append(base + k - 1); priv.append(tg.WRITE)
+        for i in range(k):
+            lo.append(base + i); hi.append(base + i); priv.append(tg.READ)
+        lo.append(base); hi.append(base + k - 1); priv.append(tg.WRITE)
+        base += k
+    n = len(priv)
+    return tg.Trace(ndim=1, dom_lo=np.array([0], np.int64), dom_hi=np.array([base - 1], np.int64),
+                    req_off=np.arange(n + 1, dtype=np.int32), lo=np.array(lo, np.int64).reshape(n, 1),
+                    hi=np.array(hi, np.int64).reshape(n, 1), priv=np.array(priv, np.uint8), name="hubs")
+
+
+@pytest.mark.parametrize("group", [1, 2, 4])
+def test_out_degrees_around_the_inline_record(group):
+    for tr in (hub_trace(), hub_trace((2, 3, 5)), tg.taskbench(1024, 60, "random", seed=9)):
+        rp_o, col_o, _ = oracle_csr(tr)
+        deg = np.diff(rp_o)
+        for blocks in (1, 7, 64):
+            g = gpu_graph(tr, body=grt.RT_BODY_CHECK, flags=grt.RT_GRAPH_TICKETS,
+                          tile=(64, 1) if tr.ndim == 1 else (16, 16))
+            g.analyze()
+            g.exec_policy(grt.RT_EXEC_OWNED)
+            g.exec_config(blocks, 1, group)
+            g.execute()
+            g.sync()
+            st, out = oracle.run_bodies(tr, oracle.BODY_CHECK)
+            assert np.array_equal(g.state.cpu().numpy(), st), (tr.name, blocks)
+            assert np.array_equal(g.out.cpu().numpy(), out), (tr.name, blocks)
+            t = g.tickets()
+            src = np.repeat(np.arange(tr.n), deg)
+            assert (t[src, 1] < t[col_o, 0]).all(), (tr.name, blocks)
+            c = g.stats()["exec_counters"]
+            assert c["tasks"] == tr.n and c["edges"] == len(col_o), (tr.name, blocks, c)
+            g.close()
+        if tr.name == "hubs" and deg.max() > 13:
+            assert {5, 6, 13, 14} <= set(deg.tolist())
 
 
 def test_bounded_wait_timeout_and_recovery():
