@@ -173,6 +173,15 @@ rt_status rt_launch_batch(rt_graph_t g, int32_t n, const int32_t* req_off, const
                           const int64_t* hi, const uint8_t* priv, const int32_t* pred_off,
                           const int32_t* pred, const int32_t* body_arg, int32_t flags);
 
+/* rt_launch_batch with the rectangle bounds as int32[R][ndim]: the same
+ * launches (Section 2.2), half the coordinate bytes on the host link. The
+ * bounds are copied as they are and widened to int64 on the device, into the
+ * graph's own arrays; arguments, ownership, validation (host or device, as
+ * the flags say) and errors are those of rt_launch_batch. */
+rt_status rt_launch_batch32(rt_graph_t g, int32_t n, const int32_t* req_off, const int32_t* lo,
+                            const int32_t* hi, const uint8_t* priv, const int32_t* pred_off,
+                            const int32_t* pred, const int32_t* body_arg, int32_t flags);
+
 /* Infers the DAG of all launches so far (tile binning, per-tile interference
  * sweep, CSR construction) and prepares the countdown counters (Algorithm 1,
  * Compile). Synchronises the stream a few times to size buffers. Errors:

@@ -116,6 +116,16 @@ __global__ void k_add_offset(int32_t* a, int64_t n, int32_t add) {
   if (i < n) a[i] += add;
 }
 
+// int32 rectangle bounds (both arrays, m values each) widened to int64 in the
+// graph's own arrays
+__global__ void k_widen_bounds(const int32_t* lo32, const int32_t* hi32, int64_t m, int64_t* lo, int64_t* hi) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+    lo[i] = lo32[i];
+    hi[i] = hi32[i];
+  }
+}
+
 // tile range of one rectangle (coordinates relative to the domain origin)
 struct TileRange {
   int64_t lx, hx, ly, hy;  // relative inclusive bounds
@@ -440,6 +450,15 @@ void launch_band_place(const int32_t* req_off, int32_t n, const int32_t* task_fi
   if (blocks > 4096) blocks = 4096;
   count_launch();
   k_band_place<<<blocks, 256, 0, s>>>(req_off, n, task_first, G, box, D, lo, hi, R, err);
+}
+
+void launch_widen_bounds(const int32_t* lo32, const int32_t* hi32, int64_t m, int64_t* lo, int64_t* hi,
+                         cudaStream_t s) {
+  if (m <= 0) return;
+  unsigned blocks = nblk(m, 256);
+  if (blocks > 8192) blocks = 8192;
+  count_launch();
+  k_widen_bounds<<<blocks, 256, 0, s>>>(lo32, hi32, m, lo, hi);
 }
 
 void launch_add_offset(int32_t* a, int64_t n, int32_t add, cudaStream_t s) {

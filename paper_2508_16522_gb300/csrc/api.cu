@@ -138,6 +138,7 @@ struct rt_graph {
   int64_t R = 0, P = 0;
   bool has_pred = false, has_body_arg = false;
   DevBuf req_off, lo, hi, priv, pred_off, pred, body_arg;
+  DevBuf stage32;  // rt_launch_batch32: the int32 bounds on their way to lo and hi
   DevBuf err;  // uint32 device-side validation bits
   bool pending_validate = false;
   // analysis
@@ -187,7 +188,7 @@ namespace {
 // every device buffer a graph holds (its footprint is the sum of their capacities)
 template <class G, class F>
 void for_each_buf(G* g, F f) {
-  auto bufs = {&g->req_off, &g->lo, &g->hi, &g->priv, &g->pred_off, &g->pred, &g->body_arg, &g->err,
+  auto bufs = {&g->req_off, &g->lo, &g->hi, &g->priv, &g->pred_off, &g->pred, &g->body_arg, &g->stage32, &g->err,
                 &g->rect_task, &g->cnt, &g->keys, &g->keys_alt, &g->pay, &g->pay_alt, &g->seg_b, &g->seg_e,
                 &g->pairs, &g->pairs_alt, &g->flags, &g->upos, &g->col, &g->row_ptr, &g->indeg, &g->count,
                 &g->rootpos, &g->root_items, &g->ws, &g->misc, &g->adj, &g->adjx, &g->bucket, &g->ring, &g->ctrl,
@@ -379,9 +380,11 @@ rt_status rt_graph_destroy(rt_graph_t g) {
 // ---------------------------------------------------------------------------
 namespace {
 
-rt_status host_validate(const rt_graph* g, int32_t n, const int32_t* req_off, const int64_t* lo,
-                        const int64_t* hi, const uint8_t* priv, const int32_t* pred_off,
-                        const int32_t* pred, const int32_t* body_arg) {
+// T: the coordinate type of lo and hi (int64_t, or int32_t for rt_launch_batch32)
+template <class T>
+rt_status host_validate(const rt_graph* g, int32_t n, const int32_t* req_off, const T* lo, const T* hi,
+                        const uint8_t* priv, const int32_t* pred_off, const int32_t* pred,
+                        const int32_t* body_arg) {
   const AnalysisDims& d = g->dims;
   if (req_off[0] != 0) return fail(RT_ERR_INVALID, "req_off[0] must be 0 (got %d)", req_off[0]);
   for (int32_t i = 0; i < n; ++i)
@@ -435,9 +438,10 @@ struct BandPlace {
   const int64_t* box;         // device int64[G][3][ndim]: its domain's lo, hi and its shift
 };
 
-rt_status append_launches(rt_graph_t g, int32_t n, const int32_t* req_off, const int64_t* lo, const int64_t* hi,
+// lo and hi are int64[R][ndim], or int32[R][ndim] with c32 (widened on the device)
+rt_status append_launches(rt_graph_t g, int32_t n, const int32_t* req_off, const void* lo, const void* hi,
                           const uint8_t* priv, const int32_t* pred_off, const int32_t* pred, const int32_t* body_arg,
-                          int32_t flags, const BandPlace* bp);
+                          int32_t flags, const BandPlace* bp, bool c32 = false);
 }  // namespace
 
 extern "C" rt_status rt_launch_batch(rt_graph_t g, int32_t n, const int32_t* req_off, const int64_t* lo,
@@ -446,10 +450,16 @@ extern "C" rt_status rt_launch_batch(rt_graph_t g, int32_t n, const int32_t* req
   return append_launches(g, n, req_off, lo, hi, priv, pred_off, pred, body_arg, flags, nullptr);
 }
 
+extern "C" rt_status rt_launch_batch32(rt_graph_t g, int32_t n, const int32_t* req_off, const int32_t* lo,
+                                       const int32_t* hi, const uint8_t* priv, const int32_t* pred_off,
+                                       const int32_t* pred, const int32_t* body_arg, int32_t flags) {
+  return append_launches(g, n, req_off, lo, hi, priv, pred_off, pred, body_arg, flags, nullptr, true);
+}
+
 namespace {
-rt_status append_launches(rt_graph_t g, int32_t n, const int32_t* req_off, const int64_t* lo, const int64_t* hi,
+rt_status append_launches(rt_graph_t g, int32_t n, const int32_t* req_off, const void* lo, const void* hi,
                           const uint8_t* priv, const int32_t* pred_off, const int32_t* pred, const int32_t* body_arg,
-                          int32_t flags, const BandPlace* bp) {
+                          int32_t flags, const BandPlace* bp, bool c32) {
   if (!g) return fail(RT_ERR_INVALID, "graph is NULL");
   if (g->analyzed) return fail(RT_ERR_STATE, "graph already analyzed; call rt_graph_clear first");
   if (n < 0) return fail(RT_ERR_INVALID, "n < 0");
@@ -474,7 +484,14 @@ rt_status append_launches(rt_graph_t g, int32_t n, const int32_t* req_off, const
     first[1] = pred_off ? pred_off[0] : 0;
     if (R < 0 || Pb < 0) return fail(RT_ERR_INVALID, "negative rect or pred count");
     if (R > 0 && (!lo || !hi || !priv)) return fail(RT_ERR_INVALID, "rect arrays are NULL");
-    if (!on_device_check) CKR(host_validate(g, n, req_off, lo, hi, priv, pred_off, pred, body_arg));
+    if (!on_device_check) {
+      if (c32)
+        CKR(host_validate(g, n, req_off, static_cast<const int32_t*>(lo), static_cast<const int32_t*>(hi), priv,
+                          pred_off, pred, body_arg));
+      else
+        CKR(host_validate(g, n, req_off, static_cast<const int64_t*>(lo), static_cast<const int64_t*>(hi), priv,
+                          pred_off, pred, body_arg));
+    }
   }
   CKR(ensure_device());
   CKR(ensure_pinned(g));
@@ -512,8 +529,17 @@ rt_status append_launches(rt_graph_t g, int32_t n, const int32_t* req_off, const
     CKR(g->lo.reserve((size_t)(R0 + R) * D * 8, s, (size_t)R0 * D * 8));
     CKR(g->hi.reserve((size_t)(R0 + R) * D * 8, s, (size_t)R0 * D * 8));
     CKR(g->priv.reserve((size_t)(R0 + R), s, (size_t)R0));
-    CKR(copy_in(g->lo.as<int64_t>() + R0 * D, lo, (size_t)R * D * 8, s));
-    CKR(copy_in(g->hi.as<int64_t>() + R0 * D, hi, (size_t)R * D * 8, s));
+    if (c32) {
+      // the int32 bounds through a staging buffer, widened into the graph's arrays
+      CKR(g->stage32.reserve((size_t)R * D * 8, s));
+      int32_t* st = g->stage32.as<int32_t>();
+      CKR(copy_in(st, lo, (size_t)R * D * 4, s));
+      CKR(copy_in(st + R * D, hi, (size_t)R * D * 4, s));
+      launch_widen_bounds(st, st + R * D, R * D, g->lo.as<int64_t>() + R0 * D, g->hi.as<int64_t>() + R0 * D, s);
+    } else {
+      CKR(copy_in(g->lo.as<int64_t>() + R0 * D, lo, (size_t)R * D * 8, s));
+      CKR(copy_in(g->hi.as<int64_t>() + R0 * D, hi, (size_t)R * D * 8, s));
+    }
     CKR(copy_in(g->priv.as<uint8_t>() + R0, priv, (size_t)R, s));
   }
   if (pred_off || g->has_pred) {

@@ -275,6 +275,9 @@ void launch_validate(const int32_t* req_off, int32_t n, int64_t r_first, const i
                      const int32_t* body_arg, int64_t body_limit, AnalysisDims d, uint32_t* err,
                      cudaStream_t s);
 void launch_add_offset(int32_t* a, int64_t n, int32_t add, cudaStream_t s);
+// lo[i] = lo32[i], hi[i] = hi32[i] for i < m
+void launch_widen_bounds(const int32_t* lo32, const int32_t* hi32, int64_t m, int64_t* lo, int64_t* hi,
+                         cudaStream_t s);
 // rt_batch_capture: checks every rectangle against its graph's own domain and
 // moves it into the graph's band (box: int64 [G][3][ndim] = lo, hi, shift)
 void launch_band_place(const int32_t* req_off, int32_t n, const int32_t* task_first, int32_t G, const int64_t* box,

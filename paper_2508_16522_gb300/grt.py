@@ -28,17 +28,15 @@ RT_GRAPH_TICKETS, RT_GRAPH_PROFILE = 1, 2
 RT_EXEC_RING, RT_EXEC_OWNED = 0, 1
 
 # every symbol include/grt.h declares (checked by the CPU tests)
-EXPORTS = ["rt_graph_create", "rt_graph_destroy", "rt_graph_clear", "rt_launch_batch", "rt_analyze",
-           "rt_get_csr", "rt_copy_csr", "rt_graph_exec_config", "rt_execute", "rt_replay", "rt_sync", "rt_graph_stats",
-           "rt_get_tickets", "rt_copy_tickets", "rt_debug_hold_task", "rt_batch_create",
-           "rt_batch_execute", "rt_batch_sync", "rt_batch_counters", "rt_batch_destroy", "rt_last_error", "rt_device_info",
-           "rt_kernel_launches", "rt_execute_csr_static", "rt_microbench_atomics", "rt_now_ns",
+EXPORTS = ["rt_graph_create", "rt_graph_destroy", "rt_graph_clear", "rt_launch_batch", "rt_launch_batch32",
+           "rt_analyze", "rt_get_csr", "rt_copy_csr", "rt_graph_exec_config", "rt_execute", "rt_replay", "rt_sync",
+           "rt_graph_stats", "rt_get_tickets", "rt_copy_tickets", "rt_debug_hold_task", "rt_batch_create",
+           "rt_batch_execute", "rt_batch_sync", "rt_batch_counters", "rt_batch_destroy", "rt_last_error",
+           "rt_device_info", "rt_kernel_launches", "rt_execute_csr_static", "rt_microbench_atomics", "rt_now_ns",
            "rt_server_create", "rt_server_submit", "rt_server_poll", "rt_server_result", "rt_server_result_state",
-           "rt_server_drain",
-           "rt_server_stats", "rt_server_destroy", "rt_tune_tile", "rt_tune_exec", "rt_tune_batch",
-           "rt_batch_create_stacked", "rt_execute_events", "rt_execute_kernels",
-           "rt_execute_stitched", "rt_copy_stitched_tickets", "rt_batch_capture", "rt_batch_info",
-           "rt_graph_exec_policy"]
+           "rt_server_drain", "rt_server_stats", "rt_server_destroy", "rt_tune_tile", "rt_tune_exec", "rt_tune_batch",
+           "rt_batch_create_stacked", "rt_execute_events", "rt_execute_kernels", "rt_execute_stitched",
+           "rt_copy_stitched_tickets", "rt_batch_capture", "rt_batch_info", "rt_graph_exec_policy"]
 
 
 class GrtError(RuntimeError):
@@ -118,6 +116,7 @@ def load(path: str = LIB_PATH):
         "rt_graph_destroy": [P],
         "rt_graph_clear": [P],
         "rt_launch_batch": [P, i32, P, P, P, P, P, P, P, i32],
+        "rt_launch_batch32": [P, i32, P, P, P, P, P, P, P, i32],
         "rt_analyze": [P],
         "rt_get_csr": [P, P, P, P, P, P],
         "rt_copy_csr": [P, P, P, P],
@@ -196,6 +195,10 @@ def rt_graph_clear(g):
 
 def rt_launch_batch(g, n, req_off, lo, hi, priv, pred_off=None, pred=None, body_arg=None, flags=0):
     _check(load().rt_launch_batch(g, n, req_off, lo, hi, priv, pred_off, pred, body_arg, flags))
+
+
+def rt_launch_batch32(g, n, req_off, lo, hi, priv, pred_off=None, pred=None, body_arg=None, flags=0):
+    _check(load().rt_launch_batch32(g, n, req_off, lo, hi, priv, pred_off, pred, body_arg, flags))
 
 
 def rt_analyze(g):
@@ -340,7 +343,8 @@ class Graph:
         return c.as_dict()
 
     def launch(self, req_off, lo, hi, priv, pred_off=None, pred=None, body_arg=None, defer_check=False):
-        """Appends launches; numpy arrays are host pointers, CUDA tensors device pointers."""
+        """Appends launches; numpy arrays are host pointers, CUDA tensors device pointers.
+        int32 bounds go through rt_launch_batch32, int64 ones through rt_launch_batch."""
         n = int(len(req_off) - 1)
         ptrs = [_ptr(a) for a in (req_off, lo, hi, priv, pred_off, pred, body_arg)]
         dev = any(p[1] for p in ptrs)
@@ -348,7 +352,13 @@ class Graph:
             raise ValueError("mixing host and device arrays in one batch")
         flags = RT_LAUNCH_DEVICE if dev else (RT_LAUNCH_DEFER_CHECK if defer_check else RT_LAUNCH_HOST)
         self._keep = [req_off, lo, hi, priv, pred_off, pred, body_arg]  # alive until analyze
-        rt_launch_batch(self.h, n, *[p[0] for p in ptrs], flags)
+        widths = {str(a.dtype).split(".")[-1] for a in (lo, hi)}
+        if widths == {"int32"}:
+            rt_launch_batch32(self.h, n, *[p[0] for p in ptrs], flags)
+        elif widths == {"int64"}:
+            rt_launch_batch(self.h, n, *[p[0] for p in ptrs], flags)
+        else:
+            raise ValueError(f"lo and hi must both be int64 or both int32 (got {sorted(widths)})")
 
     def launch_trace(self, tr, device: bool = False, defer_check: bool = False):
         arrs = [tr.req_off, tr.lo, tr.hi, tr.priv, tr.pred_off, tr.pred, tr.body_arg]

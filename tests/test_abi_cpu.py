@@ -79,7 +79,8 @@ def test_create_destroy_without_gpu(lib):
 def _launch(h, req_off, lo, hi, priv, pred_off=None, pred=None, body_arg=None):
     arrs = [req_off, lo, hi, priv, pred_off, pred, body_arg]
     ptrs = [None if a is None else a.ctypes.data for a in arrs]
-    grt.rt_launch_batch(h, len(req_off) - 1, *ptrs, grt.RT_LAUNCH_HOST)
+    entry = grt.rt_launch_batch32 if lo.dtype == np.int32 else grt.rt_launch_batch
+    entry(h, len(req_off) - 1, *ptrs, grt.RT_LAUNCH_HOST)
 
 
 CASES = [
@@ -95,13 +96,16 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("width", [np.int64, np.int32])
 @pytest.mark.parametrize("msg,arrs", CASES, ids=[c[0] + str(i) for i, c in enumerate(CASES)])
-def test_launch_rejects_on_host(lib, msg, arrs):
+def test_launch_rejects_on_host(lib, msg, arrs, width):
+    """rt_launch_batch (int64 bounds) and rt_launch_batch32 (int32 bounds)
+    refuse the same malformed batches on the host, before any device call."""
     h = grt.rt_graph_create(desc())
     try:
         req_off = np.array(arrs["req_off"], np.int32)
-        lo = np.array(arrs.get("lo", np.zeros((0, 2))), np.int64).reshape(-1, 2)
-        hi = np.array(arrs.get("hi", np.zeros((0, 2))), np.int64).reshape(-1, 2)
+        lo = np.array(arrs.get("lo", np.zeros((0, 2))), width).reshape(-1, 2)
+        hi = np.array(arrs.get("hi", np.zeros((0, 2))), width).reshape(-1, 2)
         priv = np.array(arrs.get("priv", []), np.uint8)
         po = None if "pred_off" not in arrs else np.array(arrs["pred_off"], np.int32)
         pr = None if "pred" not in arrs else np.array(arrs["pred"], np.int32)
