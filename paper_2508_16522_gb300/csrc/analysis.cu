@@ -253,7 +253,7 @@ __global__ void k_unique_flags(const uint64_t* keys, int64_t P, uint32_t* flags)
 __device__ __forceinline__ void warp_agg_inc(int32_t* base, int32_t idx, bool active) {
   int32_t key = active ? idx : -1;
   unsigned peers = __match_any_sync(0xffffffffu, key);
-  if (active && (peers & lanemask_lt()) == 0) atomicAdd(base + idx, (int32_t)__popc(peers));
+  if (active && (peers & lanemask_lt()) == 0) red_add_s32(base + idx, (int32_t)__popc(peers));
 }
 
 __global__ void k_emit_csr(const uint64_t* keys, const uint32_t* flags, const uint32_t* upos, int64_t P,
@@ -307,7 +307,7 @@ __global__ void k_bucket_count(const uint64_t* pairs, const unsigned long long* 
     const uint64_t k = i < (int64_t)P ? pairs[i] : kEmpty64;
     const int src = k != kEmpty64 ? (int)(k >> key_bits) : -1;
     const unsigned peers = __match_any_sync(0xffffffffu, src);
-    if (src >= 0 && (peers & lanemask_lt()) == 0) atomicAdd(cnt + src, (uint32_t)__popc(peers));
+    if (src >= 0 && (peers & lanemask_lt()) == 0) red_add_u32(cnt + src, (uint32_t)__popc(peers));
   }
 }
 
@@ -420,7 +420,7 @@ __global__ void k_bucket_compact(const uint32_t* off, const uint32_t* row_ptr, i
   for (uint32_t i = 0; i < u; ++i) {
     const uint32_t t = bucket[a + i];
     col[o + i] = (int32_t)t;
-    atomicAdd(indeg + t, 1);
+    red_add_s32(indeg + t, 1);
   }
 }
 

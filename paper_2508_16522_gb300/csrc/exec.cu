@@ -579,10 +579,10 @@ __global__ void __launch_bounds__(256, 1) k_exec_owned(ExecParams p) {
         for (int k = 0; k < QM; ++k) {
           if (k < nq && 4 * (g0 + k) - 3 < dmax) {  // uniform when L = 1: the chunk's largest degree
             const int j = 4 * (g0 + k) - 3;  // successor index of q[k].x
-            if (j >= 0 && j < deg) atomicSub(p.count + q[k].x, 1);  // result unused: a reduction
-            if (j + 1 >= 0 && j + 1 < deg) atomicSub(p.count + q[k].y, 1);
-            if (j + 2 >= 0 && j + 2 < deg) atomicSub(p.count + q[k].z, 1);
-            if (j + 3 < deg) atomicSub(p.count + q[k].w, 1);
+            if (j >= 0 && j < deg) red_dec_s32(p.count + q[k].x);
+            if (j + 1 >= 0 && j + 1 < deg) red_dec_s32(p.count + q[k].y);
+            if (j + 2 >= 0 && j + 2 < deg) red_dec_s32(p.count + q[k].z);
+            if (j + 3 < deg) red_dec_s32(p.count + q[k].w);
           }
         }
       }
@@ -609,7 +609,7 @@ __global__ void __launch_bounds__(256, 1) k_exec_owned(ExecParams p) {
           }
           const int oex = __shfl_sync(kFull, excl, owner);
           const int orb = __shfl_sync(kFull, rbeg, owner);
-          if (e < D) atomicSub(p.count + p.col[orb + (e - oex)], 1);
+          if (e < D) red_dec_s32(p.count + p.col[orb + (e - oex)]);
         }
       }
       if (FENCE || TICKETS) polled = ((pending >> lane) & 1u) ? ld_relaxed_s32(p.count + v) : 1;
@@ -620,7 +620,7 @@ __global__ void __launch_bounds__(256, 1) k_exec_owned(ExecParams p) {
       // a finished chunk: progress for the other warps' bounded waits, and the
       // warp takes its next chunk
       if (ck >= 0 && pending == 0u) {
-        if (lane == 0) atomicAdd(&ctrl->executed, (unsigned long long)ctasks);
+        if (lane == 0) red_add_u64(&ctrl->executed, (unsigned long long)ctasks);
         take();
       }
     }
@@ -628,7 +628,7 @@ __global__ void __launch_bounds__(256, 1) k_exec_owned(ExecParams p) {
     // release: this warp's bodies and re-armed counters before its count
     fence_acq_rel_gpu();
     __syncwarp();
-    if (lane == 0 && ran) atomicAdd(&p.done_g[0], ran);
+    if (lane == 0 && ran) red_add_u32(&p.done_g[0], ran);
   }
   cnt[kCntEdges] = __reduce_add_sync(kFull, edges);
   if (lane == 0) {

@@ -76,6 +76,21 @@ __device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t* p) {
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
+// one decrement that returns nothing (a reduction, relaxed, GPU scope): the
+// SM sends it to L2 and waits for no answer, where an atomicSub whose result
+// is unused may still be issued as an atomic that returns the old value
+__device__ __forceinline__ void red_dec_s32(int32_t* p) {
+  asm volatile("red.relaxed.gpu.global.add.s32 [%0], -1;" ::"l"(p) : "memory");
+}
+__device__ __forceinline__ void red_add_s32(int32_t* p, int32_t v) {
+  asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_add_u32(uint32_t* p, uint32_t v) {
+  asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_add_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 __device__ __forceinline__ int32_t ld_relaxed_s32(const int32_t* p) {
   int32_t v;
   asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");

@@ -268,8 +268,9 @@ rt_status rt_tune_exec(rt_graph_t g, const char* cache_path, rt_exec_config* bes
   if (s != RT_OK) return s;
   int sms = 0;
   if ((s = rt_device_info(&sms, nullptr)) != RT_OK) return s;
-  // "exec6": entries that also weigh the owned policy's grids and group sizes
-  const std::string key = "exec6/" + device_tag() + "/" + std::to_string(st.n_tasks) + "/" +
+  // "exec7": entries for the owned kernel whose decrements are reductions, with
+  // its grids and group sizes (entries of older kernels are never read)
+  const std::string key = "exec7/" + device_tag() + "/" + std::to_string(st.n_tasks) + "/" +
                           std::to_string(st.n_edges) + "/" + std::to_string(st.n_roots);
   auto apply = [&](const rt_exec_config& c) -> rt_status {
     rt_status r = rt_graph_exec_policy(g, c.policy);
