@@ -34,6 +34,10 @@
  *    error, rt_last_error() returns a thread-local message.
  *  - Device work is ordered on the stream given at creation (a cudaStream_t
  *    passed as void*); calls are asynchronous unless stated otherwise.
+ *  - Calls on distinct graphs (batches, servers) may run concurrently from
+ *    different host threads; calls on one graph must not overlap. A graph's
+ *    rt_analyze blocks only its own thread, so analyses of graphs on their
+ *    own streams overlap on the GPU when their threads run them together.
  *  - The library owns everything it allocates (CSR, counters, ring, scratch);
  *    the caller owns `state`/`out` buffers and every array it passes in.
  *  - A task id is the position of its launch in the graph's program order
