@@ -126,7 +126,8 @@ typedef struct {
 typedef struct {
   int64_t n_tasks, n_rects, n_preds;
   int64_t n_entries;      /* (rect, tile) pairs after binning */
-  int64_t n_pairs;        /* candidate (src, dst) pairs before deduplication */
+  int64_t n_pairs;        /* candidate (src, dst) pairs the sweep wrote, before deduplication
+                             (with the pair-key filter: those it did not drop) */
   int64_t n_edges;        /* distinct edges */
   int64_t n_roots;
   int32_t tile_w, tile_h;
@@ -138,6 +139,10 @@ typedef struct {
   float ms_sweep_kernel;  /* the interference sweep kernel alone */
   int32_t csr_by_buckets; /* 1: the CSR was built from per-source buckets (every row held at most
                              1024 candidate pairs), 0: from a radix sort of all the pairs */
+  int32_t pair_filter_bits; /* dense inputs (16+ binned entries per task): log2 of the slots of the
+                               pair-key filter the first sweep wrote through (a pair found again in
+                               another tile is not written again); 0: no filter */
+  int32_t pad1;
   /* diagnostic counters of the last executor launch: batches, tasks, edges,
    * ring claims, failed claim CASes, items published to the ring, idle polls,
    * waits for a reserved slot, ready successors kept by their warp */

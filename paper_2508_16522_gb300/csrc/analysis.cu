@@ -579,6 +579,14 @@ void preload_analysis() {
   cudaFuncGetAttributes(&a, k_emit_csr);
   cudaFuncGetAttributes(&a, k_root_flags);
   cudaFuncGetAttributes(&a, k_roots_emit);
+  cudaFuncGetAttributes(&a, k_band_place);
+  cudaFuncGetAttributes(&a, k_widen_bounds);
+  cudaFuncGetAttributes(&a, k_bucket_count);
+  cudaFuncGetAttributes(&a, k_bucket_maxrow);
+  cudaFuncGetAttributes(&a, k_bucket_scatter);
+  cudaFuncGetAttributes(&a, k_bucket_sort_small);
+  cudaFuncGetAttributes(&a, k_bucket_sort_large);
+  cudaFuncGetAttributes(&a, k_bucket_compact);
 }
 
 }  // namespace grt

@@ -148,6 +148,8 @@ struct rt_graph {
   bool adjx_ok = false;
   int32_t max_outdeg = 0;  // largest out-degree of the analysed graph
   DevBuf tflags;  // per tile: dropped a pair in the first sweep / in the rerun
+  DevBuf pfilt;   // dense inputs: the first sweep's pair-key filter
+  int pair_filter_bits = 0;  // log2 of its slots in the last analysis (0: not used)
   DevBuf bucket;  // CSR by buckets: per-task counts, offsets, distinct counts, long-row list, control words
   // the event-based executor (rt_execute_events): in-edges, events, waiter nodes
   DevBuf ev_pred_off, ev_pred, ev_head, ev_pending, ev_nodes, ev_ring, ev_ctrl;
@@ -192,9 +194,9 @@ void for_each_buf(G* g, F f) {
                 &g->rect_task, &g->cnt, &g->keys, &g->keys_alt, &g->pay, &g->pay_alt, &g->seg_b, &g->seg_e,
                 &g->pairs, &g->pairs_alt, &g->flags, &g->upos, &g->col, &g->row_ptr, &g->indeg, &g->count,
                 &g->rootpos, &g->root_items, &g->ws, &g->misc, &g->adj, &g->adjx, &g->bucket, &g->ring, &g->ctrl,
-                &g->gtable, &g->done_g, &g->tickets, &g->tflags, &g->ev_pred_off, &g->ev_pred, &g->ev_head,
-                &g->ev_pending, &g->ev_nodes, &g->ev_ring, &g->ev_ctrl, &g->ksink, &g->st_count, &g->st_ring,
-                &g->st_ctrl, &g->st_tickets, &g->st_err};
+                &g->gtable, &g->done_g, &g->tickets, &g->tflags, &g->pfilt, &g->ev_pred_off, &g->ev_pred,
+                &g->ev_head, &g->ev_pending, &g->ev_nodes, &g->ev_ring, &g->ev_ctrl, &g->ksink, &g->st_count,
+                &g->st_ring, &g->st_ctrl, &g->st_tickets, &g->st_err};
   for (auto* b : bufs) f(*b);
 }
 
@@ -725,7 +727,25 @@ rt_status run_analysis(rt_graph* g) {
     CK(cudaMemcpyAsync(cursor, (const void*)&h64[2], 8, cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(tile_counter, 0, 4, s));
     CK(cudaMemsetAsync(rerun, 0, 8, s));
-    SweepOut o{g->pairs.as<uint64_t>(), cap, cursor, tile_counter, B, chunk, nullptr, flags1, rerun};
+    // dense inputs (16 or more binned entries per task): the first sweep passes
+    // its pair keys through a direct-mapped filter of about one slot per entry
+    // (2^16 .. 2^26 slots), so that a pair found again in other tiles is not
+    // written again; skipped when it would pass the graph's memory cap
+    int fbits = 0;
+    if (M >= (int64_t)16 * n) {
+      fbits = 16;
+      while (fbits < 26 && (1ll << fbits) < M) ++fbits;
+      const size_t fbytes = (size_t)8 << fbits;
+      if (fbytes > g->pfilt.cap && t_capped && over_cap(fbytes - g->pfilt.cap)) {
+        fbits = 0;
+      } else {
+        CKR(g->pfilt.reserve(fbytes, s));
+        CK(cudaMemsetAsync(g->pfilt.p, 0xFF, fbytes, s));
+      }
+    }
+    g->pair_filter_bits = fbits;
+    SweepOut o{g->pairs.as<uint64_t>(), cap, cursor, tile_counter, B, chunk, nullptr, flags1, rerun,
+               fbits ? g->pfilt.as<unsigned long long>() : nullptr, fbits};
     if (prof) CK(cudaEventRecord(g->ev[EV_SW0], s));
     launch_sweep(spay, g->seg_b.as<uint32_t>(), g->seg_e.as<uint32_t>(), d, o, sweep_blocks, s);
     if (prof) CK(cudaEventRecord(g->ev[EV_SW1], s));
@@ -748,7 +768,9 @@ rt_status run_analysis(rt_graph* g) {
       CKR(g->pairs.reserve((size_t)cap * 8, s, (size_t)old_cap * 8));
       CK(cudaMemsetAsync(g->pairs.as<uint64_t>() + old_cap, 0xFF, (size_t)(Ptot - old_cap) * 8, s));
       CK(cudaMemsetAsync(tile_counter, 0, 4, s));
-      SweepOut o2{g->pairs.as<uint64_t>(), cap, cursor, tile_counter, B, chunk, flags1, flags2, rerun};
+      // the rerun writes every pair its tiles find: no filter (a pair whose
+      // first write fell past the buffer's end may already sit in it)
+      SweepOut o2{g->pairs.as<uint64_t>(), cap, cursor, tile_counter, B, chunk, flags1, flags2, rerun, nullptr, 0};
       launch_sweep(spay, g->seg_b.as<uint32_t>(), g->seg_e.as<uint32_t>(), d, o2, sweep_blocks, s);
       if (prof) CK(cudaEventRecord(g->ev[EV_SW1], s));
       CK(cudaGetLastError());
@@ -1372,6 +1394,7 @@ rt_status rt_graph_stats(rt_graph_t g, rt_graph_stats_t* out) {
   out->n_entries = g->n_entries;
   out->n_pairs = g->n_pairs;
   out->csr_by_buckets = g->csr_by_buckets ? 1 : 0;
+  out->pair_filter_bits = g->pair_filter_bits;
   out->n_edges = g->n_edges;
   out->n_roots = g->n_roots;
   out->tile_w = g->dims.tw;

@@ -847,6 +847,7 @@ void preload_exec() {
   cudaFuncGetAttributes(&a, k_reset_counts);
   cudaFuncGetAttributes(&a, k_seed);
   cudaFuncGetAttributes(&a, k_pack_adj);
+  cudaFuncGetAttributes(&a, k_pack_adjx);
   cudaFuncGetAttributes(&a, k_rebase_roots);
   cudaFuncGetAttributes(&a, k_tag_roots);
   cudaFuncGetAttributes(&a, k_check_stacked);

@@ -314,6 +314,13 @@ struct SweepOut {
   const uint8_t* only;       // non-null: sweep only the tiles flagged here
   uint8_t* flag_out;         // non-null: flag the tiles that dropped a pair
   unsigned long long* rerun; // pairs emitted by the tiles that dropped one
+  // optional, dense inputs: a direct-mapped table of 2^filt_bits pair keys
+  // (kEmpty64 = free) through which the flushes of a first sweep pass their
+  // keys; a key found there was emitted before and is not written again. Lossy
+  // only towards keeping duplicates (a slot keeps the last key that reached
+  // it); never set for a rerun, whose tiles must write every pair they find.
+  unsigned long long* filt;
+  int filt_bits;
 };
 int sweep_warps_per_block(int tw, int th);
 size_t sweep_smem_bytes(int tw, int th, int warps);
@@ -353,6 +360,15 @@ int exec_max_blocks_per_sm(int warps);
 rt_status microbench(double* out, int n_out, cudaStream_t s, const char** why);
 void launch_serve_init(ServeParams p, cudaStream_t s);
 void preload_primitives();
+// Loads every kernel of the library (cudaFuncGetAttributes on each). With
+// CUDA's lazy module loading, a kernel's first launch may wait for the device
+// to go idle; a resident kernel (the serving kernel) never lets it, so
+// everything is loaded before one starts. Each file's preload_* lists all of
+// its kernels (a CPU test checks this against the sources).
+void preload_all();
+void preload_microbench();
+void preload_static();
+void preload_stitch();
 void preload_analysis();
 void preload_sweep();
 void preload_exec();

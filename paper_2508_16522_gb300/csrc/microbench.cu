@@ -129,4 +129,16 @@ rt_status microbench(double* out, int n_out, cudaStream_t s, const char** why) {
   return RT_OK;
 }
 
+void preload_microbench() {
+  cudaFuncAttributes a;
+  cudaFuncGetAttributes(&a, k_mb_init);
+  cudaFuncGetAttributes(&a, k_mb_dep_atomic);
+  cudaFuncGetAttributes(&a, k_mb_dep_load);
+  cudaFuncGetAttributes(&a, k_mb_distinct<true>);
+  cudaFuncGetAttributes(&a, k_mb_distinct<false>);
+  cudaFuncGetAttributes(&a, k_mb_fma);
+  cudaFuncGetAttributes(&a, k_mb_contended<true>);
+  cudaFuncGetAttributes(&a, k_mb_contended<false>);
+}
+
 }  // namespace grt

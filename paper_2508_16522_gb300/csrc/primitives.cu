@@ -354,4 +354,17 @@ void preload_primitives() {
   cudaFuncGetAttributes(&a, k_radix_scatter<uint64_t, false>);
 }
 
+void preload_all() {
+  preload_primitives();
+  preload_analysis();
+  preload_sweep();
+  preload_exec();
+  preload_serve();
+  preload_events();
+  preload_task_kernel();
+  preload_stitch();
+  preload_static();
+  preload_microbench();
+}
+
 }  // namespace grt

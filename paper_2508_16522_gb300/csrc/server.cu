@@ -683,13 +683,10 @@ rt_status rt_server_create(const rt_server_desc* d, rt_server_t* out) {
   p.timeout_ns = s->desc.timeout_ns;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
-  // every kernel the workers will launch is loaded before the serving kernel
-  // starts: a lazily loaded kernel could otherwise wait for it to finish
-  preload_primitives();
-  preload_analysis();
-  preload_sweep();
-  preload_exec();
-  preload_serve();
+  // every kernel of the library is loaded before the serving kernel starts: a
+  // lazily loaded kernel (one the workers, or the caller on another stream,
+  // launch for the first time) could otherwise wait for it to finish
+  preload_all();
   // one tiny analysis per batch graph: first-use host allocations (pinned
   // staging words) happen now, not while the serving kernel runs
   {

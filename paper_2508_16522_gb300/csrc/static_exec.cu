@@ -274,4 +274,14 @@ rt_status static_execute(const int32_t* row_ptr, const int32_t* col, const int32
   return RT_OK;
 }
 
+void preload_static() {
+  cudaFuncAttributes a;
+  cudaFuncGetAttributes(&a, k_static_reset);
+  cudaFuncGetAttributes(&a, k_static_seed);
+  cudaFuncGetAttributes(&a, k_static_check_rows);
+  cudaFuncGetAttributes(&a, k_static_check_cols);
+  cudaFuncGetAttributes(&a, k_static_check_indeg);
+  cudaFuncGetAttributes(&a, k_static_clear_err);
+}
+
 }  // namespace grt

@@ -345,4 +345,14 @@ void launch_stitch(const StitchParams& p, const int32_t* indeg, const uint64_t* 
   }
 }
 
+void preload_stitch() {
+  cudaFuncAttributes a;
+  cudaFuncGetAttributes(&a, k_st_check);
+  cudaFuncGetAttributes(&a, k_st_init);
+  cudaFuncGetAttributes(&a, k_stitch<false, false>);
+  cudaFuncGetAttributes(&a, k_stitch<false, true>);
+  cudaFuncGetAttributes(&a, k_stitch<true, false>);
+  cudaFuncGetAttributes(&a, k_stitch<true, true>);
+}
+
 }  // namespace grt

@@ -44,6 +44,12 @@
 // sentinel key that the later sort moves to the end). A tile that drops pairs
 // past the buffer's end is flagged with its pair count, for a rerun of just the
 // flagged tiles.
+// On dense inputs a pair is found again in every tile where the two tasks'
+// rectangles meet; there the first sweep passes each flushed key through a
+// direct-mapped table in global memory (one atomic exchange per key) and does
+// not write a key the table already held. The table is lossy only towards
+// keeping duplicates, which the CSR stage removes anyway; the rerun of flagged
+// tiles sweeps without it.
 #include <map>
 #include <mutex>
 
@@ -162,6 +168,15 @@ __device__ __forceinline__ uint64_t pair_key(int src, int dst, int key_bits) {
   return ((uint64_t)(uint32_t)src << key_bits) | (uint32_t)dst;
 }
 
+// the pair-key filter of dense inputs: the key takes its slot (multiplicative
+// hashing by the 64-bit golden ratio); false when the slot already held it,
+// i.e. some tile emitted this pair before (its write stands, or its tile was
+// flagged for the rerun, which sweeps without the filter)
+__device__ __forceinline__ bool filt_fresh(const SweepOut& o, uint64_t key) {
+  const uint64_t h = (key * 0x9E3779B97F4A7C15ull) >> (64 - o.filt_bits);
+  return atomicExch(o.filt + h, (unsigned long long)key) != (unsigned long long)key;
+}
+
 __device__ __forceinline__ uint64_t entry_at(const Ctx& x, const WarpSmem& w, int p) {
   int q = p - x.pos;
   return (q >= 0 && q < x.cnt) ? w.stage[q] : __ldg(x.L + p);
@@ -170,6 +185,8 @@ __device__ __forceinline__ uint64_t entry_at(const Ctx& x, const WarpSmem& w, in
 // lane-level insert (may run divergently)
 __device__ void hash_insert(const WarpSmem& w, const SweepOut& o, int src, int dst) {
   if (*(volatile int*)w.hcount >= kListCap) {
+    // the list is full: written at once, unfiltered (an exchange's round trip
+    // per insert here cost more than the duplicates it saves)
     put_pair(w, o, atomicAdd(o.cursor, 1ull), pair_key(src, dst, o.key_bits));
     atomicAdd(w.npairs, 1);
     return;
@@ -236,7 +253,30 @@ __device__ void flush(Ctx& x, const WarpSmem& w, const SweepOut& o, int dst) {
   __syncwarp();
   const int cnt = *(volatile int*)w.hcount;
   const int m = cnt < kListCap ? cnt : kListCap;
-  if (m > 0) {
+  if (m > 0 && o.filt) {
+    // two list entries per lane (kListCap = 64); the keys the filter has seen
+    // are dropped before the reservation, so the buffer only takes fresh ones
+    static_assert(kListCap == 64, "two list entries per lane");
+    const int i0 = x.lane, i1 = x.lane + 32;
+    const uint64_t k0 = i0 < m ? pair_key(w.hlist[i0], dst, o.key_bits) : kEmpty64;
+    const uint64_t k1 = i1 < m ? pair_key(w.hlist[i1], dst, o.key_bits) : kEmpty64;
+    const bool f0 = i0 < m && filt_fresh(o, k0);
+    const bool f1 = i1 < m && filt_fresh(o, k1);
+    const unsigned b0 = __ballot_sync(kFull, f0), b1 = __ballot_sync(kFull, f1);
+    const uint32_t n0 = (uint32_t)__popc(b0), total = n0 + (uint32_t)__popc(b1);
+    // the tile's count bounds a rerun, which writes every pair: count them all
+    if (x.lane == 0) atomicAdd(w.npairs, m);
+    if (total > 0) {
+      const PairDst pd = reserve_pairs(x, o, total);
+      const unsigned lt = lanemask_lt();
+      if (f0) put_pair(w, o, pair_pos(pd, (uint32_t)__popc(b0 & lt)), k0);
+      if (f1) put_pair(w, o, pair_pos(pd, n0 + (uint32_t)__popc(b1 & lt)), k1);
+    }
+    if (cnt <= kListCap) {
+      if (i0 < m) w.htab[w.hslot[i0]] = -1;
+      if (i1 < m) w.htab[w.hslot[i1]] = -1;
+    }
+  } else if (m > 0) {
     const PairDst pd = reserve_pairs(x, o, (uint32_t)m);
     if (x.lane == 0) atomicAdd(w.npairs, m);
     for (int i = x.lane; i < m; i += 32) {
@@ -429,20 +469,32 @@ __device__ bool stage_lanes(Ctx& x, const WarpSmem& w, const SweepOut& o, unsign
     }
     __syncwarp();  // this level's cell updates before the next level reads them
   }
-  // emit every lane's buffer into the warp's chunk
-  int incl = nb;
+  // emit every lane's buffer into the warp's chunk (with the filter: only the
+  // keys it has not seen)
+  uint32_t fresh = nb > 0 ? (1u << nb) - 1u : 0u;
+  if (o.filt) {
+    fresh = 0u;
+#pragma unroll
+    for (int k = 0; k < kLaneBuf; ++k)
+      if (k < nb && filt_fresh(o, pair_key(w.lbuf[lane * kLaneBuf + k], b.task, o.key_bits))) fresh |= 1u << k;
+  }
+  const int nf = __popc(fresh);
+  int incl = nf;
 #pragma unroll
   for (int o2 = 1; o2 < 32; o2 <<= 1) {
     const int y = __shfl_up_sync(kFull, incl, o2);
     if (lane >= o2) incl += y;
   }
   const int total = __shfl_sync(kFull, incl, 31);
+  // the tile's count bounds a rerun, which writes every pair: count them all
+  const int all = __reduce_add_sync(kFull, (unsigned)nb);
+  if (lane == 0 && all) atomicAdd(w.npairs, all);
   if (total > 0) {
     const PairDst pd = reserve_pairs(x, o, (uint32_t)total);
-    if (lane == 0) atomicAdd(w.npairs, total);
-    const int base = incl - nb;
+    int pos = incl - nf;
     for (int k = 0; k < nb; ++k)
-      put_pair(w, o, pair_pos(pd, (uint32_t)(base + k)), pair_key(w.lbuf[lane * kLaneBuf + k], b.task, o.key_bits));
+      if ((fresh >> k) & 1u)
+        put_pair(w, o, pair_pos(pd, (uint32_t)pos++), pair_key(w.lbuf[lane * kLaneBuf + k], b.task, o.key_bits));
   }
   __syncwarp();
   return true;

@@ -130,6 +130,54 @@ def test_pair_buffer_overflow_reruns_once():
         g.close()
 
 
+def _dense_overflow_trace(K):
+    """K readers then K reducers over the whole 64 x 64 domain, then small mixed
+    boxes: at 8 x 8 tiles every task covers 64 tiles (64 binned entries per
+    task: the pair-key filter is on), and each tile finds the same K^2 pairs."""
+    rng = np.random.default_rng(11)
+    lo = [[0, 0]] * (2 * K)
+    hi = [[63, 63]] * (2 * K)
+    priv = [0] * K + [2] * K
+    for k in range(200):
+        x, y = rng.integers(0, 62, 2)
+        lo.append([x, y])
+        hi.append([x + rng.integers(0, 2), y + rng.integers(0, 2)])
+        priv.append(int(rng.integers(0, 3)))
+    return tg._finish(2, [0, 0], [63, 63], [1] * len(priv), np.array(lo).reshape(-1), np.array(hi).reshape(-1),
+                      np.array(priv, np.uint8), name=f"dense_{K}")
+
+
+@pytest.mark.parametrize("K", [64, 512])
+def test_pair_filter_on_dense_inputs(K):
+    """Dense inputs go through the pair-key filter: the CSR is the oracle's. At
+    K = 64 far fewer pairs are written than the tiles find. At K = 512 (a
+    reducer with 512 predecessors in every tile: past the per-task list, so
+    they are written unfiltered) the pairs overflow the first guess for the
+    buffer, the flagged tiles are swept again without the filter (a pair whose
+    first write fell past the buffer's end is already in the table), and
+    nothing is lost."""
+    tr = _dense_overflow_trace(K)
+    ref = oracle_csr(tr)
+    g = gpu_graph(tr, tile=(8, 8))
+    g.analyze()
+    assert_csr_equal(g, tr, ref)
+    st = g.stats()
+    assert st["pair_filter_bits"] >= 16, st
+    assert st["n_entries"] >= 16 * tr.n, st
+    found = K * K * 64  # the readers-to-reducers pairs every one of the 64 tiles finds
+    if K == 64:  # fewer distinct pairs than table slots: nearly every repeat is dropped
+        assert st["n_pairs"] < found // 4, st
+    else:  # past the first guess: the rerun ran
+        assert st["n_pairs"] > 2 * st["n_entries"], st
+    g.close()
+    # the same launches sparse enough for no filter give the same CSR
+    g = gpu_graph(tr, tile=(64, 64))
+    g.analyze()
+    assert_csr_equal(g, tr, ref)
+    assert g.stats()["pair_filter_bits"] == 0
+    g.close()
+
+
 def _max_classes(tr, tile):
     """Largest class grid (column classes x row classes) of any tile: the
     boundaries of the rectangles falling inside each tile, counted on the host."""
