@@ -4,6 +4,7 @@ mix must equal its result alone: the canonical CSR, the SPIN outputs, and with
 the order-sensitive CHECK body the request's final state and per-task outputs,
 which equal the oracle's sequential run of that request only if every edge was
 respected while it ran beside the others."""
+import os
 import time
 
 import numpy as np
@@ -237,3 +238,36 @@ def test_submit_rejects_rectangles_outside_the_domain():
         srv.submit(bad)  # a rectangle past the domain would reach the next request's band
     assert e.value.status == grt.RT_ERR_INVALID
     srv.close()
+
+
+_FRESH = r'''
+import sys
+sys.path.insert(0, sys.argv[1])
+from paper_2508_16522_gb300 import grt, tracegen as tg
+grt.load()
+# nothing has run in this process: the server is the first user of the library,
+# so every kernel its workers launch must have been loaded before its kernel
+reqs = tg.served_stream(40, rate_per_s=50000.0, seed=3)
+srv = grt.Server(2, [0, 0], [1023, 1023], body=grt.RT_BODY_EMPTY, budget_bytes=2 << 30, max_inflight=64,
+                 max_tasks=16384, workers=2, tile=(16, 16), max_batch=16)
+tickets = [srv.submit(r.trace) for r in reqs]
+srv.drain(timeout_ns=60_000_000_000)
+edges = [srv.poll(t)["n_edges"] for t in tickets]
+srv.close()
+print(sum(edges))
+'''
+
+
+def test_server_as_the_first_thing_a_process_runs():
+    """A server created before any other call of the library analyses dense
+    batches (all of the analysis kernels, the bucket CSR and the pair-key
+    filter among them) while its kernel is resident. Run in a fresh process,
+    bounded, and compared with the oracle's edge counts."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    ensure_built()
+    out = subprocess.run([sys.executable, "-c", _FRESH, root], capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr[-2000:]
+    want = sum(len(oracle_csr(r.trace)[1]) for r in tg.served_stream(40, rate_per_s=50000.0, seed=3))
+    assert int(out.stdout.strip().splitlines()[-1]) == want
