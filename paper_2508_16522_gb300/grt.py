@@ -89,6 +89,7 @@ class rt_graph_stats_t(ctypes.Structure):
                 ("ms_execute", ctypes.c_float), ("ms_exec_kernel", ctypes.c_float),
                 ("exec_blocks", ctypes.c_int32), ("exec_threads", ctypes.c_int32),
                 ("ms_sweep_kernel", ctypes.c_float), ("csr_by_buckets", ctypes.c_int32),
+                ("pair_filter_bits", ctypes.c_int32), ("pad1", ctypes.c_int32),
                 ("exec_counters", ctypes.c_int64 * 9)]
 
     COUNTER_NAMES = ("batches", "tasks", "edges", "claims", "cas_fail", "pushed", "idle", "slot_wait", "kept")
