@@ -380,6 +380,20 @@ rt_status rt_batch_capture(const rt_graph_desc* desc, int32_t n_graphs, const in
 rt_status rt_batch_execute(rt_batch_t b, int32_t replays, int32_t exec_blocks, int32_t exec_warps,
                            int32_t claim, int32_t keep);
 
+/* How rt_batch_execute runs the batch (Algorithm 1's EXECUTE_OP, as for one
+ * graph in rt_graph_exec_policy): RT_EXEC_RING (default) as described above;
+ * RT_EXEC_OWNED runs the batch's graphs as ONE DAG under the owned-chunk
+ * executor (every edge of the batch points to a later task), with count-down
+ * counters reset to the in-degrees at every launch and a run barrier between
+ * replays: replay r + 1 of every graph starts once replay r of all graphs has
+ * finished, a stricter order that gives every graph the same results; each
+ * body still sees its own graph's task ids and buffers. Under OWNED the claim
+ * width is the lanes per task (1, 2 or 4). The first OWNED launch builds each
+ * task's graph index (4 bytes per task) and, when some task has more than 5
+ * successors, 32 more bytes of trigger record per task. Errors:
+ * RT_ERR_INVALID. */
+rt_status rt_batch_exec_policy(rt_batch_t b, int32_t policy);
+
 rt_status rt_batch_sync(rt_batch_t b, float* ms_kernel);
 
 /* out[0] graphs, [1] tasks, [2] edges, [3] launches made from the cached CUDA
@@ -424,8 +438,12 @@ rt_status rt_tune_tile(const rt_graph_desc* desc, int32_t n, const int32_t* req_
  * state-changing body sees those runs. Synchronous. */
 rt_status rt_tune_exec(rt_graph_t g, const char* cache_path, rt_exec_config* best);
 
-/* The same for a batch launch of `replays` replays; returns the shape for
- * rt_batch_execute (the batch keeps no configuration). Synchronous. */
+/* The same for a batch launch of `replays` replays: the ring policy by
+ * coordinate descent, then one run of the owned policy and, only if that run
+ * comes within 1.5x of the ring, its grids (1-3 blocks of 4 or 8 warps per SM)
+ * and 1, 2 or 4 lanes per task; sets the batch's policy
+ * (rt_batch_exec_policy) to the faster one and returns the shape (with its
+ * policy) for rt_batch_execute. The bodies run once per trial. Synchronous. */
 rt_status rt_tune_batch(rt_batch_t b, int32_t replays, const char* cache_path, rt_exec_config* best);
 
 /* ---- serving (continuous batching) ---------------------------------------

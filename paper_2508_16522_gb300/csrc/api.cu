@@ -233,6 +233,13 @@ struct rt_batch {
   cudaStream_t cap_stream = nullptr;
   int64_t graph_launches = 0;  // launches that went through the cached CUDA graph
   rt_graph* owned = nullptr;   // rt_batch_capture: the stacked graph it analysed
+  // the owned-chunk policy (rt_batch_exec_policy): each task's graph, the
+  // extension records (only when some task has more than kAdjInline
+  // successors), built on the first owned launch
+  int policy = RT_EXEC_RING;
+  DevBuf task_graph, adjx, scratch;
+  bool owned_ready = false;
+  int32_t max_outdeg = 0;
 };
 
 namespace {
@@ -1717,6 +1724,39 @@ void drop_batch_graph(rt_batch* b) {
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
   b->gexec = nullptr;
 }
+
+// The owned-chunk policy's launch: the batch's graphs as one DAG (every edge
+// still points to a later task), count-down counters reset to the in-degrees,
+// a run barrier between replays; bodies run with their own graph's entry.
+rt_status enqueue_batch_owned(rt_batch* b, const ExecParams& p, int blocks, int warps, cudaStream_t s) {
+  launch_reset_counts(b->count.as<int32_t>(), b->indeg.as<int32_t>(), b->T, -1, 0, s);
+  launch_seed(p, 0, s);  // clears the control block and the completion counters
+  launch_exec(p, blocks, warps, s);
+  CK(cudaMemcpyAsync(b->hpin, &p.ctrl->status, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(reinterpret_cast<char*>(b->hpin) + 512, p.ctrl->counters, kCntCount * sizeof(unsigned long long),
+                     cudaMemcpyDeviceToHost, s));
+  return RT_OK;
+}
+
+rt_status prepare_batch_owned(rt_batch* b) {
+  if (b->owned_ready) return RT_OK;
+  cudaStream_t s = b->s;
+  CKR(b->task_graph.reserve((size_t)std::max<int64_t>(b->T, 1) * 4, s));
+  launch_fill_task_graph(b->gtable.as<ExecGraph>(), b->G, b->task_graph.as<int32_t>(), s);
+  CKR(b->scratch.reserve(64, s));
+  CK(cudaMemsetAsync(b->scratch.p, 0, 4, s));
+  launch_max_outdeg(b->row_ptr.as<int32_t>(), b->T, b->scratch.as<uint32_t>(), s);
+  CK(cudaMemcpyAsync(b->hpin + 4, b->scratch.p, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  b->max_outdeg = (int32_t)b->hpin[4];
+  if (b->max_outdeg > kAdjInline) {
+    CKR(b->adjx.reserve((size_t)b->T * 32, s));
+    launch_pack_adjx(b->row_ptr.as<int32_t>(), b->col.as<int32_t>(), b->T, b->adjx.as<int4>(), s);
+  }
+  CK(cudaGetLastError());
+  b->owned_ready = true;
+  return RT_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -1807,6 +1847,53 @@ rt_status rt_batch_execute(rt_batch_t b, int32_t replays, int32_t exec_blocks, i
   if (exec_blocks > max_blocks) return fail(RT_ERR_INVALID, "more persistent blocks than can be resident");
   const int blocks = exec_blocks > 0 ? exec_blocks : g_dev.num_sms * std::min(exec_bps_for(warps), 3);
   cudaStream_t s = b->s;
+  if (b->policy == RT_EXEC_OWNED) {
+    CKR(prepare_batch_owned(b));
+    ExecParams p{};
+    p.adj = b->adj.as<int4>();
+    p.adjx = b->max_outdeg > kAdjInline ? b->adjx.as<int4>() : nullptr;
+    p.row_ptr = b->row_ptr.as<int32_t>();
+    p.col = b->col.as<int32_t>();
+    p.indeg = b->indeg.as<int32_t>();
+    p.count = b->count.as<int32_t>();
+    p.n_graphs = b->G;
+    p.graphs = b->gtable.as<ExecGraph>();
+    p.done_g = b->done_g.as<uint32_t>();
+    p.ctrl = b->ctrl.as<ExecCtrl>();
+    p.replays = replays;
+    p.graphs_target = b->G_nonempty;
+    p.timeout_ns = 2000000000ll;
+    p.claim = claim > 0 ? claim : 1;  // lanes per task
+    p.keep = keep > 0 ? keep : 16;
+    p.need_fence = b->need_fence;
+    p.policy = RT_EXEC_OWNED;
+    p.owned_n = (int32_t)b->T;
+    p.task_graph = b->task_graph.as<int32_t>();
+    CK(cudaEventRecord(b->e0, s));
+    const int64_t key[7] = {replays, blocks, warps, p.claim, p.keep, -1 - (int64_t)RT_EXEC_OWNED, b->T};
+    if (!b->gexec || memcmp(key, b->gkey, sizeof key) != 0) {
+      drop_batch_graph(b);
+      if (!b->cap_stream) CK(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+      CK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+      rt_status st = enqueue_batch_owned(b, p, blocks, warps, b->cap_stream);
+      cudaGraph_t graph = nullptr;
+      cudaError_t e = cudaStreamEndCapture(b->cap_stream, &graph);
+      if (st != RT_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+      }
+      if (e != cudaSuccess) return fail(RT_ERR_CUDA, "batch capture: %s", cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&b->gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return fail(RT_ERR_CUDA, "batch instantiate: %s", cudaGetErrorString(e));
+      memcpy(b->gkey, key, sizeof key);
+    }
+    CK(cudaGraphLaunch(b->gexec, s));
+    ++b->graph_launches;
+    CK(cudaEventRecord(b->e1, s));
+    CK(cudaGetLastError());
+    return RT_OK;  // the ring was not touched: it stays as clean as the last ring launch left it
+  }
   bool clear = b->dirty;
   if (cap * 8 > b->ring.cap) {
     drop_batch_graph(b);
@@ -1867,6 +1954,14 @@ rt_status rt_batch_execute(rt_batch_t b, int32_t replays, int32_t exec_blocks, i
   return RT_OK;
 }
 
+rt_status rt_batch_exec_policy(rt_batch_t b, int32_t policy) {
+  if (!b) return fail(RT_ERR_INVALID, "batch is NULL");
+  if (policy != RT_EXEC_RING && policy != RT_EXEC_OWNED) return fail(RT_ERR_INVALID, "unknown policy %d", policy);
+  if (policy != b->policy) drop_batch_graph(b);
+  b->policy = policy;
+  return RT_OK;
+}
+
 rt_status rt_batch_info(rt_batch_t b, int64_t* out, int32_t n) {
   if (!b || !out || n < 0) return fail(RT_ERR_INVALID, "NULL argument");
   const int64_t v[4] = {b->G, b->T, b->E, b->graph_launches};
@@ -1900,7 +1995,8 @@ rt_status rt_batch_destroy(rt_batch_t b) {
   if (!b) return RT_OK;
   cudaStreamSynchronize(b->s);
   drop_batch_graph(b);
-  DevBuf* bufs[] = {&b->row_ptr, &b->col, &b->indeg, &b->count, &b->root_items, &b->gtable, &b->done_g, &b->ring, &b->ctrl, &b->adj};
+  DevBuf* bufs[] = {&b->row_ptr, &b->col,  &b->indeg, &b->count, &b->root_items, &b->gtable,  &b->done_g,
+                    &b->ring,    &b->ctrl, &b->adj,   &b->adjx,  &b->task_graph, &b->scratch};
   for (DevBuf* x : bufs) x->release(b->s);
   cudaStreamSynchronize(b->s);
   if (b->hpin) cudaFreeHost(b->hpin);

@@ -24,6 +24,7 @@
 // needs no re-arm and no release of it before the completion count.
 // Every wait is bounded: a warp that sees no progress of the global executed
 // counter for timeout_ns sets status TIMEOUT and returns.
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -427,10 +428,11 @@ __global__ void __launch_bounds__(256, 1) k_exec_owned(ExecParams p) {
   const int gw = (int)blockIdx.x * (int)(blockDim.x >> 5) + warp;
   ExecCtrl* ctrl = p.ctrl;
   const ExecGraph& G = p.graphs[0];
-  const int n = G.n_tasks;
+  const int n = p.owned_n > 0 ? p.owned_n : G.n_tasks;
   const int body = G.body, spin = G.spin_iters;
   int32_t* const out = G.out;
   const int nchunks = (n + C - 1) / C;
+  const bool batched = p.task_graph != nullptr;  // bodies run with their own graph's table entry
   const int R = p.adjx != nullptr ? 4 : 2;              // int4s per trigger record
   const int inl = 4 * R - 3;                            // successors a record holds
   const int g0 = h * R / L, nq = (h + 1) * R / L - g0;  // this lane's record int4s [g0, g0 + nq)
@@ -495,7 +497,7 @@ __global__ void __launch_bounds__(256, 1) k_exec_owned(ExecParams p) {
     }
     uint32_t ran = 0;  // tasks this warp ran in run r (warp-uniform)
     int next_c = gw;   // the next chunk this warp takes
-    int ck = -1, v = 0, ctasks = 0, deg = 0, dmax = 0;
+    int ck = -1, v = 0, ctasks = 0, deg = 0, dmax = 0, gi = 0;
     int4 q[QM];        // this lane's part of its task's trigger record
     int32_t polled = 1;  // the lane's countdown, polled one round ahead
     unsigned pending = 0u;
@@ -518,6 +520,7 @@ __global__ void __launch_bounds__(256, 1) k_exec_owned(ExecParams p) {
         if (k < nq && has) q[k] = __ldg(g < 2 ? p.adj + 2 * (int64_t)v + g : p.adjx + 2 * (int64_t)v + (g - 2));
       }
       if (has) polled = ld_relaxed_s32(p.count + v);
+      if (batched && has) gi = __ldg(p.task_graph + v);
       pending = __ballot_sync(kFull, has);
       ctasks = __popc(pending & heads);
       deg = __shfl_sync(kFull, q[0].y, head_lane);  // the head's int4 0: {row start, degree, in-degree, s0}
@@ -554,7 +557,10 @@ __global__ void __launch_bounds__(256, 1) k_exec_owned(ExecParams p) {
       if (ready && is_head) {
         p.count[v] = q[0].z;  // INIT's reset for the next run, done by the task itself
         if (TICKETS) p.tickets[2 * (int64_t)v] = (int32_t)atomicAdd(&ctrl->ticket, 1u);
-        if (!FENCE) {
+        if (batched) {
+          const ExecGraph& Gv = p.graphs[gi];  // a batched body sees its graph's own task ids
+          run_body<FENCE>(Gv, v - Gv.task_base);
+        } else if (!FENCE) {
           if (body == RT_BODY_SPIN) out[v] = (int32_t)spin_body((uint32_t)v, spin);
           else if (body == RT_BODY_FMA) out[v] = fma_body((uint32_t)v, spin);
         } else {
@@ -670,6 +676,23 @@ __global__ void k_pack_adjx(const int32_t* row_ptr, const int32_t* col, int64_t 
   adjx[2 * v + 1] = make_int4(c[4], c[5], c[6], c[7]);
 }
 
+// each task's graph in a batch: block k fills graph k's task range
+__global__ void k_fill_task_graph(const ExecGraph* graphs, int32_t G, int32_t* out) {
+  for (int32_t k = blockIdx.x; k < G; k += gridDim.x) {
+    const int32_t b = graphs[k].task_base, m = graphs[k].n_tasks;
+    for (int32_t i = threadIdx.x; i < m; i += blockDim.x) out[b + i] = k;
+  }
+}
+
+// the largest out-degree (atomicMax into *out, zeroed by the caller)
+__global__ void k_max_outdeg(const int32_t* row_ptr, int64_t n, uint32_t* out) {
+  uint32_t m = 0;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, (uint32_t)(row_ptr[v + 1] - row_ptr[v]));
+  m = __reduce_max_sync(0xffffffffu, m);
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
 __global__ void k_rebase_roots(const uint64_t* src, uint64_t* dst, int32_t n, int32_t graph,
                                int32_t task_base) {
   int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -738,6 +761,21 @@ void launch_pack_adjx(const int32_t* row_ptr, const int32_t* col, int64_t n, int
   if (n > 0) {
     count_launch();
     k_pack_adjx<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(row_ptr, col, n, adjx);
+  }
+}
+
+void launch_fill_task_graph(const ExecGraph* graphs, int32_t G, int32_t* out, cudaStream_t s) {
+  if (G > 0) {
+    count_launch();
+    k_fill_task_graph<<<(unsigned)std::min<int32_t>(G, 65535), 256, 0, s>>>(graphs, G, out);
+  }
+}
+
+void launch_max_outdeg(const int32_t* row_ptr, int64_t n, uint32_t* out, cudaStream_t s) {
+  if (n > 0) {
+    count_launch();
+    const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
+    k_max_outdeg<<<blocks, 256, 0, s>>>(row_ptr, n, out);
   }
 }
 
@@ -814,7 +852,7 @@ void launch_exec(ExecParams p, int blocks, int warps, cudaStream_t s) {
   const bool single = p.n_graphs == 1;
   const bool fence = p.need_fence != 0;
   count_launch();
-  if (single && p.policy == RT_EXEC_OWNED) {  // keeps nothing in shared memory
+  if (p.policy == RT_EXEC_OWNED && (single || p.task_graph)) {  // keeps nothing in shared memory
     // the claim width is the group size: lanes per task (1, 2 or 4)
     const int Lg = p.claim >= 4 ? 4 : (p.claim >= 2 ? 2 : 1);
 #define GRT_OWNED(T, F)                                                         \
@@ -848,6 +886,8 @@ void preload_exec() {
   cudaFuncGetAttributes(&a, k_seed);
   cudaFuncGetAttributes(&a, k_pack_adj);
   cudaFuncGetAttributes(&a, k_pack_adjx);
+  cudaFuncGetAttributes(&a, k_fill_task_graph);
+  cudaFuncGetAttributes(&a, k_max_outdeg);
   cudaFuncGetAttributes(&a, k_rebase_roots);
   cudaFuncGetAttributes(&a, k_tag_roots);
   cudaFuncGetAttributes(&a, k_check_stacked);

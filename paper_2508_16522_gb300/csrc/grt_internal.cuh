@@ -199,6 +199,11 @@ struct ExecParams {
   int32_t total_roots;
   int32_t need_fence;     // some body reads data written by its predecessors
   int32_t policy;         // single graph: RT_EXEC_RING (ready ring) or RT_EXEC_OWNED (owned chunks)
+  // the owned policy over a batch (one DAG of all its graphs, a run barrier
+  // between replays): its task count and each task's graph, whose table entry
+  // (task_base, body, buffers) its body runs with; 0 / null for one graph
+  int32_t owned_n;
+  const int32_t* task_graph;
 };
 
 // ---------------------------------------------------------------------------
@@ -350,6 +355,8 @@ void launch_roots_emit(const int32_t* indeg, const uint32_t* pos, int32_t n, int
 void launch_pack_adj(const int32_t* row_ptr, const int32_t* col, const int32_t* indeg, int64_t n, int4* adj,
                      uint32_t* maxdeg, cudaStream_t s);
 void launch_pack_adjx(const int32_t* row_ptr, const int32_t* col, int64_t n, int4* adjx, cudaStream_t s);
+void launch_fill_task_graph(const ExecGraph* graphs, int32_t G, int32_t* out, cudaStream_t s);
+void launch_max_outdeg(const int32_t* row_ptr, int64_t n, uint32_t* out, cudaStream_t s);
 void launch_reset_counts(int32_t* count, const int32_t* indeg, int64_t n, int32_t hold_task,
                          int32_t hold_extra, cudaStream_t s);
 void launch_rebase_roots(const uint64_t* src, uint64_t* dst, int32_t n, int32_t graph, int32_t task_base,

@@ -352,12 +352,13 @@ rt_status rt_tune_batch(rt_batch_t b, int32_t replays, const char* cache_path, r
   if (s != RT_OK) return s;
   int sms = 0;
   if ((s = rt_device_info(&sms, nullptr)) != RT_OK) return s;
-  const std::string key = "batch/" + device_tag() + "/" + std::to_string(G) + "/" + std::to_string(T) + "/" +
+  // "batch2": entries that also weigh the owned policy (the batch as one DAG)
+  const std::string key = "batch2/" + device_tag() + "/" + std::to_string(G) + "/" + std::to_string(T) + "/" +
                           std::to_string(E) + "/" + std::to_string(replays);
   std::vector<double> c;
-  if (cache_get(cache_path, key, &c) && c.size() >= 5) {
-    *best = rt_exec_config{(int32_t)c[0], (int32_t)c[1], (int32_t)c[2], (int32_t)c[3], (float)c[4], 0};
-    return RT_OK;
+  if (cache_get(cache_path, key, &c) && c.size() >= 6) {
+    *best = rt_exec_config{(int32_t)c[0], (int32_t)c[1], (int32_t)c[2], (int32_t)c[3], (float)c[4], 0, (int32_t)c[5]};
+    return rt_batch_exec_policy(b, best->policy);
   }
   auto run = [&](const Shape& sh) -> double {
     float ms = 0;
@@ -369,11 +370,54 @@ rt_status rt_tune_batch(rt_batch_t b, int32_t replays, const char* cache_path, r
   Shape sh{};
   float ms = 0;
   int trials = 0;
+  rt_batch_exec_policy(b, RT_EXEC_RING);
   const int bps4 = std::max(exec_max_blocks_per_sm(4), 1);
   if ((s = search(sms, Shape{4, std::min(bps4, 3), 32, 32}, run, &sh, &ms, &trials)) != RT_OK)
     return tfail(s, std::string("batch trial failed: ") + rt_last_error());
-  *best = rt_exec_config{sms * sh.bps, sh.warps, sh.claim, sh.keep, ms, trials};
-  cache_put(cache_path, key, {(double)best->blocks, (double)sh.warps, (double)sh.claim, (double)sh.keep, ms});
+  *best = rt_exec_config{sms * sh.bps, sh.warps, sh.claim, sh.keep, ms, trials, RT_EXEC_RING};
+  // the owned policy: one probe at two blocks of 8 warps per SM (one run: on
+  // a batch of unrelated graphs a warp's chunks lie in many graphs and one
+  // graph's progress waits for the others', so it can be many times slower);
+  // only if that probe comes within 1.5x of the ring, the other grids (one to
+  // three blocks of 4 or 8 warps per SM) and 2 and 4 lanes per task
+  rt_batch_exec_policy(b, RT_EXEC_OWNED);
+  bool failed = false;
+  auto owned_trial = [&](int blocks, int warps, int group, int reps) {
+    if (blocks > sms * std::max(exec_max_blocks_per_sm(warps), 1)) return;
+    double t = 1e30;
+    for (int rep = 0; rep < reps && !failed; ++rep) {
+      float m = 0;
+      if (rt_batch_execute(b, replays, blocks, warps, group, 16) != RT_OK || rt_batch_sync(b, &m) != RT_OK)
+        failed = true;
+      t = std::min<double>(t, m);
+    }
+    ++trials;
+    if (!failed && t < best->ms) *best = rt_exec_config{blocks, warps, group, 16, (float)t, trials, RT_EXEC_OWNED};
+  };
+  const double ring_ms = best->ms;
+  double probe_ms = 1e30;
+  {
+    float m = 0;
+    if (rt_batch_execute(b, replays, sms * 2, 8, 1, 16) == RT_OK && rt_batch_sync(b, &m) == RT_OK)
+      probe_ms = m;
+    ++trials;
+  }
+  if (probe_ms < 1.5 * ring_ms) {
+    const int grids[][2] = {{1, 4}, {1, 8}, {2, 4}, {2, 8}, {3, 8}};  // (blocks per SM, warps)
+    for (const auto& gw : grids) owned_trial(sms * gw[0], gw[1], 1, 2);
+    if (!failed && best->policy == RT_EXEC_OWNED) {
+      const int gb = best->blocks, gwp = best->warps;
+      for (int group : {2, 4}) owned_trial(gb, gwp, group, 2);
+    }
+  }
+  if (failed) {
+    rt_batch_exec_policy(b, RT_EXEC_RING);
+    return tfail(RT_ERR_CUDA, std::string("batch trial failed: ") + rt_last_error());
+  }
+  best->trials = trials;
+  rt_batch_exec_policy(b, best->policy);
+  cache_put(cache_path, key, {(double)best->blocks, (double)best->warps, (double)best->claim, (double)best->keep,
+                              best->ms, (double)best->policy});
   return RT_OK;
 }
 

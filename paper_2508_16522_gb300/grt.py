@@ -36,7 +36,8 @@ EXPORTS = ["rt_graph_create", "rt_graph_destroy", "rt_graph_clear", "rt_launch_b
            "rt_server_create", "rt_server_submit", "rt_server_poll", "rt_server_result", "rt_server_result_state",
            "rt_server_drain", "rt_server_stats", "rt_server_destroy", "rt_tune_tile", "rt_tune_exec", "rt_tune_batch",
            "rt_batch_create_stacked", "rt_execute_events", "rt_execute_kernels", "rt_execute_stitched",
-           "rt_copy_stitched_tickets", "rt_batch_capture", "rt_batch_info", "rt_graph_exec_policy"]
+           "rt_copy_stitched_tickets", "rt_batch_capture", "rt_batch_info", "rt_graph_exec_policy",
+           "rt_batch_exec_policy"]
 
 
 class GrtError(RuntimeError):
@@ -154,6 +155,7 @@ def load(path: str = LIB_PATH):
                              ctypes.POINTER(P)],
         "rt_batch_info": [P, ctypes.POINTER(i64), i32],
         "rt_graph_exec_policy": [P, i32],
+        "rt_batch_exec_policy": [P, i32],
         "rt_execute_events": [P, ctypes.POINTER(ctypes.c_float)],
         "rt_execute_kernels": [P, i32, i32, i32, ctypes.POINTER(ctypes.c_float)],
         "rt_execute_stitched": [P, i32, ctypes.POINTER(ctypes.c_float)],
@@ -517,6 +519,11 @@ class Batch:
 
     def graph_stats(self) -> dict:
         return rt_graph_stats(self.graph_h)
+
+    def exec_policy(self, policy: int):
+        """RT_EXEC_RING (default) or RT_EXEC_OWNED (the batch as one DAG, a run
+        barrier between replays)."""
+        _check(load().rt_batch_exec_policy(self.h, policy))
 
     def execute(self, replays: int = 1, blocks: int = 0, warps: int = 0, claim: int = 0, keep: int = 0):
         _check(load().rt_batch_execute(self.h, replays, blocks, warps, claim, keep))

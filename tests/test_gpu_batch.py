@@ -21,8 +21,12 @@ def _oracle_repeat(tr, body, reps, spin_iters=256, state_elems=None):
     return st, out
 
 
+POLICIES = [grt.RT_EXEC_RING, grt.RT_EXEC_OWNED]
+
+
+@pytest.mark.parametrize("policy", POLICIES)
 @pytest.mark.parametrize("replays", [1, 3])
-def test_mixed_batch_equals_each_graph_alone(replays):
+def test_mixed_batch_equals_each_graph_alone(replays, policy):
     traces, bodies = [], []
     for k in range(24):
         if k % 4 == 0:
@@ -44,6 +48,7 @@ def test_mixed_batch_equals_each_graph_alone(replays):
         g.analyze()
         graphs.append(g)
     batch = grt.Batch(graphs)
+    batch.exec_policy(policy)
     batch.execute(replays=replays)
     ms = batch.sync()
     assert ms > 0
@@ -66,7 +71,8 @@ def test_mixed_batch_equals_each_graph_alone(replays):
         g.close()
 
 
-def test_batch_with_empty_and_single_task_graphs():
+@pytest.mark.parametrize("policy", POLICIES)
+def test_batch_with_empty_and_single_task_graphs(policy):
     import torch
     empty = grt.Graph(2, [0, 0], [3, 3])
     empty.analyze()
@@ -76,6 +82,7 @@ def test_batch_with_empty_and_single_task_graphs():
     big = gpu_graph(tg.taskbench(64, 30, "random"), body=grt.RT_BODY_SPIN, spin_iters=5)
     big.analyze()
     b = grt.Batch([empty, one, big])
+    b.exec_policy(policy)
     b.execute(replays=4)
     b.sync()
     assert one.out.cpu().tolist() == [oracle.spin(0, 5)]
@@ -87,8 +94,12 @@ def test_batch_with_empty_and_single_task_graphs():
     del torch
 
 
-@pytest.mark.parametrize("shape", [(0, 0, 0, 0), (152, 2, 8, 8), (304, 4, 32, 64), (1, 1, 1, 0)])
+@pytest.mark.parametrize("shape", [(0, 0, 0, 0, 0), (152, 2, 8, 8, 0), (304, 4, 32, 64, 0), (1, 1, 1, 0, 0),
+                                   (0, 0, 0, 0, 1), (152, 8, 1, 0, 1), (7, 1, 4, 0, 1), (304, 8, 2, 0, 1),
+                                   (1, 1, 1, 0, 1)])
 def test_batch_launch_shapes_give_same_results(shape):
+    """(blocks, warps, claim, keep, policy): the ring policy's shapes, and the
+    owned policy's (claim = lanes per task), down to one block of one warp."""
     gs_tr = tg.batch_graphs(60, n_range=(64, 4096), seed=3)
     graphs = []
     for tr in gs_tr:
@@ -96,7 +107,8 @@ def test_batch_launch_shapes_give_same_results(shape):
         g.analyze()
         graphs.append(g)
     b = grt.Batch(graphs)
-    blocks, warps, claim, keep = shape
+    blocks, warps, claim, keep, policy = shape
+    b.exec_policy(policy)
     b.execute(replays=2, blocks=blocks, warps=warps, claim=claim, keep=keep)
     b.sync()
     for tr, g in zip(gs_tr, graphs):
@@ -204,6 +216,15 @@ def test_capture_places_graphs_in_bands_itself():
     assert b.info()["graph_launches"] >= 1
     # a batched body sees its graph's own task ids, in the stacked domain's cells
     st_o, out_o = _stacked_local_ids_state(traces, host, 6)
+    assert np.array_equal(state.cpu().numpy(), st_o)
+    assert np.array_equal(out.cpu().numpy(), out_o)
+    # the owned policy (the batch as one DAG, a run barrier between replays)
+    # continues from that state: 2 more launches of 2 replays
+    b.exec_policy(grt.RT_EXEC_OWNED)
+    for _ in range(2):
+        b.execute(replays=2)
+        b.sync()
+    st_o, out_o = _stacked_local_ids_state(traces, host, 10)
     assert np.array_equal(state.cpu().numpy(), st_o)
     assert np.array_equal(out.cpu().numpy(), out_o)
     b.close()
