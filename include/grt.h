@@ -421,7 +421,8 @@ typedef struct {
 } rt_exec_config;
 
 /* Analyses the launches (host arrays, as rt_launch_batch) once per candidate
- * tile -- 8, 16, 32, 64 square in 2-D; 128..1024 in 1-D -- in a temporary
+ * tile -- 8, 16, 32, 64 square and 8x16, 16x8, 32x4, 32x8, 64x4 in 2-D;
+ * 128..1024 in 1-D -- in a temporary
  * graph built from desc (body, state, out and flags ignored), and returns the
  * tile whose analysis was fastest (its ms in *ms, may be NULL). Errors:
  * RT_ERR_INVALID (bad arguments, or no candidate could analyse the trace). */
