@@ -18,6 +18,7 @@ def traces():
     return [tg.random_rects(grid=(300, 200), n=2500, rects=(1, 4), side=(1, 40), seed=31),
             tg.random_rects(grid=(5000,), n=1500, rects=(1, 3), side=(1, 300), seed=32, ndim=1),
             tg.taskbench(256, 40, "random", seed=4),
+            tg.taskbench(64, 30, "stencil", seed=6, encode="explicit"),  # explicit predecessors too
             # a domain away from the origin, negative coordinates included
             tg.random_rects(grid=(90, 70), n=800, side=(1, 20), seed=33)]
 
@@ -35,7 +36,7 @@ def test_int32_bounds_equal_oracle(how):
     import torch
     ensure_built()
     trs = traces()
-    trs[3] = shifted(trs[3], -1000)
+    trs[-1] = shifted(trs[-1], -1000)
     for tr in trs:
         lo32, hi32 = tr.lo.astype(np.int32), tr.hi.astype(np.int32)
         g = grt.Graph(tr.ndim, tr.dom_lo, tr.dom_hi, tile=(16, 16) if tr.ndim == 2 else (128, 1))
