@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(256, 1) k_exec(ExecParams p) {
 // timeout_ns without global progress.
 constexpr uint32_t kOwnedBackoffMax = 256;  // ns between polls of a warp whose tasks are all waiting
 
-template <bool TICKETS, bool FENCE, int L>
+template <bool TICKETS, bool FENCE, int L, bool BATCHED>
 __global__ void __launch_bounds__(256, 1) k_exec_owned(ExecParams p) {
   constexpr int C = 32 / L;   // tasks per chunk
   constexpr int QM = 4 / L;   // record int4s one lane holds at most
@@ -428,11 +428,11 @@ __global__ void __launch_bounds__(256, 1) k_exec_owned(ExecParams p) {
   const int gw = (int)blockIdx.x * (int)(blockDim.x >> 5) + warp;
   ExecCtrl* ctrl = p.ctrl;
   const ExecGraph& G = p.graphs[0];
-  const int n = p.owned_n > 0 ? p.owned_n : G.n_tasks;
+  const int n = BATCHED ? p.owned_n : G.n_tasks;
   const int body = G.body, spin = G.spin_iters;
   int32_t* const out = G.out;
   const int nchunks = (n + C - 1) / C;
-  const bool batched = p.task_graph != nullptr;  // bodies run with their own graph's table entry
+  constexpr bool batched = BATCHED;  // a batch: bodies run with their own graph's table entry
   const int R = p.adjx != nullptr ? 4 : 2;              // int4s per trigger record
   const int inl = 4 * R - 3;                            // successors a record holds
   const int g0 = h * R / L, nq = (h + 1) * R / L - g0;  // this lane's record int4s [g0, g0 + nq)
@@ -814,10 +814,15 @@ int exec_max_blocks_per_sm(int warps) {
 
 // every instantiation of the owned-chunk executor
 std::vector<void (*)(ExecParams)> owned_kernels() {
-  return {k_exec_owned<false, false, 1>, k_exec_owned<false, false, 2>, k_exec_owned<false, false, 4>,
-          k_exec_owned<false, true, 1>,  k_exec_owned<false, true, 2>,  k_exec_owned<false, true, 4>,
-          k_exec_owned<true, false, 1>,  k_exec_owned<true, false, 2>,  k_exec_owned<true, false, 4>,
-          k_exec_owned<true, true, 1>,   k_exec_owned<true, true, 2>,   k_exec_owned<true, true, 4>};
+  return {k_exec_owned<false, false, 1, false>, k_exec_owned<false, false, 2, false>,
+          k_exec_owned<false, false, 4, false>, k_exec_owned<false, true, 1, false>,
+          k_exec_owned<false, true, 2, false>,  k_exec_owned<false, true, 4, false>,
+          k_exec_owned<true, false, 1, false>,  k_exec_owned<true, false, 2, false>,
+          k_exec_owned<true, false, 4, false>,  k_exec_owned<true, true, 1, false>,
+          k_exec_owned<true, true, 2, false>,   k_exec_owned<true, true, 4, false>,
+          k_exec_owned<false, false, 1, true>,  k_exec_owned<false, false, 2, true>,
+          k_exec_owned<false, false, 4, true>,  k_exec_owned<false, true, 1, true>,
+          k_exec_owned<false, true, 2, true>,   k_exec_owned<false, true, 4, true>};
 }
 
 template <bool T, bool F, bool S>
@@ -855,16 +860,18 @@ void launch_exec(ExecParams p, int blocks, int warps, cudaStream_t s) {
   if (p.policy == RT_EXEC_OWNED && (single || p.task_graph)) {  // keeps nothing in shared memory
     // the claim width is the group size: lanes per task (1, 2 or 4)
     const int Lg = p.claim >= 4 ? 4 : (p.claim >= 2 ? 2 : 1);
-#define GRT_OWNED(T, F)                                                         \
-  do {                                                                         \
-    if (Lg == 4) k_exec_owned<T, F, 4><<<blocks, warps * 32, 0, s>>>(p);        \
-    else if (Lg == 2) k_exec_owned<T, F, 2><<<blocks, warps * 32, 0, s>>>(p);   \
-    else k_exec_owned<T, F, 1><<<blocks, warps * 32, 0, s>>>(p);               \
+#define GRT_OWNED(T, F, B)                                                         \
+  do {                                                                            \
+    if (Lg == 4) k_exec_owned<T, F, 4, B><<<blocks, warps * 32, 0, s>>>(p);        \
+    else if (Lg == 2) k_exec_owned<T, F, 2, B><<<blocks, warps * 32, 0, s>>>(p);   \
+    else k_exec_owned<T, F, 1, B><<<blocks, warps * 32, 0, s>>>(p);               \
   } while (0)
-    if (p.tickets) {
-      if (fence) GRT_OWNED(true, true); else GRT_OWNED(true, false);
+    if (p.task_graph) {  // a batch (it records no tickets)
+      if (fence) GRT_OWNED(false, true, true); else GRT_OWNED(false, false, true);
+    } else if (p.tickets) {
+      if (fence) GRT_OWNED(true, true, false); else GRT_OWNED(true, false, false);
     } else {
-      if (fence) GRT_OWNED(false, true); else GRT_OWNED(false, false);
+      if (fence) GRT_OWNED(false, true, false); else GRT_OWNED(false, false, false);
     }
 #undef GRT_OWNED
     return;
