@@ -33,9 +33,13 @@
 //     candidate per lane, overlapping ones ordered by conflict levels;
 //   * cell-parallel: the warp's lanes split the cells of one candidate's box;
 //   * segment mode (tiles whose candidates cover 8+ class cells each on
-//     average): each class row is kept as segments of equal run state, one
-//     lane per row of the box, so a candidate costs its rows' segments, not
-//     its cells.
+//     average): each class row is kept as segments of equal run state, so a
+//     candidate costs its rows' segments, not its cells. In 2-D tiles (row
+//     mode) each lane takes whole class rows and runs a staged window's
+//     candidates over them without waiting for the other lanes, and the
+//     predecessors inside the window are bits of the window, OR-ed per task;
+//     a task with more than 32 candidates in the tile (and 1-D tiles) takes
+//     the rows of one candidate's box at a time, one lane per row.
 // Predecessors found by several lanes are merged with match_any, and the
 // survivors go through a per-warp shared-memory hash set, so each (src, dst)
 // pair leaves the tile once per task. Pairs are appended to per-warp chunks of
@@ -65,6 +69,9 @@ constexpr int kSmallCells = 16;  // largest box the lane-parallel path takes
 constexpr int kMaxRounds = 16;   // deeper conflict chains go to the warp-wide path
 constexpr int kLongSpan = 64;    // run spans the whole warp scans together
 constexpr int kSegMinArea = 8;   // mean class cells per candidate from which rows go segmented
+constexpr int kExtSlots = 256;   // row mode: hash set of (predecessor, task) pairs from before the window
+constexpr int kExtMax = 192;     // ... entries it takes before further pairs are written at once
+constexpr int kExtProbes = 32;
 constexpr unsigned kFull = 0xffffffffu;
 
 // cells of the class grid one warp sweeps at once (taller grids go in strips)
@@ -73,11 +80,24 @@ __host__ __device__ inline int class_cap(int tw, int th) { return tw * th < kMax
 // class maps: tw + th uint16 entries
 __host__ __device__ inline size_t class_map_bytes(int tw, int th) { return (size_t)((2 * (tw + th) + 15) & ~15); }
 
+// segment starts: one bit per class column, one row of words per class row
+// swept at once (rows x words never exceed the class cells of a strip)
+__host__ __device__ inline size_t seg_bytes(int tw, int th) {
+  const int C = class_cap(tw, th), words = th * ((tw + 31) >> 5);
+  return (size_t)((4 * (words < C ? words : C) + 15) & ~15);
+}
+
+// row mode's window tables (2-D tiles): class boxes and predecessor masks of
+// the 32 staged candidates, and two column masks per class column
+__host__ __device__ inline size_t row_table_bytes(int tw) {
+  return tw <= kMaxTileSide2D ? (size_t)((32 * 4 * 2 + 8 * tw + 15) & ~15) : 0;
+}
+
 __host__ __device__ inline size_t per_warp_bytes(int tw, int th) {
   const int C = class_cap(tw, th);
   return (size_t)16 * C + (size_t)((C + 15) & ~15) + 32 * 8 + kHashSlots * 4 + kListCap * 8 + 16 +
-         32 * kLaneBuf * 4 + class_map_bytes(tw, th) + (size_t)((4 * C + 15) & ~15);  // 16-byte multiple:
-                                                                                      // warps' uint4 cells stay aligned
+         32 * kLaneBuf * 4 + class_map_bytes(tw, th) + seg_bytes(tw, th) + row_table_bytes(tw);  // 16-byte
+                                                                       // multiple: warps' uint4 cells stay aligned
 }
 
 struct WarpSmem {
@@ -94,6 +114,14 @@ struct WarpSmem {
   int* dropped;   // a pair of the current tile fell past the buffer's end
   int* npairs;    // pairs the current tile emitted
   uint32_t* seg;  // segment mode: per class row, bit x set where a segment starts
+  // row mode (segment tiles in 2-D), per staged window:
+  uint32_t* rbox;   // [32] candidate k's class box, x0 | x1 << 8 | y0 << 16 | y1 << 24
+  uint32_t* rpred;  // [32] per task (its first candidate's index): window candidates it follows
+  uint32_t* rlo;    // [class column x] bit k: candidate k's box starts at or left of x
+  uint32_t* rhi;    // [class column x] bit k: candidate k's box ends at or right of x
+  unsigned long long* xtab;  // [kExtSlots] (predecessor << 5 | task index) pairs from before the window
+                            // (in the lane-parallel path's buffer)
+  int* xcount;              // its entries
 };
 
 // in place: a[i] <- a[0] + ... + a[i] over a[0..L) (one warp, convergent)
@@ -681,6 +709,233 @@ __device__ void process_group_seg(Ctx& x, const WarpSmem& w, const SweepOut& o, 
   flush(x, w, o, dst);
 }
 
+// ---- row mode ----------------------------------------------------------------
+// In a segment tile the cells of different class rows never interact, so a lane
+// can take whole class rows and run every candidate of a staged window over its
+// rows in program order, without waiting for the other lanes between
+// candidates (the segment path above runs one candidate at a time, one lane per
+// row of its box). A predecessor inside the window is recorded as a bit of the
+// window: a run's first and last members by their own positions, the members
+// between them (runs of three or more) as the window's candidates that cover
+// the row, overlap the segment and lie between the two. Each lane ORs its bits
+// into the task's mask in shared memory; the masks become pairs once per
+// window. Members from before the window (the runs a window's first accesses
+// meet) go through a per-warp hash set of (predecessor, task) keys.
+
+__device__ __forceinline__ uint32_t pack_cbox(const Box& b) {
+  return (uint32_t)b.x0 | ((uint32_t)b.x1 << 8) | ((uint32_t)b.y0 << 16) | ((uint32_t)b.y1 << 24);
+}
+
+// (src, window task j) into the warp's set; once the set is full (or a key
+// finds no slot within kExtProbes) the pair is written at once, through the
+// pair-key filter on dense inputs (lane-level, may run divergently)
+__device__ __forceinline__ void ext_add(const WarpSmem& w, const SweepOut& o, int src, int j, int dst) {
+  const unsigned long long key = ((unsigned long long)(uint32_t)src << 5) | (unsigned long long)(uint32_t)j;
+  if (*(volatile int*)w.xcount < kExtMax) {
+    uint32_t h = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 56);  // 8 bits: kExtSlots
+    for (int t = 0; t < kExtProbes; ++t) {
+      const unsigned long long old = atomicCAS(w.xtab + h, (unsigned long long)kEmpty64, key);
+      if (old == key) return;
+      if (old == (unsigned long long)kEmpty64) {
+        atomicAdd(w.xcount, 1);
+        return;
+      }
+      h = (h + 1) & (kExtSlots - 1);
+    }
+  }
+  // the tile's count bounds a rerun (which writes every pair): count it
+  atomicAdd(w.npairs, 1);
+  const uint64_t pk = pair_key(src, dst, o.key_bits);
+  if (!o.filt || filt_fresh(o, pk)) put_pair(w, o, atomicAdd(o.cursor, 1ull), pk);
+}
+
+// The access with privilege pk of window task j (first candidate at window
+// index j, task id dst) to segment [sx, ex] of class row y: updates the state
+// and records the members of the run it follows (window ones as bits of acc).
+// cover: the window candidates whose box holds row y.
+__device__ __forceinline__ void row_seg(const Ctx& x, const WarpSmem& w, const SweepOut& o, int y, int sx, int ex,
+                                        int pk, int j, unsigned cover, unsigned& acc, int dst) {
+  const int c = y * x.tw + sx;
+  uint32_t rs, rl, rc;
+  apply_cell(w, c, x.pos + j, pk, rs, rl, rc);
+  if (pk == kKindWrite) {
+    w.cell[c].z = 0u;
+    w.cell[c].w = 0u;
+  }
+  if (rc == 0u) return;
+  const int pos = x.pos;
+  // members in the window: the first and the last by their positions, the
+  // ones strictly between them (runs of three or more) as the candidates that
+  // cover row y, overlap the segment and lie between the two (rl precedes
+  // this task, so rl - pos <= 30)
+  if ((int)rs >= pos) acc |= 1u << ((int)rs - pos);
+  if (rc >= 2u && (int)rl >= pos) acc |= 1u << ((int)rl - pos);
+  if (rc == 3u) {
+    const int a = (int)rs + 1 > pos ? (int)rs + 1 : pos, b = (int)rl - 1;
+    if (b >= a) acc |= ((2u << (b - pos)) - 1u) & ~((1u << (a - pos)) - 1u) & cover & w.rlo[ex] & w.rhi[sx];
+  }
+  if ((int)rs >= pos) return;
+  // members from before the window, in one pass: the first, the candidates
+  // strictly between the first and the last that meet the segment (runs of
+  // three or more), then the last
+  const int last = (rc >= 2u && (int)rl < pos) ? (int)rl : -1;
+  const int qe = rc == 3u ? ((int)rl < pos ? (int)rl : pos) : (int)rs + 1;  // end of the scan
+  for (int q = (int)rs;;) {
+    int src = -1;
+    if (q == (int)rs || q == last) {
+      src = (int)(uint32_t)entry_at(x, w, q);
+    } else {
+      const Box e = unpack_c(x, w, entry_at(x, w, q));
+      if (e.y0 <= y && y <= e.y1 && e.x0 <= ex && sx <= e.x1) src = e.task;
+    }
+    if (src >= 0) ext_add(w, o, src, j, dst);
+    if (q + 1 < qe) ++q;
+    else if (q < last) q = last;
+    else break;
+  }
+}
+
+// privilege of window candidate k from the window's privilege planes
+__device__ __forceinline__ int row_priv(unsigned wp, unsigned dp, int k) {
+  return ((wp >> k) & 1u) ? kKindWrite : (((dp >> k) & 1u) ? kKindReduce : kKindRead);
+}
+
+// Row mode over the staged window's candidates [0, end) (whole tasks; bit k of
+// starts: candidate k is its task's first) in a segment tile (convergent).
+__device__ void row_window(Ctx& x, const WarpSmem& w, const SweepOut& o, unsigned starts, int end) {
+  const int lane = x.lane;
+  const bool mine = lane < end;
+  Box b;
+  b.x0 = b.y0 = 1;
+  b.x1 = b.y1 = 0;
+  b.priv = kKindRead;
+  if (mine) b = unpack_c(x, w, w.stage[lane]);
+  w.rbox[lane] = pack_cbox(b);
+  w.rpred[lane] = 0u;
+  const unsigned wp = __ballot_sync(kFull, mine && b.priv == kKindWrite);
+  const unsigned dp = __ballot_sync(kFull, mine && b.priv == kKindReduce);
+  const bool live = mine && b.x0 <= b.x1 && b.y0 <= b.y1;
+  for (int cx = 0; cx < x.tw; ++cx) {
+    const unsigned lo = __ballot_sync(kFull, live && b.x0 <= cx);
+    const unsigned hi = __ballot_sync(kFull, live && b.x1 >= cx);
+    if (lane == 0) {
+      w.rlo[cx] = lo;
+      w.rhi[cx] = hi;
+    }
+  }
+  __syncwarp();
+  const int rows = x.yhi - x.ylo + 1, W = (x.tw + 31) >> 5;
+  for (int y = lane; y < rows; y += 32) {
+    uint32_t* row = w.seg + y * W;
+    unsigned cover = 0u;
+    for (int k = 0; k < end; ++k) {
+      const uint32_t bx = w.rbox[k];
+      if ((int)((bx >> 16) & 255u) <= y && y <= (int)(bx >> 24)) cover |= 1u << k;
+    }
+    for (unsigned tm = cover; tm;) {
+      const int k = __ffs((int)tm) - 1;
+      // k's task: its first candidate j and the window bits G of its candidates
+      const unsigned upto = starts & ((2u << k) - 1u), later = starts & ~((2u << k) - 1u);
+      const int j = 31 - __clz((int)upto);
+      const unsigned G = (later ? (1u << (__ffs((int)later) - 1)) - 1u : kFull) & ~((1u << j) - 1u);
+      const unsigned K = tm & G;  // its candidates on this row
+      tm &= ~G;
+      const int dst = (int)(uint32_t)w.stage[j];
+      // split at the edges of the task's candidates on this row, then run each
+      // segment of their union once, with the privileges of the candidates
+      // holding it combined (one candidate: its own)
+      unsigned acc = 0u;
+      int u0 = 1 << 30, u1 = -1;
+      for (unsigned kk = K; kk; kk &= kk - 1u) {
+        const uint32_t bx = w.rbox[__ffs((int)kk) - 1];
+        const int x0 = (int)(bx & 255u), x1 = (int)((bx >> 8) & 255u);
+        seg_split(x, w, row, y, x0);
+        seg_split(x, w, row, y, x1 + 1);
+        u0 = x0 < u0 ? x0 : u0;
+        u1 = x1 > u1 ? x1 : u1;
+      }
+      for (int sx = u0; sx <= u1;) {
+        const int ex = seg_next(row, sx, x.tw) - 1;
+        uint32_t pk = 0xFFu;
+        for (unsigned kk = K; kk; kk &= kk - 1u) {
+          const int q = __ffs((int)kk) - 1;
+          const uint32_t bx = w.rbox[q];
+          if ((int)(bx & 255u) <= sx && sx <= (int)((bx >> 8) & 255u)) pk = combine_priv(pk, (uint32_t)row_priv(wp, dp, q));
+        }
+        if (pk != 0xFFu) row_seg(x, w, o, y, sx, ex, (int)pk, j, cover, acc, dst);
+        sx = ex + 1;
+      }
+      seg_merge(x, w, row, y, u0, u1);
+      if (acc) atomicOr(w.rpred + j, acc);
+    }
+  }
+  __syncwarp();
+
+  // pairs: lane j (a task's first candidate) turns its mask into the tasks it
+  // follows; lane l takes the set's slots l, l + 32, ...
+  const bool lead = mine && ((starts >> lane) & 1u);
+  const unsigned P = lead ? w.rpred[lane] : 0u;
+  const int dst = lead ? (int)(uint32_t)w.stage[lane] : 0;
+  unsigned src = 0u;  // first candidates of the tasks this one follows
+  for (unsigned r = P; r;) {
+    const int q = 31 - __clz((int)r);
+    const int g = 31 - __clz((int)(starts & ((2u << q) - 1u)));
+    src |= 1u << g;
+    r &= (1u << g) - 1u;
+  }
+  const bool any_ext = *(volatile int*)w.xcount > 0;
+  constexpr int kPer = kExtSlots / 32;
+  unsigned fresh = src, xfresh = 0u;  // xfresh bit i: slot lane + 32 i holds a pair to write
+  int nx = 0;
+  if (any_ext) {
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const unsigned long long e = w.xtab[lane + 32 * i];
+      if (e != (unsigned long long)kEmpty64) {
+        ++nx;
+        if (!o.filt || filt_fresh(o, pair_key((int)(uint32_t)(e >> 5), (int)(uint32_t)w.stage[e & 31u], o.key_bits)))
+          xfresh |= 1u << i;
+      }
+    }
+  }
+  if (o.filt) {
+    fresh = 0u;
+    for (unsigned r = src; r; r &= r - 1u) {
+      const int g = __ffs((int)r) - 1;
+      if (filt_fresh(o, pair_key((int)(uint32_t)w.stage[g], dst, o.key_bits))) fresh |= 1u << g;
+    }
+  }
+  // the tile's count bounds a rerun, which writes every pair: count them all
+  const unsigned all = __reduce_add_sync(kFull, (unsigned)(__popc(src) + nx));
+  if (lane == 0 && all) atomicAdd(w.npairs, (int)all);
+  const int mine_n = __popc(fresh) + __popc(xfresh);
+  int incl = mine_n;
+#pragma unroll
+  for (int o2 = 1; o2 < 32; o2 <<= 1) {
+    const int t = __shfl_up_sync(kFull, incl, o2);
+    if (lane >= o2) incl += t;
+  }
+  const int total = __shfl_sync(kFull, incl, 31);
+  if (total > 0) {
+    const PairDst pd = reserve_pairs(x, o, (uint32_t)total);
+    uint32_t at = (uint32_t)(incl - mine_n);
+    for (unsigned r = fresh; r; r &= r - 1u)
+      put_pair(w, o, pair_pos(pd, at++), pair_key((int)(uint32_t)w.stage[__ffs((int)r) - 1], dst, o.key_bits));
+    for (unsigned r = xfresh; r; r &= r - 1u) {
+      const unsigned long long e = w.xtab[lane + 32 * (__ffs((int)r) - 1)];
+      put_pair(w, o, pair_pos(pd, at++), pair_key((int)(uint32_t)(e >> 5), (int)(uint32_t)w.stage[e & 31u], o.key_bits));
+    }
+  }
+  if (any_ext) {
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) w.xtab[lane + 32 * i] = (unsigned long long)kEmpty64;
+  }
+  __syncwarp();
+  if (lane == 0) *w.xcount = 0;
+  __syncwarp();
+}
+
 // one task's candidates at positions [a, b) of the tile list
 __device__ void process_group(Ctx& x, const WarpSmem& w, const SweepOut& o, int a, int b) {
   const uint64_t first = entry_at(x, w, a);
@@ -743,13 +998,23 @@ __global__ void __launch_bounds__(256, 3) k_sweep(const uint64_t* __restrict__ p
   w.cmx = reinterpret_cast<uint16_t*>(w.lbuf + 32 * kLaneBuf);
   w.cmy = w.cmx + d.tw;
   w.seg = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(w.cmx) + class_map_bytes(d.tw, d.th));
+  w.rbox = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(w.seg) + seg_bytes(d.tw, d.th));
+  w.rpred = w.rbox + 32;
+  w.rlo = w.rpred + 32;
+  w.rhi = w.rlo + d.tw;
+  static_assert(kExtSlots * 8 <= 32 * kLaneBuf * 4, "the set fits the lane-parallel path's buffer");
+  w.xtab = reinterpret_cast<unsigned long long*>(w.lbuf);
   w.dropped = w.hcount + 1;
   w.npairs = w.hcount + 2;
+  w.xcount = w.hcount + 3;
+  // row mode runs in 2-D segment tiles, whose class columns the tables cover
+  const bool rowmode = d.ndim == 2 && row_table_bytes(d.tw) > 0;
   for (int i = lane; i < kHashSlots; i += 32) w.htab[i] = -1;
   if (lane == 0) {
     *w.hcount = 0;
     *w.dropped = 0;
     *w.npairs = 0;
+    *w.xcount = 0;
   }
   __syncwarp();
 
@@ -810,6 +1075,9 @@ __global__ void __launch_bounds__(256, 3) k_sweep(const uint64_t* __restrict__ p
           w.cell[y * cw] = make_uint4((uint32_t)kKindNone << 30, 0u, 0u, 0u);
           w.scr[y * cw] = 0xFFu;
         }
+        // row mode's set shares its memory with the lane-parallel path's buffers
+        if (rowmode)
+          for (int i = lane; i < kExtSlots; i += 32) w.xtab[i] = (unsigned long long)kEmpty64;
       } else {
         for (int c = lane; c < cw * rows; c += 32) {
           w.cell[c] = make_uint4((uint32_t)kKindNone << 30, 0u, 0u, 0u);
@@ -857,7 +1125,12 @@ __global__ void __launch_bounds__(256, 3) k_sweep(const uint64_t* __restrict__ p
           continue;
         }
         unsigned gs = starts & (end == 32 ? kFull : ((1u << end) - 1u));
-        if (!x.segmode && stage_lanes(x, w, o, gs, end)) gs = 0;
+        if (x.segmode && rowmode) {
+          row_window(x, w, o, gs, end);
+          gs = 0;
+        } else if (!x.segmode && stage_lanes(x, w, o, gs, end)) {
+          gs = 0;
+        }
         while (gs) {
           const int a = __ffs((int)gs) - 1;
           gs &= gs - 1;
@@ -889,7 +1162,9 @@ __global__ void __launch_bounds__(256, 3) k_sweep(const uint64_t* __restrict__ p
 }  // namespace
 
 int sweep_warps_per_block(int tw, int th) {
-  int w = (int)((96 * 1024) / per_warp_bytes(tw, th));
+  // three blocks per SM (the kernel's launch bounds): 228 KB of shared memory,
+  // less 1 KB the hardware keeps per block, is 75 KB a block
+  int w = (int)((75 * 1024) / per_warp_bytes(tw, th));
   return w < 1 ? 1 : (w > 8 ? 8 : w);
 }
 

@@ -199,9 +199,9 @@ rt_status rt_tune_tile(const rt_graph_desc* desc, int32_t n, const int32_t* req_
   }
   char hb[32];
   snprintf(hb, sizeof hb, "%016llx", (unsigned long long)h);
-  // "tile2": entries of the sweep with its current window and filter paths,
-  // and of the candidate list below (older entries are never read)
-  const std::string key = "tile2/" + device_tag() + "/" + std::to_string(D) + "/" +
+  // "tile3": entries of the sweep with its row mode for segment tiles, and of
+  // the candidate list below (older entries are never read)
+  const std::string key = "tile3/" + device_tag() + "/" + std::to_string(D) + "/" +
                           std::to_string(desc->dom_hi[0] - desc->dom_lo[0] + 1) + "x" +
                           std::to_string(D == 2 ? desc->dom_hi[1] - desc->dom_lo[1] + 1 : 1) + "/" +
                           std::to_string(n) + "/" + std::to_string(R) + "/" + hb;
@@ -215,9 +215,12 @@ rt_status rt_tune_tile(const rt_graph_desc* desc, int32_t n, const int32_t* req_
   std::vector<std::pair<int, int>> cands;
   if (D == 2) {
     // squares, and flat or tall ones (a Task Bench step is a row of the domain:
-    // 8 x 16 sweeps its stencil graph in 0.81 ms against 1.12 ms for 16 x 16)
+    // 8 x 16 sweeps its stencil graph in 0.81 ms against 1.12 ms for 16 x 16;
+    // dense tiles sweep their class rows one lane each, so 32 rows keep a
+    // warp's lanes busy)
     for (int t : {8, 16, 32, 64}) cands.push_back({t, t});
-    for (auto wh : {std::pair<int, int>{8, 16}, {16, 8}, {32, 4}, {32, 8}, {64, 4}}) cands.push_back(wh);
+    for (auto wh : {std::pair<int, int>{8, 16}, {16, 8}, {32, 4}, {32, 8}, {64, 4}, {8, 32}, {16, 32}, {32, 16}})
+      cands.push_back(wh);
   } else {
     for (int t : {128, 256, 512, 1024}) cands.push_back({t, 1});
   }

@@ -178,6 +178,25 @@ def test_pair_filter_on_dense_inputs(K):
     g.close()
 
 
+@pytest.mark.parametrize("tile", [(16, 16), (32, 32), (16, 8)])
+def test_dense_tiles_with_several_rectangles_per_task(tile):
+    """Dense tiles (swept as segments, one lane per class row) whose tasks hold
+    up to 4 rectangles that often overlap one another in the same rows (one
+    combined privilege per cell), with runs that reach back over many staged
+    windows: the CSR and the CHECK body's results are the oracle's."""
+    for seed, side in ((21, (4, 40)), (22, (8, 64))):
+        tr = tg.random_rects(grid=(64, 48), n=700, rects=(1, 4), side=side, seed=seed)
+        g = gpu_graph(tr, body=grt.RT_BODY_CHECK, tile=tile)
+        g.analyze()
+        assert_csr_equal(g, tr)
+        g.execute()
+        g.sync()
+        st, out = oracle.run_bodies(tr, oracle.oracle.BODY_CHECK)
+        assert np.array_equal(g.state.cpu().numpy(), st[:tr.n_cells]), tr.name
+        assert np.array_equal(g.out.cpu().numpy(), out[:tr.n]), tr.name
+        g.close()
+
+
 def _max_classes(tr, tile):
     """Largest class grid (column classes x row classes) of any tile: the
     boundaries of the rectangles falling inside each tile, counted on the host."""
