@@ -800,6 +800,114 @@ __device__ __forceinline__ int row_priv(unsigned wp, unsigned dp, int k) {
   return ((wp >> k) & 1u) ? kKindWrite : (((dp >> k) & 1u) ? kKindReduce : kKindRead);
 }
 
+// Segment starts of one row for row mode: in shared memory, or (ONE: class
+// width up to 32) one word held in a register by the row's lane.
+template <bool ONE>
+struct RowSeg;
+
+template <>
+struct RowSeg<false> {
+  static __device__ __forceinline__ void split(const Ctx& x, const WarpSmem& w, uint32_t* row, uint32_t&, int y,
+                                               int X) {
+    seg_split(x, w, row, y, X);
+  }
+  static __device__ __forceinline__ int next(const uint32_t* row, uint32_t, int X, int cw) {
+    return seg_next(row, X, cw);
+  }
+  static __device__ __forceinline__ void merge(const Ctx& x, const WarpSmem& w, uint32_t* row, uint32_t&, int y,
+                                               int x0, int x1) {
+    seg_merge(x, w, row, y, x0, x1);
+  }
+};
+
+template <>
+struct RowSeg<true> {
+  static __device__ __forceinline__ int start_le(uint32_t m, int X) {  // X <= 31; bit 0 is always set
+    return 31 - __clz((int)(m & ((2u << X) - 1u)));
+  }
+  static __device__ __forceinline__ int next(const uint32_t*, uint32_t m, int X, int cw) {  // first start > X, or cw
+    const uint32_t r = m & ~((2u << X) - 1u);
+    const int b = r ? __ffs((int)r) - 1 : cw;
+    return b < cw ? b : cw;
+  }
+  static __device__ __forceinline__ void split(const Ctx& x, const WarpSmem& w, uint32_t*, uint32_t& m, int y,
+                                               int X) {
+    if (X <= 0 || X >= x.tw || ((m >> X) & 1u)) return;
+    const int s0 = start_le(m, X);
+    w.cell[y * x.tw + X] = w.cell[y * x.tw + s0];
+    w.scr[y * x.tw + X] = w.scr[y * x.tw + s0];
+    m |= 1u << X;
+  }
+  static __device__ __forceinline__ void merge(const Ctx& x, const WarpSmem& w, uint32_t*, uint32_t& m, int y,
+                                               int x0, int x1) {
+    const int end = x1 + 1 < x.tw ? x1 + 1 : x.tw - 1;
+    int prev = x0 > 0 ? start_le(m, x0 - 1) : -1;
+    for (int t = x0; t <= end; t = next(nullptr, m, t, x.tw)) {
+      if (!((m >> t) & 1u)) continue;
+      if (prev >= 0) {
+        const uint4 a = w.cell[y * x.tw + prev], b = w.cell[y * x.tw + t];
+        if (a.x == b.x && a.y == b.y && a.z == b.z && a.w == b.w && w.scr[y * x.tw + prev] == w.scr[y * x.tw + t]) {
+          m &= ~(1u << t);
+          continue;
+        }
+      }
+      prev = t;
+    }
+  }
+};
+
+// one class row y of a row-mode window: every staged candidate that holds the
+// row, in program order (ONE: the row's segment starts fit one word, kept in
+// a register for the window)
+template <bool ONE>
+__device__ __forceinline__ void row_pass(const Ctx& x, const WarpSmem& w, const SweepOut& o, int y, unsigned starts,
+                                         int end, unsigned wp, unsigned dp) {
+  uint32_t* row = w.seg + y * ((x.tw + 31) >> 5);
+  uint32_t m = ONE ? row[0] : 0u;
+  unsigned cover = 0u;
+  for (int k = 0; k < end; ++k) {
+    const uint32_t bx = w.rbox[k];
+    if ((int)((bx >> 16) & 255u) <= y && y <= (int)(bx >> 24)) cover |= 1u << k;
+  }
+  for (unsigned tm = cover; tm;) {
+    const int k = __ffs((int)tm) - 1;
+    // k's task: its first candidate j and the window bits G of its candidates
+    const unsigned upto = starts & ((2u << k) - 1u), later = starts & ~((2u << k) - 1u);
+    const int j = 31 - __clz((int)upto);
+    const unsigned G = (later ? (1u << (__ffs((int)later) - 1)) - 1u : kFull) & ~((1u << j) - 1u);
+    const unsigned K = tm & G;  // its candidates on this row
+    tm &= ~G;
+    const int dst = (int)(uint32_t)w.stage[j];
+    // split at the edges of the task's candidates on this row, then run each
+    // segment of their union once, with the privileges of the candidates
+    // holding it combined (one candidate: its own)
+    unsigned acc = 0u;
+    int u0 = 1 << 30, u1 = -1;
+    for (unsigned kk = K; kk; kk &= kk - 1u) {
+      const uint32_t bx = w.rbox[__ffs((int)kk) - 1];
+      const int x0 = (int)(bx & 255u), x1 = (int)((bx >> 8) & 255u);
+      RowSeg<ONE>::split(x, w, row, m, y, x0);
+      RowSeg<ONE>::split(x, w, row, m, y, x1 + 1);
+      u0 = x0 < u0 ? x0 : u0;
+      u1 = x1 > u1 ? x1 : u1;
+    }
+    for (int sx = u0; sx <= u1;) {
+      const int ex = RowSeg<ONE>::next(row, m, sx, x.tw) - 1;
+      uint32_t pk = 0xFFu;
+      for (unsigned kk = K; kk; kk &= kk - 1u) {
+        const int q = __ffs((int)kk) - 1;
+        const uint32_t bx = w.rbox[q];
+        if ((int)(bx & 255u) <= sx && sx <= (int)((bx >> 8) & 255u)) pk = combine_priv(pk, (uint32_t)row_priv(wp, dp, q));
+      }
+      if (pk != 0xFFu) row_seg(x, w, o, y, sx, ex, (int)pk, j, cover, acc, dst);
+      sx = ex + 1;
+    }
+    RowSeg<ONE>::merge(x, w, row, m, y, u0, u1);
+    if (acc) atomicOr(w.rpred + j, acc);
+  }
+  if (ONE) row[0] = m;
+}
+
 // Row mode over the staged window's candidates [0, end) (whole tasks; bit k of
 // starts: candidate k is its task's first) in a segment tile (convergent).
 __device__ void row_window(Ctx& x, const WarpSmem& w, const SweepOut& o, unsigned starts, int end) {
@@ -826,48 +934,8 @@ __device__ void row_window(Ctx& x, const WarpSmem& w, const SweepOut& o, unsigne
   __syncwarp();
   const int rows = x.yhi - x.ylo + 1, W = (x.tw + 31) >> 5;
   for (int y = lane; y < rows; y += 32) {
-    uint32_t* row = w.seg + y * W;
-    unsigned cover = 0u;
-    for (int k = 0; k < end; ++k) {
-      const uint32_t bx = w.rbox[k];
-      if ((int)((bx >> 16) & 255u) <= y && y <= (int)(bx >> 24)) cover |= 1u << k;
-    }
-    for (unsigned tm = cover; tm;) {
-      const int k = __ffs((int)tm) - 1;
-      // k's task: its first candidate j and the window bits G of its candidates
-      const unsigned upto = starts & ((2u << k) - 1u), later = starts & ~((2u << k) - 1u);
-      const int j = 31 - __clz((int)upto);
-      const unsigned G = (later ? (1u << (__ffs((int)later) - 1)) - 1u : kFull) & ~((1u << j) - 1u);
-      const unsigned K = tm & G;  // its candidates on this row
-      tm &= ~G;
-      const int dst = (int)(uint32_t)w.stage[j];
-      // split at the edges of the task's candidates on this row, then run each
-      // segment of their union once, with the privileges of the candidates
-      // holding it combined (one candidate: its own)
-      unsigned acc = 0u;
-      int u0 = 1 << 30, u1 = -1;
-      for (unsigned kk = K; kk; kk &= kk - 1u) {
-        const uint32_t bx = w.rbox[__ffs((int)kk) - 1];
-        const int x0 = (int)(bx & 255u), x1 = (int)((bx >> 8) & 255u);
-        seg_split(x, w, row, y, x0);
-        seg_split(x, w, row, y, x1 + 1);
-        u0 = x0 < u0 ? x0 : u0;
-        u1 = x1 > u1 ? x1 : u1;
-      }
-      for (int sx = u0; sx <= u1;) {
-        const int ex = seg_next(row, sx, x.tw) - 1;
-        uint32_t pk = 0xFFu;
-        for (unsigned kk = K; kk; kk &= kk - 1u) {
-          const int q = __ffs((int)kk) - 1;
-          const uint32_t bx = w.rbox[q];
-          if ((int)(bx & 255u) <= sx && sx <= (int)((bx >> 8) & 255u)) pk = combine_priv(pk, (uint32_t)row_priv(wp, dp, q));
-        }
-        if (pk != 0xFFu) row_seg(x, w, o, y, sx, ex, (int)pk, j, cover, acc, dst);
-        sx = ex + 1;
-      }
-      seg_merge(x, w, row, y, u0, u1);
-      if (acc) atomicOr(w.rpred + j, acc);
-    }
+    if (W == 1) row_pass<true>(x, w, o, y, starts, end, wp, dp);
+    else row_pass<false>(x, w, o, y, starts, end, wp, dp);
   }
   __syncwarp();
 
