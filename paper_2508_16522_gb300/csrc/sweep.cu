@@ -730,6 +730,10 @@ __device__ __forceinline__ uint32_t pack_cbox(const Box& b) {
 // finds no slot within kExtProbes) the pair is written at once, through the
 // pair-key filter on dense inputs (lane-level, may run divergently)
 __device__ __forceinline__ void ext_add(const WarpSmem& w, const SweepOut& o, int src, int j, int dst) {
+  // the tile's count bounds a rerun, which writes every pair: each call writes
+  // at most one (in the set or at once), whatever order the lanes reach the
+  // set in, so every call is counted
+  atomicAdd(w.npairs, 1);
   const unsigned long long key = ((unsigned long long)(uint32_t)src << 5) | (unsigned long long)(uint32_t)j;
   if (*(volatile int*)w.xcount < kExtMax) {
     uint32_t h = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 56);  // 8 bits: kExtSlots
@@ -743,8 +747,6 @@ __device__ __forceinline__ void ext_add(const WarpSmem& w, const SweepOut& o, in
       h = (h + 1) & (kExtSlots - 1);
     }
   }
-  // the tile's count bounds a rerun (which writes every pair): count it
-  atomicAdd(w.npairs, 1);
   const uint64_t pk = pair_key(src, dst, o.key_bits);
   if (!o.filt || filt_fresh(o, pk)) put_pair(w, o, atomicAdd(o.cursor, 1ull), pk);
 }
@@ -954,13 +956,11 @@ __device__ void row_window(Ctx& x, const WarpSmem& w, const SweepOut& o, unsigne
   const bool any_ext = *(volatile int*)w.xcount > 0;
   constexpr int kPer = kExtSlots / 32;
   unsigned fresh = src, xfresh = 0u;  // xfresh bit i: slot lane + 32 i holds a pair to write
-  int nx = 0;
   if (any_ext) {
 #pragma unroll
     for (int i = 0; i < kPer; ++i) {
       const unsigned long long e = w.xtab[lane + 32 * i];
       if (e != (unsigned long long)kEmpty64) {
-        ++nx;
         if (!o.filt || filt_fresh(o, pair_key((int)(uint32_t)(e >> 5), (int)(uint32_t)w.stage[e & 31u], o.key_bits)))
           xfresh |= 1u << i;
       }
@@ -973,8 +973,9 @@ __device__ void row_window(Ctx& x, const WarpSmem& w, const SweepOut& o, unsigne
       if (filt_fresh(o, pair_key((int)(uint32_t)w.stage[g], dst, o.key_bits))) fresh |= 1u << g;
     }
   }
-  // the tile's count bounds a rerun, which writes every pair: count them all
-  const unsigned all = __reduce_add_sync(kFull, (unsigned)(__popc(src) + nx));
+  // the tile's count bounds a rerun, which writes every pair: the window's own
+  // (the set's were counted as they were added)
+  const unsigned all = __reduce_add_sync(kFull, (unsigned)__popc(src));
   if (lane == 0 && all) atomicAdd(w.npairs, (int)all);
   const int mine_n = __popc(fresh) + __popc(xfresh);
   int incl = mine_n;
