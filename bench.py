@@ -11,8 +11,8 @@ dependence analysis (binning, tile sweep, CSR) and one execution of the DAG.
 
 --impl reference times the CPU oracle on the same workload (host cores).
 With N > 1 (torchrun) every rank runs its own replica of the plain step (weak
-scaling); the batched leg's 4096 graphs are split across the ranks by
-footprint (strong scaling, no exchange between GPUs).
+scaling); the batched leg's 4096 graphs and the served leg's requests are
+split across the ranks by footprint (strong scaling, no exchange between GPUs).
 """
 from __future__ import annotations
 
@@ -304,17 +304,24 @@ def stacked_batch(traces, max_batch, band=1024):
                       np.concatenate([t.priv for t in traces]), name="served_batch")
 
 
-def run_served(grt, n_requests=SERVE_REQUESTS, rate=SERVE_RATE):
+def run_served(grt, n_requests=SERVE_REQUESTS, rate=SERVE_RATE, world=1, rank=0):
     """The served form: Poisson arrivals (mean 50k graphs/s) of graphs with task
     counts log-uniform 32..16384, 1-4 rects per launch on a 1024^2 grid (sides
     log-uniform 4..256), admitted under an 8 GB device-memory budget. Requests
     are submitted when due and stamped with their due time, so submission lag
-    counts as latency."""
+    counts as latency. With several ranks each serves its share of the stream
+    (shard.py: in arrival order, each request to the rank with the smallest
+    share so far), at the requests' own arrival times."""
     t0 = time.perf_counter()
-    reqs = tg.served_stream(n_requests, rate_per_s=rate, seed=0)
+    stream_all = tg.served_stream(n_requests, rate_per_s=rate, seed=0)
+    reqs = stream_all
+    if world > 1:
+        from paper_2508_16522_gb300 import shard
+        reqs = [stream_all[k] for k in shard.my_arrivals([shard.footprint(r.trace) for r in stream_all], world, rank)]
     gen_s = time.perf_counter() - t0
     # the tile is tuned on a batch of the size the stream produces (about 43)
-    tile = list(grt.rt_tune_tile(stacked_batch([r.trace for r in reqs[:43]], SERVE_MAX_BATCH), TUNE_CACHE)[:2])
+    cache = TUNE_CACHE if world == 1 else None  # ranks would append to one file at once
+    tile = list(grt.rt_tune_tile(stacked_batch([r.trace for r in stream_all[:43]], SERVE_MAX_BATCH), cache)[:2])
     srv = grt.Server(2, [0, 0], [1023, 1023], body=grt.RT_BODY_EMPTY, budget_bytes=8 << 30,
                      max_inflight=SERVE_SLOTS, max_tasks=16384, workers=SERVE_WORKERS, tile=tile,
                      max_batch=SERVE_MAX_BATCH, exec_warps=SERVE_EXEC_WARPS)
@@ -347,6 +354,7 @@ def run_served(grt, n_requests=SERVE_REQUESTS, rate=SERVE_RATE):
     ana = np.array([i["posted_ns"] - i["admit_ns"] for i in infos]) / 1e6
     span = (max(i["done_ns"] for i in infos) - base) / 1e9
     tasks = sum(i["n_tasks"] for i in infos)
+    n_requests = len(reqs)
     return {"workload": f"{n_requests} requests, Poisson arrivals at {rate:.0f} graphs/s, task counts "
                         "log-uniform 32..16384, 1-4 rects per launch on 1024^2 (sides log-uniform 4..256), "
                         f"EMPTY bodies, 8 GB budget, {SERVE_SLOTS} request slots, {SERVE_WORKERS} analysis "
@@ -358,7 +366,41 @@ def run_served(grt, n_requests=SERVE_REQUESTS, rate=SERVE_RATE):
             "analysis_ms": {"p50": float(np.percentile(ana, 50)), "p99": float(np.percentile(ana, 99))},
             "mean_batch": sst["batched_requests"] / max(sst["batches"], 1), "autotune": {"tile": tile},
             "submit_lag_ms": {"p50": float(np.percentile(lag, 50)) / 1e6, "p99": float(np.percentile(lag, 99)) / 1e6},
-            "generate_s": gen_s}
+            "generate_s": gen_s, "span_s": span}
+
+
+def run_served_split(grt, world, rank):
+    """The served stream split across the ranks (each serves its share on its
+    own GPU; no exchange): the job serves every request, in the time of its
+    slowest rank. A rank whose leg fails still takes part in the reductions
+    (so that no rank waits for it) and the line reports the failure."""
+    import torch
+    import torch.distributed as dist
+    err = None
+    try:
+        r = run_served(grt, world=world, rank=rank)
+        vals = [r["span_s"], r["latency_ms"]["p50"], r["latency_ms"]["p99"], r["analysis_ms"]["p50"]]
+        sums = [float(r["requests"]), float(r["tasks"])]
+    except Exception as e:  # reported below, after the reductions
+        err = f"rank {rank}: {type(e).__name__}: {e}"[:300]
+        vals, sums = [0.0] * 4, [0.0, 0.0]
+    ok = torch.tensor([0.0 if err else 1.0], dtype=torch.float64, device="cuda")
+    mx = torch.tensor(vals, dtype=torch.float64, device="cuda")
+    sm = torch.tensor(sums, dtype=torch.float64, device="cuda")
+    dist.all_reduce(ok, op=dist.ReduceOp.MIN)
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    if ok.item() < 1.0:
+        return {"error": err or "another rank's served leg failed", "ranks": world}
+    span, p50, p99, ana = mx.tolist()
+    n, tasks = sm.tolist()
+    return {"workload": f"{SERVE_REQUESTS} requests, Poisson arrivals at {SERVE_RATE:.0f} graphs/s, split across "
+                        f"{world} ranks", "requests": int(n), "tasks": int(tasks), "offered_graphs_per_s": SERVE_RATE,
+            "achieved_graphs_per_s": n / span, "tasks_per_s": tasks / span,
+            "latency_ms": {"p50": p50, "p99": p99, "note": "the largest of the ranks' percentiles"},
+            "analysis_ms": {"p50": ana}, "span_s": span, "ranks": world,
+            "split": "requests placed on ranks in arrival order, each on the rank with the smallest share so far "
+                     "(no exchange); time = slowest rank's", "scaling": "strong"}
 
 
 def run_stencil1d(grt, torch, reps=200):
@@ -920,6 +962,8 @@ def run_ours(args):
         async_nodes = run_async_nodes(grt, torch)
         stitched = run_stitched(grt, torch)
     served = None
+    if world > 1 and not args.no_served:
+        served = run_served_split(grt, world, rank)
     if world == 1 and not args.no_served:
         served = run_served(grt)
         # the same stream offered at 3/4 of the rate just achieved: latency

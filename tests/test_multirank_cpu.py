@@ -1,8 +1,9 @@
 """The multi-process path on CPU (gloo, world size 2): the job's time is the
 slowest rank's; under torchrun only rank 0 prints the result line; and
-independent graphs split across ranks by footprint are each taken by exactly
-one rank, the shares are balanced, and the union of what the ranks compute
-for their shares equals what one rank computes for all of them."""
+independent graphs split across ranks by footprint (a batch largest first, a
+served stream in arrival order) are each taken by exactly one rank, the shares
+are balanced, and the union of what the ranks compute for their shares equals
+what one rank computes for all of them."""
 import json
 import os
 import socket
@@ -101,6 +102,90 @@ def test_batch_split_across_two_gloo_ranks():
     fps = [shard.footprint(t) for t in traces]
     assert sum(loads) == sum(fps)
     assert max(loads) - min(loads) <= max(fps)  # greedy largest-first balance
+
+
+def _served_rank(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    sys.path.insert(0, ROOT)
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import oracle_pool
+    from paper_2508_16522_gb300 import shard
+    from paper_2508_16522_gb300 import tracegen as tg
+    import oracle
+    reqs = tg.served_stream(80, n_range=(32, 512), seed=5)
+    share = shard.my_arrivals([shard.footprint(r.trace) for r in reqs], world, rank)
+    mine = {}
+    for k in share:
+        tr = reqs[k].trace
+        s, d = oracle.analyze(tr)
+        mine[k] = oracle_pool.csr_digest(*oracle.csr_from_pairs(tr.n, s, d))
+    gathered = [None] * world
+    dist.all_gather_object(gathered, mine)
+    loads = [None] * world
+    dist.all_gather_object(loads, sum(shard.footprint(reqs[k].trace) for k in share))
+    q.put((rank, gathered, loads, share))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_served_stream_split_across_two_gloo_ranks():
+    """Requests of a served stream placed in arrival order: each is taken by
+    exactly one rank, every rank's share keeps the arrival order, the shares
+    differ by at most the largest request, and the union of the ranks' CSRs
+    equals one rank computing all of them."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = free_port()
+    procs = [ctx.Process(target=_served_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(300)
+        assert p.exitcode == 0
+    got = {r: (g, l, sh) for r, g, l, sh in (q.get(timeout=10) for _ in range(2))}
+    gathered, loads, _ = got[0]
+    assert got[1][0] == gathered and got[1][1] == loads
+    for r in range(2):
+        assert got[r][2] == sorted(got[r][2])  # arrival order kept
+    sys.path.insert(0, ROOT)
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import oracle
+    import oracle_pool
+    from paper_2508_16522_gb300 import shard
+    from paper_2508_16522_gb300 import tracegen as tg
+    reqs = tg.served_stream(80, n_range=(32, 512), seed=5)
+    keys = [k for part in gathered for k in part]
+    assert sorted(keys) == list(range(len(reqs))), "a request was taken by no rank or by two"
+    union = {k: v for part in gathered for k, v in part.items()}
+    for k, r in enumerate(reqs):
+        s, d = oracle.analyze(r.trace)
+        assert union[k] == oracle_pool.csr_digest(*oracle.csr_from_pairs(r.trace.n, s, d))
+    fps = [shard.footprint(r.trace) for r in reqs]
+    assert sum(loads) == sum(fps)
+    assert max(loads) - min(loads) <= max(fps)
+
+
+def test_arrival_order_assignment_properties():
+    sys.path.insert(0, ROOT)
+    from paper_2508_16522_gb300 import shard
+    import numpy as np
+    rng = np.random.default_rng(2)
+    for world in (1, 2, 3, 4, 8):
+        fp = rng.integers(1, 10_000, size=300)
+        owner = shard.assign_in_arrival_order(fp, world)
+        loads = np.bincount(owner, weights=fp, minlength=world)
+        assert owner.min() >= 0 and owner.max() < world
+        # greedy in arrival order: a request goes where the share is smallest,
+        # so no share passes the smallest by more than the largest request
+        assert loads.max() - loads.min() <= fp.max()
+        for k in range(len(fp)):  # each request went to a smallest share at its arrival
+            before = np.bincount(owner[:k], weights=fp[:k], minlength=world)
+            assert before[owner[k]] == before.min() and owner[k] == int(np.argmin(before))
+        assert sorted(k for r in range(world) for k in shard.my_arrivals(fp, world, r)) == list(range(300))
+    assert shard.assign_in_arrival_order([], 2).tolist() == []
+    with pytest.raises(ValueError):
+        shard.assign_in_arrival_order([1], 0)
 
 
 def test_assignment_properties():
