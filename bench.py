@@ -369,24 +369,26 @@ def run_served(grt, n_requests=SERVE_REQUESTS, rate=SERVE_RATE, world=1, rank=0)
             "generate_s": gen_s, "span_s": span}
 
 
-def run_served_split(grt, world, rank):
+def run_served_split(grt, world, rank, device="cuda", leg=None):
     """The served stream split across the ranks (each serves its share on its
     own GPU; no exchange): the job serves every request, in the time of its
     slowest rank. A rank whose leg fails still takes part in the reductions
-    (so that no rank waits for it) and the line reports the failure."""
+    (so that no rank waits for it) and the line reports the failure. `device`
+    holds the reduction tensors (the process group's); `leg` runs one rank's
+    share (run_served)."""
     import torch
     import torch.distributed as dist
     err = None
     try:
-        r = run_served(grt, world=world, rank=rank)
+        r = (leg or run_served)(grt, world=world, rank=rank)
         vals = [r["span_s"], r["latency_ms"]["p50"], r["latency_ms"]["p99"], r["analysis_ms"]["p50"]]
         sums = [float(r["requests"]), float(r["tasks"])]
     except Exception as e:  # reported below, after the reductions
         err = f"rank {rank}: {type(e).__name__}: {e}"[:300]
         vals, sums = [0.0] * 4, [0.0, 0.0]
-    ok = torch.tensor([0.0 if err else 1.0], dtype=torch.float64, device="cuda")
-    mx = torch.tensor(vals, dtype=torch.float64, device="cuda")
-    sm = torch.tensor(sums, dtype=torch.float64, device="cuda")
+    ok = torch.tensor([0.0 if err else 1.0], dtype=torch.float64, device=device)
+    mx = torch.tensor(vals, dtype=torch.float64, device=device)
+    sm = torch.tensor(sums, dtype=torch.float64, device=device)
     dist.all_reduce(ok, op=dist.ReduceOp.MIN)
     dist.all_reduce(mx, op=dist.ReduceOp.MAX)
     dist.all_reduce(sm, op=dist.ReduceOp.SUM)

@@ -166,6 +166,48 @@ def test_served_stream_split_across_two_gloo_ranks():
     assert max(loads) - min(loads) <= max(fps)
 
 
+def _served_combine_rank(rank, world, port, fail_rank, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    sys.path.insert(0, ROOT)
+    import bench
+
+    def leg(grt, world, rank):  # one rank's share, as run_served reports it
+        if rank == fail_rank:
+            raise RuntimeError("server start failed")
+        return {"span_s": 1.0 + rank, "requests": 10 * (rank + 1), "tasks": 1000 * (rank + 1),
+                "latency_ms": {"p50": 5.0 + rank, "p99": 9.0 + rank}, "analysis_ms": {"p50": 2.0 * (rank + 1)}}
+
+    q.put((rank, bench.run_served_split(None, world, rank, device="cpu", leg=leg)))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("fail_rank", [-1, 1])
+def test_served_split_combines_ranks_and_survives_a_failed_rank(fail_rank):
+    """The served leg over two ranks: all requests over the slowest rank's span
+    (sums and maxima); when one rank's leg fails, both ranks still finish (no
+    rank waits for the failed one) and both report the failure."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = free_port()
+    procs = [ctx.Process(target=_served_combine_rank, args=(r, 2, port, fail_rank, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    got = dict(q.get(timeout=10) for _ in range(2))
+    if fail_rank < 0:
+        for r in range(2):
+            d = got[r]
+            assert d["requests"] == 30 and d["tasks"] == 3000 and d["span_s"] == 2.0
+            assert d["achieved_graphs_per_s"] == 15.0 and d["latency_ms"]["p99"] == 10.0 and d["ranks"] == 2
+    else:
+        assert all("error" in got[r] for r in range(2))
+        assert "server start failed" in got[fail_rank]["error"]
+
+
 def test_arrival_order_assignment_properties():
     sys.path.insert(0, ROOT)
     from paper_2508_16522_gb300 import shard
